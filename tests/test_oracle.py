@@ -1,0 +1,515 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: numpy's own
+FFT or an explicit triple sum, closed forms (homogeneous media, the exact
+layered-medium solution), a dense displacement-based solve of the same
+Galerkin problem, rigorous bounds, the paper's printed tables, and the special
+cases of the two-level scheme. The mutation tests at the end plant plausible
+mistakes in the oracle and confirm that a pin catches each one.
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import hh_oracle as O
+
+RNG = np.random.default_rng(20220804)
+
+
+def rand_spd6(rng, scale=50.0):
+    A = rng.standard_normal((6, 6))
+    return scale * (A @ A.T / 6.0 + np.eye(6))
+
+
+# ---------------------------------------------------------------- FFT ------
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (4, 6, 8), (2, 1, 9), (1, 1, 1), (12, 10, 15)])
+def test_fft_matches_numpy(shape):
+    a = RNG.standard_normal(shape) + 1j * RNG.standard_normal(shape)
+    ref = np.fft.fftn(a)
+    got = O.fft3(a)
+    assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+    back = O.ifft3(got)
+    assert np.abs(back - a).max() <= 1e-12
+
+
+def test_fft_explicit_sum():
+    shape = (2, 3, 4)
+    a = RNG.standard_normal(shape)
+    nz, ny, nx = shape
+    got = O.fft3(a)
+    for kz in range(nz):
+        for ky in range(ny):
+            for kx in range(nx):
+                s = 0.0
+                for z in range(nz):
+                    for y in range(ny):
+                        for x in range(nx):
+                            s += a[z, y, x] * np.exp(-2j * np.pi * (kz * z / nz + ky * y / ny + kx * x / nx))
+                assert abs(got[kz, ky, kx] - s) < 1e-12
+
+
+# --------------------------------------------------------- projection ------
+
+def _rand_hat(shape):
+    return RNG.standard_normal((6,) + shape) + 1j * RNG.standard_normal((6,) + shape)
+
+
+def _cinner(a, b):
+    return np.sum(O.FROB_W[:, None, None, None] * a * np.conj(b))
+
+
+@pytest.mark.parametrize("shape", [(5, 7, 3), (4, 6, 8)])
+@pytest.mark.parametrize("rule", ["component", "mode"])
+def test_projection_is_orthogonal_projection(shape, rule):
+    xi, zero = O.wave_vectors(shape, rule)
+    a = _rand_hat(shape)
+    b = _rand_hat(shape)
+    Pa = O.project_sym(a, xi, zero)
+    assert np.abs(O.project_sym(Pa, xi, zero) - Pa).max() < 1e-12
+    lhs = _cinner(Pa, b)
+    rhs = _cinner(a, O.project_sym(b, xi, zero))
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+    assert np.all(Pa[:, 0, 0, 0] == 0)
+
+
+def test_projection_range_and_kernel():
+    shape = (5, 5, 5)
+    xi, zero = O.wave_vectors(shape)
+    norm = np.sqrt((xi ** 2).sum(0))
+    n = xi / np.where(norm > 0, norm, 1)
+    a = RNG.standard_normal((3,) + shape) + 1j * RNG.standard_normal((3,) + shape)
+    # compatible: sym(a (x) n) is kept unchanged
+    S = 0.5 * (np.einsum("i...,j...->ij...", a, n) + np.einsum("i...,j...->ij...", n, a))
+    s6 = O.from_full(S)
+    P = O.project_sym(s6, xi, zero)
+    assert np.abs(P - np.where(zero, 0, s6)).max() < 1e-12
+    # equilibrated: tau with tau n = 0 is annihilated; build tau = Q M Q with Q = I - n n
+    M = RNG.standard_normal((3, 3) + shape)
+    M = M + np.swapaxes(M, 0, 1)
+    Q = np.eye(3)[:, :, None, None, None] - np.einsum("i...,j...->ij...", n, n)
+    T = np.einsum("ik...,kl...,lj...->ij...", Q, M, Q)
+    assert np.abs(O.project_sym(O.from_full(T), xi, zero)).max() < 1e-12
+
+
+@pytest.mark.parametrize("shape", [(4, 6, 8), (6, 6, 6)])
+def test_projection_keeps_real_fields_real_on_even_grids(shape):
+    xi, zero = O.wave_vectors(shape, "component")
+    tau = RNG.standard_normal((6,) + shape)
+    out = O.ifft3(O.project_sym(O.fft3(tau), xi, zero))
+    assert np.abs(out.imag).max() < 1e-12 * np.abs(out.real).max()
+
+
+# ------------------------------------------------- solver vs brute force ---
+
+def _displacement_solve(medium, E):
+    """Dense solve of the same Galerkin problem in displacement form.
+
+    Unknown: periodic displacement u (3 per voxel); strain fluctuation
+    eps*(u) = sym grad u by spectral differentiation (numpy FFT); minimise the
+    total strain energy sum_x gamma^T C gamma with gamma the engineering
+    Voigt strain of E + eps*(u). Odd grids only (no Nyquist modes).
+    """
+    shape = medium.shape
+    V = int(np.prod(shape))
+    nz, ny, nx = shape
+    f = [np.fft.fftfreq(nx), np.fft.fftfreq(ny), np.fft.fftfreq(nz)]
+    XI = np.zeros((3,) + shape)
+    XI[0] = f[0][None, None, :]
+    XI[1] = f[1][None, :, None]
+    XI[2] = f[2][:, None, None]
+
+    def strain(uvec):
+        u = uvec.reshape((3,) + shape)
+        uh = np.fft.fftn(u, axes=(1, 2, 3))
+        G = 1j * np.einsum("i...,j...->ij...", uh, XI)  # du_i/dx_j
+        eh = 0.5 * (G + np.swapaxes(G, 0, 1))
+        e = np.real(np.fft.ifftn(eh, axes=(2, 3, 4)))
+        return O.from_full(e)
+
+    B = np.zeros((6 * V, 3 * V))
+    for m in range(3 * V):
+        e = np.zeros(3 * V)
+        e[m] = 1.0
+        B[:, m] = strain(e).ravel()
+    Cv = medium.voigt()  # (6,6,...)
+    Wt = np.repeat(O.FROB_W, V)
+    DB = Wt[:, None] * B
+    Cblk = np.zeros((6 * V, 6 * V))
+    for i in range(6):
+        for j in range(6):
+            Cblk[i * V:(i + 1) * V, j * V:(j + 1) * V] = np.diag(Cv[i, j].ravel())
+    gE = np.repeat(O.FROB_W * E, V)
+    H = DB.T @ Cblk @ DB
+    g = DB.T @ Cblk @ gE
+    u, *_ = np.linalg.lstsq(H, -g, rcond=None)
+    return (B @ u).reshape((6,) + shape)
+
+
+def _bruteforce_error(n, phases, a):
+    img = (RNG.random((n, n, n)) < 0.4).astype(np.uint8)
+    med = O.IsoMedium.from_labels(img, phases)
+    E = O.unit_load(a)
+    x, it, _ = O.solve_cg(med, E, tol=1e-13, max_iter=5000)
+    ref = _displacement_solve(med, E)
+    return np.abs(x - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,a", [(3, 0), (3, 3), (5, 4)])
+def test_cg_matches_dense_displacement_solve(n, a):
+    assert _bruteforce_error(n, synth.PHASES_APPENDIX_B, a) < 1e-9
+
+
+@pytest.mark.parametrize("n", [3, 5, 7])
+def test_six_and_nine_component_forms_agree(n):
+    img = (RNG.random((n, n, n)) < 0.5).astype(np.uint8)
+    med = O.IsoMedium.from_labels(img, synth.PHASES_APPENDIX_B)
+    for a in (0, 5):
+        x6, _, _ = O.solve_cg(med, O.unit_load(a), tol=1e-13)
+        x9 = O.solve_cg_grad(med, O.unit_load(a), tol=1e-13)
+        assert np.abs(x6 - x9).max() < 1e-10 * np.abs(x6).max()
+
+
+def test_fixed_iterations_reproduce_converged_path():
+    img = synth.grf_two_phase(n=8, ell=2.0)
+    med = O.IsoMedium.from_labels(img, synth.PHASES_SOLID_PORE)
+    x1, it1, r1 = O.solve_cg(med, O.unit_load(1), fixed_iters=7)
+    assert it1 == 7
+    x2, it2, _ = O.solve_cg(med, O.unit_load(1), tol=r1 * 1.0000001)
+    assert it2 == 7 and np.array_equal(x1, x2)
+
+
+def test_basic_scheme_reaches_the_cg_solution():
+    img = (RNG.random((7, 7, 7)) < 0.5).astype(np.uint8)
+    ph = synth.PHASES_APPENDIX_B
+    med = O.IsoMedium.from_labels(img, ph)
+    lam = ph[:, 0] - 2 * ph[:, 1] / 3
+    lam0 = 0.5 * (lam.min() + lam.max())
+    mu0 = 0.5 * (ph[:, 1].min() + ph[:, 1].max())
+    E = O.unit_load(2)
+    xb, it, res = O.solve_basic(med, E, lam0, mu0, tol=1e-11)
+    xc, _, _ = O.solve_cg(med, E, tol=1e-12)
+    assert res <= 1e-11 and it > 5
+    assert np.abs(xb - xc).max() < 1e-8 * np.abs(xc).max()
+
+
+# --------------------------------------------------------- closed forms ----
+
+def test_homogeneous_isotropic_returns_phase_moduli_exactly():
+    img = np.zeros((6, 5, 4), dtype=np.uint8)
+    for K, G in [(37.0, 44.0), (36.0, 45.0), (1e-4, 1e-4)]:
+        ph = np.array([[K, G]])
+        res = O.homogenize_direct(img, ph)
+        assert np.all(res["iters"] == 0)
+        assert np.abs(res["C"] - O.iso_voigt(K, G)).max() <= 4e-16 * (K + 2 * G)
+        assert abs(res["K"] - K) <= 1e-12 * K and abs(res["G"] - G) <= 1e-12 * G
+
+
+def test_homogeneous_anisotropic_returns_its_stiffness():
+    C = rand_spd6(RNG)
+    shape = (5, 4, 6)
+    med = O.AnisoMedium(np.broadcast_to(C[:, :, None, None, None], (6, 6) + shape).copy())
+    res = O.homogenize_box(med, (slice(None),) * 3)
+    assert np.all(res["iters"] == 0)
+    assert np.abs(res["C"] - C).max() <= 1e-13 * np.abs(C).max()
+
+
+def test_paper_phase_moduli(golden_dir):
+    rows = [l.split() for l in open(os.path.join(golden_dir, "phase_moduli.txt")) if not l.startswith("#")]
+    for name, K, G, C11, C12, C44 in rows:
+        C = O.iso_voigt(float(K), float(G))
+        assert C[0, 0] == pytest.approx(float(C11), rel=1e-12)
+        assert C[0, 1] == pytest.approx(float(C12), rel=1e-12)
+        assert C[3, 3] == pytest.approx(float(C44), rel=1e-12)
+        k, g = O.moduli_voigt(C)
+        kr, gr = O.moduli_reuss(C)
+        assert k == pytest.approx(float(K), rel=1e-12) and g == pytest.approx(float(G), rel=1e-12)
+        assert kr == pytest.approx(float(K), rel=1e-10) and gr == pytest.approx(float(G), rel=1e-10)
+
+
+NORM = [2, 3, 4]   # Voigt 33, 23, 13: traction components on a z-normal plane
+TANG = [0, 1, 5]   # Voigt 11, 22, 12: in-plane strains
+
+
+def backus(Cs, f):
+    """Exact effective stiffness of a z-layered medium (layer stiffness Cs[l],
+    volume fraction f[l]): traction sigma_N and in-plane strain gamma_T are
+    uniform across layers."""
+    f = np.asarray(f) / np.sum(f)
+    iNN = [np.linalg.inv(C[np.ix_(NORM, NORM)]) for C in Cs]
+    A = sum(fl * m for fl, m in zip(f, iNN))
+    CNN = np.linalg.inv(A)
+    B = sum(fl * m @ C[np.ix_(NORM, TANG)] for fl, m, C in zip(f, iNN, Cs))
+    D = sum(fl * C[np.ix_(TANG, NORM)] @ m for fl, m, C in zip(f, iNN, Cs))
+    T = sum(fl * (C[np.ix_(TANG, TANG)] - C[np.ix_(TANG, NORM)] @ m @ C[np.ix_(NORM, TANG)])
+            for fl, m, C in zip(f, iNN, Cs))
+    out = np.zeros((6, 6))
+    out[np.ix_(NORM, NORM)] = CNN
+    out[np.ix_(NORM, TANG)] = CNN @ B
+    out[np.ix_(TANG, NORM)] = D @ CNN
+    out[np.ix_(TANG, TANG)] = T + D @ CNN @ B
+    return out
+
+
+def test_isotropic_laminate_matches_backus_closed_form():
+    labels = [0, 0, 1, 0, 1, 1, 1]
+    img = synth.laminate((7, 3, 5), labels)
+    ph = synth.PHASES_APPENDIX_B
+    res = O.homogenize_direct(img, ph, tol=1e-13)
+    ref = backus([O.iso_voigt(*ph[l]) for l in labels], np.ones(7))
+    assert np.abs(res["C"] - ref).max() <= 1e-9 * np.abs(ref).max()
+    # the scalar form of the same closed form: Reuss across, Voigt along
+    Ms = [ph[l, 0] + 4 * ph[l, 1] / 3 for l in labels]
+    mus = [ph[l, 1] for l in labels]
+    assert res["C"][2, 2] == pytest.approx(1 / np.mean([1 / m for m in Ms]), rel=1e-9)
+    assert res["C"][3, 3] == pytest.approx(1 / np.mean([1 / m for m in mus]), rel=1e-9)
+    assert res["C"][5, 5] == pytest.approx(np.mean(mus), rel=1e-9)
+
+
+def test_anisotropic_laminate_matches_backus_closed_form():
+    nz = 5
+    Cs = [rand_spd6(RNG) for _ in range(nz)]
+    shape = (nz, 3, 3)
+    C = np.zeros((6, 6) + shape)
+    for z in range(nz):
+        C[:, :, z] = Cs[z][:, :, None, None]
+    res = O.homogenize_box(O.AnisoMedium(C), (slice(None),) * 3, tol=1e-13)
+    ref = backus(Cs, np.ones(nz))
+    assert np.abs(res["C"] - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_buffered_laminate_core_averages():
+    """A layered box with a buffer: core averages of the exact layered solution
+    give Sigma and Eps (Eps != I), and C_R = Sigma Eps^-1."""
+    labels = [1, 0, 0, 1, 0, 1, 1, 0, 1]
+    nz = len(labels)
+    ph = synth.PHASES_APPENDIX_B
+    img = synth.laminate((nz, 3, 3), labels)
+    core = (slice(2, 7), slice(0, 3), slice(0, 3))
+    med = O.IsoMedium.from_labels(img, ph)
+    res = O.homogenize_box(med, core, tol=1e-13)
+    Cs = [O.iso_voigt(*ph[l]) for l in labels]
+    Sig = np.zeros((6, 6))
+    Eps = np.zeros((6, 6))
+    iNN = [np.linalg.inv(C[np.ix_(NORM, NORM)]) for C in Cs]
+    A = np.mean(iNN, axis=0)
+    for a in range(6):
+        gE = np.zeros(6)
+        gE[a] = 1.0
+        gT = gE[TANG]
+        sN = np.linalg.solve(A, gE[NORM] + np.mean([m @ C[np.ix_(NORM, TANG)] @ gT for m, C in zip(iNN, Cs)], 0))
+        g_layers = []
+        s_layers = []
+        for m, C in zip(iNN, Cs):
+            g = np.zeros(6)
+            g[TANG] = gT
+            g[NORM] = m @ (sN - C[np.ix_(NORM, TANG)] @ gT)
+            g_layers.append(g)
+            s_layers.append(C @ g)
+        Eps[:, a] = np.mean(g_layers[2:7], axis=0)
+        Sig[:, a] = np.mean(s_layers[2:7], axis=0)
+    assert np.abs(Eps - np.eye(6)).max() > 1e-2
+    ref = Sig @ np.linalg.inv(Eps)
+    assert np.abs(res["Eps"] - Eps).max() < 1e-9
+    assert np.abs(res["C"] - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert np.abs(res["C"] - np.linalg.inv(Eps) @ Sig).max() > 1e-3 * np.abs(ref).max()
+
+
+# --------------------------------------------------------------- bounds ----
+
+@pytest.mark.parametrize("shape,ph", [((6, 6, 6), synth.PHASES_APPENDIX_B),
+                                      ((5, 7, 6), synth.PHASES_SOLID_CLAY_PORE)])
+def test_voigt_reuss_bounds_and_symmetry(shape, ph):
+    img = (RNG.random(shape) * len(ph)).astype(np.uint8)
+    med = O.IsoMedium.from_labels(img, ph)
+    res = O.homogenize_box(med, (slice(None),) * 3, tol=1e-10, max_iter=50000)
+    C = res["C"]
+    Cv = med.voigt().reshape(6, 6, -1)
+    CV = Cv.mean(axis=2)
+    CR = np.linalg.inv(np.mean([np.linalg.inv(Cv[:, :, i]) for i in range(Cv.shape[2])], axis=0))
+    s = np.abs(C).max()
+    assert np.linalg.norm(C - C.T) / np.linalg.norm(C) <= 1e-8
+    Cs = O.symmetrize(C)
+    assert np.linalg.eigvalsh(CV - Cs).min() >= -1e-8 * s
+    assert np.linalg.eigvalsh(Cs - CR).min() >= -1e-8 * s
+    K, G = O.moduli_voigt(Cs)
+    KR, GR = O.moduli_reuss(Cs)
+    assert KR <= K + 1e-12 and GR <= G + 1e-12
+    KV, GV = O.moduli_voigt(CV)
+    KRR, GRR = O.moduli_reuss(CR)
+    assert KRR - 1e-9 <= K <= KV + 1e-9 and GRR - 1e-9 <= G <= GV + 1e-9
+
+
+def test_hashin_shtrikman_bounds_two_phase_isotropic():
+    """Soft check on a statistically isotropic field: K and G within the
+    two-phase Hashin-Shtrikman bounds."""
+    img = synth.grf_two_phase(n=16, ell=2.0, porosity=0.4, seed=7)
+    ph = synth.PHASES_APPENDIX_B
+    res = O.homogenize_direct(img, ph, tol=1e-8)
+    f2 = img.mean()
+    f1 = 1 - f2
+    (K1, G1), (K2, G2) = ph
+
+    def hs(Ka, Ga, Kb, Gb, fa, fb):
+        K = Ka + fb / (1 / (Kb - Ka) + fa / (Ka + 4 * Ga / 3))
+        z = Ga / 6 * (9 * Ka + 8 * Ga) / (Ka + 2 * Ga)
+        G = Ga + fb / (1 / (Gb - Ga) + fa / (Ga + z))
+        return K, G
+
+    Ku, Gu = hs(K1, G1, K2, G2, f1, f2)
+    Kl, Gl = hs(K2, G2, K1, G1, f2, f1)
+    assert Kl <= res["K"] <= Ku
+    assert Gl <= res["G"] <= Gu
+
+
+# --------------------------------------------------- hierarchical scheme ---
+
+def test_single_box_hierarchical_equals_direct():
+    img = synth.grf_two_phase(n=8, ell=2.0)
+    ph = synth.PHASES_APPENDIX_B
+    d = O.homogenize_direct(img, ph, tol=1e-10)
+    h = O.homogenize_hierarchical(img, ph, synth.uniform_partition(8, 8, 0), unit=8, tol=1e-10)
+    assert np.all(h["level2"]["iters"] == 0)
+    assert np.abs(h["C_sym"] - d["C_sym"]).max() <= 1e-13 * np.abs(d["C_sym"]).max()
+
+
+def test_voxel_boxes_hierarchical_equals_direct():
+    img = (RNG.random((5, 5, 5)) < 0.5).astype(np.uint8)
+    ph = synth.PHASES_APPENDIX_B
+    d = O.homogenize_direct(img, ph, tol=1e-12)
+    h = O.homogenize_hierarchical(img, ph, synth.uniform_partition(5, 1, 0), unit=1, tol=1e-12)
+    for r, lab in zip(h["per_box"], img.ravel()):
+        assert np.all(r["iters"] == 0)
+    assert np.abs(h["coarse"][:, :, 2, 3, 1] - O.iso_voigt(*ph[img[2, 3, 1]])).max() < 1e-12
+    assert np.abs(h["C_sym"] - d["C_sym"]).max() <= 1e-9 * np.abs(d["C_sym"]).max()
+    K, G = O.moduli_voigt(np.mean([O.iso_voigt(*ph[l]) for l in img.ravel()], axis=0))
+    assert h["K_am"] == pytest.approx(K, rel=1e-12) and h["G_am"] == pytest.approx(G, rel=1e-12)
+
+
+def test_extract_box_wraps_periodically():
+    img = RNG.integers(0, 3, size=(6, 7, 8)).astype(np.uint8)
+    box = (6, 0, 4, 2, 3, 2, 2)  # ox oy oz nx ny nz b
+    sub = O.extract_box(img, box)
+    assert sub.shape == (2 + 4, 3 + 4, 2 + 4)
+    for k in range(sub.shape[0]):
+        for j in range(sub.shape[1]):
+            for i in range(sub.shape[2]):
+                assert sub[k, j, i] == img[(4 - 2 + k) % 6, (0 - 2 + j) % 7, (6 - 2 + i) % 8]
+
+
+def test_uneven_partition_tiles_the_image():
+    boxes = synth.uneven_partition()
+    assert boxes.shape == (27000, 7)
+    assert set(np.unique(boxes[:, 3:6])) == {16, 24, 32}
+    assert boxes[:, 6].min() == 0 and boxes[:, 6].max() == 8
+    cover = np.zeros((64, 64, 64), dtype=np.int32)
+    for ox, oy, oz, nx, ny, nz, b in boxes:
+        cover[oz // 8:(oz + nz) // 8, oy // 8:(oy + ny) // 8, ox // 8:(ox + nx) // 8] += 1
+    assert np.all(cover == 1)
+    sizes = boxes[:, 3:6] + 2 * boxes[:, 6:7]
+    assert sizes.min() == 16 and sizes.max() == 48
+
+
+# ---------------------------------------------------------- power law ------
+
+def test_fit_inverse_n_exact():
+    ns = [16, 24, 32, 64, 128]
+    M = [3.0 + 5.0 / n for n in ns]
+    Mi, C = O.fit_inverse_n(ns, M)
+    assert Mi == pytest.approx(3.0, abs=1e-12) and C == pytest.approx(5.0, abs=1e-10)
+    n1, n2, m1, m2 = 16, 32, 4.1, 3.7
+    Mi, C = O.fit_inverse_n([n1, n2], [m1, m2])
+    assert Mi == pytest.approx((n2 * m2 - n1 * m1) / (n2 - n1), rel=1e-13)
+
+
+def test_fit_reproduces_paper_tables(golden_dir):
+    ns = np.array([75, 90, 100, 150, 180, 225, 300], dtype=float)
+    A = np.stack([np.ones_like(ns), 1 / ns], axis=1)
+    W = np.linalg.pinv(A)
+    # tolerance from the printed rounding: inputs and outputs carry +-0.005
+    tol_m = np.abs(W[0]).sum() * 0.005 + 0.005
+    tol_c = np.abs(W[1]).sum() * 0.005 + 0.005
+    count = 0
+    for line in open(os.path.join(golden_dir, "power_law_fit.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        M = np.array([float(v) for v in f[3:10]])
+        Mi, C = O.fit_inverse_n(ns, M)
+        assert abs(Mi - float(f[10])) <= tol_m, line
+        assert abs(C - float(f[11])) <= tol_c, line
+        count += 1
+    assert count == 17
+
+
+# ------------------------------------------------------------ mutations ----
+
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """Plant plausible mistakes in the oracle and check that a pin fails."""
+    good = O.project_sym
+
+    def dropped_term(tau_hat, xi, zero):
+        norm = np.sqrt(np.sum(xi * xi, axis=0))
+        n = xi / np.where(norm > 0, norm, 1.0)
+        T = O.to_full(tau_hat)
+        v = np.einsum("ij...,j...->i...", T, n)
+        P = np.einsum("i...,j...->ij...", n, v) + np.einsum("i...,j...->ij...", v, n)
+        out = O.from_full(P)
+        out[:, zero] = 0
+        return out
+
+    # 1. projection without the n n (n.v) term: same kernel, but no longer a
+    #    projection; the orthogonal-projection pin catches it.
+    monkeypatch.setattr(O, "project_sym", dropped_term)
+    with pytest.raises(AssertionError):
+        test_projection_is_orthogonal_projection((5, 7, 3), "component")
+    monkeypatch.setattr(O, "project_sym", good)
+
+    # 2. shear components 23 and 13 swapped when the 3x3 tensor is formed
+    good_full = O.to_full
+
+    def swapped_full(t6):
+        t = t6.copy()
+        t[[3, 4]] = t6[[4, 3]]
+        return good_full(t)
+
+    monkeypatch.setattr(O, "to_full", swapped_full)
+    assert _bruteforce_error(3, synth.PHASES_APPENDIX_B, 0) > 1e-3
+    monkeypatch.setattr(O, "to_full", good_full)
+
+    # 3. wave-vector components x and z transposed: the laminate pin catches it
+    good_wv = O.wave_vectors
+
+    def swapped(shape, nyquist="component"):
+        xi, zero = good_wv(shape, nyquist)
+        return np.stack([xi[2], xi[1], xi[0]]), zero
+
+    monkeypatch.setattr(O, "wave_vectors", swapped)
+    labels = [0, 1, 1, 0, 1]
+    img = synth.laminate((5, 3, 3), labels)
+    ph = synth.PHASES_APPENDIX_B
+    res = O.homogenize_direct(img, ph, tol=1e-12)
+    ref = backus([O.iso_voigt(*ph[l]) for l in labels], np.ones(5))
+    assert np.abs(res["C"] - ref).max() > 1e-3 * np.abs(ref).max()
+    monkeypatch.setattr(O, "wave_vectors", good_wv)
+
+    # 4. Eps^-1 Sigma instead of Sigma Eps^-1: the buffered laminate catches it
+    good_hb = O.homogenize_box
+
+    def transposed(*a, **k):
+        r = good_hb(*a, **k)
+        r["C"] = np.linalg.inv(r["Eps"]) @ r["Sigma"]
+        return r
+
+    monkeypatch.setattr(O, "homogenize_box", transposed)
+    with pytest.raises(AssertionError):
+        test_buffered_laminate_core_averages()
+    monkeypatch.setattr(O, "homogenize_box", good_hb)
+
+    # 5. plain instead of engineering shear in the strain weights
+    monkeypatch.setattr(O, "FROB_W", np.array([1.0, 1, 1, 1, 1, 1]))
+    with pytest.raises(AssertionError):
+        test_homogeneous_isotropic_returns_phase_moduli_exactly()
