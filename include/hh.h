@@ -1,0 +1,199 @@
+/*
+ * hh.h -- C ABI of the GB300 hierarchical-homogenization library (libhh).
+ *
+ * Computes effective elastic stiffness of segmented 3D images by the
+ * hierarchical homogenization of Ahmad, Liu, Ortiz, Mukerji and Cai (2022):
+ * every subimage (core plus buffer, periodic) is homogenized by an FFT-based
+ * Galerkin elasticity solver (Appendix A), the resulting anisotropic 6x6
+ * stiffnesses are assembled into an intermediate image (Section 3) and that
+ * image is homogenized again; K and G of the result are extrapolated in 1/n
+ * (Section 5, Eq. fit_power_law).
+ *
+ * Conventions shared by every call
+ *  - Images are uint8 labels, x fastest: index = (z * ny + y) * nx + x.
+ *  - A label indexes the caller's phase table; every label must be < nphase.
+ *  - Voigt order (11, 22, 33, 23, 13, 12); stress Voigt vectors hold sigma_ij,
+ *    strain Voigt vectors hold engineering shear (2 eps_ij), so an isotropic
+ *    phase has C44 = G. Matrices are 6x6 row-major doubles.
+ *  - Ownership: the caller owns every buffer it passes; the library never
+ *    keeps a caller pointer after a call returns. A context owns its device
+ *    workspace, FFT tables and pinned staging memory.
+ *  - `*_on_device` = 1 means the pointer is device memory readable on the
+ *    context's stream; 0 means host memory.
+ *  - Every call returns hh_status (0 = OK, < 0 error, > 0 warning). No call
+ *    throws or aborts. On an error, outputs are left in an unspecified state.
+ *  - Calls on one context are not thread-safe; use one context per thread.
+ */
+#ifndef HH_H
+#define HH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hh_status;
+#define HH_OK 0
+#define HH_WARN_NOT_CONVERGED 1   /* a solve hit max_iter; results filled, resid_max reported */
+#define HH_ERR_ARG (-1)           /* invalid argument (dims, labels, moduli, partition, options) */
+#define HH_ERR_OOM (-2)           /* device or pinned allocation failed */
+#define HH_ERR_CUDA (-3)          /* a CUDA runtime call failed */
+#define HH_ERR_NONFINITE (-4)     /* NaN/Inf in a CG scalar */
+#define HH_ERR_DEVICE_TIMEOUT (-5)/* a bounded device-side wait ran out */
+#define HH_ERR_BAD_STIFFNESS (-6) /* a stiffness that is not symmetric positive definite */
+#define HH_ERR_UNSUPPORTED (-7)   /* FFT length with a prime factor above 31, or plane too large */
+
+#define HH_FP32 0                 /* FP32 fields and FFTs, FP64 scalars and averages */
+#define HH_FP64 1                 /* FP64 everywhere */
+#define HH_CG 0                   /* conjugate gradients (Appendix A) */
+#define HH_BASIC 1                /* basic fixed point with an isotropic reference medium */
+#define HH_NYQ_ZERO_COMPONENT 0   /* even N: Nyquist wave-vector component set to 0 */
+#define HH_NYQ_ZERO_MODE 1        /* even N: projection zero on every Nyquist mode */
+
+typedef struct hh_ctx hh_ctx;
+
+typedef struct {
+    double K; /* bulk modulus, GPa, > 0 */
+    double G; /* shear modulus, GPa, > 0 */
+} hh_phase;
+
+typedef struct {
+    int precision;        /* HH_FP32 (default) or HH_FP64 */
+    double tol;           /* stop when ||r|| <= tol ||b|| (Frobenius norm), default 1e-6 */
+    int max_iter;         /* per load case, default 20000 */
+    int scheme;           /* HH_CG (default) or HH_BASIC */
+    int nyquist;          /* HH_NYQ_ZERO_COMPONENT (default) or HH_NYQ_ZERO_MODE */
+    int fixed_iters;      /* > 0: run exactly this many iterations, ignore tol (parity runs) */
+    double ref_lambda;    /* HH_BASIC reference medium; <= 0: mean of the extreme phase values */
+    double ref_mu;
+    int64_t workspace_bytes; /* device workspace budget for batched solves; 0 = 3/4 of free memory */
+    int use_graphs;       /* 1 (default): capture the iteration loop in CUDA graphs */
+    int check_every;      /* iterations between host convergence checks, default 32 */
+    int replace;          /* residual replacement at every check: r <- -G*(C:(E + x));
+                             1 on, 0 off, -1 (default) on in FP32 and off in FP64 */
+    int max_restarts;     /* restarts allowed when the final true residual exceeds
+                             2 tol (default 4) */
+} hh_options;
+
+typedef struct {
+    double C[36];         /* effective stiffness, raw Sigma Eps^-1 of the last solve, row-major Voigt */
+    double C_sym[36];     /* (C + C^T) / 2 */
+    double K, G;          /* isotropic Voigt projection of C_sym */
+    double K_reuss, G_reuss; /* isotropic Reuss projection of C_sym */
+    double K_am, G_am;    /* core-volume-weighted mean of subimage K, G (hierarchical calls only) */
+    int iters_max;        /* most iterations of any load case of any solve */
+    int n_subimages;      /* level-1 subimages solved (hierarchical calls) */
+    int n_surrogate_accepted;
+    int pad_;
+    double resid_max;     /* largest final true residual ||b - A x|| / ||b|| */
+    long long voxel_iters;/* sum over solves of (voxels x iterations), all load cases */
+    hh_status status;
+    int pad2_;
+} hh_result;
+
+/* Text of the last error on this context (or of the last failed hh_create
+ * when ctx is NULL); never NULL. */
+const char *hh_last_error(hh_ctx *ctx);
+
+/* Library version string. */
+const char *hh_version(void);
+
+/* Human-readable text for a status code; never NULL. */
+const char *hh_status_string(hh_status s);
+
+/* Fill `o` with defaults (FP32, tol 1e-6, max_iter 20000, CG, component rule). */
+hh_status hh_options_default(hh_options *o);
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t to
+ * run on (e.g. a PyTorch stream) or NULL for a context-owned stream. */
+hh_status hh_create(hh_ctx **out, int device, void *cuda_stream);
+
+/* Free everything the context owns. NULL is allowed. */
+void hh_destroy(hh_ctx *ctx);
+
+/* Direct (brute-force) homogenization of a whole periodic image: the six load
+ * cases of Section 4 on the full grid, averages over the whole grid, C =
+ * Sigma Eps^-1 (Section 5: the reference M_N). `out` receives C, K, G. */
+hh_status hh_homogenize_direct(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                               int img_on_device, const hh_phase *phases, int nphase,
+                               const hh_options *opt, hh_result *out);
+
+/* Two-level hierarchical homogenization with a uniform partition (Section 3,
+ * Fig. 2; Section 4, Fig. 4): cores of edge n (n divides nx, ny, nz), buffer
+ * b >= 0 voxels wrapped periodically at the image edge, C_R = Sigma Eps^-1
+ * over each core, assembly of sym(C_R) into an (nx/n, ny/n, nz/n) image,
+ * second solve. `per_sub_C` (caller-owned, may be NULL) receives the raw 36
+ * values of every subimage, subimages ordered x fastest then y then z;
+ * `per_sub_iters` (may be NULL) receives the 6 iteration counts of each. */
+hh_status hh_homogenize_hierarchical(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                                     int img_on_device, const hh_phase *phases, int nphase,
+                                     int n, int b, const hh_options *opt, hh_result *out,
+                                     double *per_sub_C, int *per_sub_iters);
+
+/* Two-level scheme on an arbitrary partition. `boxes` holds nbox rows of 7
+ * int32 (ox, oy, oz, cnx, cny, cnz, b): core origin, core size, buffer width.
+ * Every core edge and origin must be a multiple of `unit`, and the cores must
+ * tile the image; the coarse image has (nx/unit, ny/unit, nz/unit) voxels
+ * and each subimage fills its block of coarse voxels. Outputs as above,
+ * in box order. */
+hh_status hh_homogenize_partition(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                                  int img_on_device, const hh_phase *phases, int nphase,
+                                  const int32_t *boxes, int nbox, int unit,
+                                  const hh_options *opt, hh_result *out,
+                                  double *per_sub_C, int *per_sub_iters);
+
+/* Level-1 only: the subimage stiffnesses of a partition (Section 4), without
+ * assembly or second solve. `boxes` as above (no tiling requirement, unit
+ * ignored). Outputs per box: raw C (36), Sigma and Eps (36 each, columns =
+ * load cases, may be NULL), iterations (6), final residuals (6, may be NULL). */
+hh_status hh_solve_subimages(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                             int img_on_device, const hh_phase *phases, int nphase,
+                             const int32_t *boxes, int nbox, const hh_options *opt,
+                             double *C_out, double *Sigma_out, double *Eps_out,
+                             int *iters_out, double *resid_out);
+
+/* Homogenization of an anisotropic image (Section 3: the assembled
+ * intermediate image; Section 4: fully anisotropic voxels). `C21` holds the
+ * upper triangle of each voxel's 6x6 Voigt stiffness, component-major:
+ * C21[k * V + voxel], k over (00 01 02 03 04 05 11 12 ... 55). Every voxel
+ * stiffness must be symmetric positive definite (checked: HH_ERR_BAD_STIFFNESS). */
+hh_status hh_homogenize_aniso(hh_ctx *ctx, const double *C21, int nx, int ny, int nz,
+                              int c21_on_device, const hh_options *opt, hh_result *out);
+
+/* One application of the discrete operator of Appendix A to a strain field:
+ * q = G * (C : p), with C from labels + phases (C21 == NULL) or from C21
+ * (labels ignored). p and q are host doubles [6][nz][ny][nx] (tensor
+ * components 11 22 33 23 13 12). Runs in the requested precision. */
+hh_status hh_apply_operator(hh_ctx *ctx, const uint8_t *labels, const hh_phase *phases,
+                            int nphase, const double *C21, int nx, int ny, int nz,
+                            const double *p, double *q, const hh_options *opt);
+
+/* Extraction of the buffered subimages (Section 4, Fig. 4) exactly as the
+ * solver sees them: out receives the concatenated Omega_B label arrays of all
+ * boxes (each (cnz+2b)(cny+2b)(cnx+2b), x fastest), indices wrapped
+ * periodically. `out_len` is the capacity of out in bytes. */
+hh_status hh_extract_subimages(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                               int img_on_device, const int32_t *boxes, int nbox,
+                               uint8_t *out, int64_t out_len);
+
+/* Hierarchical homogenization for each subimage edge in ns[0..count) (buffer
+ * b), then the least-squares fit M(n) = M_inf + C / n (Section 5, Eq.
+ * fit_power_law; with two sizes this is Richardson extrapolation) for K and G.
+ * `per_n` (caller-owned [count] or NULL) receives each hierarchical result. */
+hh_status hh_extrapolate(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                         int img_on_device, const hh_phase *phases, int nphase,
+                         const int *ns, int count, int b, const hh_options *opt,
+                         double *K_inf, double *C_K, double *G_inf, double *C_G,
+                         hh_result *per_n);
+
+/* Least-squares fit of M(n) = M_inf + C / n over count >= 2 points (Section 5,
+ * Eq. fit_power_law), evaluated in FP64 on the context's device. */
+hh_status hh_fit_inverse_n(hh_ctx *ctx, const int *ns, const double *M, int count,
+                           double *M_inf, double *C);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HH_H */

@@ -1,0 +1,332 @@
+"""ctypes binding of libhh (include/hh.h): argument marshalling only.
+
+Every computation runs in the CUDA library. If libhh.so has not been built,
+or no CUDA device is present, the calls raise; there is no CPU fallback.
+Arrays may be numpy arrays (host) or CUDA torch tensors (passed by device
+pointer on the context's stream).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhh.so")
+
+HH_OK = 0
+HH_WARN_NOT_CONVERGED = 1
+HH_ERR_ARG = -1
+HH_ERR_OOM = -2
+HH_ERR_CUDA = -3
+HH_ERR_NONFINITE = -4
+HH_ERR_DEVICE_TIMEOUT = -5
+HH_ERR_BAD_STIFFNESS = -6
+HH_ERR_UNSUPPORTED = -7
+HH_FP32, HH_FP64 = 0, 1
+HH_CG, HH_BASIC = 0, 1
+HH_NYQ_ZERO_COMPONENT, HH_NYQ_ZERO_MODE = 0, 1
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("tol", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("scheme", ctypes.c_int),
+        ("nyquist", ctypes.c_int),
+        ("fixed_iters", ctypes.c_int),
+        ("ref_lambda", ctypes.c_double),
+        ("ref_mu", ctypes.c_double),
+        ("workspace_bytes", ctypes.c_int64),
+        ("use_graphs", ctypes.c_int),
+        ("check_every", ctypes.c_int),
+        ("replace", ctypes.c_int),
+        ("max_restarts", ctypes.c_int),
+    ]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [
+        ("C", ctypes.c_double * 36),
+        ("C_sym", ctypes.c_double * 36),
+        ("K", ctypes.c_double),
+        ("G", ctypes.c_double),
+        ("K_reuss", ctypes.c_double),
+        ("G_reuss", ctypes.c_double),
+        ("K_am", ctypes.c_double),
+        ("G_am", ctypes.c_double),
+        ("iters_max", ctypes.c_int),
+        ("n_subimages", ctypes.c_int),
+        ("n_surrogate_accepted", ctypes.c_int),
+        ("pad_", ctypes.c_int),
+        ("resid_max", ctypes.c_double),
+        ("voxel_iters", ctypes.c_longlong),
+        ("status", ctypes.c_int),
+        ("pad2_", ctypes.c_int),
+    ]
+
+    def as_dict(self) -> dict:
+        return dict(C=np.array(self.C).reshape(6, 6), C_sym=np.array(self.C_sym).reshape(6, 6),
+                    K=self.K, G=self.G, K_reuss=self.K_reuss, G_reuss=self.G_reuss,
+                    K_am=self.K_am, G_am=self.G_am, iters_max=self.iters_max,
+                    n_subimages=self.n_subimages, resid_max=self.resid_max,
+                    voxel_iters=self.voxel_iters, status=self.status)
+
+
+class Phase(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_double), ("G", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SIGNATURES = {
+    "hh_version": (ctypes.c_char_p, []),
+    "hh_status_string": (ctypes.c_char_p, [_I]),
+    "hh_last_error": (ctypes.c_char_p, [_P]),
+    "hh_options_default": (_I, [_P]),
+    "hh_create": (_I, [_P, _I, _P]),
+    "hh_destroy": (None, [_P]),
+    "hh_homogenize_direct": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P]),
+    "hh_homogenize_hierarchical": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _I, _I, _P, _P, _P, _P]),
+    "hh_homogenize_partition": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _P, _P, _P]),
+    "hh_solve_subimages": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P]),
+    "hh_homogenize_aniso": (_I, [_P, _P, _I, _I, _I, _I, _P, _P]),
+    "hh_apply_operator": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P, _P, _P]),
+    "hh_extract_subimages": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, ctypes.c_int64]),
+    "hh_extrapolate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P]),
+    "hh_fit_inverse_n": (_I, [_P, _P, _P, _I, _P, _P]),
+}
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load libhh.so (built by paper_2208_02320_gb300._build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libhh.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def options(**kw) -> Options:
+    o = Options()
+    load().hh_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp32": HH_FP32, "fp64": HH_FP64}[v]
+        if k == "nyquist" and isinstance(v, str):
+            v = {"component": HH_NYQ_ZERO_COMPONENT, "mode": HH_NYQ_ZERO_MODE}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def _u8(img):
+    """(pointer, on_device, keepalive) for a uint8 image [z][y][x]."""
+    if _is_torch_cuda(img):
+        import torch
+        t = img.contiguous()
+        if t.dtype != torch.uint8:
+            raise TypeError("image must be uint8")
+        return ctypes.c_void_p(t.data_ptr()), 1, t
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def _phases(phases):
+    ph = np.asarray(phases, dtype=np.float64).reshape(-1, 2)
+    arr = (Phase * len(ph))(*[Phase(float(k), float(g)) for k, g in ph])
+    return arr, len(ph)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """A libhh context on one CUDA device (optionally bound to a CUDA stream)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._lib = load()
+        self._h = ctypes.c_void_p()
+        s = self._lib.hh_create(ctypes.byref(self._h), int(device), ctypes.c_void_p(stream or 0))
+        if s != HH_OK:
+            raise HHError(s, "hh_create: " + self._lib.hh_last_error(None).decode())
+
+    def close(self):
+        if self._h:
+            self._lib.hh_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, s: int, what: str, allow_warn: bool = True):
+        if s < 0 or (s > 0 and not allow_warn):
+            raise HHError(s, f"{what}: {self._lib.hh_last_error(self._h).decode()}")
+        return s
+
+    # -------------------------------------------------------------- solves
+    def homogenize_direct(self, img, phases, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        o = options(**opt)
+        r = Result()
+        s = self._lib.hh_homogenize_direct(self._h, p, nx, ny, nz, dev, ph, nph, ctypes.byref(o), ctypes.byref(r))
+        self._check(s, "hh_homogenize_direct")
+        return r.as_dict()
+
+    def homogenize_hierarchical(self, img, phases, n: int, b: int = 0, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        o = options(**opt)
+        nbox = (nx // n) * (ny // n) * (nz // n) if n > 0 and nx % n == 0 and ny % n == 0 and nz % n == 0 else 0
+        Cb = np.zeros((max(nbox, 1), 6, 6))
+        It = np.zeros((max(nbox, 1), 6), dtype=np.int32)
+        r = Result()
+        s = self._lib.hh_homogenize_hierarchical(self._h, p, nx, ny, nz, dev, ph, nph, int(n), int(b),
+                                                 ctypes.byref(o), ctypes.byref(r), _ptr(Cb), _ptr(It))
+        self._check(s, "hh_homogenize_hierarchical")
+        d = r.as_dict()
+        d.update(C_boxes=Cb[:nbox], iters_boxes=It[:nbox])
+        return d
+
+    def homogenize_partition(self, img, phases, boxes, unit: int, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        bx = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 7)
+        o = options(**opt)
+        Cb = np.zeros((len(bx), 6, 6))
+        It = np.zeros((len(bx), 6), dtype=np.int32)
+        r = Result()
+        s = self._lib.hh_homogenize_partition(self._h, p, nx, ny, nz, dev, ph, nph, _ptr(bx), len(bx), int(unit),
+                                              ctypes.byref(o), ctypes.byref(r), _ptr(Cb), _ptr(It))
+        self._check(s, "hh_homogenize_partition")
+        d = r.as_dict()
+        d.update(C_boxes=Cb, iters_boxes=It)
+        return d
+
+    def solve_subimages(self, img, phases, boxes, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        bx = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 7)
+        o = options(**opt)
+        nb = len(bx)
+        C = np.zeros((nb, 6, 6))
+        S = np.zeros((nb, 6, 6))
+        E = np.zeros((nb, 6, 6))
+        It = np.zeros((nb, 6), dtype=np.int32)
+        Rs = np.zeros((nb, 6))
+        s = self._lib.hh_solve_subimages(self._h, p, nx, ny, nz, dev, ph, nph, _ptr(bx), nb, ctypes.byref(o),
+                                         _ptr(C), _ptr(S), _ptr(E), _ptr(It), _ptr(Rs))
+        st = self._check(s, "hh_solve_subimages")
+        return dict(C=C, Sigma=S, Eps=E, iters=It, resid=Rs, status=st)
+
+    def homogenize_aniso(self, C21, **opt) -> dict:
+        if _is_torch_cuda(C21):
+            t = C21.contiguous()
+            ptr, dev, keep = ctypes.c_void_p(t.data_ptr()), 1, t
+            shape = tuple(t.shape)
+        else:
+            keep = np.ascontiguousarray(C21, dtype=np.float64)
+            ptr, dev, shape = _ptr(keep), 0, keep.shape
+        assert shape[0] == 21
+        nz, ny, nx = shape[1:]
+        o = options(**opt)
+        r = Result()
+        s = self._lib.hh_homogenize_aniso(self._h, ptr, nx, ny, nz, dev, ctypes.byref(o), ctypes.byref(r))
+        self._check(s, "hh_homogenize_aniso")
+        return r.as_dict()
+
+    def apply_operator(self, p_field, labels=None, phases=None, C21=None, **opt) -> np.ndarray:
+        pf = np.ascontiguousarray(p_field, dtype=np.float64)
+        nz, ny, nx = pf.shape[1:]
+        q = np.zeros_like(pf)
+        o = options(**opt)
+        if C21 is not None:
+            c = np.ascontiguousarray(C21, dtype=np.float64)
+            s = self._lib.hh_apply_operator(self._h, None, None, 0, _ptr(c), nx, ny, nz, _ptr(pf), _ptr(q),
+                                            ctypes.byref(o))
+        else:
+            lab = np.ascontiguousarray(labels, dtype=np.uint8)
+            ph, nph = _phases(phases)
+            s = self._lib.hh_apply_operator(self._h, _ptr(lab), ph, nph, None, nx, ny, nz, _ptr(pf), _ptr(q),
+                                            ctypes.byref(o))
+        self._check(s, "hh_apply_operator", allow_warn=False)
+        return q
+
+    def extract_subimages(self, img, boxes) -> list:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        bx = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 7)
+        dims = [(int(r[5]) + 2 * int(r[6]), int(r[4]) + 2 * int(r[6]), int(r[3]) + 2 * int(r[6])) for r in bx]
+        tot = sum(a * b * c for a, b, c in dims)
+        out = np.zeros(max(tot, 1), dtype=np.uint8)
+        s = self._lib.hh_extract_subimages(self._h, p, nx, ny, nz, dev, _ptr(bx), len(bx), _ptr(out), out.size)
+        self._check(s, "hh_extract_subimages", allow_warn=False)
+        res, o = [], 0
+        for d in dims:
+            n = d[0] * d[1] * d[2]
+            res.append(out[o:o + n].reshape(d))
+            o += n
+        return res
+
+    def extrapolate(self, img, phases, ns, b: int = 0, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        nsa = np.ascontiguousarray(ns, dtype=np.int32)
+        o = options(**opt)
+        per = (Result * len(nsa))()
+        out = [ctypes.c_double() for _ in range(4)]
+        s = self._lib.hh_extrapolate(self._h, p, nx, ny, nz, dev, ph, nph, _ptr(nsa), len(nsa), int(b),
+                                     ctypes.byref(o), *[ctypes.byref(v) for v in out], per)
+        self._check(s, "hh_extrapolate")
+        return dict(K_inf=out[0].value, C_K=out[1].value, G_inf=out[2].value, C_G=out[3].value,
+                    per_n=[r.as_dict() for r in per])
+
+    def fit_inverse_n(self, ns, M):
+        nsa = np.ascontiguousarray(ns, dtype=np.int32)
+        Ma = np.ascontiguousarray(M, dtype=np.float64)
+        mi, c = ctypes.c_double(), ctypes.c_double()
+        s = self._lib.hh_fit_inverse_n(self._h, _ptr(nsa), _ptr(Ma), len(nsa), ctypes.byref(mi), ctypes.byref(c))
+        self._check(s, "hh_fit_inverse_n", allow_warn=False)
+        return mi.value, c.value
+
+    # raw status calls (tests of the error paths)
+    def raw(self):
+        return self._lib, self._h

@@ -1,0 +1,1026 @@
+// Device-side types and kernels of the FFT Galerkin elasticity solver.
+//
+// The discrete problem (Appendix A): find the compatible strain fluctuation
+// eps* with G*(C:eps*) = -G*(C:E), solved by conjugate gradients. G is the
+// orthogonal projection of a symmetric tensor field onto compatible strains,
+// applied mode by mode in Fourier space:
+//     (P tau)_ij = n_i v_j + v_i n_j - n_i n_j (n . v),  v = tau n,  n = xi/|xi|,
+// with P = 0 at xi = 0. One operator application q = P(C:p) is split into
+//   plane pass  : per z-plane, the constitutive law sigma = C(x):p fused into
+//                 the x (real-to-complex) and y transforms, in shared memory;
+//   column pass : per ky, the z transform, the projection, the inverse z
+//                 transform, in shared memory;
+//   inverse pass: per z-plane, inverse y and complex-to-real x transforms and
+//                 the FP64 partial of <p, q>.
+// Transforms are in-place mixed-radix Cooley-Tukey: decimation in frequency
+// (natural order in, digit-reversed order out) forward, decimation in time
+// (digit-reversed in, natural out) inverse, so no reordering pass is needed.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hh {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) C2 {
+  T x, y;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ C2<T> mk(T a, T b) {
+  C2<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T>
+__device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T>
+__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename T>
+__device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+// multiply by -i (forward) or +i (inverse)
+template <typename T, bool INV>
+__device__ __forceinline__ C2<T> rot(C2<T> a) {
+  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+}
+
+constexpr int kMaxStages = 16;
+constexpr int kMaxRadix = 31;
+
+// One transform length. Twiddles W_n[t] = exp(-2 pi i t / n) live in a shared
+// table of doubles at tw_off; pos_of_freq (natural frequency -> storage
+// position after the forward transform) and sfreq (storage position -> signed
+// frequency in (-n/2, n/2]) live in an int table.
+struct AxisPlan {
+  int n;
+  int nst;
+  int rad[kMaxStages];
+  int tw_off;
+  int pf_off;
+  int sf_off;
+  int pad;
+};
+
+// One (subimage, load case) solve.
+struct Prob {
+  int nx, ny, nz, nxh;
+  int c0x, c0y, c0z, cnx, cny, cnz;  // core region inside the buffered box
+  int px, py, pz;                    // plan index per axis
+  int lc;                            // load case 0..5
+  int box;                           // subimage index in the request
+  int plane0;                        // first plane item of this problem
+  int col0;                          // first column item of this problem
+  int pad;
+  long long med_off;                 // iso: byte offset of labels; aniso: element offset of C21
+  long long fld_off;                 // element offset of r, p, q (6 V each)
+  long long spc_off;                 // complex offset of the spectrum (6 nz ny nxh)
+};
+
+// FP64 conjugate-gradient scalars of one problem.
+struct PState {
+  double rho, rho0, rho_prev, alpha, beta;
+  double xbar[6];  // sum over the core of eps* (final pass)
+  double sbar[6];  // sum over the core of C:(E + eps*) (final pass)
+  double resid;    // final ||b - A x|| / ||b|| from the true residual
+  double rt_best;  // smallest true <r, r> seen at a checkpoint
+  int iters, active, status, trueflag, homog, restarts, stall, pad1;
+};
+
+enum : int { MED_ISO = 0, MED_ANISO = 1 };
+enum : int { MODE_RHS = 0, MODE_ITER = 1, MODE_APPLY = 2, MODE_TRUE = 3 };
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NONFINITE = 2 };
+
+constexpr int kAvgParts = 12;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
+
+template <typename T>
+struct KParams {
+  const Prob* prob;
+  PState* st;
+  const int2* items;  // (problem, z or ky index)
+  int nitems;
+  int medium;         // MED_ISO / MED_ANISO
+  int nyq_mode;       // 0 component rule, 1 mode rule
+  int rch;            // rows per chunk in the plane passes
+  int nphase;
+  const AxisPlan* plans;
+  const double* tw;   // interleaved (re, im) twiddles
+  const int* itab;
+  const uint8_t* labels;
+  const T* lammu;     // per phase (lambda, mu)
+  const T* c21;       // aniso stiffness, component-major
+  T* r;
+  T* p;
+  T* q;
+  T* x;
+  C2<T>* spec;
+  double* part;       // per-item partial sums
+  double tol;
+  double rhs_floor;
+  int max_iter;
+  int fixed_iters;
+  int nprob;
+};
+
+// ---------------------------------------------------------------------------
+// Small DFTs of size R on registers (forward: exp(-2 pi i rq / R)).
+// ---------------------------------------------------------------------------
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void small_dft(C2<T>* a, const C2<T>* tw, int N) {
+  if constexpr (R == 2) {
+    C2<T> t = a[0];
+    a[0] = cadd(t, a[1]);
+    a[1] = csub(t, a[1]);
+  } else if constexpr (R == 3) {
+    const T h = T(0.86602540378443864676);  // sqrt(3)/2
+    C2<T> s = cadd(a[1], a[2]);
+    C2<T> d = csub(a[1], a[2]);
+    C2<T> m = mk<T>(a[0].x - T(0.5) * s.x, a[0].y - T(0.5) * s.y);
+    a[0] = cadd(a[0], s);
+    // -i h d (forward) / +i h d (inverse)
+    C2<T> t = rot<T, INV>(mk<T>(h * d.x, h * d.y));
+    a[1] = cadd(m, t);
+    a[2] = csub(m, t);
+  } else if constexpr (R == 4) {
+    C2<T> s02 = cadd(a[0], a[2]);
+    C2<T> d02 = csub(a[0], a[2]);
+    C2<T> s13 = cadd(a[1], a[3]);
+    C2<T> d13 = rot<T, INV>(csub(a[1], a[3]));
+    a[0] = cadd(s02, s13);
+    a[2] = csub(s02, s13);
+    a[1] = cadd(d02, d13);
+    a[3] = csub(d02, d13);
+  } else {
+    C2<T> y[R];
+    const int st = N / R;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      C2<T> acc = a[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2<T> w = tw[((r * q) % R) * st];
+        if (INV) w.y = -w.y;
+        acc = cadd(acc, cmul(a[r], w));
+      }
+      y[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[q] = y[q];
+  }
+}
+
+// Lines addressed as off(l) = (l / lpg) * gstride + (l % lpg) * lstride, element
+// k of a line at off(l) + k * es.
+struct Lines {
+  int n;       // number of lines
+  int lpg;     // lines per group
+  int gstride;
+  int lstride;
+  int es;
+  bool fast;   // adjacent threads take adjacent lines (column access)
+};
+
+template <typename T, int R, bool INV>
+__device__ void fft_stage(C2<T>* base, const Lines& L, int N, int span, const C2<T>* tw) {
+  const int sub = span / R;
+  const int tstep = N / span;
+  const int nb = N / R;
+  const int total = L.n * nb;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int line, b;
+    if (L.fast) {
+      line = idx % L.n;
+      b = idx / L.n;
+    } else {
+      line = idx / nb;
+      b = idx - line * nb;
+    }
+    const int blk = b / sub;
+    const int j = b - blk * sub;
+    C2<T>* x = base + (line / L.lpg) * L.gstride + (line % L.lpg) * L.lstride + (blk * span + j) * L.es;
+    const int step = sub * L.es;
+    C2<T> a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = x[r * step];
+    if (!INV) {
+      small_dft<T, R, false>(a, tw, N);
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[q] = cmul(a[q], tw[q * j * tstep]);
+    } else {
+#pragma unroll
+      for (int q = 1; q < R; ++q) a[q] = cmulc(a[q], tw[q * j * tstep]);
+      small_dft<T, R, true>(a, tw, N);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) x[r * step] = a[r];
+  }
+}
+
+// Stage of a prime radix R >= 7 (rare lengths): runtime R, direct O(R^2) DFT.
+template <typename T, bool INV>
+__device__ __noinline__ void fft_stage_generic(C2<T>* base, const Lines& L, int N, int span, int R, const C2<T>* tw) {
+  const int sub = span / R;
+  const int tstep = N / span;
+  const int nb = N / R;
+  const int total = L.n * nb;
+  const int st = N / R;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    int line, b;
+    if (L.fast) {
+      line = idx % L.n;
+      b = idx / L.n;
+    } else {
+      line = idx / nb;
+      b = idx - line * nb;
+    }
+    const int blk = b / sub;
+    const int j = b - blk * sub;
+    C2<T>* x = base + (line / L.lpg) * L.gstride + (line % L.lpg) * L.lstride + (blk * span + j) * L.es;
+    const int step = sub * L.es;
+    C2<T> a[kMaxRadix];
+    C2<T> y[kMaxRadix];
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+      a[r] = x[r * step];
+      if (INV && r > 0) a[r] = cmulc(a[r], tw[r * j * tstep]);
+    }
+#pragma unroll 1
+    for (int q = 0; q < R; ++q) {
+      C2<T> acc = a[0];
+      int m = 0;
+#pragma unroll 1
+      for (int r = 1; r < R; ++r) {
+        m += q;
+        if (m >= R) m -= R;
+        C2<T> w = tw[m * st];
+        if (INV) w.y = -w.y;
+        acc = cadd(acc, cmul(a[r], w));
+      }
+      y[q] = (!INV && q > 0) ? cmul(acc, tw[q * j * tstep]) : acc;
+    }
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) x[r * step] = y[r];
+  }
+}
+
+// In-place transform of a set of lines in shared memory (all threads of the
+// block take part; ends with __syncthreads()).
+template <typename T, bool INV>
+__device__ __noinline__ void fft_lines(C2<T>* base, const Lines L, const AxisPlan& pl, const C2<T>* tw) {
+  const int N = pl.n;
+  int spans[kMaxStages];
+  int s = N;
+  for (int i = 0; i < pl.nst; ++i) {
+    spans[i] = s;
+    s /= pl.rad[i];
+  }
+  for (int k = 0; k < pl.nst; ++k) {
+    const int i = INV ? pl.nst - 1 - k : k;
+    const int span = spans[i];
+    switch (pl.rad[i]) {
+      case 2: fft_stage<T, 2, INV>(base, L, N, span, tw); break;
+      case 3: fft_stage<T, 3, INV>(base, L, N, span, tw); break;
+      case 4: fft_stage<T, 4, INV>(base, L, N, span, tw); break;
+      case 5: fft_stage<T, 5, INV>(base, L, N, span, tw); break;
+      default: fft_stage_generic<T, INV>(base, L, N, span, pl.rad[i], tw); break;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block reduction of K doubles (fixed order: warp shuffle tree, then warp 0).
+// Result valid in thread 0. Uses `red` (>= 32 * K doubles of shared memory).
+// ---------------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void block_reduce(double (&v)[K], double* red) {
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    v[k] = x;
+  }
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = v[k];
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = lane < nw ? red[lane * K + k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[k] = x;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double frob_w(int c) { return c < 3 ? 1.0 : 2.0; }
+
+// ---------------------------------------------------------------------------
+// Constitutive law (Section 4): isotropic sigma = lam tr(eps) I + 2 mu eps, or
+// anisotropic Voigt sigma = C gamma with engineering shear gamma.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stress_iso(const T (&e)[6], T lam, T mu, T (&s)[6]) {
+  const T tr = e[0] + e[1] + e[2];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s[c] = T(2) * mu * e[c];
+  s[0] += lam * tr;
+  s[1] += lam * tr;
+  s[2] += lam * tr;
+}
+
+template <typename T>
+__device__ __forceinline__ void stress_aniso(const T (&e)[6], const T* c21, long long V, long long v, T (&s)[6]) {
+  const T g[6] = {e[0], e[1], e[2], T(2) * e[3], T(2) * e[4], T(2) * e[5]};
+  T C[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) C[k] = c21[k * V + v];
+  // upper-triangle index of (i, j), i <= j: i*6 - i*(i-1)/2 + (j - i)
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    T acc = T(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int a = i < j ? i : j;
+      const int b = i < j ? j : i;
+      acc += C[a * 6 - a * (a - 1) / 2 + (b - a)] * g[j];
+    }
+    s[i] = acc;
+  }
+}
+
+// Projection of one mode (6 complex tensor components, in place).
+template <typename T>
+__device__ __forceinline__ void project_mode(C2<T> (&t)[6], T x0, T x1, T x2) {
+  const T nn = x0 * x0 + x1 * x1 + x2 * x2;
+  if (!(nn > T(0))) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = mk<T>(T(0), T(0));
+    return;
+  }
+  const T inv = T(1) / sqrt(nn);
+  const T n0 = x0 * inv, n1 = x1 * inv, n2 = x2 * inv;
+  // tensor: 0=11 1=22 2=33 3=23 4=13 5=12
+  C2<T> v0, v1, v2;
+  v0.x = t[0].x * n0 + t[5].x * n1 + t[4].x * n2;
+  v0.y = t[0].y * n0 + t[5].y * n1 + t[4].y * n2;
+  v1.x = t[5].x * n0 + t[1].x * n1 + t[3].x * n2;
+  v1.y = t[5].y * n0 + t[1].y * n1 + t[3].y * n2;
+  v2.x = t[4].x * n0 + t[3].x * n1 + t[2].x * n2;
+  v2.y = t[4].y * n0 + t[3].y * n1 + t[2].y * n2;
+  C2<T> s;
+  s.x = n0 * v0.x + n1 * v1.x + n2 * v2.x;
+  s.y = n0 * v0.y + n1 * v1.y + n2 * v2.y;
+  // P_ij = n_i v_j + v_i n_j - n_i n_j s
+  t[0] = mk<T>(T(2) * n0 * v0.x - n0 * n0 * s.x, T(2) * n0 * v0.y - n0 * n0 * s.y);
+  t[1] = mk<T>(T(2) * n1 * v1.x - n1 * n1 * s.x, T(2) * n1 * v1.y - n1 * n1 * s.y);
+  t[2] = mk<T>(T(2) * n2 * v2.x - n2 * n2 * s.x, T(2) * n2 * v2.y - n2 * n2 * s.y);
+  t[3] = mk<T>(n1 * v2.x + v1.x * n2 - n1 * n2 * s.x, n1 * v2.y + v1.y * n2 - n1 * n2 * s.y);
+  t[4] = mk<T>(n0 * v2.x + v0.x * n2 - n0 * n2 * s.x, n0 * v2.y + v0.y * n2 - n0 * n2 * s.y);
+  t[5] = mk<T>(n0 * v1.x + v0.x * n1 - n0 * n1 * s.x, n0 * v1.y + v0.y * n1 - n0 * n1 * s.y);
+}
+
+// Copy an axis' twiddles (double -> T) into shared memory.
+template <typename T>
+__device__ __forceinline__ void load_tw(C2<T>* dst, const double* tw, const AxisPlan& pl) {
+  for (int t = threadIdx.x; t < pl.n; t += blockDim.x)
+    dst[t] = mk<T>(T(tw[2 * (pl.tw_off + t)]), T(tw[2 * (pl.tw_off + t) + 1]));
+}
+
+__device__ __forceinline__ int odd_pitch(int n) { return n | 1; }
+
+// Shared-memory layout of the plane passes (must match plane_smem_bytes on the host).
+template <typename T>
+struct PlaneSmem {
+  C2<T>* S;    // 6 * ny * nxh (component-major, rows of nxh)
+  C2<T>* Z;    // 3 * rch * PX
+  C2<T>* twx;  // nx
+  C2<T>* twy;  // ny
+  int* pfx;    // nx
+  T* lm;       // 2 * nphase
+  double* red; // 32 * 16
+};
+
+template <typename T>
+__device__ __forceinline__ PlaneSmem<T> plane_layout(char* base, int nx, int ny, int nxh, int rch, int nphase) {
+  PlaneSmem<T> s;
+  size_t o = 0;
+  s.red = reinterpret_cast<double*>(base + o);
+  o += 32 * 16 * sizeof(double);
+  s.S = reinterpret_cast<C2<T>*>(base + o);
+  o += sizeof(C2<T>) * 6 * ny * nxh;
+  s.Z = reinterpret_cast<C2<T>*>(base + o);
+  o += sizeof(C2<T>) * 3 * rch * odd_pitch(nx);
+  s.twx = reinterpret_cast<C2<T>*>(base + o);
+  o += sizeof(C2<T>) * nx;
+  s.twy = reinterpret_cast<C2<T>*>(base + o);
+  o += sizeof(C2<T>) * ny;
+  s.pfx = reinterpret_cast<int*>(base + o);
+  o += sizeof(int) * ((nx + 3) & ~3);
+  s.lm = reinterpret_cast<T*>(base + o);
+  return s;
+}
+
+// Plane pass (forward): constitutive law fused into the x and y transforms.
+//   MODE_RHS  : tau = C : E (E = unit load of the problem); partial <tau, tau>_F
+//   MODE_ITER : p <- r + beta p (stored), tau = C : p
+//   MODE_TRUE : tau = C : (E + x)  (true residual r = -G*tau follows)
+//   MODE_APPLY: tau = C : p (p read only)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool skip_problem(const PState* st, int pr, int mode) {
+  if (mode == MODE_ITER) return !st[pr].active;
+  if (mode == MODE_TRUE) return !st[pr].trueflag;
+  return false;
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
+  extern __shared__ __align__(16) char smem[];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (skip_problem<T>(P.st, w.x, MODE)) continue;
+    const Prob d = P.prob[w.x];
+    const int z = w.y;
+    const int nx = d.nx, ny = d.ny, nxh = d.nxh;
+    const int rch = min(P.rch, ny);
+    const int PX = odd_pitch(nx);
+    const long long V = (long long)nx * ny * d.nz;
+    PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, nxh, rch, P.nphase);
+    const AxisPlan ax = P.plans[d.px];
+    const AxisPlan ay = P.plans[d.py];
+    load_tw<T>(sm.twx, P.tw, ax);
+    load_tw<T>(sm.twy, P.tw, ay);
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) sm.pfx[t] = P.itab[ax.pf_off + t];
+    if (P.medium == MED_ISO)
+      for (int t = threadIdx.x; t < 2 * P.nphase; t += blockDim.x) sm.lm[t] = P.lammu[t];
+    const T beta = (MODE == MODE_ITER) ? T(P.st[w.x].beta) : T(0);
+    __syncthreads();
+
+    double acc[1] = {0.0};
+    T* rr = P.r + d.fld_off;
+    T* pp = P.p + d.fld_off;
+    const T* xx = P.x + d.fld_off;
+    const long long zoff = (long long)z * ny * nx;
+    const T Ed = d.lc < 3 ? T(1) : T(0.5);
+
+    for (int y0 = 0; y0 < ny; y0 += rch) {
+      const int nr = min(rch, ny - y0);
+      // voxel phase: stress of the chunk rows into Z (pairs of components packed as complex)
+      for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
+        const int yy = v / nx;
+        const int x = v - yy * nx;
+        const int y = y0 + yy;
+        const long long vo = zoff + (long long)y * nx + x;
+        T e[6];
+        if (MODE == MODE_RHS) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) e[c] = T(0);
+          e[d.lc] = Ed;
+        } else if (MODE == MODE_ITER) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const T pv = rr[c * V + vo] + beta * pp[c * V + vo];
+            pp[c * V + vo] = pv;
+            e[c] = pv;
+          }
+        } else if (MODE == MODE_TRUE) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
+          e[d.lc] += Ed;
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
+        }
+        T s[6];
+        if (P.medium == MED_ISO) {
+          const int lab = P.labels[d.med_off + vo];
+          stress_iso<T>(e, sm.lm[2 * lab], sm.lm[2 * lab + 1], s);
+        } else {
+          stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
+        }
+        if (MODE == MODE_RHS) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) acc[0] += frob_w(c) * double(s[c]) * double(s[c]);
+        }
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) sm.Z[(c2 * rch + yy) * PX + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
+      }
+      __syncthreads();
+      // x transforms of the packed rows
+      Lines Lx{3 * rch, 1 << 30, 0, PX, 1, false};
+      if (nr < rch) {
+        // ragged last chunk: only rows < nr of each component pair are valid
+        Lx.n = 3 * nr;
+        Lx.lpg = nr;
+        Lx.gstride = rch * PX;
+      }
+      fft_lines<T, false>(sm.Z, Lx, ax, sm.twx);
+      // unpack the two real spectra of every packed row into S
+      for (int e = threadIdx.x; e < 3 * nr * nxh; e += blockDim.x) {
+        const int k = e % nxh;
+        const int l = e / nxh;
+        const int c2 = l / nr;
+        const int yy = l - c2 * nr;
+        const C2<T>* row = sm.Z + (c2 * rch + yy) * PX;
+        const C2<T> a = row[sm.pfx[k]];
+        const C2<T> b = row[sm.pfx[k == 0 ? 0 : nx - k]];
+        const C2<T> A = mk<T>(T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y));
+        const C2<T> B = mk<T>(T(0.5) * (a.y + b.y), T(-0.5) * (a.x - b.x));
+        sm.S[((2 * c2) * ny + y0 + yy) * nxh + k] = A;
+        sm.S[((2 * c2 + 1) * ny + y0 + yy) * nxh + k] = B;
+      }
+      __syncthreads();
+    }
+    // y transforms of all 6 * nxh columns
+    Lines Ly{6 * nxh, nxh, ny * nxh, 1, nxh, true};
+    fft_lines<T, false>(sm.S, Ly, ay, sm.twy);
+    // store the plane of the spectrum: spec[c][z][kyp][kx]
+    C2<T>* sp = P.spec + d.spc_off;
+    const int pl = ny * nxh;
+    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
+      const int c = e / pl;
+      const int rem = e - c * pl;
+      sp[((long long)c * d.nz + z) * pl + rem] = sm.S[e];
+    }
+    if (MODE == MODE_RHS) {
+      block_reduce<1>(acc, sm.red);
+      if (threadIdx.x == 0) P.part[(long long)it * 16 + 0] = acc[0];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column pass: z transform, projection, inverse z transform for one ky.
+// `skip_mode` selects which problems take part (as in the plane passes).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
+  extern __shared__ __align__(16) char smem[];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
+    const Prob d = P.prob[w.x];
+    const int kyp = w.y;
+    const int nx = d.nx, ny = d.ny, nz = d.nz, nxh = d.nxh;
+    C2<T>* tile = reinterpret_cast<C2<T>*>(smem);
+    C2<T>* twz = tile + 6 * nz * nxh;
+    int* sfz = reinterpret_cast<int*>(twz + nz);
+    const AxisPlan az = P.plans[d.pz];
+    const AxisPlan ay = P.plans[d.py];
+    load_tw<T>(twz, P.tw, az);
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) sfz[t] = P.itab[az.sf_off + t];
+    C2<T>* sp = P.spec + d.spc_off;
+    const int pl = ny * nxh;
+    for (int e = threadIdx.x; e < 6 * nz * nxh; e += blockDim.x) {
+      const int kx = e % nxh;
+      const int cz = e / nxh;  // c * nz + z
+      tile[e] = sp[(long long)cz * pl + kyp * nxh + kx];
+    }
+    __syncthreads();
+    Lines Lz{6 * nxh, nxh, nz * nxh, 1, nxh, true};
+    fft_lines<T, false>(tile, Lz, az, twz);
+    // projection of every (kz, kx) mode of this ky
+    const int my = P.itab[ay.sf_off + kyp];
+    const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
+    for (int e = threadIdx.x; e < nz * nxh; e += blockDim.x) {
+      const int kx = e % nxh;
+      const int kzp = e / nxh;
+      const int mz = sfz[kzp];
+      const bool nyq_x = (nx % 2 == 0) && (2 * kx == nx);
+      const bool nyq_z = (nz % 2 == 0) && (2 * mz == nz);
+      T x0 = T(kx) / T(nx), x1 = T(my) / T(ny), x2 = T(mz) / T(nz);
+      if (P.nyq_mode == 0) {
+        if (nyq_x) x0 = T(0);
+        if (nyq_y) x1 = T(0);
+        if (nyq_z) x2 = T(0);
+      } else if (nyq_x || nyq_y || nyq_z) {
+        x0 = x1 = x2 = T(0);
+      }
+      C2<T> t[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) t[c] = tile[(c * nz + kzp) * nxh + kx];
+      project_mode<T>(t, x0, x1, x2);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) tile[(c * nz + kzp) * nxh + kx] = t[c];
+    }
+    __syncthreads();
+    fft_lines<T, true>(tile, Lz, az, twz);
+    for (int e = threadIdx.x; e < 6 * nz * nxh; e += blockDim.x) {
+      const int kx = e % nxh;
+      const int cz = e / nxh;
+      sp[(long long)cz * pl + kyp * nxh + kx] = tile[e];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Plane pass (inverse): inverse y and complex-to-real x transforms.
+//   MODE_RHS  : r = p = -q, x = 0, partial <r, r>_F
+//   MODE_ITER : store q, partial <p, q>_F
+//   MODE_TRUE : r = -q (true residual), partial <r, r>_F
+//   MODE_APPLY: store q
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256) k_plane_inv(KParams<T> P) {
+  extern __shared__ __align__(16) char smem[];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (skip_problem<T>(P.st, w.x, MODE)) continue;
+    const Prob d = P.prob[w.x];
+    const int z = w.y;
+    const int nx = d.nx, ny = d.ny, nxh = d.nxh;
+    const int rch = min(P.rch, ny);
+    const int PX = odd_pitch(nx);
+    const long long V = (long long)nx * ny * d.nz;
+    PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, nxh, rch, P.nphase);
+    const AxisPlan ax = P.plans[d.px];
+    const AxisPlan ay = P.plans[d.py];
+    load_tw<T>(sm.twx, P.tw, ax);
+    load_tw<T>(sm.twy, P.tw, ay);
+    for (int t = threadIdx.x; t < nx; t += blockDim.x) sm.pfx[t] = P.itab[ax.pf_off + t];
+    const C2<T>* sp = P.spec + d.spc_off;
+    const int pl = ny * nxh;
+    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
+      const int c = e / pl;
+      const int rem = e - c * pl;
+      sm.S[e] = sp[((long long)c * d.nz + z) * pl + rem];
+    }
+    __syncthreads();
+    Lines Ly{6 * nxh, nxh, ny * nxh, 1, nxh, true};
+    fft_lines<T, true>(sm.S, Ly, ay, sm.twy);
+
+    double acc[1] = {0.0};
+    const T invV = T(1) / T(V);
+    T* rr = P.r + d.fld_off;
+    T* pp = P.p + d.fld_off;
+    T* qq = P.q + d.fld_off;
+    T* xx = P.x + d.fld_off;
+    const long long zoff = (long long)z * ny * nx;
+    for (int y0 = 0; y0 < ny; y0 += rch) {
+      const int nr = min(rch, ny - y0);
+      // pack A + iB with the Hermitian extension, into digit-reversed positions
+      for (int e = threadIdx.x; e < 3 * nr * nx; e += blockDim.x) {
+        const int k = e % nx;
+        const int l = e / nx;
+        const int c2 = l / nr;
+        const int yy = l - c2 * nr;
+        const int y = y0 + yy;
+        C2<T> A, B;
+        if (k < nxh) {
+          A = sm.S[((2 * c2) * ny + y) * nxh + k];
+          B = sm.S[((2 * c2 + 1) * ny + y) * nxh + k];
+        } else {
+          A = sm.S[((2 * c2) * ny + y) * nxh + (nx - k)];
+          B = sm.S[((2 * c2 + 1) * ny + y) * nxh + (nx - k)];
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+        sm.Z[(c2 * rch + yy) * PX + sm.pfx[k]] = mk<T>(A.x - B.y, A.y + B.x);
+      }
+      __syncthreads();
+      Lines Lx{3 * rch, 1 << 30, 0, PX, 1, false};
+      if (nr < rch) {
+        Lx.n = 3 * nr;
+        Lx.lpg = nr;
+        Lx.gstride = rch * PX;
+      }
+      fft_lines<T, true>(sm.Z, Lx, ax, sm.twx);
+      for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
+        const int yy = v / nx;
+        const int x = v - yy * nx;
+        const long long vo = zoff + (long long)(y0 + yy) * nx + x;
+        T qv[6];
+#pragma unroll
+        for (int c2 = 0; c2 < 3; ++c2) {
+          const C2<T> zz = sm.Z[(c2 * rch + yy) * PX + x];
+          qv[2 * c2] = zz.x * invV;
+          qv[2 * c2 + 1] = zz.y * invV;
+        }
+        if (MODE == MODE_RHS || MODE == MODE_TRUE) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            const T rv = -qv[c];
+            rr[c * V + vo] = rv;
+            if (MODE == MODE_RHS) {
+              pp[c * V + vo] = rv;
+              xx[c * V + vo] = T(0);
+            }
+            acc[0] += frob_w(c) * double(rv) * double(rv);
+          }
+        } else if (MODE == MODE_ITER) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) {
+            qq[c * V + vo] = qv[c];
+            acc[0] += frob_w(c) * double(pp[c * V + vo]) * double(qv[c]);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) qq[c * V + vo] = qv[c];
+        }
+      }
+      __syncthreads();
+    }
+    if (MODE != MODE_APPLY) {
+      block_reduce<1>(acc, sm.red);
+      if (threadIdx.x == 0) P.part[(long long)it * 16 + 12] = acc[0];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CG update on one plane: r <- r - alpha q, x <- x + alpha p, partial <r, r>_F.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(KParams<T> P) {
+  __shared__ double red[32];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (!P.st[w.x].active) continue;
+    const Prob d = P.prob[w.x];
+    const int z = w.y;
+    const long long V = (long long)d.nx * d.ny * d.nz;
+    const int pl = d.nx * d.ny;
+    const T alpha = T(P.st[w.x].alpha);
+    const long long o0 = d.fld_off + (long long)z * pl;
+    T* rr = P.r + o0;
+    T* xx = P.x + o0;
+    const T* qq = P.q + o0;
+    const T* pp = P.p + o0;
+    double acc[1] = {0.0};
+    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
+      const int c = e / pl;
+      const long long o = c * V + (e - c * pl);
+      const T rv = rr[o] - alpha * qq[o];
+      rr[o] = rv;
+      xx[o] = xx[o] + alpha * pp[o];
+      acc[0] += frob_w(c) * double(rv) * double(rv);
+    }
+    block_reduce<1>(acc, red);
+    if (threadIdx.x == 0) P.part[(long long)it * 16 + 13] = acc[0];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Core sums of eps* and of C:(E + eps*) on one plane (final averages).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_avg(KParams<T> P) {
+  __shared__ double red[32 * kAvgParts];
+  __shared__ T lm[512];
+  if (P.medium == MED_ISO)
+    for (int t = threadIdx.x; t < 2 * P.nphase; t += blockDim.x) lm[t] = P.lammu[t];
+  __syncthreads();
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    const Prob d = P.prob[w.x];
+    const int z = w.y;
+    const long long V = (long long)d.nx * d.ny * d.nz;
+    double acc[kAvgParts];
+#pragma unroll
+    for (int k = 0; k < kAvgParts; ++k) acc[k] = 0.0;
+    if (z >= d.c0z && z < d.c0z + d.cnz) {
+      const T* xx = P.x + d.fld_off;
+      const T Ed = d.lc < 3 ? T(1) : T(0.5);
+      const int cells = d.cny * d.cnx;
+      for (int v = threadIdx.x; v < cells; v += blockDim.x) {
+        const int y = d.c0y + v / d.cnx;
+        const int x = d.c0x + v % d.cnx;
+        const long long vo = ((long long)z * d.ny + y) * d.nx + x;
+        T e[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          e[c] = xx[c * V + vo];
+          acc[c] += double(e[c]);
+        }
+        e[d.lc] += Ed;
+        T s[6];
+        if (P.medium == MED_ISO) {
+          const int lab = P.labels[d.med_off + vo];
+          stress_iso<T>(e, lm[2 * lab], lm[2 * lab + 1], s);
+        } else {
+          stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
+        }
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[6 + c] += double(s[c]);
+      }
+    }
+    block_reduce<kAvgParts>(acc, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < kAvgParts; ++k) P.part[(long long)it * 16 + k] = acc[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 scalar steps of conjugate gradients, one thread per problem. Partials
+// of a problem's plane items are summed in item order (deterministic).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double sum_parts(const double* part, const Prob& d, int slot) {
+  double a = 0.0;
+  for (int z = 0; z < d.nz; ++z) a += part[(long long)(d.plane0 + z) * 16 + slot];
+  return a;
+}
+
+__global__ void k_scal_init(const Prob* prob, PState* st, const double* part, int nprob, double floor2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  const Prob d = prob[i];
+  PState s;
+  const double tt = sum_parts(part, d, 0);
+  const double rho = sum_parts(part, d, 12);
+  s.rho = rho;
+  s.rho0 = rho;
+  s.rho_prev = rho;
+  s.alpha = 0.0;
+  s.beta = 0.0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    s.xbar[c] = 0.0;
+    s.sbar[c] = 0.0;
+  }
+  s.iters = 0;
+  s.status = ST_OK;
+  s.resid = 0.0;
+  s.active = 1;
+  s.trueflag = 0;
+  s.homog = 0;
+  s.restarts = 0;
+  s.stall = 0;
+  s.pad1 = 0;
+  s.rt_best = rho;
+  if (!isfinite(rho) || !isfinite(tt)) {
+    s.active = 0;
+    s.status = ST_NONFINITE;
+  } else if (rho <= floor2 * tt) {
+    s.active = 0;  // right-hand side zero to working precision: eps* = 0
+    s.homog = 1;
+  }
+  st[i] = s;
+}
+
+__global__ void k_scal_alpha(const Prob* prob, PState* st, const double* part, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob || !st[i].active) return;
+  const double pq = sum_parts(part, prob[i], 12);
+  PState& s = st[i];
+  if (!isfinite(pq)) {
+    s.active = 0;
+    s.status = ST_NONFINITE;
+    return;
+  }
+  if (!(pq > 0.0)) {
+    // <p, A p> lost positivity to rounding: the recursion has stalled; the
+    // true-residual check decides convergence.
+    s.active = 0;
+    return;
+  }
+  s.alpha = s.rho / pq;
+}
+
+__global__ void k_scal_beta(const Prob* prob, PState* st, const double* part, int nprob, double tol,
+                            int max_iter, int fixed_iters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob || !st[i].active) return;
+  const double rr = sum_parts(part, prob[i], 13);
+  PState& s = st[i];
+  s.iters += 1;
+  if (!isfinite(rr)) {
+    s.active = 0;
+    s.status = ST_NONFINITE;
+    return;
+  }
+  const bool conv = fixed_iters > 0 ? (s.iters >= fixed_iters) : (sqrt(rr) <= tol * sqrt(s.rho0));
+  s.rho_prev = s.rho;
+  s.rho = rr;
+  if (conv || rr == 0.0 || s.iters >= max_iter) {
+    s.active = 0;
+    if (!conv && rr != 0.0) s.status = ST_NOT_CONVERGED;
+    return;
+  }
+  s.beta = rr / s.rho_prev;
+}
+
+// which = 0: flag the active problems (residual replacement);
+// which = 1: flag every problem that iterated and is finite (final check).
+__global__ void k_mark_true(PState* st, int nprob, int which) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  PState& s = st[i];
+  s.trueflag = which == 0 ? s.active : ((!s.homog && s.status != ST_NONFINITE) ? 1 : 0);
+}
+
+// Residual replacement: r was overwritten by the true residual; restart the
+// beta recursion from it (p keeps its direction). Checkpoint safeguards for
+// the precision floor: stop when the true residual has grown tenfold (in
+// norm) over the best seen, or has not improved for 8 checkpoints.
+__global__ void k_scal_replace(const Prob* prob, PState* st, const double* part, int nprob, double tol,
+                               int fixed_iters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob || !st[i].trueflag) return;
+  PState& s = st[i];
+  s.trueflag = 0;
+  const double rr = sum_parts(part, prob[i], 12);
+  if (!isfinite(rr)) {
+    s.active = 0;
+    s.status = ST_NONFINITE;
+    return;
+  }
+  s.beta = (s.rho_prev > 0.0) ? rr / s.rho_prev : 0.0;
+  s.rho = rr;
+  if (fixed_iters > 0) return;
+  if (sqrt(rr) <= tol * sqrt(s.rho0)) {
+    s.active = 0;
+    return;
+  }
+  if (rr > 100.0 * s.rt_best) {
+    s.active = 0;
+    s.status = ST_NOT_CONVERGED;
+    return;
+  }
+  if (rr < s.rt_best) {
+    s.rt_best = rr;
+    s.stall = 0;
+  } else if (++s.stall >= 8) {
+    s.active = 0;
+    s.status = ST_NOT_CONVERGED;
+  }
+}
+
+// Final check on the true residual; problems above `slack * tol` restart
+// (at most max_restarts times) with r = b - A x and p = r, unless the
+// checkpoint safeguards already stopped them.
+__global__ void k_scal_true_final(const Prob* prob, PState* st, const double* part, int nprob, double tol,
+                                  double slack, int max_restarts, int max_iter, int fixed_iters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob || !st[i].trueflag) return;
+  PState& s = st[i];
+  s.trueflag = 0;
+  const double rr = sum_parts(part, prob[i], 12);
+  if (!isfinite(rr)) {
+    s.status = ST_NONFINITE;
+    return;
+  }
+  s.resid = (s.rho0 > 0.0) ? sqrt(rr / s.rho0) : 0.0;
+  if (fixed_iters > 0) return;
+  if (s.resid > slack * tol) {
+    const bool improving = rr < s.rt_best;
+    if (rr < s.rt_best) s.rt_best = rr;
+    if (s.status == ST_OK && s.iters < max_iter && s.restarts < max_restarts && improving) {
+      s.active = 1;
+      s.restarts += 1;
+      s.stall = 0;
+      s.rho = rr;
+      s.rho_prev = rr;
+      s.beta = 0.0;  // p <- r on the next plane pass
+    } else {
+      s.status = ST_NOT_CONVERGED;
+    }
+  }
+}
+
+__global__ void k_scal_avg(const Prob* prob, PState* st, const double* part, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  const Prob d = prob[i];
+  PState& s = st[i];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    s.xbar[c] = sum_parts(part, d, c);
+    s.sbar[c] = sum_parts(part, d, 6 + c);
+  }
+}
+
+__global__ void k_count_active(const PState* st, int nprob, int* out) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  int c = 0;
+  for (int i = threadIdx.x; i < nprob; i += blockDim.x) c += st[i].active;
+  atomicAdd(&cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *out = cnt;
+}
+
+}  // namespace hh

@@ -1,0 +1,1263 @@
+// Host side of libhh: FFT planning, context and workspace, the batched
+// wave driver of the conjugate-gradient solves (CUDA-graph-captured iteration
+// chunks), and the C ABI declared in include/hh.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hh.h"
+#include "hh_device.cuh"
+#include "hh_post.cuh"
+
+namespace hh {
+
+// ---------------------------------------------------------------------------
+// FFT planning: radices, twiddles, digit-reversal tables.
+// ---------------------------------------------------------------------------
+static bool factorize(int n, std::vector<int>& rad) {
+  rad.clear();
+  while (n % 4 == 0) {
+    rad.push_back(4);
+    n /= 4;
+  }
+  while (n % 2 == 0) {
+    rad.push_back(2);
+    n /= 2;
+  }
+  const int primes[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
+  for (int p : primes)
+    while (n % p == 0) {
+      rad.push_back(p);
+      n /= p;
+    }
+  return n == 1 && (int)rad.size() <= kMaxStages;
+}
+
+struct Tables {
+  std::vector<AxisPlan> plans;
+  std::vector<double> tw;
+  std::vector<int> itab;
+  std::map<int, int> index;
+};
+
+// Returns the plan index for length n, or -1 if n is not supported.
+static int plan_for(Tables& T, int n) {
+  auto it = T.index.find(n);
+  if (it != T.index.end()) return it->second;
+  std::vector<int> rad;
+  if (n < 1 || !factorize(n, rad)) return -1;
+  AxisPlan p;
+  std::memset(&p, 0, sizeof(p));
+  p.n = n;
+  p.nst = (int)rad.size();
+  for (int i = 0; i < p.nst; ++i) p.rad[i] = rad[i];
+  p.tw_off = (int)(T.tw.size() / 2);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int t = 0; t < n; ++t) {
+    const long double a = two_pi * (long double)t / (long double)n;
+    T.tw.push_back((double)cosl(a));
+    T.tw.push_back((double)-sinl(a));
+  }
+  p.pf_off = (int)T.itab.size();
+  std::vector<int> pf(n), sf(n);
+  for (int k = 0; k < n; ++k) {
+    int rem = k, span = n, pos = 0;
+    for (int s = 0; s < p.nst; ++s) {
+      const int R = rad[s];
+      const int q = rem % R;
+      rem /= R;
+      span /= R;
+      pos += q * span;
+    }
+    pf[k] = pos;
+  }
+  for (int k = 0; k < n; ++k) sf[pf[k]] = (2 * k <= n) ? k : k - n;
+  T.itab.insert(T.itab.end(), pf.begin(), pf.end());
+  p.sf_off = (int)T.itab.size();
+  T.itab.insert(T.itab.end(), sf.begin(), sf.end());
+  const int idx = (int)T.plans.size();
+  T.plans.push_back(p);
+  T.index[n] = idx;
+  return idx;
+}
+
+// ---------------------------------------------------------------------------
+// Context and workspace.
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+};
+
+struct Ctx {
+  int dev = 0;
+  int nsm = 0;
+  size_t smem_optin = 0;
+  cudaStream_t st = nullptr;   // internal stream (captures graphs)
+  cudaStream_t user = nullptr; // caller's stream, or nullptr
+  Tables tab;
+  size_t tab_uploaded = 0;
+  DevBuf d_plans, d_tw, d_itab;
+  std::map<std::string, DevBuf> bufs;
+  int* h_int = nullptr;        // pinned scratch
+  double* h_dbl = nullptr;
+  std::string err;
+};
+
+#define HH_CK(call)                                                         \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess) {                                                \
+      c.err = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+      return e_ == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA;    \
+    }                                                                       \
+  } while (0)
+
+static hh_status ensure(Ctx& c, const char* name, size_t bytes, void** out) {
+  DevBuf& b = c.bufs[name];
+  if (b.n < bytes) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    HH_CK(cudaMalloc(&b.p, want));
+    b.n = want;
+  }
+  *out = b.p;
+  return HH_OK;
+}
+
+static hh_status upload_tables(Ctx& c) {
+  const size_t sig = c.tab.plans.size();
+  if (sig == c.tab_uploaded) return HH_OK;
+  auto up = [&](DevBuf& b, const void* src, size_t bytes) -> hh_status {
+    if (b.n < bytes) {
+      if (b.p) cudaFree(b.p);
+      b.p = nullptr;
+      HH_CK(cudaMalloc(&b.p, std::max<size_t>(bytes, 256)));
+      b.n = std::max<size_t>(bytes, 256);
+    }
+    HH_CK(cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, c.st));
+    return HH_OK;
+  };
+  hh_status s;
+  if ((s = up(c.d_plans, c.tab.plans.data(), c.tab.plans.size() * sizeof(AxisPlan))) != HH_OK) return s;
+  if ((s = up(c.d_tw, c.tab.tw.data(), c.tab.tw.size() * sizeof(double))) != HH_OK) return s;
+  if ((s = up(c.d_itab, c.tab.itab.data(), c.tab.itab.size() * sizeof(int))) != HH_OK) return s;
+  HH_CK(cudaStreamSynchronize(c.st));
+  c.tab_uploaded = sig;
+  return HH_OK;
+}
+
+template <typename T>
+static size_t plane_smem_bytes(int nx, int ny, int rch, int nphase) {
+  const int nxh = nx / 2 + 1;
+  size_t o = 32 * 16 * sizeof(double);
+  o += sizeof(C2<T>) * 6 * (size_t)ny * nxh;
+  o += sizeof(C2<T>) * 3 * (size_t)rch * (nx | 1);
+  o += sizeof(C2<T>) * (size_t)nx;
+  o += sizeof(C2<T>) * (size_t)ny;
+  o += sizeof(int) * (size_t)((nx + 3) & ~3);
+  o += sizeof(T) * 2 * (size_t)std::max(nphase, 1);
+  return (o + 15) & ~size_t(15);
+}
+
+template <typename T>
+static size_t column_smem_bytes(int nx, int nz) {
+  const int nxh = nx / 2 + 1;
+  size_t o = sizeof(C2<T>) * 6 * (size_t)nz * nxh + sizeof(C2<T>) * nz + sizeof(int) * nz;
+  return (o + 15) & ~size_t(15);
+}
+
+// ---------------------------------------------------------------------------
+// The batched solver.
+// ---------------------------------------------------------------------------
+struct Medium {
+  int kind = MED_ISO;
+  // iso: device image and phase table
+  const uint8_t* d_img = nullptr;
+  int Nx = 0, Ny = 0, Nz = 0;
+  std::vector<double> lam, mu;
+  // aniso: device FP64 C21 field of the single whole-grid box
+  const double* d_c21 = nullptr;
+};
+
+struct Stats {
+  int iters_max = 0;
+  double resid_max = 0.0;
+  long long voxel_iters = 0;
+  int worst = ST_OK;
+};
+
+template <typename T>
+static int grid_for(Ctx& c, const void* kern, int threads, size_t smem, int nitems) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) != cudaSuccess || nb < 1) nb = 1;
+  long long g = (long long)nb * c.nsm;
+  if (g > nitems) g = nitems;
+  return (int)std::max<long long>(g, 1);
+}
+
+// Solve the six load cases of every box; per-box results land in d_res[box].
+template <typename T>
+static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, const std::vector<BoxReq>& boxes_in,
+                             BoxRes* d_res, Stats& stats) {
+  const int nbox = (int)boxes_in.size();
+  if (nbox == 0) return HH_OK;
+  const int threads = 256;
+  // plans for every axis length in the request
+  std::vector<int> bdim(3 * nbox);
+  for (int b = 0; b < nbox; ++b) {
+    const BoxReq& B = boxes_in[b];
+    const int n3[3] = {B.cnx + 2 * B.b, B.cny + 2 * B.b, B.cnz + 2 * B.b};
+    for (int a = 0; a < 3; ++a) {
+      const int pi = plan_for(c.tab, n3[a]);
+      if (pi < 0) {
+        c.err = "unsupported FFT length " + std::to_string(n3[a]);
+        return HH_ERR_UNSUPPORTED;
+      }
+      bdim[3 * b + a] = n3[a];
+    }
+  }
+  hh_status s = upload_tables(c);
+  if (s != HH_OK) return s;
+  const int nphase = (int)med.lam.size();
+
+  // per-box workspace bytes
+  auto box_bytes = [&](int b) -> size_t {
+    const size_t nx = bdim[3 * b], ny = bdim[3 * b + 1], nz = bdim[3 * b + 2];
+    const size_t V = nx * ny * nz, nxh = nx / 2 + 1;
+    size_t m = (med.kind == MED_ISO) ? V : 21 * V * sizeof(T);
+    m += 6 * (24 * V * sizeof(T) + 12 * nz * ny * nxh * sizeof(T) + nz * 16 * sizeof(double) + 64 * sizeof(int2));
+    m += 6 * (sizeof(Prob) + sizeof(PState)) + sizeof(BoxReq) + 4096;
+    return m;
+  };
+  size_t budget = (size_t)o.workspace_bytes;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    HH_CK(cudaMemGetInfo(&fr, &tot));
+    size_t have = 0;
+    for (auto& kv : c.bufs) have += kv.second.n;
+    budget = (size_t)((fr + have) * 0.75);
+  }
+
+  // shared-memory limits: rows per chunk
+  int maxny = 0, maxnx = 0, maxnz = 0;
+  for (int b = 0; b < nbox; ++b) {
+    maxnx = std::max(maxnx, bdim[3 * b]);
+    maxny = std::max(maxny, bdim[3 * b + 1]);
+    maxnz = std::max(maxnz, bdim[3 * b + 2]);
+  }
+  int rch = 1;
+  size_t plane_smem = 0;
+  {
+    // largest rch (<= max ny) that fits every box of the request
+    int best = 0;
+    for (int r = maxny; r >= 1; --r) {
+      size_t need = 0;
+      for (int b = 0; b < nbox; ++b)
+        need = std::max(need, plane_smem_bytes<T>(bdim[3 * b], bdim[3 * b + 1], std::min(r, bdim[3 * b + 1]), nphase));
+      if (need <= c.smem_optin) {
+        best = r;
+        plane_smem = need;
+        break;
+      }
+      if (r > 8) r = std::max(9, r * 3 / 4 + 1);
+    }
+    if (best == 0) {
+      c.err = "plane too large for shared memory";
+      return HH_ERR_UNSUPPORTED;
+    }
+    rch = best;
+  }
+  size_t col_smem = 0;
+  for (int b = 0; b < nbox; ++b)
+    col_smem = std::max(col_smem, column_smem_bytes<T>(bdim[3 * b], bdim[3 * b + 2]));
+  if (col_smem > c.smem_optin) {
+    c.err = "column too large for shared memory";
+    return HH_ERR_UNSUPPORTED;
+  }
+
+  auto* kf_rhs = k_plane_fwd<T, MODE_RHS>;
+  auto* kf_it = k_plane_fwd<T, MODE_ITER>;
+  auto* kf_tr = k_plane_fwd<T, MODE_TRUE>;
+  auto* ki_rhs = k_plane_inv<T, MODE_RHS>;
+  auto* ki_it = k_plane_inv<T, MODE_ITER>;
+  auto* ki_tr = k_plane_inv<T, MODE_TRUE>;
+  auto* kc = k_column<T>;
+  auto* ku = k_update<T>;
+  auto* ka = k_avg<T>;
+  for (const void* f : {(const void*)kf_rhs, (const void*)kf_it, (const void*)kf_tr, (const void*)ki_rhs,
+                        (const void*)ki_it, (const void*)ki_tr})
+    HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem));
+  HH_CK(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+  const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
+
+  // lambda/mu table
+  std::vector<T> lm(2 * std::max(nphase, 1));
+  for (int i = 0; i < nphase; ++i) {
+    lm[2 * i] = T(med.lam[i]);
+    lm[2 * i + 1] = T(med.mu[i]);
+  }
+  T* d_lm = nullptr;
+  if ((s = ensure(c, "lammu", lm.size() * sizeof(T), (void**)&d_lm)) != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d_lm, lm.data(), lm.size() * sizeof(T), cudaMemcpyHostToDevice, c.st));
+
+  const double floor2 = (sizeof(T) == 4) ? 1e-12 : 1e-28;
+  int b0 = 0;
+  while (b0 < nbox) {
+    // ---- choose the wave [b0, b1)
+    int b1 = b0;
+    size_t used = 0;
+    while (b1 < nbox && (b1 == b0 || used + box_bytes(b1) <= budget)) used += box_bytes(b1++);
+    const int nb = b1 - b0;
+    const int np = 6 * nb;
+    std::vector<Prob> probs(np);
+    std::vector<BoxReq> wboxes(boxes_in.begin() + b0, boxes_in.begin() + b1);
+    std::vector<int2> pitems, citems, gitems;
+    long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0;
+    for (int b = 0; b < nb; ++b) {
+      const BoxReq& B = wboxes[b];
+      const int nx = bdim[3 * (b0 + b)], ny = bdim[3 * (b0 + b) + 1], nz = bdim[3 * (b0 + b) + 2];
+      const long long V = (long long)nx * ny * nz;
+      const int nxh = nx / 2 + 1;
+      wboxes[b].lab_off = lab_off;
+      for (int k = 0; k < nz; ++k) gitems.push_back(make_int2(b, k));
+      for (int a = 0; a < 6; ++a) {
+        Prob& d = probs[6 * b + a];
+        std::memset(&d, 0, sizeof(d));
+        d.nx = nx;
+        d.ny = ny;
+        d.nz = nz;
+        d.nxh = nxh;
+        d.c0x = B.b;
+        d.c0y = B.b;
+        d.c0z = B.b;
+        d.cnx = B.cnx;
+        d.cny = B.cny;
+        d.cnz = B.cnz;
+        d.px = c.tab.index[nx];
+        d.py = c.tab.index[ny];
+        d.pz = c.tab.index[nz];
+        d.lc = a;
+        d.box = b0 + b;
+        d.plane0 = (int)pitems.size();
+        d.col0 = (int)citems.size();
+        d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
+        d.fld_off = fld_off;
+        d.spc_off = spc_off;
+        for (int k = 0; k < nz; ++k) pitems.push_back(make_int2(6 * b + a, k));
+        for (int k = 0; k < ny; ++k) citems.push_back(make_int2(6 * b + a, k));
+        fld_off += 6 * V;
+        spc_off += 6LL * nz * ny * nxh;
+      }
+      lab_off += V;
+      c21_off += 21 * V;
+    }
+    // ---- device buffers
+    Prob* d_prob;
+    PState* d_st;
+    int2 *d_pit, *d_cit, *d_git;
+    BoxReq* d_boxes;
+    T *d_r, *d_p, *d_q, *d_x, *d_c21 = nullptr;
+    C2<T>* d_spec;
+    double* d_part;
+    uint8_t* d_lab = nullptr;
+    int* d_flag;
+    if ((s = ensure(c, "prob", np * sizeof(Prob), (void**)&d_prob)) != HH_OK) return s;
+    if ((s = ensure(c, "state", np * sizeof(PState), (void**)&d_st)) != HH_OK) return s;
+    if ((s = ensure(c, "pitems", pitems.size() * sizeof(int2), (void**)&d_pit)) != HH_OK) return s;
+    if ((s = ensure(c, "citems", citems.size() * sizeof(int2), (void**)&d_cit)) != HH_OK) return s;
+    if ((s = ensure(c, "gitems", gitems.size() * sizeof(int2), (void**)&d_git)) != HH_OK) return s;
+    if ((s = ensure(c, "boxes", nb * sizeof(BoxReq), (void**)&d_boxes)) != HH_OK) return s;
+    if ((s = ensure(c, "r", fld_off * sizeof(T), (void**)&d_r)) != HH_OK) return s;
+    if ((s = ensure(c, "p", fld_off * sizeof(T), (void**)&d_p)) != HH_OK) return s;
+    if ((s = ensure(c, "q", fld_off * sizeof(T), (void**)&d_q)) != HH_OK) return s;
+    if ((s = ensure(c, "x", fld_off * sizeof(T), (void**)&d_x)) != HH_OK) return s;
+    if ((s = ensure(c, "spec", spc_off * sizeof(C2<T>), (void**)&d_spec)) != HH_OK) return s;
+    if ((s = ensure(c, "part", pitems.size() * 16 * sizeof(double), (void**)&d_part)) != HH_OK) return s;
+    if ((s = ensure(c, "flag", 64, (void**)&d_flag)) != HH_OK) return s;
+    HH_CK(cudaMemcpyAsync(d_prob, probs.data(), np * sizeof(Prob), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_pit, pitems.data(), pitems.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_cit, citems.data(), citems.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_git, gitems.data(), gitems.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_boxes, wboxes.data(), nb * sizeof(BoxReq), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemsetAsync(d_flag, 0, 64, c.st));
+    if (med.kind == MED_ISO) {
+      if ((s = ensure(c, "labels", lab_off, (void**)&d_lab)) != HH_OK) return s;
+      k_gather<<<grid_for<T>(c, (const void*)k_gather, 256, 0, (int)gitems.size()), 256, 0, c.st>>>(
+          med.d_img, med.Nx, med.Ny, med.Nz, d_boxes, d_git, (int)gitems.size(), d_lab, nphase, d_flag);
+      HH_CK(cudaGetLastError());
+    } else {
+      if ((s = ensure(c, "c21T", c21_off * sizeof(T), (void**)&d_c21)) != HH_OK) return s;
+      const long long V = c21_off / 21;
+      k_c21_prepare<T><<<std::max(1, std::min<int>(c.nsm * 8, (int)((V + 255) / 256))), 256, 0, c.st>>>(
+          med.d_c21, d_c21, V, d_flag);
+      HH_CK(cudaGetLastError());
+    }
+    HH_CK(cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    HH_CK(cudaStreamSynchronize(c.st));
+    if (c.h_int[0]) {
+      if (med.kind == MED_ISO) {
+        c.err = "label >= nphase in image";
+        return HH_ERR_ARG;
+      }
+      c.err = "stiffness not symmetric positive definite";
+      return HH_ERR_BAD_STIFFNESS;
+    }
+
+    KParams<T> kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.prob = d_prob;
+    kp.st = d_st;
+    kp.medium = med.kind;
+    kp.nyq_mode = o.nyquist;
+    kp.rch = rch;
+    kp.nphase = std::max(nphase, 1);
+    kp.plans = (const AxisPlan*)c.d_plans.p;
+    kp.tw = (const double*)c.d_tw.p;
+    kp.itab = (const int*)c.d_itab.p;
+    kp.labels = d_lab;
+    kp.lammu = d_lm;
+    kp.c21 = d_c21;
+    kp.r = d_r;
+    kp.p = d_p;
+    kp.q = d_q;
+    kp.x = d_x;
+    kp.spec = d_spec;
+    kp.part = d_part;
+    kp.tol = o.tol;
+    kp.max_iter = o.max_iter;
+    kp.fixed_iters = o.fixed_iters;
+    kp.nprob = np;
+    KParams<T> kpp = kp, kpc = kp;
+    kpp.items = d_pit;
+    kpp.nitems = (int)pitems.size();
+    kpc.items = d_cit;
+    kpc.nitems = (int)citems.size();
+    const int gp_f = grid_for<T>(c, (const void*)kf_it, threads, plane_smem, kpp.nitems);
+    const int gp_i = grid_for<T>(c, (const void*)ki_it, threads, plane_smem, kpp.nitems);
+    const int gc = grid_for<T>(c, (const void*)kc, threads, col_smem, kpc.nitems);
+    const int gu = grid_for<T>(c, (const void*)ku, threads, 0, kpp.nitems);
+    const int gs = (np + 127) / 128;
+
+    // ---- right-hand side b = -G*(C:E), r = p = b, x = 0
+    kf_rhs<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+    kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_RHS);
+    ki_rhs<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+    k_scal_init<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, floor2);
+    HH_CK(cudaGetLastError());
+
+    // true residual r = -G*(C:(E + x)) of the flagged problems
+    auto true_pass = [&]() {
+      kf_tr<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+      kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_TRUE);
+      ki_tr<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+    };
+    // ---- iterations, in chunks captured as CUDA graphs; residual
+    //      replacement at the end of every chunk (when enabled)
+    const int chunk = std::max(1, o.check_every);
+    auto launch_chunk = [&]() {
+      for (int m = 0; m < chunk; ++m) {
+        kf_it<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+        kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_ITER);
+        ki_it<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+        k_scal_alpha<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np);
+        ku<<<gu, threads, 0, c.st>>>(kpp);
+        k_scal_beta<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
+      }
+      if (replace) {
+        k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 0);
+        true_pass();
+        k_scal_replace<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.fixed_iters);
+      }
+    };
+    cudaGraphExec_t exec = nullptr;
+    if (o.use_graphs) {
+      cudaGraph_t g = nullptr;
+      HH_CK(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+      launch_chunk();
+      cudaError_t ce = cudaStreamEndCapture(c.st, &g);
+      if (ce != cudaSuccess) {
+        c.err = std::string("graph capture: ") + cudaGetErrorString(ce);
+        return HH_ERR_CUDA;
+      }
+      ce = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        c.err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
+        return HH_ERR_CUDA;
+      }
+    }
+    const long long max_chunks =
+        ((long long)(o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) / chunk + 2) * (o.max_restarts + 2);
+    long long chunks = 0;
+    int final_rounds = 0;
+    hh_status rs = HH_OK;
+    auto count_active = [&](int* out) -> cudaError_t {
+      k_count_active<<<1, 256, 0, c.st>>>(d_st, np, d_flag);
+      cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+      cudaError_t e = cudaStreamSynchronize(c.st);
+      *out = c.h_int[0];
+      return e;
+    };
+    while (true) {
+      int nact = 0;
+      cudaError_t e = count_active(&nact);
+      if (e != cudaSuccess) {
+        c.err = std::string("solve: ") + cudaGetErrorString(e);
+        rs = HH_ERR_CUDA;
+        break;
+      }
+      if (nact == 0) {
+        // every problem stopped on its recursive residual: check the true one
+        if (final_rounds > o.max_restarts) break;
+        k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 1);
+        true_pass();
+        k_scal_true_final<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, 2.0, o.max_restarts, o.max_iter,
+                                                 o.fixed_iters);
+        ++final_rounds;
+        if ((e = count_active(&nact)) != cudaSuccess) {
+          c.err = std::string("solve: ") + cudaGetErrorString(e);
+          rs = HH_ERR_CUDA;
+          break;
+        }
+        if (nact == 0) break;
+      }
+      if (chunks >= max_chunks) break;
+      if (exec) {
+        e = cudaGraphLaunch(exec, c.st);
+      } else {
+        launch_chunk();
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) {
+        c.err = std::string("launch: ") + cudaGetErrorString(e);
+        rs = HH_ERR_CUDA;
+        break;
+      }
+      ++chunks;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (rs != HH_OK) return rs;
+
+    // ---- core averages from x
+    {
+      const int ga = grid_for<T>(c, (const void*)ka, threads, 0, kpp.nitems);
+      ka<<<ga, threads, 0, c.st>>>(kpp);
+      k_scal_avg<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np);
+      HH_CK(cudaGetLastError());
+    }
+
+    // ---- per-box results
+    k_finalize<<<(nb + 63) / 64, 64, 0, c.st>>>(d_prob, d_st, nb, d_res, b0);
+    HH_CK(cudaGetLastError());
+    // statistics
+    std::vector<PState> hst(np);
+    HH_CK(cudaMemcpyAsync(hst.data(), d_st, np * sizeof(PState), cudaMemcpyDeviceToHost, c.st));
+    HH_CK(cudaStreamSynchronize(c.st));
+    for (int i = 0; i < np; ++i) {
+      const Prob& d = probs[i];
+      stats.iters_max = std::max(stats.iters_max, hst[i].iters);
+      stats.resid_max = std::max(stats.resid_max, hst[i].resid);
+      stats.voxel_iters += (long long)d.nx * d.ny * d.nz * hst[i].iters;
+      if (hst[i].status == ST_NONFINITE) stats.worst = ST_NONFINITE;
+      else if (hst[i].status == ST_NOT_CONVERGED && stats.worst == ST_OK) stats.worst = ST_NOT_CONVERGED;
+    }
+    b0 = b1;
+  }
+  return HH_OK;
+}
+
+// q = G*(C:p) for one field (parity of the operator).
+template <typename T>
+static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, int nx, int ny, int nz,
+                                const double* h_p, double* h_q) {
+  const int px = plan_for(c.tab, nx), py = plan_for(c.tab, ny), pz = plan_for(c.tab, nz);
+  if (px < 0 || py < 0 || pz < 0) {
+    c.err = "unsupported FFT length";
+    return HH_ERR_UNSUPPORTED;
+  }
+  hh_status s = upload_tables(c);
+  if (s != HH_OK) return s;
+  const int nphase = (int)med.lam.size();
+  const long long V = (long long)nx * ny * nz;
+  const int nxh = nx / 2 + 1;
+  int rch = ny;
+  while (rch > 1 && plane_smem_bytes<T>(nx, ny, rch, nphase) > c.smem_optin) --rch;
+  const size_t psm = plane_smem_bytes<T>(nx, ny, rch, nphase);
+  const size_t csm = column_smem_bytes<T>(nx, nz);
+  if (psm > c.smem_optin || csm > c.smem_optin) {
+    c.err = "plane too large for shared memory";
+    return HH_ERR_UNSUPPORTED;
+  }
+  Prob d;
+  std::memset(&d, 0, sizeof(d));
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.nxh = nxh;
+  d.cnx = nx;
+  d.cny = ny;
+  d.cnz = nz;
+  d.px = px;
+  d.py = py;
+  d.pz = pz;
+  std::vector<int2> pit, cit;
+  for (int k = 0; k < nz; ++k) pit.push_back(make_int2(0, k));
+  for (int k = 0; k < ny; ++k) cit.push_back(make_int2(0, k));
+  Prob* d_prob;
+  int2 *d_pit, *d_cit;
+  T *d_p, *d_q, *d_c21 = nullptr, *d_lm;
+  C2<T>* d_spec;
+  uint8_t* d_lab = nullptr;
+  int* d_flag;
+  if ((s = ensure(c, "prob", sizeof(Prob), (void**)&d_prob)) != HH_OK) return s;
+  if ((s = ensure(c, "pitems", pit.size() * sizeof(int2), (void**)&d_pit)) != HH_OK) return s;
+  if ((s = ensure(c, "citems", cit.size() * sizeof(int2), (void**)&d_cit)) != HH_OK) return s;
+  if ((s = ensure(c, "p", 6 * V * sizeof(T), (void**)&d_p)) != HH_OK) return s;
+  if ((s = ensure(c, "q", 6 * V * sizeof(T), (void**)&d_q)) != HH_OK) return s;
+  if ((s = ensure(c, "spec", 6LL * nz * ny * nxh * sizeof(C2<T>), (void**)&d_spec)) != HH_OK) return s;
+  if ((s = ensure(c, "lammu", 2 * std::max(nphase, 1) * sizeof(T), (void**)&d_lm)) != HH_OK) return s;
+  if ((s = ensure(c, "flag", 64, (void**)&d_flag)) != HH_OK) return s;
+  std::vector<T> hp(6 * V);
+  for (long long i = 0; i < 6 * V; ++i) hp[i] = T(h_p[i]);
+  HH_CK(cudaMemcpyAsync(d_prob, &d, sizeof(Prob), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemcpyAsync(d_pit, pit.data(), pit.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemcpyAsync(d_cit, cit.data(), cit.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemcpyAsync(d_p, hp.data(), 6 * V * sizeof(T), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemsetAsync(d_flag, 0, 64, c.st));
+  std::vector<T> lm(2 * std::max(nphase, 1));
+  for (int i = 0; i < nphase; ++i) {
+    lm[2 * i] = T(med.lam[i]);
+    lm[2 * i + 1] = T(med.mu[i]);
+  }
+  HH_CK(cudaMemcpyAsync(d_lm, lm.data(), lm.size() * sizeof(T), cudaMemcpyHostToDevice, c.st));
+  if (med.kind == MED_ISO) {
+    if ((s = ensure(c, "labels", V, (void**)&d_lab)) != HH_OK) return s;
+    HH_CK(cudaMemcpyAsync(d_lab, med.d_img, V, cudaMemcpyDeviceToDevice, c.st));
+  } else {
+    if ((s = ensure(c, "c21T", 21 * V * sizeof(T), (void**)&d_c21)) != HH_OK) return s;
+    k_c21_prepare<T><<<std::max(1, std::min<int>(c.nsm * 8, (int)((V + 255) / 256))), 256, 0, c.st>>>(
+        med.d_c21, d_c21, V, d_flag);
+    HH_CK(cudaGetLastError());
+  }
+  KParams<T> kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.prob = d_prob;
+  kp.medium = med.kind;
+  kp.nyq_mode = o.nyquist;
+  kp.rch = rch;
+  kp.nphase = std::max(nphase, 1);
+  kp.plans = (const AxisPlan*)c.d_plans.p;
+  kp.tw = (const double*)c.d_tw.p;
+  kp.itab = (const int*)c.d_itab.p;
+  kp.labels = d_lab;
+  kp.lammu = d_lm;
+  kp.c21 = d_c21;
+  kp.p = d_p;
+  kp.q = d_q;
+  kp.r = d_q;
+  kp.x = d_q;
+  kp.spec = d_spec;
+  kp.nprob = 1;
+  KParams<T> kpp = kp, kpc = kp;
+  kpp.items = d_pit;
+  kpp.nitems = nz;
+  kpc.items = d_cit;
+  kpc.nitems = ny;
+  auto* kf = k_plane_fwd<T, MODE_APPLY>;
+  auto* ki = k_plane_inv<T, MODE_APPLY>;
+  auto* kc = k_column<T>;
+  HH_CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+  HH_CK(cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
+  HH_CK(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+  kf<<<std::min(nz, 4 * c.nsm), 256, psm, c.st>>>(kpp);
+  kc<<<std::min(ny, 4 * c.nsm), 256, csm, c.st>>>(kpc, MODE_APPLY);
+  ki<<<std::min(nz, 4 * c.nsm), 256, psm, c.st>>>(kpp);
+  HH_CK(cudaGetLastError());
+  HH_CK(cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st));
+  std::vector<T> hq(6 * V);
+  HH_CK(cudaMemcpyAsync(hq.data(), d_q, 6 * V * sizeof(T), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  if (med.kind == MED_ANISO && c.h_int[0]) {
+    c.err = "stiffness not symmetric positive definite";
+    return HH_ERR_BAD_STIFFNESS;
+  }
+  for (long long i = 0; i < 6 * V; ++i) h_q[i] = double(hq[i]);
+  return HH_OK;
+}
+
+}  // namespace hh
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace hh;
+
+struct hh_ctx {
+  Ctx c;
+};
+
+static thread_local std::string g_last_error;
+
+static hh_status fail(hh_ctx* ctx, hh_status s, const std::string& msg) {
+  if (ctx) ctx->c.err = msg;
+  g_last_error = msg;
+  return s;
+}
+
+extern "C" const char* hh_version(void) { return "libhh 0.1 (sm_103a)"; }
+
+extern "C" const char* hh_status_string(hh_status s) {
+  switch (s) {
+    case HH_OK: return "ok";
+    case HH_WARN_NOT_CONVERGED: return "warning: not converged within max_iter";
+    case HH_ERR_ARG: return "error: invalid argument";
+    case HH_ERR_OOM: return "error: out of memory";
+    case HH_ERR_CUDA: return "error: CUDA runtime failure";
+    case HH_ERR_NONFINITE: return "error: non-finite value in the solver";
+    case HH_ERR_DEVICE_TIMEOUT: return "error: bounded device wait ran out";
+    case HH_ERR_BAD_STIFFNESS: return "error: stiffness not symmetric positive definite";
+    case HH_ERR_UNSUPPORTED: return "error: unsupported size";
+    default: return "error: unknown status";
+  }
+}
+
+extern "C" const char* hh_last_error(hh_ctx* ctx) {
+  return ctx ? ctx->c.err.c_str() : g_last_error.c_str();
+}
+
+extern "C" hh_status hh_options_default(hh_options* o) {
+  if (!o) return HH_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = HH_FP32;
+  o->tol = 1e-6;
+  o->max_iter = 20000;
+  o->scheme = HH_CG;
+  o->nyquist = HH_NYQ_ZERO_COMPONENT;
+  o->fixed_iters = 0;
+  o->use_graphs = 1;
+  o->check_every = 32;
+  o->replace = -1;
+  o->max_restarts = 4;
+  return HH_OK;
+}
+
+extern "C" hh_status hh_create(hh_ctx** out, int device, void* cuda_stream) {
+  if (!out) return HH_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n)
+    return fail(nullptr, HH_ERR_ARG, "no such CUDA device");
+  hh_ctx* h = new (std::nothrow) hh_ctx();
+  if (!h) return HH_ERR_OOM;
+  Ctx& c = h->c;
+  c.dev = device;
+  auto bad = [&](cudaError_t e) {
+    g_last_error = cudaGetErrorString(e);
+    delete h;
+    return e == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return bad(e);
+  cudaDeviceProp prop;
+  if ((e = cudaGetDeviceProperties(&prop, device)) != cudaSuccess) return bad(e);
+  c.nsm = prop.multiProcessorCount;
+  c.smem_optin = prop.sharedMemPerBlockOptin;
+  if ((e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+  c.user = (cudaStream_t)cuda_stream;
+  if ((e = cudaMallocHost((void**)&c.h_int, 64 * sizeof(int))) != cudaSuccess) return bad(e);
+  if ((e = cudaMallocHost((void**)&c.h_dbl, 64 * sizeof(double))) != cudaSuccess) return bad(e);
+  *out = h;
+  return HH_OK;
+}
+
+extern "C" void hh_destroy(hh_ctx* h) {
+  if (!h) return;
+  Ctx& c = h->c;
+  cudaSetDevice(c.dev);
+  if (c.st) cudaStreamSynchronize(c.st);
+  for (auto& kv : c.bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (c.d_plans.p) cudaFree(c.d_plans.p);
+  if (c.d_tw.p) cudaFree(c.d_tw.p);
+  if (c.d_itab.p) cudaFree(c.d_itab.p);
+  if (c.h_int) cudaFreeHost(c.h_int);
+  if (c.h_dbl) cudaFreeHost(c.h_dbl);
+  if (c.st) cudaStreamDestroy(c.st);
+  delete h;
+}
+
+// Order the internal stream after the caller's stream (for device inputs).
+static hh_status enter(hh_ctx* h) {
+  Ctx& c = h->c;
+  HH_CK(cudaSetDevice(c.dev));
+  if (c.user) {
+    cudaEvent_t ev;
+    HH_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HH_CK(cudaEventRecord(ev, c.user));
+    HH_CK(cudaStreamWaitEvent(c.st, ev, 0));
+    cudaEventDestroy(ev);
+  }
+  return HH_OK;
+}
+
+static hh_status check_opts(hh_ctx* h, const hh_options* o) {
+  if (!o) return fail(h, HH_ERR_ARG, "options is NULL");
+  if (o->precision != HH_FP32 && o->precision != HH_FP64) return fail(h, HH_ERR_ARG, "bad precision");
+  if (!(o->tol > 0.0) && o->fixed_iters <= 0) return fail(h, HH_ERR_ARG, "tol must be > 0");
+  if (o->max_iter < 1 || o->fixed_iters < 0) return fail(h, HH_ERR_ARG, "bad iteration limits");
+  if (o->nyquist != HH_NYQ_ZERO_COMPONENT && o->nyquist != HH_NYQ_ZERO_MODE) return fail(h, HH_ERR_ARG, "bad nyquist");
+  if (o->scheme != HH_CG) return fail(h, HH_ERR_UNSUPPORTED, "only the conjugate-gradient scheme is built");
+  if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1)
+    return fail(h, HH_ERR_ARG, "bad check_every, replace or max_restarts");
+  return HH_OK;
+}
+
+static hh_status check_phases(hh_ctx* h, const hh_phase* ph, int nphase, Medium& m) {
+  if (!ph || nphase < 1 || nphase > 256) return fail(h, HH_ERR_ARG, "phase table");
+  m.lam.resize(nphase);
+  m.mu.resize(nphase);
+  for (int i = 0; i < nphase; ++i) {
+    if (!(ph[i].K > 0.0) || !(ph[i].G > 0.0) || !std::isfinite(ph[i].K) || !std::isfinite(ph[i].G))
+      return fail(h, HH_ERR_ARG, "phase moduli must be finite and > 0");
+    m.lam[i] = ph[i].K - 2.0 * ph[i].G / 3.0;
+    m.mu[i] = ph[i].G;
+  }
+  return HH_OK;
+}
+
+// Place the image on the device (copy of a host image into context memory).
+static hh_status stage_image(hh_ctx* h, const uint8_t* img, long long V, int on_dev, const uint8_t** d_img) {
+  Ctx& c = h->c;
+  if (!img) return fail(h, HH_ERR_ARG, "image is NULL");
+  if (on_dev) {
+    *d_img = img;
+    return HH_OK;
+  }
+  uint8_t* d;
+  hh_status s = ensure(c, "image", (size_t)V, (void**)&d);
+  if (s != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d, img, (size_t)V, cudaMemcpyHostToDevice, c.st));
+  *d_img = d;
+  return HH_OK;
+}
+
+static void fill_result(hh_result* out, const BoxRes& R, const Stats& st) {
+  std::memcpy(out->C, R.C, sizeof(out->C));
+  std::memcpy(out->C_sym, R.Csym, sizeof(out->C_sym));
+  out->K = R.K;
+  out->G = R.G;
+  out->K_reuss = R.KR;
+  out->G_reuss = R.GR;
+  out->iters_max = st.iters_max;
+  out->resid_max = st.resid_max;
+  out->voxel_iters = st.voxel_iters;
+  out->status = st.worst == ST_NONFINITE ? HH_ERR_NONFINITE : (st.worst == ST_NOT_CONVERGED ? HH_WARN_NOT_CONVERGED : HH_OK);
+}
+
+template <typename T>
+static hh_status run_boxes(hh_ctx* h, const hh_options& o, const Medium& m, const std::vector<BoxReq>& boxes,
+                           BoxRes** d_res_out, Stats& st) {
+  Ctx& c = h->c;
+  BoxRes* d_res;
+  hh_status s = ensure(c, "boxres", boxes.size() * sizeof(BoxRes), (void**)&d_res);
+  if (s != HH_OK) return s;
+  s = solve_boxes<T>(c, o, m, boxes, d_res, st);
+  *d_res_out = d_res;
+  return s;
+}
+
+static hh_status run_boxes_p(hh_ctx* h, const hh_options& o, const Medium& m, const std::vector<BoxReq>& boxes,
+                             BoxRes** d_res, Stats& st) {
+  return o.precision == HH_FP64 ? run_boxes<double>(h, o, m, boxes, d_res, st)
+                                : run_boxes<float>(h, o, m, boxes, d_res, st);
+}
+
+static hh_status status_of(const Stats& st) {
+  return st.worst == ST_NONFINITE ? HH_ERR_NONFINITE : (st.worst == ST_NOT_CONVERGED ? HH_WARN_NOT_CONVERGED : HH_OK);
+}
+
+extern "C" hh_status hh_homogenize_direct(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                          const hh_phase* phases, int nphase, const hh_options* opt,
+                                          hh_result* out) {
+  if (!h || !out) return fail(h, HH_ERR_ARG, "NULL context or output");
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  Medium m;
+  if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
+  if ((s = enter(h)) != HH_OK) return s;
+  m.kind = MED_ISO;
+  m.Nx = nx;
+  m.Ny = ny;
+  m.Nz = nz;
+  if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
+  std::vector<BoxReq> boxes(1);
+  std::memset(boxes.data(), 0, sizeof(BoxReq));
+  boxes[0].cnx = nx;
+  boxes[0].cny = ny;
+  boxes[0].cnz = nz;
+  Stats st;
+  BoxRes* d_res;
+  if ((s = run_boxes_p(h, *opt, m, boxes, &d_res, st)) != HH_OK) return s;
+  Ctx& c = h->c;
+  BoxRes R;
+  HH_CK(cudaMemcpyAsync(&R, d_res, sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  std::memset(out, 0, sizeof(*out));
+  fill_result(out, R, st);
+  out->n_subimages = 1;
+  out->K_am = R.K;
+  out->G_am = R.G;
+  return out->status;
+}
+
+static hh_status parse_boxes(hh_ctx* h, const int32_t* boxes, int nbox, int nx, int ny, int nz,
+                             std::vector<BoxReq>& out) {
+  if (!boxes || nbox < 1) return fail(h, HH_ERR_ARG, "no boxes");
+  out.resize(nbox);
+  for (int i = 0; i < nbox; ++i) {
+    const int32_t* r = boxes + 7 * i;
+    BoxReq& B = out[i];
+    std::memset(&B, 0, sizeof(B));
+    B.ox = r[0];
+    B.oy = r[1];
+    B.oz = r[2];
+    B.cnx = r[3];
+    B.cny = r[4];
+    B.cnz = r[5];
+    B.b = r[6];
+    if (B.cnx < 1 || B.cny < 1 || B.cnz < 1 || B.b < 0 || B.ox < 0 || B.oy < 0 || B.oz < 0 || B.ox >= nx ||
+        B.oy >= ny || B.oz >= nz || B.cnx > nx || B.cny > ny || B.cnz > nz)
+      return fail(h, HH_ERR_ARG, "box " + std::to_string(i) + " out of range");
+  }
+  return HH_OK;
+}
+
+// level 1 + assembly + level 2 on a validated tiling partition
+static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, const std::vector<BoxReq>& boxes, int unit,
+                                   hh_result* out, double* per_sub_C, int* per_sub_iters) {
+  Ctx& c = h->c;
+  hh_status s;
+  Stats st1;
+  BoxRes* d_res;
+  if ((s = run_boxes_p(h, o, m, boxes, &d_res, st1)) != HH_OK) return s;
+  const int nbox = (int)boxes.size();
+  // assembly of the intermediate image (FP64)
+  const int Cx = m.Nx / unit, Cy = m.Ny / unit, Cz = m.Nz / unit;
+  const long long Vc = (long long)Cx * Cy * Cz;
+  double* d_c21;
+  BoxReq* d_boxes;
+  double* d_am;
+  BoxRes* d_res1;
+  // keep level-1 results: move them out of the buffer the level-2 solve reuses
+  if ((s = ensure(c, "boxres1", nbox * sizeof(BoxRes), (void**)&d_res1)) != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d_res1, d_res, nbox * sizeof(BoxRes), cudaMemcpyDeviceToDevice, c.st));
+  if ((s = ensure(c, "coarse", 21 * Vc * sizeof(double), (void**)&d_c21)) != HH_OK) return s;
+  if ((s = ensure(c, "aboxes", nbox * sizeof(BoxReq), (void**)&d_boxes)) != HH_OK) return s;
+  if ((s = ensure(c, "am", 4 * sizeof(double), (void**)&d_am)) != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d_boxes, boxes.data(), nbox * sizeof(BoxReq), cudaMemcpyHostToDevice, c.st));
+  k_assemble<<<nbox, 128, 0, c.st>>>(d_boxes, d_res1, nbox, unit, Cx, Cy, Cz, d_c21);
+  k_am<<<1, 256, 0, c.st>>>(d_res1, d_boxes, nbox, d_am);
+  HH_CK(cudaGetLastError());
+  // level 2
+  Medium m2;
+  m2.kind = MED_ANISO;
+  m2.d_c21 = d_c21;
+  m2.Nx = Cx;
+  m2.Ny = Cy;
+  m2.Nz = Cz;
+  std::vector<BoxReq> one(1);
+  std::memset(one.data(), 0, sizeof(BoxReq));
+  one[0].cnx = Cx;
+  one[0].cny = Cy;
+  one[0].cnz = Cz;
+  Stats st2;
+  BoxRes* d_res2;
+  if ((s = run_boxes_p(h, o, m2, one, &d_res2, st2)) != HH_OK) return s;
+  BoxRes R;
+  double am[4];
+  HH_CK(cudaMemcpyAsync(&R, d_res2, sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaMemcpyAsync(am, d_am, 4 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  std::vector<BoxRes> all;
+  if (per_sub_C || per_sub_iters) {
+    all.resize(nbox);
+    HH_CK(cudaMemcpyAsync(all.data(), d_res1, nbox * sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));
+  }
+  HH_CK(cudaStreamSynchronize(c.st));
+  Stats tot;
+  tot.iters_max = std::max(st1.iters_max, st2.iters_max);
+  tot.resid_max = std::max(st1.resid_max, st2.resid_max);
+  tot.voxel_iters = st1.voxel_iters + st2.voxel_iters;
+  tot.worst = std::max(st1.worst, st2.worst);
+  std::memset(out, 0, sizeof(*out));
+  fill_result(out, R, tot);
+  out->K_am = am[0];
+  out->G_am = am[1];
+  out->n_subimages = nbox;
+  for (int b = 0; b < (int)all.size(); ++b) {
+    if (per_sub_C) std::memcpy(per_sub_C + 36 * b, all[b].C, 36 * sizeof(double));
+    if (per_sub_iters) std::memcpy(per_sub_iters + 6 * b, all[b].iters, 6 * sizeof(int));
+  }
+  return out->status;
+}
+
+static hh_status check_tiling(hh_ctx* h, const std::vector<BoxReq>& boxes, int unit, int nx, int ny, int nz) {
+  if (unit < 1 || nx % unit || ny % unit || nz % unit) return fail(h, HH_ERR_ARG, "unit must divide the image");
+  const int Cx = nx / unit, Cy = ny / unit, Cz = nz / unit;
+  std::vector<uint8_t> cover((size_t)Cx * Cy * Cz, 0);
+  for (const BoxReq& B : boxes) {
+    if (B.ox % unit || B.oy % unit || B.oz % unit || B.cnx % unit || B.cny % unit || B.cnz % unit ||
+        B.ox + B.cnx > nx || B.oy + B.cny > ny || B.oz + B.cnz > nz)
+      return fail(h, HH_ERR_ARG, "box not aligned to unit or outside the image");
+    for (int k = B.oz / unit; k < (B.oz + B.cnz) / unit; ++k)
+      for (int j = B.oy / unit; j < (B.oy + B.cny) / unit; ++j)
+        for (int i = B.ox / unit; i < (B.ox + B.cnx) / unit; ++i) {
+          uint8_t& v = cover[((size_t)k * Cy + j) * Cx + i];
+          if (v) return fail(h, HH_ERR_ARG, "boxes overlap");
+          v = 1;
+        }
+  }
+  for (uint8_t v : cover)
+    if (!v) return fail(h, HH_ERR_ARG, "boxes do not tile the image");
+  return HH_OK;
+}
+
+extern "C" hh_status hh_homogenize_partition(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                             const hh_phase* phases, int nphase, const int32_t* boxes, int nbox,
+                                             int unit, const hh_options* opt, hh_result* out, double* per_sub_C,
+                                             int* per_sub_iters) {
+  if (!h || !out) return fail(h, HH_ERR_ARG, "NULL context or output");
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  Medium m;
+  if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
+  std::vector<BoxReq> bx;
+  if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
+  if ((s = check_tiling(h, bx, unit, nx, ny, nz)) != HH_OK) return s;
+  if ((s = enter(h)) != HH_OK) return s;
+  m.kind = MED_ISO;
+  m.Nx = nx;
+  m.Ny = ny;
+  m.Nz = nz;
+  if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
+  return hierarchical_core(h, *opt, m, bx, unit, out, per_sub_C, per_sub_iters);
+}
+
+extern "C" hh_status hh_homogenize_hierarchical(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                                const hh_phase* phases, int nphase, int n, int b,
+                                                const hh_options* opt, hh_result* out, double* per_sub_C,
+                                                int* per_sub_iters) {
+  if (n < 1 || b < 0 || nx % n || ny % n || nz % n) return fail(h, HH_ERR_ARG, "n must divide the image, b >= 0");
+  std::vector<int32_t> rows;
+  for (int k = 0; k < nz / n; ++k)
+    for (int j = 0; j < ny / n; ++j)
+      for (int i = 0; i < nx / n; ++i) {
+        const int32_t r[7] = {i * n, j * n, k * n, n, n, n, b};
+        rows.insert(rows.end(), r, r + 7);
+      }
+  return hh_homogenize_partition(h, img, nx, ny, nz, on_dev, phases, nphase, rows.data(), (int)(rows.size() / 7), n,
+                                 opt, out, per_sub_C, per_sub_iters);
+}
+
+extern "C" hh_status hh_solve_subimages(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                        const hh_phase* phases, int nphase, const int32_t* boxes, int nbox,
+                                        const hh_options* opt, double* C_out, double* Sigma_out, double* Eps_out,
+                                        int* iters_out, double* resid_out) {
+  if (!h) return HH_ERR_ARG;
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  Medium m;
+  if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
+  std::vector<BoxReq> bx;
+  if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
+  if ((s = enter(h)) != HH_OK) return s;
+  m.kind = MED_ISO;
+  m.Nx = nx;
+  m.Ny = ny;
+  m.Nz = nz;
+  if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
+  Stats st;
+  BoxRes* d_res;
+  if ((s = run_boxes_p(h, *opt, m, bx, &d_res, st)) != HH_OK) return s;
+  Ctx& c = h->c;
+  std::vector<BoxRes> all(nbox);
+  HH_CK(cudaMemcpyAsync(all.data(), d_res, nbox * sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  for (int b = 0; b < nbox; ++b) {
+    if (C_out) std::memcpy(C_out + 36 * b, all[b].C, 36 * sizeof(double));
+    if (Sigma_out) std::memcpy(Sigma_out + 36 * b, all[b].Sig, 36 * sizeof(double));
+    if (Eps_out) std::memcpy(Eps_out + 36 * b, all[b].Eps, 36 * sizeof(double));
+    if (iters_out) std::memcpy(iters_out + 6 * b, all[b].iters, 6 * sizeof(int));
+    if (resid_out) std::memcpy(resid_out + 6 * b, all[b].resid, 6 * sizeof(double));
+  }
+  return status_of(st);
+}
+
+extern "C" hh_status hh_homogenize_aniso(hh_ctx* h, const double* C21, int nx, int ny, int nz, int on_dev,
+                                         const hh_options* opt, hh_result* out) {
+  if (!h || !out || !C21) return fail(h, HH_ERR_ARG, "NULL argument");
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  if ((s = enter(h)) != HH_OK) return s;
+  Ctx& c = h->c;
+  const long long V = (long long)nx * ny * nz;
+  const double* d_c21 = C21;
+  if (!on_dev) {
+    double* d;
+    if ((s = ensure(c, "c21in", 21 * V * sizeof(double), (void**)&d)) != HH_OK) return s;
+    HH_CK(cudaMemcpyAsync(d, C21, 21 * V * sizeof(double), cudaMemcpyHostToDevice, c.st));
+    d_c21 = d;
+  }
+  Medium m;
+  m.kind = MED_ANISO;
+  m.d_c21 = d_c21;
+  m.Nx = nx;
+  m.Ny = ny;
+  m.Nz = nz;
+  std::vector<BoxReq> one(1);
+  std::memset(one.data(), 0, sizeof(BoxReq));
+  one[0].cnx = nx;
+  one[0].cny = ny;
+  one[0].cnz = nz;
+  Stats st;
+  BoxRes* d_res;
+  if ((s = run_boxes_p(h, *opt, m, one, &d_res, st)) != HH_OK) return s;
+  BoxRes R;
+  HH_CK(cudaMemcpyAsync(&R, d_res, sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  std::memset(out, 0, sizeof(*out));
+  fill_result(out, R, st);
+  return out->status;
+}
+
+extern "C" hh_status hh_apply_operator(hh_ctx* h, const uint8_t* labels, const hh_phase* phases, int nphase,
+                                       const double* C21, int nx, int ny, int nz, const double* p, double* q,
+                                       const hh_options* opt) {
+  if (!h || !p || !q) return fail(h, HH_ERR_ARG, "NULL argument");
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  if ((s = enter(h)) != HH_OK) return s;
+  Ctx& c = h->c;
+  const long long V = (long long)nx * ny * nz;
+  Medium m;
+  if (C21) {
+    m.kind = MED_ANISO;
+    double* d;
+    if ((s = ensure(c, "c21in", 21 * V * sizeof(double), (void**)&d)) != HH_OK) return s;
+    HH_CK(cudaMemcpyAsync(d, C21, 21 * V * sizeof(double), cudaMemcpyHostToDevice, c.st));
+    m.d_c21 = d;
+  } else {
+    if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
+    if (!labels) return fail(h, HH_ERR_ARG, "labels is NULL");
+    for (long long i = 0; i < V; ++i)
+      if (labels[i] >= nphase) return fail(h, HH_ERR_ARG, "label >= nphase");
+    m.kind = MED_ISO;
+    if ((s = stage_image(h, labels, V, 0, &m.d_img)) != HH_OK) return s;
+  }
+  return opt->precision == HH_FP64 ? apply_operator<double>(c, *opt, m, nx, ny, nz, p, q)
+                                   : apply_operator<float>(c, *opt, m, nx, ny, nz, p, q);
+}
+
+extern "C" hh_status hh_extract_subimages(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                          const int32_t* boxes, int nbox, uint8_t* out, int64_t out_len) {
+  if (!h || !out) return fail(h, HH_ERR_ARG, "NULL argument");
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  hh_status s;
+  std::vector<BoxReq> bx;
+  if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
+  long long tot = 0;
+  std::vector<int2> items;
+  for (int b = 0; b < nbox; ++b) {
+    bx[b].lab_off = tot;
+    const long long ex = bx[b].cnx + 2LL * bx[b].b, ey = bx[b].cny + 2LL * bx[b].b, ez = bx[b].cnz + 2LL * bx[b].b;
+    tot += ex * ey * ez;
+    for (int k = 0; k < ez; ++k) items.push_back(make_int2(b, k));
+  }
+  if (out_len < tot) return fail(h, HH_ERR_ARG, "output buffer too small");
+  if ((s = enter(h)) != HH_OK) return s;
+  Ctx& c = h->c;
+  const uint8_t* d_img;
+  if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &d_img)) != HH_OK) return s;
+  uint8_t* d_out;
+  BoxReq* d_b;
+  int2* d_it;
+  int* d_flag;
+  if ((s = ensure(c, "labels", tot, (void**)&d_out)) != HH_OK) return s;
+  if ((s = ensure(c, "boxes", nbox * sizeof(BoxReq), (void**)&d_b)) != HH_OK) return s;
+  if ((s = ensure(c, "gitems", items.size() * sizeof(int2), (void**)&d_it)) != HH_OK) return s;
+  if ((s = ensure(c, "flag", 64, (void**)&d_flag)) != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d_b, bx.data(), nbox * sizeof(BoxReq), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemcpyAsync(d_it, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemsetAsync(d_flag, 0, 64, c.st));
+  k_gather<<<std::min<int>((int)items.size(), 8 * c.nsm), 256, 0, c.st>>>(d_img, nx, ny, nz, d_b, d_it,
+                                                                           (int)items.size(), d_out, 256, d_flag);
+  HH_CK(cudaGetLastError());
+  HH_CK(cudaMemcpyAsync(out, d_out, tot, cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  return HH_OK;
+}
+
+extern "C" hh_status hh_fit_inverse_n(hh_ctx* h, const int* ns, const double* M, int count, double* M_inf,
+                                      double* C) {
+  if (!h || !ns || !M || !M_inf || !C || count < 2) return fail(h, HH_ERR_ARG, "fit needs >= 2 points");
+  bool distinct = false;
+  for (int i = 0; i < count; ++i) {
+    if (ns[i] < 1) return fail(h, HH_ERR_ARG, "n must be >= 1");
+    if (ns[i] != ns[0]) distinct = true;
+  }
+  if (!distinct) return fail(h, HH_ERR_ARG, "fit needs two distinct n");
+  hh_status s;
+  if ((s = enter(h)) != HH_OK) return s;
+  Ctx& c = h->c;
+  int* d_n;
+  double *d_m, *d_o;
+  if ((s = ensure(c, "fit_n", count * sizeof(int), (void**)&d_n)) != HH_OK) return s;
+  if ((s = ensure(c, "fit_m", count * sizeof(double), (void**)&d_m)) != HH_OK) return s;
+  if ((s = ensure(c, "fit_o", 2 * sizeof(double), (void**)&d_o)) != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d_n, ns, count * sizeof(int), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemcpyAsync(d_m, M, count * sizeof(double), cudaMemcpyHostToDevice, c.st));
+  k_fit_inverse_n<<<1, 32, 0, c.st>>>(d_n, d_m, count, d_o);
+  HH_CK(cudaGetLastError());
+  HH_CK(cudaMemcpyAsync(c.h_dbl, d_o, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  *M_inf = c.h_dbl[0];
+  *C = c.h_dbl[1];
+  return HH_OK;
+}
+
+extern "C" hh_status hh_extrapolate(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                    const hh_phase* phases, int nphase, const int* ns, int count, int b,
+                                    const hh_options* opt, double* K_inf, double* C_K, double* G_inf, double* C_G,
+                                    hh_result* per_n) {
+  if (!h || !ns || count < 2 || !K_inf || !C_K || !G_inf || !C_G) return fail(h, HH_ERR_ARG, "bad arguments");
+  std::vector<double> Ks(count), Gs(count);
+  hh_status worst = HH_OK;
+  for (int i = 0; i < count; ++i) {
+    hh_result r;
+    hh_status s = hh_homogenize_hierarchical(h, img, nx, ny, nz, on_dev, phases, nphase, ns[i], b, opt, &r, nullptr,
+                                             nullptr);
+    if (s < 0) return s;
+    if (s > 0) worst = s;
+    Ks[i] = r.K;
+    Gs[i] = r.G;
+    if (per_n) per_n[i] = r;
+  }
+  hh_status s = hh_fit_inverse_n(h, ns, Ks.data(), count, K_inf, C_K);
+  if (s != HH_OK) return s;
+  s = hh_fit_inverse_n(h, ns, Gs.data(), count, G_inf, C_G);
+  if (s != HH_OK) return s;
+  return worst;
+}
