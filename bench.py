@@ -1,0 +1,318 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of hierarchical homogenization on GB300.
+
+Workload: the 512^3 overlapping-sphere sandstone (porosity 0.15, solid K=37
+G=44 GPa, pore 1e-4 GPa) cut into 27,000 uneven cores of edge 16/24/32 with
+seeded buffers 0..8 (buffered subimages 16..48), coarse unit 8. The cores form
+30 z-slabs of 900; one step is the full hierarchical homogenization of one
+slab: extraction of its 900 buffered subimages (buffers wrap in the whole
+image), 6 load cases each solved to tolerance, C_R = Sigma Eps^-1, assembly of
+the slab's 64 x 64 x h/8 coarse image, its level-2 solve and the moduli.
+
+Metric: voxel-iterations per second (one unit = one voxel of one load case
+through one conjugate-gradient iteration), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel·iters/s; 512³ hierarchical homogenization s vs plain FP64 at ≤0.5% K,G err"
+UNIT = "voxel·iters/s"
+IMAGE_SEED = 2208023203
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload():
+    import synth
+    img = synth.boolean_spheres(n=512, seed=IMAGE_SEED)
+    boxes = synth.uneven_partition(N=512, seed=IMAGE_SEED)
+    zs = sorted(set(int(v) for v in boxes[:, 2]))
+    slabs = [boxes[boxes[:, 2] == z] for z in zs]
+    return img, synth.PHASES_SOLID_PORE, boxes, slabs
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def ncu_traffic():
+    """dram bytes per algorithmic byte of the dominant kernel, from the committed
+    ncu summary (profiles/roofline_traffic.txt); None if absent."""
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    try:
+        kv = dict(l.strip().split("=", 1) for l in open(p) if "=" in l and not l.startswith("#"))
+        return kv["kernel"], float(kv["dram_bytes_per_algorithmic_byte"])
+    except (OSError, KeyError, ValueError):
+        return None, None
+
+
+def cpu_baseline(img, ph, boxes, seconds: float):
+    """The FP64 oracle, as it stands, on a bounded sample: conjugate-gradient
+    iterations of one buffered subimage of the workload (one load case)."""
+    from oracle import hh_oracle as O
+    sizes = (boxes[:, 3:6] + 2 * boxes[:, 6:7]).prod(axis=1)
+    k = int(sizes.argsort()[len(sizes) // 2])  # a median-size subimage
+    b = boxes[k]
+    sub = O.extract_box(img, b)
+    med = O.IsoMedium.from_labels(sub, ph)
+    V = sub.size
+    t0 = time.perf_counter()
+    O.solve_cg(med, O.unit_load(0), fixed_iters=2)
+    per = (time.perf_counter() - t0) / 3.0  # rhs + 2 iterations
+    iters = max(2, int(seconds / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    O.solve_cg(med, O.unit_load(0), fixed_iters=iters)
+    dt = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count() or 1
+    return {"value": V * iters / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": f"oracle CG, subimage {k} of the partition (Omega_B {tuple(int(v) for v in sub.shape)}, "
+                      f"{V} voxels), load case 11, {iters} iterations in {dt:.1f} s"}
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def reduce_max_sum(vals_max, vals_sum, ws):
+    if ws == 1:
+        return vals_max, vals_sum
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    a = torch.tensor(vals_max, dtype=torch.float64, device=dev)
+    b = torch.tensor(vals_sum, dtype=torch.float64, device=dev)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return a.tolist(), b.tolist()
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def run_reference(args):
+    ws, rank, local = dist_init()
+    if rank != 0:
+        return
+    img, ph, boxes, slabs = workload()
+    per = max(2.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        cpu_baseline(img, ph, slabs[0], min(per, 2.0))
+    vals = []
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(img, ph, slabs[0], per)
+        vals.append(last["value"])
+    v = statistics.median(vals)
+    last["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "spheres512 (bounded oracle sample per step)", "precision": "fp64"},
+            "cpu_baseline": last, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_init()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    from paper_2208_02320_gb300 import Context, _build
+    _build.build()
+    img, ph, boxes, slabs = workload()
+    dimg = torch.from_numpy(img).to(f"cuda:{local}")
+    ctx = Context(local)
+    opt = dict(precision=args.precision, tol=args.tol, profile=1)
+
+    def step(i, device=True):
+        sl = slabs[(i * ws + rank) % len(slabs)]
+        src = dimg if device else img
+        return ctx.homogenize_partition(src, ph, sl, unit=8, **opt)
+
+    for i in range(args.warmup):
+        step(i)
+    ctx.profile_reset()
+    barrier(ws)
+    torch.cuda.synchronize()
+    units = 0
+    dev_ms = 0.0
+    launches = 0
+    stats = []
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.warmup, args.warmup + args.steps):
+            r = step(i)
+            units += r["voxel_iters"]
+            dev_ms += r["device_ms"]
+            launches += r["kernel_launches"]
+            stats.append(r)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    barrier(ws)
+    prof = ctx.profile()
+    # end to end through the public API with host buffers (image H2D every step)
+    e2e_units, e2e_s = 0, 0.0
+    for i in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = step(args.warmup + args.steps + i, device=False)
+        e2e_s += time.perf_counter() - t0
+        e2e_units += r["voxel_iters"]
+    (dev_s_max, wall_max, e2e_max), (units_sum, e2e_units_sum) = reduce_max_sum(
+        [dev_ms / 1e3, wall, e2e_s], [units, e2e_units], ws)
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["sampled_ms"]) if prof else None
+    roof = None
+    if dom:
+        name, st = dom
+        achieved = st["sampled_bytes"] / (st["sampled_ms"] / 1e3) / 1e9
+        tk, ratio = ncu_traffic()
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": (ratio * st["sampled_bytes"] / st["sampled"]) if (tk == name and ratio) else None,
+                "algorithmic_bytes_per_launch": st["sampled_bytes"] / max(st["sampled"], 1),
+                "avg_launch_ms": st["sampled_ms"] / max(st["sampled"], 1), "peak_source": peak_src,
+                "kernels": {k: {"sampled": v["sampled"], "avg_ms": v["sampled_ms"] / max(v["sampled"], 1),
+                                "GBps": v["sampled_bytes"] / max(v["sampled_ms"], 1e-9) / 1e6} for k, v in prof.items()}}
+    nbox = sum(len(slabs[(i * ws + rank) % len(slabs)]) for i in range(args.warmup, args.warmup + args.steps))
+    value = units_sum / dev_s_max
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dev_s_max * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {
+            "workload": "spheres512: 512^3 overlapping-sphere sandstone, 27000 uneven cores 16/24/32 + buffers "
+                        "0..8 (subimages 16..48), unit 8; one step = full hierarchical homogenization of one "
+                        "z-slab (900 cores x 6 load cases to tol, assembly, level-2 solve)",
+            "tol": args.tol, "precision": args.precision + " fields and FFTs, fp64 scalars and averages",
+            "phases": "solid K=37 G=44, pore K=G=1e-4 GPa (contrast 4.4e5)",
+            "cores_per_step": nbox // max(args.steps, 1), "parallelism": f"{ws} independent ranks (slabs)",
+            "l2": "working set per step >> 129 MB L2 (inputs larger than L2)",
+            "full_job_voxel_iters_est": None,
+            "wall_s": wall_max, "iters_max": max(s["iters_max"] for s in stats),
+            "resid_max": max(s["resid_max"] for s in stats),
+            "status": [s["status"] for s in stats], "K_G_last": [stats[-1]["K"], stats[-1]["G"]],
+        },
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_units_sum / e2e_max if e2e_max > 0 else None, "unit": UNIT,
+                "h2d_bytes_per_step": int(img.nbytes + 28 * nbox // max(args.steps, 1)),
+                "d2h_bytes_per_step": int((36 * 8 + 6 * 4) * nbox // max(args.steps, 1) + 1024)},
+        "gpu_launches": launches,
+        "roofline": roof,
+    }
+    line["cpu_baseline"] = cpu_baseline(img, ph, slabs[0], args.cpu_seconds) if ws == 1 else None
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

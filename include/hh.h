@@ -74,6 +74,8 @@ typedef struct {
                              1 on, 0 off, -1 (default) on in FP32 and off in FP64 */
     int max_restarts;     /* restarts allowed when the final true residual exceeds
                              2 tol (default 4) */
+    int profile;          /* 1: time the field kernels of the first iteration of every
+                             chunk with CUDA events (read with hh_profile_read) */
 } hh_options;
 
 typedef struct {
@@ -85,12 +87,25 @@ typedef struct {
     int iters_max;        /* most iterations of any load case of any solve */
     int n_subimages;      /* level-1 subimages solved (hierarchical calls) */
     int n_surrogate_accepted;
-    int pad_;
+    int n_clipped;        /* subimages whose sym(C_R) was raised to the stiffness floor
+                             min(3K, 2G) before assembly (indefinite with a buffer) */
     double resid_max;     /* largest final true residual ||b - A x|| / ||b|| */
     long long voxel_iters;/* sum over solves of (voxels x iterations), all load cases */
+    long long kernel_launches; /* libhh kernels launched by this call */
+    double device_ms;     /* device time of the call: CUDA events on the library's stream */
     hh_status status;
     int pad2_;
 } hh_result;
+
+/* Per-kernel timing gathered while options.profile = 1. */
+typedef struct {
+    char name[32];
+    long long launches;       /* launches of this kernel in profiled calls */
+    long long sampled;        /* launches bracketed by CUDA events */
+    double sampled_ms;        /* device time of the sampled launches */
+    double sampled_bytes;     /* algorithmic DRAM bytes of the sampled launches: every field
+                                 byte the kernel must read or write once */
+} hh_kernel_stat;
 
 /* Text of the last error on this context (or of the last failed hh_create
  * when ctx is NULL); never NULL. */
@@ -134,9 +149,10 @@ hh_status hh_homogenize_hierarchical(hh_ctx *ctx, const uint8_t *img, int nx, in
 /* Two-level scheme on an arbitrary partition. `boxes` holds nbox rows of 7
  * int32 (ox, oy, oz, cnx, cny, cnz, b): core origin, core size, buffer width.
  * Every core edge and origin must be a multiple of `unit`, and the cores must
- * tile the image; the coarse image has (nx/unit, ny/unit, nz/unit) voxels
- * and each subimage fills its block of coarse voxels. Outputs as above,
- * in box order. */
+ * tile a box-shaped region of the image (normally the whole image). The
+ * coarse image covers that region with unit-size voxels, each subimage
+ * filling its block; buffers always wrap periodically in the whole image.
+ * Outputs as above, in box order. */
 hh_status hh_homogenize_partition(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
                                   int img_on_device, const hh_phase *phases, int nphase,
                                   const int32_t *boxes, int nbox, int unit,
@@ -186,6 +202,13 @@ hh_status hh_extrapolate(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz
                          const int *ns, int count, int b, const hh_options *opt,
                          double *K_inf, double *C_K, double *G_inf, double *C_G,
                          hh_result *per_n);
+
+/* Copy up to `cap` per-kernel statistics gathered since the last reset;
+ * *count receives the number available. */
+hh_status hh_profile_read(hh_ctx *ctx, hh_kernel_stat *out, int cap, int *count);
+
+/* Clear the per-kernel statistics. */
+hh_status hh_profile_reset(hh_ctx *ctx);
 
 /* Least-squares fit of M(n) = M_inf + C / n over count >= 2 points (Section 5,
  * Eq. fit_power_law), evaluated in FP64 on the context's device. */

@@ -46,6 +46,14 @@ Readings of the paper taken here (where it is silent or ambiguous)
   each subimage fills its block of coarse voxels with its stiffness.
 * The arithmetic mean (AM) of subimage moduli is weighted by core volume
   (a plain mean for a uniform partition).
+* Level-2 voxel stiffness: sym(C_R). With a buffer, Sigma Eps^-1 need not be
+  symmetric and its symmetric part can be indefinite when the core is not much
+  larger than the correlation length; the conjugate-gradient solve of the
+  intermediate image needs positive-definite voxels, so sym(C_R) is projected
+  onto {C >= c_min I} (as a tensor, i.e. in Mandel form) by raising its
+  eigenvalues to c_min, the smallest tensor eigenvalue min(3K, 2G) over the
+  phases (the Frobenius-nearest tensor in that set). Positive-definite sym(C_R) (always the case without a
+  buffer) passes unchanged.
 """
 
 from __future__ import annotations
@@ -419,6 +427,29 @@ def symmetrize(C: np.ndarray) -> np.ndarray:
     return 0.5 * (C + C.T)
 
 
+def stiffness_floor(phases) -> float:
+    """Smallest tensor eigenvalue min(3K, 2G) over the phases."""
+    ph = np.asarray(phases, dtype=np.float64)
+    return float(np.min(np.minimum(3.0 * ph[:, 0], 2.0 * ph[:, 1])))
+
+
+MANDEL = np.array([1.0, 1.0, 1.0, np.sqrt(2.0), np.sqrt(2.0), np.sqrt(2.0)])
+
+
+def clip_spd(C: np.ndarray, floor: float) -> np.ndarray:
+    """Symmetric Voigt stiffness C with every tensor eigenvalue below `floor`
+    raised to `floor`: eigenvalues are taken in the Mandel form D C D,
+    D = diag(1, 1, 1, sqrt2, sqrt2, sqrt2), an orthonormal basis of symmetric
+    tensors. C is returned unchanged when no eigenvalue is below
+    floor (1 - 1e-12)."""
+    M = MANDEL[:, None] * C * MANDEL[None, :]
+    w, V = np.linalg.eigh(M)
+    if w.min() >= floor * (1.0 - 1e-12):
+        return C
+    Mc = (V * np.maximum(w, floor)) @ V.T
+    return Mc / MANDEL[:, None] / MANDEL[None, :]
+
+
 def moduli_voigt(C: np.ndarray):
     """Isotropic Voigt projection: K = (C11+C22+C33+2(C12+C13+C23))/9,
     G = (C11+C22+C33-(C12+C13+C23)+3(C44+C55+C66))/15."""
@@ -499,13 +530,17 @@ def homogenize_hierarchical(image, phases, boxes, unit, tol=1e-6, max_iter=20000
     per_box = []
     Cs = []
     Ks, Gs, w = [], [], []
+    cmin = stiffness_floor(phases)
+    clipped = 0
     for box in boxes:
         sub = extract_box(image, box)
         med = IsoMedium.from_labels(sub, phases)
         r = homogenize_box(med, core_slices(box), tol, max_iter, nyquist, fixed_iters)
         per_box.append(r)
         C = symmetrize(r["C"])
-        Cs.append(C)
+        Cc = clip_spd(C, cmin)
+        clipped += int(Cc is not C)
+        Cs.append(Cc)
         k, g = moduli_voigt(C)
         Ks.append(k)
         Gs.append(g)
@@ -519,7 +554,7 @@ def homogenize_hierarchical(image, phases, boxes, unit, tol=1e-6, max_iter=20000
     w = np.array(w)
     return dict(C=res2["C"], C_sym=Ceff, K=K, G=G, K_reuss=KR, G_reuss=GR,
                 K_am=float(np.sum(w * Ks) / w.sum()), G_am=float(np.sum(w * Gs) / w.sum()),
-                per_box=per_box, C_boxes=np.array(Cs), coarse=coarse, level2=res2)
+                per_box=per_box, C_boxes=np.array(Cs), coarse=coarse, level2=res2, n_clipped=clipped)
 
 
 # --------------------------------------------------------------------------

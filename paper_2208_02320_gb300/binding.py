@@ -45,6 +45,7 @@ class Options(ctypes.Structure):
         ("check_every", ctypes.c_int),
         ("replace", ctypes.c_int),
         ("max_restarts", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -61,9 +62,11 @@ class Result(ctypes.Structure):
         ("iters_max", ctypes.c_int),
         ("n_subimages", ctypes.c_int),
         ("n_surrogate_accepted", ctypes.c_int),
-        ("pad_", ctypes.c_int),
+        ("n_clipped", ctypes.c_int),
         ("resid_max", ctypes.c_double),
         ("voxel_iters", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+        ("device_ms", ctypes.c_double),
         ("status", ctypes.c_int),
         ("pad2_", ctypes.c_int),
     ]
@@ -72,8 +75,19 @@ class Result(ctypes.Structure):
         return dict(C=np.array(self.C).reshape(6, 6), C_sym=np.array(self.C_sym).reshape(6, 6),
                     K=self.K, G=self.G, K_reuss=self.K_reuss, G_reuss=self.G_reuss,
                     K_am=self.K_am, G_am=self.G_am, iters_max=self.iters_max,
-                    n_subimages=self.n_subimages, resid_max=self.resid_max,
-                    voxel_iters=self.voxel_iters, status=self.status)
+                    n_subimages=self.n_subimages, n_clipped=self.n_clipped, resid_max=self.resid_max,
+                    voxel_iters=self.voxel_iters, kernel_launches=self.kernel_launches,
+                    device_ms=self.device_ms, status=self.status)
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [
+        ("name", ctypes.c_char * 32),
+        ("launches", ctypes.c_longlong),
+        ("sampled", ctypes.c_longlong),
+        ("sampled_ms", ctypes.c_double),
+        ("sampled_bytes", ctypes.c_double),
+    ]
 
 
 class Phase(ctypes.Structure):
@@ -99,6 +113,8 @@ _SIGNATURES = {
     "hh_extract_subimages": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, ctypes.c_int64]),
     "hh_extrapolate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P]),
     "hh_fit_inverse_n": (_I, [_P, _P, _P, _I, _P, _P]),
+    "hh_profile_read": (_I, [_P, _P, _I, _P]),
+    "hh_profile_reset": (_I, [_P]),
 }
 
 _lib = None
@@ -326,6 +342,17 @@ class Context:
         s = self._lib.hh_fit_inverse_n(self._h, _ptr(nsa), _ptr(Ma), len(nsa), ctypes.byref(mi), ctypes.byref(c))
         self._check(s, "hh_fit_inverse_n", allow_warn=False)
         return mi.value, c.value
+
+    def profile(self) -> dict:
+        arr = (KernelStat * 64)()
+        n = ctypes.c_int()
+        self._check(self._lib.hh_profile_read(self._h, arr, 64, ctypes.byref(n)), "hh_profile_read")
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, sampled=arr[i].sampled,
+                                           sampled_ms=arr[i].sampled_ms, sampled_bytes=arr[i].sampled_bytes)
+                for i in range(min(n.value, 64))}
+
+    def profile_reset(self):
+        self._check(self._lib.hh_profile_reset(self._h), "hh_profile_reset")
 
     # raw status calls (tests of the error paths)
     def raw(self):

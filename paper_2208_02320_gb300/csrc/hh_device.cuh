@@ -1012,15 +1012,36 @@ __global__ void k_scal_avg(const Prob* prob, PState* st, const double* part, int
   }
 }
 
-__global__ void k_count_active(const PState* st, int nprob, int* out) {
+// Number of active problems and, over them, the real-field voxels and the
+// half-spectrum elements (6 nz ny nxh) one iteration touches.
+__global__ void k_count_active(const PState* st, const Prob* prob, int nprob, int* out_n,
+                               unsigned long long* out_vs) {
   __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = 0;
+  __shared__ unsigned long long sv, ss;
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    sv = 0;
+    ss = 0;
+  }
   __syncthreads();
   int c = 0;
-  for (int i = threadIdx.x; i < nprob; i += blockDim.x) c += st[i].active;
+  unsigned long long v = 0, sp = 0;
+  for (int i = threadIdx.x; i < nprob; i += blockDim.x)
+    if (st[i].active) {
+      const Prob& d = prob[i];
+      ++c;
+      v += (unsigned long long)d.nx * d.ny * d.nz;
+      sp += 6ull * d.nz * d.ny * d.nxh;
+    }
   atomicAdd(&cnt, c);
+  atomicAdd(&sv, v);
+  atomicAdd(&ss, sp);
   __syncthreads();
-  if (threadIdx.x == 0) *out = cnt;
+  if (threadIdx.x == 0) {
+    *out_n = cnt;
+    out_vs[0] = sv;
+    out_vs[1] = ss;
+  }
 }
 
 }  // namespace hh

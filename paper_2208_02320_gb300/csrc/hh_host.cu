@@ -108,13 +108,21 @@ struct Ctx {
   int* h_int = nullptr;        // pinned scratch
   double* h_dbl = nullptr;
   std::string err;
+  long long launches = 0;      // kernels launched on this context
+  cudaEvent_t ev_call0 = nullptr, ev_call1 = nullptr;
+  struct KStat {
+    long long launches = 0, sampled = 0;
+    double ms = 0.0, bytes = 0.0;
+  };
+  std::map<std::string, KStat> prof;
 };
 
 #define HH_CK(call)                                                         \
   do {                                                                      \
     cudaError_t e_ = (call);                                                \
     if (e_ != cudaSuccess) {                                                \
-      c.err = std::string(#call) + ": " + cudaGetErrorString(e_);           \
+      c.err = std::string(#call) + " (line " + std::to_string(__LINE__) +   \
+              "): " + cudaGetErrorString(e_);                                \
       return e_ == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA;    \
     }                                                                       \
   } while (0)
@@ -186,6 +194,8 @@ struct Medium {
   std::vector<double> lam, mu;
   // aniso: device FP64 C21 field of the single whole-grid box
   const double* d_c21 = nullptr;
+  // smallest tensor eigenvalue min(3K, 2G) of the phases (level-2 voxel floor)
+  double floor = 0.0;
 };
 
 struct Stats {
@@ -391,12 +401,14 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     HH_CK(cudaMemsetAsync(d_flag, 0, 64, c.st));
     if (med.kind == MED_ISO) {
       if ((s = ensure(c, "labels", lab_off, (void**)&d_lab)) != HH_OK) return s;
+      ++c.launches;
       k_gather<<<grid_for<T>(c, (const void*)k_gather, 256, 0, (int)gitems.size()), 256, 0, c.st>>>(
           med.d_img, med.Nx, med.Ny, med.Nz, d_boxes, d_git, (int)gitems.size(), d_lab, nphase, d_flag);
       HH_CK(cudaGetLastError());
     } else {
       if ((s = ensure(c, "c21T", c21_off * sizeof(T), (void**)&d_c21)) != HH_OK) return s;
       const long long V = c21_off / 21;
+      ++c.launches;
       k_c21_prepare<T><<<std::max(1, std::min<int>(c.nsm * 8, (int)((V + 255) / 256))), 256, 0, c.st>>>(
           med.d_c21, d_c21, V, d_flag);
       HH_CK(cudaGetLastError());
@@ -448,16 +460,34 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     const int gs = (np + 127) / 128;
 
     // ---- right-hand side b = -G*(C:E), r = p = b, x = 0
+    ++c.launches;
     kf_rhs<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+    ++c.launches;
     kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_RHS);
+    ++c.launches;
     ki_rhs<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+    ++c.launches;
     k_scal_init<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, floor2);
     HH_CK(cudaGetLastError());
 
+    // profiling: events around the field kernels of the first iteration of every chunk
+    const bool prof = o.profile != 0;
+    cudaEvent_t pev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (prof)
+      for (auto& e : pev) HH_CK(cudaEventCreate(&e));
+    // external record nodes, so that the events are timed inside graph replays
+    auto rec = [&](int m, int k) {
+      if (prof && m == 0) {
+        if (cudaEventRecordWithFlags(pev[k], c.st, cudaEventRecordExternal) != cudaSuccess) (void)cudaGetLastError();
+      }
+    };
     // true residual r = -G*(C:(E + x)) of the flagged problems
     auto true_pass = [&]() {
+      ++c.launches;
       kf_tr<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+      ++c.launches;
       kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_TRUE);
+      ++c.launches;
       ki_tr<<<gp_i, threads, plane_smem, c.st>>>(kpp);
     };
     // ---- iterations, in chunks captured as CUDA graphs; residual
@@ -465,24 +495,42 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     const int chunk = std::max(1, o.check_every);
     auto launch_chunk = [&]() {
       for (int m = 0; m < chunk; ++m) {
+        rec(m, 0);
+        ++c.launches;
         kf_it<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+        rec(m, 1);
+        ++c.launches;
         kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_ITER);
+        rec(m, 2);
+        ++c.launches;
         ki_it<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+        rec(m, 3);
+        ++c.launches;
         k_scal_alpha<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np);
+        rec(m, 4);
+        ++c.launches;
         ku<<<gu, threads, 0, c.st>>>(kpp);
+        rec(m, 5);
+        ++c.launches;
         k_scal_beta<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
       }
       if (replace) {
+        ++c.launches;
         k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 0);
         true_pass();
+        ++c.launches;
         k_scal_replace<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.fixed_iters);
       }
     };
     cudaGraphExec_t exec = nullptr;
+    long long chunk_kernels = 0;
     if (o.use_graphs) {
       cudaGraph_t g = nullptr;
       HH_CK(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+      const long long l0 = c.launches;
       launch_chunk();
+      chunk_kernels = c.launches - l0;
+      c.launches = l0;
       cudaError_t ce = cudaStreamEndCapture(c.st, &g);
       if (ce != cudaSuccess) {
         c.err = std::string("graph capture: ") + cudaGetErrorString(ce);
@@ -500,11 +548,42 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     long long chunks = 0;
     int final_rounds = 0;
     hh_status rs = HH_OK;
+    // algorithmic bytes per voxel (a) and per half-spectrum element (b) of the
+    // four field kernels: every field value read or written once
+    const double Tb = sizeof(T);
+    const double lab_b = (med.kind == MED_ISO) ? 1.0 : 21.0 * Tb;
+    const char* pnames[4] = {"plane_fwd", "column", "plane_inv", "update"};
+    const double pa[4] = {18.0 * Tb + lab_b, 0.0, 12.0 * Tb, 36.0 * Tb};
+    const double pb[4] = {2.0 * Tb, 4.0 * Tb, 2.0 * Tb, 0.0};
+    unsigned long long* h_vs = reinterpret_cast<unsigned long long*>(c.h_dbl);
+    double act_v = 0.0, act_s = 0.0;
+    bool sampled_pending = false;
     auto count_active = [&](int* out) -> cudaError_t {
-      k_count_active<<<1, 256, 0, c.st>>>(d_st, np, d_flag);
+      ++c.launches;
+      k_count_active<<<1, 256, 0, c.st>>>(d_st, d_prob, np, d_flag, reinterpret_cast<unsigned long long*>(d_flag + 4));
       cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+      cudaMemcpyAsync(h_vs, d_flag + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.st);
       cudaError_t e = cudaStreamSynchronize(c.st);
       *out = c.h_int[0];
+      if (e == cudaSuccess && prof && sampled_pending) {
+        const int pairs[4][2] = {{0, 1}, {1, 2}, {2, 3}, {4, 5}};
+        for (int k = 0; k < 4; ++k) {
+          float ms = 0.f;
+          if (cudaEventElapsedTime(&ms, pev[pairs[k][0]], pev[pairs[k][1]]) == cudaSuccess) {
+            Ctx::KStat& ks = c.prof[pnames[k]];
+            ks.sampled += 1;
+            ks.ms += ms;
+            ks.bytes += pa[k] * act_v + pb[k] * act_s;
+          } else {
+            (void)cudaGetLastError();  // profiling is best effort; keep the error state clean
+          }
+        }
+        sampled_pending = false;
+      }
+      if (e == cudaSuccess) {
+        act_v = double(h_vs[0]);
+        act_s = double(h_vs[1]);
+      }
       return e;
     };
     while (true) {
@@ -518,8 +597,10 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       if (nact == 0) {
         // every problem stopped on its recursive residual: check the true one
         if (final_rounds > o.max_restarts) break;
+        ++c.launches;
         k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 1);
         true_pass();
+        ++c.launches;
         k_scal_true_final<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, 2.0, o.max_restarts, o.max_iter,
                                                  o.fixed_iters);
         ++final_rounds;
@@ -533,9 +614,14 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       if (chunks >= max_chunks) break;
       if (exec) {
         e = cudaGraphLaunch(exec, c.st);
+        c.launches += chunk_kernels;
       } else {
         launch_chunk();
         e = cudaGetLastError();
+      }
+      if (prof) {
+        sampled_pending = true;
+        for (int k = 0; k < 4; ++k) c.prof[pnames[k]].launches += chunk;
       }
       if (e != cudaSuccess) {
         c.err = std::string("launch: ") + cudaGetErrorString(e);
@@ -545,18 +631,23 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       ++chunks;
     }
     if (exec) cudaGraphExecDestroy(exec);
+    for (auto& e : pev)
+      if (e) cudaEventDestroy(e);
     if (rs != HH_OK) return rs;
 
     // ---- core averages from x
     {
       const int ga = grid_for<T>(c, (const void*)ka, threads, 0, kpp.nitems);
+      ++c.launches;
       ka<<<ga, threads, 0, c.st>>>(kpp);
+      ++c.launches;
       k_scal_avg<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np);
       HH_CK(cudaGetLastError());
     }
 
     // ---- per-box results
-    k_finalize<<<(nb + 63) / 64, 64, 0, c.st>>>(d_prob, d_st, nb, d_res, b0);
+    ++c.launches;
+    k_finalize<<<(nb + 63) / 64, 64, 0, c.st>>>(d_prob, d_st, nb, d_res, b0, med.floor);
     HH_CK(cudaGetLastError());
     // statistics
     std::vector<PState> hst(np);
@@ -644,6 +735,7 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
     HH_CK(cudaMemcpyAsync(d_lab, med.d_img, V, cudaMemcpyDeviceToDevice, c.st));
   } else {
     if ((s = ensure(c, "c21T", 21 * V * sizeof(T), (void**)&d_c21)) != HH_OK) return s;
+    ++c.launches;
     k_c21_prepare<T><<<std::max(1, std::min<int>(c.nsm * 8, (int)((V + 255) / 256))), 256, 0, c.st>>>(
         med.d_c21, d_c21, V, d_flag);
     HH_CK(cudaGetLastError());
@@ -678,8 +770,11 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   HH_CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
   HH_CK(cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
   HH_CK(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+  ++c.launches;
   kf<<<std::min(nz, 4 * c.nsm), 256, psm, c.st>>>(kpp);
+  ++c.launches;
   kc<<<std::min(ny, 4 * c.nsm), 256, csm, c.st>>>(kpc, MODE_APPLY);
+  ++c.launches;
   ki<<<std::min(nz, 4 * c.nsm), 256, psm, c.st>>>(kpp);
   HH_CK(cudaGetLastError());
   HH_CK(cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st));
@@ -775,6 +870,8 @@ extern "C" hh_status hh_create(hh_ctx** out, int device, void* cuda_stream) {
   c.user = (cudaStream_t)cuda_stream;
   if ((e = cudaMallocHost((void**)&c.h_int, 64 * sizeof(int))) != cudaSuccess) return bad(e);
   if ((e = cudaMallocHost((void**)&c.h_dbl, 64 * sizeof(double))) != cudaSuccess) return bad(e);
+  if ((e = cudaEventCreate(&c.ev_call0)) != cudaSuccess) return bad(e);
+  if ((e = cudaEventCreate(&c.ev_call1)) != cudaSuccess) return bad(e);
   *out = h;
   return HH_OK;
 }
@@ -791,14 +888,19 @@ extern "C" void hh_destroy(hh_ctx* h) {
   if (c.d_itab.p) cudaFree(c.d_itab.p);
   if (c.h_int) cudaFreeHost(c.h_int);
   if (c.h_dbl) cudaFreeHost(c.h_dbl);
+  if (c.ev_call0) cudaEventDestroy(c.ev_call0);
+  if (c.ev_call1) cudaEventDestroy(c.ev_call1);
   if (c.st) cudaStreamDestroy(c.st);
   delete h;
 }
 
-// Order the internal stream after the caller's stream (for device inputs).
+// Order the internal stream after the caller's stream (for device inputs),
+// and start the call's device timer.
+static thread_local long long g_launch0 = 0;
 static hh_status enter(hh_ctx* h) {
   Ctx& c = h->c;
   HH_CK(cudaSetDevice(c.dev));
+  g_launch0 = c.launches;
   if (c.user) {
     cudaEvent_t ev;
     HH_CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -806,7 +908,21 @@ static hh_status enter(hh_ctx* h) {
     HH_CK(cudaStreamWaitEvent(c.st, ev, 0));
     cudaEventDestroy(ev);
   }
+  HH_CK(cudaEventRecord(c.ev_call0, c.st));
   return HH_OK;
+}
+
+// Stop the device timer of a call and fill the counters of its result.
+static hh_status finish(hh_ctx* h, hh_status s, hh_result* out) {
+  Ctx& c = h->c;
+  if (s < 0) return s;
+  float ms = 0.f;
+  if (cudaEventRecord(c.ev_call1, c.st) == cudaSuccess && cudaEventSynchronize(c.ev_call1) == cudaSuccess &&
+      cudaEventElapsedTime(&ms, c.ev_call0, c.ev_call1) == cudaSuccess && out) {
+    out->device_ms = ms;
+  }
+  if (out) out->kernel_launches = c.launches - g_launch0;
+  return s;
 }
 
 static hh_status check_opts(hh_ctx* h, const hh_options* o) {
@@ -830,6 +946,8 @@ static hh_status check_phases(hh_ctx* h, const hh_phase* ph, int nphase, Medium&
       return fail(h, HH_ERR_ARG, "phase moduli must be finite and > 0");
     m.lam[i] = ph[i].K - 2.0 * ph[i].G / 3.0;
     m.mu[i] = ph[i].G;
+    const double f = std::min(3.0 * ph[i].K, 2.0 * ph[i].G);
+    m.floor = (i == 0) ? f : std::min(m.floor, f);
   }
   return HH_OK;
 }
@@ -917,7 +1035,7 @@ extern "C" hh_status hh_homogenize_direct(hh_ctx* h, const uint8_t* img, int nx,
   out->n_subimages = 1;
   out->K_am = R.K;
   out->G_am = R.G;
-  return out->status;
+  return finish(h, out->status, out);
 }
 
 static hh_status parse_boxes(hh_ctx* h, const int32_t* boxes, int nbox, int nx, int ny, int nz,
@@ -944,7 +1062,7 @@ static hh_status parse_boxes(hh_ctx* h, const int32_t* boxes, int nbox, int nx, 
 
 // level 1 + assembly + level 2 on a validated tiling partition
 static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, const std::vector<BoxReq>& boxes, int unit,
-                                   hh_result* out, double* per_sub_C, int* per_sub_iters) {
+                                   const int* reg, hh_result* out, double* per_sub_C, int* per_sub_iters) {
   Ctx& c = h->c;
   hh_status s;
   Stats st1;
@@ -952,7 +1070,7 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   if ((s = run_boxes_p(h, o, m, boxes, &d_res, st1)) != HH_OK) return s;
   const int nbox = (int)boxes.size();
   // assembly of the intermediate image (FP64)
-  const int Cx = m.Nx / unit, Cy = m.Ny / unit, Cz = m.Nz / unit;
+  const int Cx = reg[3], Cy = reg[4], Cz = reg[5];
   const long long Vc = (long long)Cx * Cy * Cz;
   double* d_c21;
   BoxReq* d_boxes;
@@ -965,7 +1083,9 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   if ((s = ensure(c, "aboxes", nbox * sizeof(BoxReq), (void**)&d_boxes)) != HH_OK) return s;
   if ((s = ensure(c, "am", 4 * sizeof(double), (void**)&d_am)) != HH_OK) return s;
   HH_CK(cudaMemcpyAsync(d_boxes, boxes.data(), nbox * sizeof(BoxReq), cudaMemcpyHostToDevice, c.st));
-  k_assemble<<<nbox, 128, 0, c.st>>>(d_boxes, d_res1, nbox, unit, Cx, Cy, Cz, d_c21);
+  ++c.launches;
+  k_assemble<<<nbox, 128, 0, c.st>>>(d_boxes, d_res1, nbox, unit, reg[0], reg[1], reg[2], Cx, Cy, Cz, d_c21);
+  ++c.launches;
   k_am<<<1, 256, 0, c.st>>>(d_res1, d_boxes, nbox, d_am);
   HH_CK(cudaGetLastError());
   // level 2
@@ -1003,6 +1123,7 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   out->K_am = am[0];
   out->G_am = am[1];
   out->n_subimages = nbox;
+  out->n_clipped = (int)am[3];
   for (int b = 0; b < (int)all.size(); ++b) {
     if (per_sub_C) std::memcpy(per_sub_C + 36 * b, all[b].C, 36 * sizeof(double));
     if (per_sub_iters) std::memcpy(per_sub_iters + 6 * b, all[b].iters, 6 * sizeof(int));
@@ -1010,24 +1131,41 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   return out->status;
 }
 
-static hh_status check_tiling(hh_ctx* h, const std::vector<BoxReq>& boxes, int unit, int nx, int ny, int nz) {
-  if (unit < 1 || nx % unit || ny % unit || nz % unit) return fail(h, HH_ERR_ARG, "unit must divide the image");
-  const int Cx = nx / unit, Cy = ny / unit, Cz = nz / unit;
-  std::vector<uint8_t> cover((size_t)Cx * Cy * Cz, 0);
+// The cores must tile their bounding box (in unit cells); reg receives the
+// box origin and extent in unit cells.
+static hh_status check_tiling(hh_ctx* h, const std::vector<BoxReq>& boxes, int unit, int nx, int ny, int nz, int* reg) {
+  if (unit < 1) return fail(h, HH_ERR_ARG, "unit must be >= 1");
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {0, 0, 0};
   for (const BoxReq& B : boxes) {
     if (B.ox % unit || B.oy % unit || B.oz % unit || B.cnx % unit || B.cny % unit || B.cnz % unit ||
         B.ox + B.cnx > nx || B.oy + B.cny > ny || B.oz + B.cnz > nz)
       return fail(h, HH_ERR_ARG, "box not aligned to unit or outside the image");
+    const int o3[3] = {B.ox / unit, B.oy / unit, B.oz / unit};
+    const int e3[3] = {(B.ox + B.cnx) / unit, (B.oy + B.cny) / unit, (B.oz + B.cnz) / unit};
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], o3[a]);
+      hi[a] = std::max(hi[a], e3[a]);
+    }
+  }
+  const int Cx = hi[0] - lo[0], Cy = hi[1] - lo[1], Cz = hi[2] - lo[2];
+  std::vector<uint8_t> cover((size_t)Cx * Cy * Cz, 0);
+  for (const BoxReq& B : boxes) {
     for (int k = B.oz / unit; k < (B.oz + B.cnz) / unit; ++k)
       for (int j = B.oy / unit; j < (B.oy + B.cny) / unit; ++j)
         for (int i = B.ox / unit; i < (B.ox + B.cnx) / unit; ++i) {
-          uint8_t& v = cover[((size_t)k * Cy + j) * Cx + i];
+          uint8_t& v = cover[((size_t)(k - lo[2]) * Cy + (j - lo[1])) * Cx + (i - lo[0])];
           if (v) return fail(h, HH_ERR_ARG, "boxes overlap");
           v = 1;
         }
   }
   for (uint8_t v : cover)
-    if (!v) return fail(h, HH_ERR_ARG, "boxes do not tile the image");
+    if (!v) return fail(h, HH_ERR_ARG, "boxes do not tile a box-shaped region");
+  reg[0] = lo[0];
+  reg[1] = lo[1];
+  reg[2] = lo[2];
+  reg[3] = Cx;
+  reg[4] = Cy;
+  reg[5] = Cz;
   return HH_OK;
 }
 
@@ -1043,14 +1181,15 @@ extern "C" hh_status hh_homogenize_partition(hh_ctx* h, const uint8_t* img, int 
   if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
   std::vector<BoxReq> bx;
   if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
-  if ((s = check_tiling(h, bx, unit, nx, ny, nz)) != HH_OK) return s;
+  int reg[6];
+  if ((s = check_tiling(h, bx, unit, nx, ny, nz, reg)) != HH_OK) return s;
   if ((s = enter(h)) != HH_OK) return s;
   m.kind = MED_ISO;
   m.Nx = nx;
   m.Ny = ny;
   m.Nz = nz;
   if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
-  return hierarchical_core(h, *opt, m, bx, unit, out, per_sub_C, per_sub_iters);
+  return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, per_sub_iters), out);
 }
 
 extern "C" hh_status hh_homogenize_hierarchical(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
@@ -1139,7 +1278,7 @@ extern "C" hh_status hh_homogenize_aniso(hh_ctx* h, const double* C21, int nx, i
   HH_CK(cudaStreamSynchronize(c.st));
   std::memset(out, 0, sizeof(*out));
   fill_result(out, R, st);
-  return out->status;
+  return finish(h, out->status, out);
 }
 
 extern "C" hh_status hh_apply_operator(hh_ctx* h, const uint8_t* labels, const hh_phase* phases, int nphase,
@@ -1202,11 +1341,38 @@ extern "C" hh_status hh_extract_subimages(hh_ctx* h, const uint8_t* img, int nx,
   HH_CK(cudaMemcpyAsync(d_b, bx.data(), nbox * sizeof(BoxReq), cudaMemcpyHostToDevice, c.st));
   HH_CK(cudaMemcpyAsync(d_it, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
   HH_CK(cudaMemsetAsync(d_flag, 0, 64, c.st));
+  ++c.launches;
   k_gather<<<std::min<int>((int)items.size(), 8 * c.nsm), 256, 0, c.st>>>(d_img, nx, ny, nz, d_b, d_it,
                                                                            (int)items.size(), d_out, 256, d_flag);
   HH_CK(cudaGetLastError());
   HH_CK(cudaMemcpyAsync(out, d_out, tot, cudaMemcpyDeviceToHost, c.st));
   HH_CK(cudaStreamSynchronize(c.st));
+  return HH_OK;
+}
+
+extern "C" hh_status hh_profile_read(hh_ctx* h, hh_kernel_stat* out, int cap, int* count) {
+  if (!h || !count || (cap > 0 && !out)) return fail(h, HH_ERR_ARG, "bad arguments");
+  Ctx& c = h->c;
+  int i = 0;
+  for (auto& kv : c.prof) {
+    if (i < cap) {
+      hh_kernel_stat& k = out[i];
+      std::memset(&k, 0, sizeof(k));
+      std::strncpy(k.name, kv.first.c_str(), sizeof(k.name) - 1);
+      k.launches = kv.second.launches;
+      k.sampled = kv.second.sampled;
+      k.sampled_ms = kv.second.ms;
+      k.sampled_bytes = kv.second.bytes;
+    }
+    ++i;
+  }
+  *count = i;
+  return HH_OK;
+}
+
+extern "C" hh_status hh_profile_reset(hh_ctx* h) {
+  if (!h) return HH_ERR_ARG;
+  h->c.prof.clear();
   return HH_OK;
 }
 
@@ -1229,6 +1395,7 @@ extern "C" hh_status hh_fit_inverse_n(hh_ctx* h, const int* ns, const double* M,
   if ((s = ensure(c, "fit_o", 2 * sizeof(double), (void**)&d_o)) != HH_OK) return s;
   HH_CK(cudaMemcpyAsync(d_n, ns, count * sizeof(int), cudaMemcpyHostToDevice, c.st));
   HH_CK(cudaMemcpyAsync(d_m, M, count * sizeof(double), cudaMemcpyHostToDevice, c.st));
+  ++c.launches;
   k_fit_inverse_n<<<1, 32, 0, c.st>>>(d_n, d_m, count, d_o);
   HH_CK(cudaGetLastError());
   HH_CK(cudaMemcpyAsync(c.h_dbl, d_o, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));

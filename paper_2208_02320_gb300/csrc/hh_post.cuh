@@ -19,11 +19,12 @@ struct BoxRes {
   double Sig[36];   // columns = load cases (stress Voigt)
   double Eps[36];   // columns = load cases (engineering strain Voigt)
   double Csym[36];
+  double Cspd[36];  // sym(C_R) raised to the stiffness floor (level-2 voxel)
   double K, G, KR, GR;
   double resid[6];
   int iters[6];
   int status;
-  int pad;
+  int clipped;
 };
 
 // Extraction of the buffered boxes with periodic wrap; one block per (box, z).
@@ -90,6 +91,75 @@ __device__ inline bool inv6(const double* A, double* X) {
   return true;
 }
 
+// Cyclic Jacobi eigen-decomposition of a symmetric 6x6 matrix (row-major
+// A[36], overwritten): A = V diag(w) V^T. Each rotation zeroes the (p, q)
+// pair and updates the symmetric pairs of rows/columns p and q explicitly.
+__device__ inline void jacobi6(double* A, double* V, double* w) {
+  for (int i = 0; i < 36; ++i) V[i] = (i % 7 == 0) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int p = 0; p < 6; ++p) {
+      diag += A[p * 6 + p] * A[p * 6 + p];
+      for (int q = p + 1; q < 6; ++q) off += A[p * 6 + q] * A[p * 6 + q];
+    }
+    if (off <= 1e-32 * diag) break;
+    for (int p = 0; p < 5; ++p)
+      for (int q = p + 1; q < 6; ++q) {
+        const double apq = A[p * 6 + q];
+        if (apq == 0.0) continue;
+        const double app = A[p * 6 + p], aqq = A[q * 6 + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0);
+        const double sn = t * c;
+        A[p * 6 + p] = app - t * apq;
+        A[q * 6 + q] = aqq + t * apq;
+        A[p * 6 + q] = 0.0;
+        A[q * 6 + p] = 0.0;
+        for (int r = 0; r < 6; ++r) {
+          if (r == p || r == q) continue;
+          const double arp = A[r * 6 + p], arq = A[r * 6 + q];
+          const double nrp = c * arp - sn * arq, nrq = sn * arp + c * arq;
+          A[r * 6 + p] = nrp;
+          A[p * 6 + r] = nrp;
+          A[r * 6 + q] = nrq;
+          A[q * 6 + r] = nrq;
+        }
+        for (int r = 0; r < 6; ++r) {
+          const double vrp = V[r * 6 + p], vrq = V[r * 6 + q];
+          V[r * 6 + p] = c * vrp - sn * vrq;
+          V[r * 6 + q] = sn * vrp + c * vrq;
+        }
+      }
+  }
+  for (int i = 0; i < 6; ++i) w[i] = A[i * 7];
+}
+
+// sym(C) with every tensor eigenvalue (Mandel form D C D, D = diag(1,1,1,
+// sqrt2,sqrt2,sqrt2)) below `floor` raised to `floor`; returns whether it
+// changed anything. Used for the level-2 voxels of buffered subimages.
+__device__ inline bool clip_spd6(const double* Cs, double floor, double* out) {
+  const double D[6] = {1.0, 1.0, 1.0, 1.4142135623730951, 1.4142135623730951, 1.4142135623730951};
+  double A[36], V[36], w[6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) A[i * 6 + j] = D[i] * Cs[i * 6 + j] * D[j];
+  jacobi6(A, V, w);
+  double wmin = w[0];
+  for (int i = 1; i < 6; ++i) wmin = fmin(wmin, w[i]);
+  if (!(floor > 0.0) || wmin >= floor * (1.0 - 1e-12)) {
+    for (int i = 0; i < 36; ++i) out[i] = Cs[i];
+    return false;
+  }
+  for (int i = 0; i < 6; ++i) w[i] = fmax(w[i], floor);
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double acc = 0.0;
+      for (int k = 0; k < 6; ++k) acc += V[i * 6 + k] * w[k] * V[j * 6 + k];
+      out[i * 6 + j] = acc / (D[i] * D[j]);
+    }
+  return true;
+}
+
 // Isotropic Voigt and Reuss projections of a 6x6 stiffness.
 __device__ inline void moduli(const double* C, double* K, double* G, double* KR, double* GR) {
   const double a = C[0] + C[7] + C[14];
@@ -113,7 +183,7 @@ __device__ inline void moduli(const double* C, double* K, double* G, double* KR,
 // Sigma, Eps and C_R of each box from the CG scalars of its six load cases
 // (problems 6 b .. 6 b + 5 of the wave). Core averages:
 //   <sigma>_R = sum_R C:(E + eps*) / |R|,  <eps>_R = E + sum_R eps* / |R|.
-__global__ void k_finalize(const Prob* prob, const PState* st, int nbox, BoxRes* out, int box_base) {
+__global__ void k_finalize(const Prob* prob, const PState* st, int nbox, BoxRes* out, int box_base, double floor) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbox) return;
   BoxRes R;
@@ -143,20 +213,20 @@ __global__ void k_finalize(const Prob* prob, const PState* st, int nbox, BoxRes*
   for (int i = 0; i < 6; ++i)
     for (int j = 0; j < 6; ++j) R.Csym[i * 6 + j] = 0.5 * (R.C[i * 6 + j] + R.C[j * 6 + i]);
   moduli(R.Csym, &R.K, &R.G, &R.KR, &R.GR);
+  R.clipped = clip_spd6(R.Csym, floor, R.Cspd) ? 1 : 0;
   R.status = status;
-  R.pad = 0;
   out[box_base + b] = R;
 }
 
 // Assembly (Section 3): each box fills its block of unit-size coarse cells
 // with the 21 upper-triangle entries of sym(C_R) (component-major, FP64).
-__global__ void k_assemble(const BoxReq* boxes, const BoxRes* res, int nbox, int unit, int Cx, int Cy, int Cz,
-                           double* c21) {
+__global__ void k_assemble(const BoxReq* boxes, const BoxRes* res, int nbox, int unit, int rx, int ry, int rz, int Cx,
+                           int Cy, int Cz, double* c21) {
   const int b = blockIdx.x;
   if (b >= nbox) return;
   const BoxReq B = boxes[b];
   const long long V = (long long)Cx * Cy * Cz;
-  const int x0 = B.ox / unit, y0 = B.oy / unit, z0 = B.oz / unit;
+  const int x0 = B.ox / unit - rx, y0 = B.oy / unit - ry, z0 = B.oz / unit - rz;
   const int ex = B.cnx / unit, ey = B.cny / unit, ez = B.cnz / unit;
   const int cells = ex * ey * ez;
   for (int e = threadIdx.x; e < cells * 21; e += blockDim.x) {
@@ -172,7 +242,7 @@ __global__ void k_assemble(const BoxReq* boxes, const BoxRes* res, int nbox, int
     }
     const int bcol = a + t;
     const long long v = ((long long)(z0 + l) * Cy + (y0 + j)) * Cx + (x0 + i);
-    c21[k * V + v] = res[b].Csym[a * 6 + bcol];
+    c21[k * V + v] = res[b].Cspd[a * 6 + bcol];
   }
 }
 
@@ -213,19 +283,21 @@ __global__ void k_c21_prepare(const double* src, T* dst, long long V, int* bad) 
 
 // Core-volume-weighted means of subimage K and G (one block, fixed order).
 __global__ void k_am(const BoxRes* res, const BoxReq* boxes, int nbox, double* out3) {
-  __shared__ double red[32 * 3];
-  double v[3] = {0.0, 0.0, 0.0};
+  __shared__ double red[32 * 4];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nbox; b += blockDim.x) {
     const double w = double(boxes[b].cnx) * boxes[b].cny * boxes[b].cnz;
     v[0] += w * res[b].K;
     v[1] += w * res[b].G;
     v[2] += w;
+    v[3] += res[b].clipped;
   }
-  block_reduce<3>(v, red);
+  block_reduce<4>(v, red);
   if (threadIdx.x == 0) {
     out3[0] = v[0] / v[2];
     out3[1] = v[1] / v[2];
     out3[2] = v[2];
+    out3[3] = v[3];
   }
 }
 

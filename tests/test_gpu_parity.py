@@ -227,6 +227,24 @@ def test_hierarchical_uneven_partition_parity(ctx):
     assert abs(got["K_am"] - ref["K_am"]) / ref["K_am"] < 1e-9
 
 
+def test_buffered_sandstone_projection_and_level2(ctx):
+    """Buffered 16^3 cores of the sphere-pack sandstone at contrast 4.4e5: some
+    sym(C_R) are indefinite. From the GPU's level-1 stiffness, the oracle's
+    projection, assembly and level-2 solve reproduce the GPU's result."""
+    img = synth.boolean_spheres(n=64, seed=41)
+    ph = synth.PHASES_SOLID_PORE
+    boxes = synth.uneven_partition(N=64, counts=((16, 4),), bmax=8, seed=42)
+    got = ctx.homogenize_partition(img, ph, boxes, unit=16, precision="fp64", tol=1e-8)
+    assert got["status"] == 0
+    floor = O.stiffness_floor(ph)
+    Cs = [O.clip_spd(O.symmetrize(C), floor) for C in got["C_boxes"]]
+    clipped = sum(int(not np.array_equal(C, O.symmetrize(Cr))) for C, Cr in zip(Cs, got["C_boxes"]))
+    assert clipped == got["n_clipped"]
+    coarse = O.assemble_coarse(img.shape, boxes, Cs, 16)
+    ref = O.homogenize_box(O.AnisoMedium(coarse), (slice(None),) * 3, tol=1e-10)
+    assert rel(got["C"], ref["C"]) < 1e-6
+
+
 def test_grf32_fixed_iteration_parity(ctx):
     """The 32^3 two-phase workload (contrast 4e5) at a fixed iteration count:
     direct solve and the 64 level-1 subimages of 8^3, FP32 against the FP64

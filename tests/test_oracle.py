@@ -413,6 +413,39 @@ def test_uneven_partition_tiles_the_image():
     assert sizes.min() == 16 and sizes.max() == 48
 
 
+def test_clip_spd_is_the_nearest_tensor_above_the_floor():
+    D = np.array([1, 1, 1, np.sqrt(2), np.sqrt(2), np.sqrt(2)])
+    Q, _ = np.linalg.qr(RNG.standard_normal((6, 6)))
+    w = np.array([-3.0, -1e-3, 2e-4, 0.5, 7.0, 40.0])
+    M = (Q * w) @ Q.T                  # Mandel form
+    A = M / D[:, None] / D[None, :]    # Voigt form
+    B = O.clip_spd(A, 1e-2)
+    MB = D[:, None] * B * D[None, :]
+    assert np.allclose(np.sort(np.linalg.eigvalsh(MB)), np.sort(np.maximum(w, 1e-2)), atol=1e-12)
+    for lam in (0.5, 7.0, 40.0):
+        v = Q[:, list(w).index(lam)]
+        assert np.allclose(MB @ v, lam * v, atol=1e-12)
+    d0 = np.linalg.norm(M - MB)
+    for _ in range(200):
+        P = RNG.standard_normal((6, 6))
+        P = P @ P.T + 1e-2 * np.eye(6)
+        assert np.linalg.norm(M - P) >= d0 - 1e-12
+    # isotropic tensor eigenvalues are 3K and 2G: phases at the floor pass unchanged
+    for K, G in [(37.0, 44.0), (1e-4, 1e-4), (9.8, 3.76)]:
+        C = O.iso_voigt(K, G)
+        assert O.clip_spd(C, min(3 * K, 2 * G)) is C
+    assert O.stiffness_floor([[37.0, 44.0], [1e-4, 1e-4]]) == pytest.approx(2e-4)
+
+
+def test_unbuffered_subimage_stiffness_is_positive_definite():
+    img = synth.grf_two_phase(n=8, ell=2.0, porosity=0.3, seed=31)
+    res = O.homogenize_hierarchical(img, synth.PHASES_APPENDIX_B, synth.uniform_partition(8, 4, 0), unit=4,
+                                    tol=1e-10)
+    assert res["n_clipped"] == 0
+    for C in res["C_boxes"]:
+        assert np.linalg.eigvalsh(C).min() > 0
+
+
 # ---------------------------------------------------------- power law ------
 
 def test_fit_inverse_n_exact():
