@@ -4,10 +4,12 @@
 Workload: the 512^3 overlapping-sphere sandstone (porosity 0.15, solid K=37
 G=44 GPa, pore 1e-4 GPa) cut into 27,000 uneven cores of edge 16/24/32 with
 seeded buffers 0..8 (buffered subimages 16..48), coarse unit 8. The cores form
-30 z-slabs of 900; one step is the full hierarchical homogenization of one
-slab: extraction of its 900 buffered subimages (buffers wrap in the whole
-image), 6 load cases each solved to tolerance, C_R = Sigma Eps^-1, assembly of
-the slab's 64 x 64 x h/8 coarse image, its level-2 solve and the moduli.
+a 30 x 30 x 30 grid; a tile is one z-slab of it by `--tile-rows` rows in y
+(default 6: 180 cores, 150 tiles in the image). One step is the full
+hierarchical homogenization of one tile: extraction of its buffered
+subimages (buffers wrap in the whole image), 6 load cases each solved to
+tolerance, C_R = Sigma Eps^-1, assembly of the tile's coarse image, its
+level-2 solve and the moduli.
 
 Metric: voxel-iterations per second (one unit = one voxel of one load case
 through one conjugate-gradient iteration), whole job over all ranks.
@@ -44,16 +46,24 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tile-rows", type=int, default=6)
     return ap.parse_args()
 
 
-def workload():
+def workload(tile_rows: int = 6):
+    """Image, phases, partition and the list of tiles (z-slab x tile_rows y-rows)."""
+    import numpy as np
     import synth
     img = synth.boolean_spheres(n=512, seed=IMAGE_SEED)
     boxes = synth.uneven_partition(N=512, seed=IMAGE_SEED)
     zs = sorted(set(int(v) for v in boxes[:, 2]))
-    slabs = [boxes[boxes[:, 2] == z] for z in zs]
-    return img, synth.PHASES_SOLID_PORE, boxes, slabs
+    ys = sorted(set(int(v) for v in boxes[:, 1]))
+    tiles = []
+    for z in zs:
+        slab = boxes[boxes[:, 2] == z]
+        for j in range(0, len(ys), tile_rows):
+            tiles.append(slab[np.isin(slab[:, 1], ys[j:j + tile_rows])])
+    return img, synth.PHASES_SOLID_PORE, boxes, tiles
 
 
 class ClockSampler:
@@ -118,12 +128,24 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("hh_device.cuh", "hh_post.cuh", "hh_host.cu"):
+        with open(os.path.join(ROOT, "paper_2208_02320_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def ncu_traffic():
-    """dram bytes per algorithmic byte of the dominant kernel, from the committed
-    ncu summary (profiles/roofline_traffic.txt); None if absent."""
+    """DRAM bytes per algorithmic byte of the dominant kernel from the committed
+    ncu summary (profiles/roofline_traffic.txt); (None, None) if absent or if
+    the kernel sources have changed since the capture."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     try:
         kv = dict(l.strip().split("=", 1) for l in open(p) if "=" in l and not l.startswith("#"))
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None, None
         return kv["kernel"], float(kv["dram_bytes_per_algorithmic_byte"])
     except (OSError, KeyError, ValueError):
         return None, None
@@ -190,7 +212,7 @@ def run_reference(args):
     ws, rank, local = dist_init()
     if rank != 0:
         return
-    img, ph, boxes, slabs = workload()
+    img, ph, boxes, slabs = workload(args.tile_rows)
     per = max(2.0, args.cpu_seconds / max(args.steps + args.warmup, 1))
     for _ in range(args.warmup):
         cpu_baseline(img, ph, slabs[0], min(per, 2.0))
@@ -219,7 +241,7 @@ def run_gb300(args):
     torch.cuda.set_device(local)
     from paper_2208_02320_gb300 import Context, _build
     _build.build()
-    img, ph, boxes, slabs = workload()
+    img, ph, boxes, slabs = workload(args.tile_rows)
     dimg = torch.from_numpy(img).to(f"cuda:{local}")
     ctx = Context(local)
     opt = dict(precision=args.precision, tol=args.tol, profile=1)
@@ -285,10 +307,12 @@ def run_gb300(args):
         "config": {
             "workload": "spheres512: 512^3 overlapping-sphere sandstone, 27000 uneven cores 16/24/32 + buffers "
                         "0..8 (subimages 16..48), unit 8; one step = full hierarchical homogenization of one "
-                        "z-slab (900 cores x 6 load cases to tol, assembly, level-2 solve)",
+                        f"tile (one z-slab x {args.tile_rows} y-rows of cores: each x 6 load cases to tol, "
+                        "assembly, level-2 solve)",
             "tol": args.tol, "precision": args.precision + " fields and FFTs, fp64 scalars and averages",
             "phases": "solid K=37 G=44, pore K=G=1e-4 GPa (contrast 4.4e5)",
-            "cores_per_step": nbox // max(args.steps, 1), "parallelism": f"{ws} independent ranks (slabs)",
+            "cores_per_step": nbox // max(args.steps, 1), "parallelism": f"{ws} independent ranks (tiles)",
+            "tiles_in_image": len(slabs),
             "l2": "working set per step >> 129 MB L2 (inputs larger than L2)",
             "full_job_voxel_iters_est": None,
             "wall_s": wall_max, "iters_max": max(s["iters_max"] for s in stats),

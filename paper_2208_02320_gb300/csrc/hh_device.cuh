@@ -128,6 +128,7 @@ struct KParams {
   int max_iter;
   int fixed_iters;
   int nprob;
+  int colw;          // kx columns per column-pass item
 };
 
 // ---------------------------------------------------------------------------
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
     }
     if (MODE == MODE_RHS) {
       block_reduce<1>(acc, sm.red);
-      if (threadIdx.x == 0) P.part[(long long)it * 16 + 0] = acc[0];
+      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 0] = acc[0];
     }
     __syncthreads();
   }
@@ -579,10 +580,12 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
     const Prob d = P.prob[w.x];
-    const int kyp = w.y;
+    const int kyp = w.y & 0xffff;
+    const int kx0 = w.y >> 16;
     const int nx = d.nx, ny = d.ny, nz = d.nz, nxh = d.nxh;
+    const int W = min(P.colw, nxh - kx0);  // kx columns of this item
     C2<T>* tile = reinterpret_cast<C2<T>*>(smem);
-    C2<T>* twz = tile + 6 * nz * nxh;
+    C2<T>* twz = tile + 6 * nz * P.colw;
     int* sfz = reinterpret_cast<int*>(twz + nz);
     const AxisPlan az = P.plans[d.pz];
     const AxisPlan ay = P.plans[d.py];
@@ -590,20 +593,21 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
     for (int t = threadIdx.x; t < nz; t += blockDim.x) sfz[t] = P.itab[az.sf_off + t];
     C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
-    for (int e = threadIdx.x; e < 6 * nz * nxh; e += blockDim.x) {
-      const int kx = e % nxh;
-      const int cz = e / nxh;  // c * nz + z
-      tile[e] = sp[(long long)cz * pl + kyp * nxh + kx];
+    for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
+      const int kx = e % W;
+      const int cz = e / W;  // c * nz + z
+      tile[e] = sp[(long long)cz * pl + kyp * nxh + kx0 + kx];
     }
     __syncthreads();
-    Lines Lz{6 * nxh, nxh, nz * nxh, 1, nxh, true};
+    Lines Lz{6 * W, W, nz * W, 1, W, true};
     fft_lines<T, false>(tile, Lz, az, twz);
     // projection of every (kz, kx) mode of this ky
     const int my = P.itab[ay.sf_off + kyp];
     const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
-    for (int e = threadIdx.x; e < nz * nxh; e += blockDim.x) {
-      const int kx = e % nxh;
-      const int kzp = e / nxh;
+    for (int e = threadIdx.x; e < nz * W; e += blockDim.x) {
+      const int kxl = e % W;
+      const int kx = kx0 + kxl;
+      const int kzp = e / W;
       const int mz = sfz[kzp];
       const bool nyq_x = (nx % 2 == 0) && (2 * kx == nx);
       const bool nyq_z = (nz % 2 == 0) && (2 * mz == nz);
@@ -617,17 +621,17 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
       }
       C2<T> t[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) t[c] = tile[(c * nz + kzp) * nxh + kx];
+      for (int c = 0; c < 6; ++c) t[c] = tile[(c * nz + kzp) * W + kxl];
       project_mode<T>(t, x0, x1, x2);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) tile[(c * nz + kzp) * nxh + kx] = t[c];
+      for (int c = 0; c < 6; ++c) tile[(c * nz + kzp) * W + kxl] = t[c];
     }
     __syncthreads();
     fft_lines<T, true>(tile, Lz, az, twz);
-    for (int e = threadIdx.x; e < 6 * nz * nxh; e += blockDim.x) {
-      const int kx = e % nxh;
-      const int cz = e / nxh;
-      sp[(long long)cz * pl + kyp * nxh + kx] = tile[e];
+    for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
+      const int kx = e % W;
+      const int cz = e / W;
+      sp[(long long)cz * pl + kyp * nxh + kx0 + kx] = tile[e];
     }
     __syncthreads();
   }
@@ -742,7 +746,7 @@ __global__ void __launch_bounds__(256) k_plane_inv(KParams<T> P) {
     }
     if (MODE != MODE_APPLY) {
       block_reduce<1>(acc, sm.red);
-      if (threadIdx.x == 0) P.part[(long long)it * 16 + 12] = acc[0];
+      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 12] = acc[0];
     }
     __syncthreads();
   }
@@ -777,7 +781,7 @@ __global__ void __launch_bounds__(256) k_update(KParams<T> P) {
       acc[0] += frob_w(c) * double(rv) * double(rv);
     }
     block_reduce<1>(acc, red);
-    if (threadIdx.x == 0) P.part[(long long)it * 16 + 13] = acc[0];
+    if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 13] = acc[0];
   }
 }
 
@@ -828,7 +832,7 @@ __global__ void __launch_bounds__(256) k_avg(KParams<T> P) {
     block_reduce<kAvgParts>(acc, red);
     if (threadIdx.x == 0) {
 #pragma unroll
-      for (int k = 0; k < kAvgParts; ++k) P.part[(long long)it * 16 + k] = acc[k];
+      for (int k = 0; k < kAvgParts; ++k) P.part[(long long)(d.plane0 + z) * 16 + k] = acc[k];
     }
   }
 }

@@ -177,11 +177,21 @@ static size_t plane_smem_bytes(int nx, int ny, int rch, int nphase) {
 }
 
 template <typename T>
-static size_t column_smem_bytes(int nx, int nz) {
-  const int nxh = nx / 2 + 1;
-  size_t o = sizeof(C2<T>) * 6 * (size_t)nz * nxh + sizeof(C2<T>) * nz + sizeof(int) * nz;
+static size_t column_smem_bytes(int colw, int nz) {
+  size_t o = sizeof(C2<T>) * 6 * (size_t)nz * colw + sizeof(C2<T>) * nz + sizeof(int) * nz;
   return (o + 15) & ~size_t(15);
 }
+
+// Launch classes: shared-memory footprints are rounded up to these sizes and
+// every class gets its own launch, so small subimages are not held to the
+// occupancy of the largest one.
+static size_t smem_bucket(size_t bytes) {
+  static const size_t kb[] = {12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 227};
+  for (size_t k : kb)
+    if (bytes <= k * 1024) return k * 1024;
+  return bytes;
+}
+constexpr int kRowsPerChunk = 8;
 
 // ---------------------------------------------------------------------------
 // The batched solver.
@@ -257,43 +267,17 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     budget = (size_t)((fr + have) * 0.75);
   }
 
-  // shared-memory limits: rows per chunk
-  int maxny = 0, maxnx = 0, maxnz = 0;
+  // shared memory: planes are processed kRowsPerChunk rows at a time, columns
+  // colw kx at a time; every box must fit the per-block limit
+  const int colw = (sizeof(T) == 4) ? 16 : 8;
   for (int b = 0; b < nbox; ++b) {
-    maxnx = std::max(maxnx, bdim[3 * b]);
-    maxny = std::max(maxny, bdim[3 * b + 1]);
-    maxnz = std::max(maxnz, bdim[3 * b + 2]);
-  }
-  int rch = 1;
-  size_t plane_smem = 0;
-  {
-    // largest rch (<= max ny) that fits every box of the request
-    int best = 0;
-    for (int r = maxny; r >= 1; --r) {
-      size_t need = 0;
-      for (int b = 0; b < nbox; ++b)
-        need = std::max(need, plane_smem_bytes<T>(bdim[3 * b], bdim[3 * b + 1], std::min(r, bdim[3 * b + 1]), nphase));
-      if (need <= c.smem_optin) {
-        best = r;
-        plane_smem = need;
-        break;
-      }
-      if (r > 8) r = std::max(9, r * 3 / 4 + 1);
-    }
-    if (best == 0) {
+    const int nx = bdim[3 * b], ny = bdim[3 * b + 1], nz = bdim[3 * b + 2];
+    if (plane_smem_bytes<T>(nx, ny, std::min(kRowsPerChunk, ny), nphase) > c.smem_optin ||
+        column_smem_bytes<T>(colw, nz) > c.smem_optin) {
       c.err = "plane too large for shared memory";
       return HH_ERR_UNSUPPORTED;
     }
-    rch = best;
   }
-  size_t col_smem = 0;
-  for (int b = 0; b < nbox; ++b)
-    col_smem = std::max(col_smem, column_smem_bytes<T>(bdim[3 * b], bdim[3 * b + 2]));
-  if (col_smem > c.smem_optin) {
-    c.err = "column too large for shared memory";
-    return HH_ERR_UNSUPPORTED;
-  }
-
   auto* kf_rhs = k_plane_fwd<T, MODE_RHS>;
   auto* kf_it = k_plane_fwd<T, MODE_ITER>;
   auto* kf_tr = k_plane_fwd<T, MODE_TRUE>;
@@ -304,9 +288,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   auto* ku = k_update<T>;
   auto* ka = k_avg<T>;
   for (const void* f : {(const void*)kf_rhs, (const void*)kf_it, (const void*)kf_tr, (const void*)ki_rhs,
-                        (const void*)ki_it, (const void*)ki_tr})
-    HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem));
-  HH_CK(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)col_smem));
+                        (const void*)ki_it, (const void*)ki_tr, (const void*)kc})
+    HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
   const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
 
   // lambda/mu table
@@ -331,6 +314,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     std::vector<Prob> probs(np);
     std::vector<BoxReq> wboxes(boxes_in.begin() + b0, boxes_in.begin() + b1);
     std::vector<int2> pitems, citems, gitems;
+    std::map<size_t, std::vector<int2>> pclass, cclass;  // launch classes by shared-memory size
     long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0;
     for (int b = 0; b < nb; ++b) {
       const BoxReq& B = wboxes[b];
@@ -362,14 +346,41 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
         d.fld_off = fld_off;
         d.spc_off = spc_off;
-        for (int k = 0; k < nz; ++k) pitems.push_back(make_int2(6 * b + a, k));
-        for (int k = 0; k < ny; ++k) citems.push_back(make_int2(6 * b + a, k));
+        const size_t pkey = smem_bucket(plane_smem_bytes<T>(nx, ny, std::min(kRowsPerChunk, ny), nphase));
+        const size_t ckey = smem_bucket(column_smem_bytes<T>(colw, nz));
+        std::vector<int2>& pc = pclass[pkey];
+        std::vector<int2>& cc = cclass[ckey];
+        for (int k = 0; k < nz; ++k) {
+          pitems.push_back(make_int2(6 * b + a, k));
+          pc.push_back(make_int2(6 * b + a, k));
+        }
+        for (int k = 0; k < ny; ++k)
+          for (int x0 = 0; x0 < nxh; x0 += colw) cc.push_back(make_int2(6 * b + a, k | (x0 << 16)));
         fld_off += 6 * V;
         spc_off += 6LL * nz * ny * nxh;
       }
       lab_off += V;
       c21_off += 21 * V;
     }
+    // class item lists, concatenated: plane classes first, then column classes
+    struct Cls {
+      size_t smem;
+      long long off;
+      int n;
+      int grid_f, grid_i;
+    };
+    std::vector<Cls> pcl, ccl;
+    citems.clear();
+    std::vector<int2> clsitems;
+    for (auto& kv : pclass) {
+      pcl.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0});
+      clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
+    }
+    for (auto& kv : cclass) {
+      ccl.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0});
+      clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
+    }
+    citems = clsitems;
     // ---- device buffers
     Prob* d_prob;
     PState* d_st;
@@ -430,7 +441,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kp.st = d_st;
     kp.medium = med.kind;
     kp.nyq_mode = o.nyquist;
-    kp.rch = rch;
+    kp.rch = kRowsPerChunk;
+    kp.colw = colw;
     kp.nphase = std::max(nphase, 1);
     kp.plans = (const AxisPlan*)c.d_plans.p;
     kp.tw = (const double*)c.d_tw.p;
@@ -448,24 +460,40 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kp.max_iter = o.max_iter;
     kp.fixed_iters = o.fixed_iters;
     kp.nprob = np;
-    KParams<T> kpp = kp, kpc = kp;
+    KParams<T> kpp = kp;
     kpp.items = d_pit;
     kpp.nitems = (int)pitems.size();
-    kpc.items = d_cit;
-    kpc.nitems = (int)citems.size();
-    const int gp_f = grid_for<T>(c, (const void*)kf_it, threads, plane_smem, kpp.nitems);
-    const int gp_i = grid_for<T>(c, (const void*)ki_it, threads, plane_smem, kpp.nitems);
-    const int gc = grid_for<T>(c, (const void*)kc, threads, col_smem, kpc.nitems);
+    for (Cls& k : pcl) {
+      k.grid_f = grid_for<T>(c, (const void*)kf_it, threads, k.smem, k.n);
+      k.grid_i = grid_for<T>(c, (const void*)ki_it, threads, k.smem, k.n);
+    }
+    for (Cls& k : ccl) k.grid_f = grid_for<T>(c, (const void*)kc, threads, k.smem, k.n);
+    auto cls_params = [&](const Cls& k) {
+      KParams<T> q = kp;
+      q.items = d_cit + k.off;
+      q.nitems = k.n;
+      return q;
+    };
+    // one launch per class for the plane and column passes
+    auto plane_pass = [&](auto kern, bool fwd) {
+      for (const Cls& k : pcl) {
+        ++c.launches;
+        kern<<<fwd ? k.grid_f : k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
+      }
+    };
+    auto column_pass = [&](int mode) {
+      for (const Cls& k : ccl) {
+        ++c.launches;
+        kc<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
+      }
+    };
     const int gu = grid_for<T>(c, (const void*)ku, threads, 0, kpp.nitems);
     const int gs = (np + 127) / 128;
 
     // ---- right-hand side b = -G*(C:E), r = p = b, x = 0
-    ++c.launches;
-    kf_rhs<<<gp_f, threads, plane_smem, c.st>>>(kpp);
-    ++c.launches;
-    kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_RHS);
-    ++c.launches;
-    ki_rhs<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+    plane_pass(kf_rhs, true);
+    column_pass(MODE_RHS);
+    plane_pass(ki_rhs, false);
     ++c.launches;
     k_scal_init<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, floor2);
     HH_CK(cudaGetLastError());
@@ -483,12 +511,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     };
     // true residual r = -G*(C:(E + x)) of the flagged problems
     auto true_pass = [&]() {
-      ++c.launches;
-      kf_tr<<<gp_f, threads, plane_smem, c.st>>>(kpp);
-      ++c.launches;
-      kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_TRUE);
-      ++c.launches;
-      ki_tr<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+      plane_pass(kf_tr, true);
+      column_pass(MODE_TRUE);
+      plane_pass(ki_tr, false);
     };
     // ---- iterations, in chunks captured as CUDA graphs; residual
     //      replacement at the end of every chunk (when enabled)
@@ -496,14 +521,11 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     auto launch_chunk = [&]() {
       for (int m = 0; m < chunk; ++m) {
         rec(m, 0);
-        ++c.launches;
-        kf_it<<<gp_f, threads, plane_smem, c.st>>>(kpp);
+        plane_pass(kf_it, true);
         rec(m, 1);
-        ++c.launches;
-        kc<<<gc, threads, col_smem, c.st>>>(kpc, MODE_ITER);
+        column_pass(MODE_ITER);
         rec(m, 2);
-        ++c.launches;
-        ki_it<<<gp_i, threads, plane_smem, c.st>>>(kpp);
+        plane_pass(ki_it, false);
         rec(m, 3);
         ++c.launches;
         k_scal_alpha<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np);
@@ -621,7 +643,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       }
       if (prof) {
         sampled_pending = true;
-        for (int k = 0; k < 4; ++k) c.prof[pnames[k]].launches += chunk;
+        const long long per[4] = {(long long)pcl.size(), (long long)ccl.size(), (long long)pcl.size(), 1};
+        for (int k = 0; k < 4; ++k) c.prof[pnames[k]].launches += chunk * per[k];
       }
       if (e != cudaSuccess) {
         c.err = std::string("launch: ") + cudaGetErrorString(e);
@@ -683,7 +706,9 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   int rch = ny;
   while (rch > 1 && plane_smem_bytes<T>(nx, ny, rch, nphase) > c.smem_optin) --rch;
   const size_t psm = plane_smem_bytes<T>(nx, ny, rch, nphase);
-  const size_t csm = column_smem_bytes<T>(nx, nz);
+  int colw = nxh;
+  while (colw > 1 && column_smem_bytes<T>(colw, nz) > c.smem_optin) colw = (colw + 1) / 2;
+  const size_t csm = column_smem_bytes<T>(colw, nz);
   if (psm > c.smem_optin || csm > c.smem_optin) {
     c.err = "plane too large for shared memory";
     return HH_ERR_UNSUPPORTED;
@@ -702,7 +727,8 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   d.pz = pz;
   std::vector<int2> pit, cit;
   for (int k = 0; k < nz; ++k) pit.push_back(make_int2(0, k));
-  for (int k = 0; k < ny; ++k) cit.push_back(make_int2(0, k));
+  for (int k = 0; k < ny; ++k)
+    for (int x0 = 0; x0 < nxh; x0 += colw) cit.push_back(make_int2(0, k | (x0 << 16)));
   Prob* d_prob;
   int2 *d_pit, *d_cit;
   T *d_p, *d_q, *d_c21 = nullptr, *d_lm;
@@ -746,6 +772,7 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   kp.medium = med.kind;
   kp.nyq_mode = o.nyquist;
   kp.rch = rch;
+  kp.colw = colw;
   kp.nphase = std::max(nphase, 1);
   kp.plans = (const AxisPlan*)c.d_plans.p;
   kp.tw = (const double*)c.d_tw.p;
@@ -763,7 +790,7 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   kpp.items = d_pit;
   kpp.nitems = nz;
   kpc.items = d_cit;
-  kpc.nitems = ny;
+  kpc.nitems = (int)cit.size();
   auto* kf = k_plane_fwd<T, MODE_APPLY>;
   auto* ki = k_plane_inv<T, MODE_APPLY>;
   auto* kc = k_column<T>;
@@ -773,7 +800,7 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   ++c.launches;
   kf<<<std::min(nz, 4 * c.nsm), 256, psm, c.st>>>(kpp);
   ++c.launches;
-  kc<<<std::min(ny, 4 * c.nsm), 256, csm, c.st>>>(kpc, MODE_APPLY);
+  kc<<<std::min((int)cit.size(), 4 * c.nsm), 256, csm, c.st>>>(kpc, MODE_APPLY);
   ++c.launches;
   ki<<<std::min(nz, 4 * c.nsm), 256, psm, c.st>>>(kpp);
   HH_CK(cudaGetLastError());
