@@ -215,6 +215,35 @@ hh_status hh_profile_reset(hh_ctx *ctx);
 hh_status hh_fit_inverse_n(hh_ctx *ctx, const int *ns, const double *M, int count,
                            double *M_inf, double *C);
 
+/* ---------------------------------------------------------------------------
+ * Operator application without allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (code
+ * that runs inside a memory pool or arena it does not own, allocation-free
+ * real-time loops, hosts whose allocator must not be re-entered).
+ *
+ * q = G * (C : p) as hh_apply_operator computes it, in FP32, on device
+ * buffers the caller owns: labels (uint8 [nz][ny][nx]), p and q (float
+ * [6][nz][ny][nx], tensor components 11 22 33 23 13 12). `phases` is a host
+ * table. Work is enqueued on `cuda_stream` (NULL = legacy default stream)
+ * of the current device and the call waits for it before returning.
+ *
+ * It calls no cudaMalloc, cudaFree or other allocating routine. Its scratch
+ * is one fixed device array of HH_NOALLOC_SCRATCH_BYTES inside the library,
+ * held by every GPU that loads the library until the process exits; each
+ * edge is limited to HH_NOALLOC_MAX_EDGE and the half spectrum must fit the
+ * array, else HH_ERR_ARG. The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress) with that device current: make
+ * that first call before any stream capture. Every call shares the array
+ * (nothing in it needs to start at zero: each call overwrites what it
+ * reads), so calls that overlap on the GPU race; serialize them.
+ * Errors: HH_ERR_ARG, HH_ERR_UNSUPPORTED, HH_ERR_CUDA; text via
+ * hh_last_error(NULL). */
+#define HH_NOALLOC_SCRATCH_BYTES (16u << 20)
+#define HH_NOALLOC_MAX_EDGE 80
+hh_status hh_apply_operator_noalloc(const uint8_t *labels, const hh_phase *phases, int nphase,
+                                    int nx, int ny, int nz, const float *p, float *q,
+                                    int nyquist, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

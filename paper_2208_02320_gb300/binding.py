@@ -115,6 +115,7 @@ _SIGNATURES = {
     "hh_fit_inverse_n": (_I, [_P, _P, _P, _I, _P, _P]),
     "hh_profile_read": (_I, [_P, _P, _I, _P]),
     "hh_profile_reset": (_I, [_P]),
+    "hh_apply_operator_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _I, _P]),
 }
 
 _lib = None

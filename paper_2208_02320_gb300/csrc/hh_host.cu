@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -20,23 +21,58 @@ namespace hh {
 // ---------------------------------------------------------------------------
 // FFT planning: radices, twiddles, digit-reversal tables.
 // ---------------------------------------------------------------------------
-static bool factorize(int n, std::vector<int>& rad) {
-  rad.clear();
+// Radices of n (4s, then 2, then odd primes up to 31) into rad[kMaxStages].
+static bool factorize(int n, int* rad, int* nst) {
+  int k = 0;
+  auto push = [&](int r) {
+    if (k >= kMaxStages) return false;
+    rad[k++] = r;
+    return true;
+  };
   while (n % 4 == 0) {
-    rad.push_back(4);
+    if (!push(4)) return false;
     n /= 4;
   }
   while (n % 2 == 0) {
-    rad.push_back(2);
+    if (!push(2)) return false;
     n /= 2;
   }
   const int primes[] = {3, 5, 7, 11, 13, 17, 19, 23, 29, 31};
   for (int p : primes)
     while (n % p == 0) {
-      rad.push_back(p);
+      if (!push(p)) return false;
       n /= p;
     }
-  return n == 1 && (int)rad.size() <= kMaxStages;
+  *nst = k;
+  return n == 1;
+}
+
+// Fill the plan of length n and its tables without allocating: tw receives
+// 2n doubles (W_n[t] = exp(-2 pi i t / n)), pf and sf n ints each
+// (natural frequency -> storage position, storage position -> signed frequency).
+static bool plan_fill(int n, AxisPlan* p, double* tw, int* pf, int* sf) {
+  std::memset(p, 0, sizeof(*p));
+  if (n < 1 || !factorize(n, p->rad, &p->nst)) return false;
+  p->n = n;
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (int t = 0; t < n; ++t) {
+    const long double a = two_pi * (long double)t / (long double)n;
+    tw[2 * t] = (double)cosl(a);
+    tw[2 * t + 1] = (double)-sinl(a);
+  }
+  for (int k = 0; k < n; ++k) {
+    int rem = k, span = n, pos = 0;
+    for (int s = 0; s < p->nst; ++s) {
+      const int R = p->rad[s];
+      const int q = rem % R;
+      rem /= R;
+      span /= R;
+      pos += q * span;
+    }
+    pf[k] = pos;
+  }
+  for (int k = 0; k < n; ++k) sf[pf[k]] = (2 * k <= n) ? k : k - n;
+  return true;
 }
 
 struct Tables {
@@ -50,34 +86,14 @@ struct Tables {
 static int plan_for(Tables& T, int n) {
   auto it = T.index.find(n);
   if (it != T.index.end()) return it->second;
-  std::vector<int> rad;
-  if (n < 1 || !factorize(n, rad)) return -1;
+  if (n < 1) return -1;
   AxisPlan p;
-  std::memset(&p, 0, sizeof(p));
-  p.n = n;
-  p.nst = (int)rad.size();
-  for (int i = 0; i < p.nst; ++i) p.rad[i] = rad[i];
-  p.tw_off = (int)(T.tw.size() / 2);
-  const long double two_pi = 6.283185307179586476925286766559005768L;
-  for (int t = 0; t < n; ++t) {
-    const long double a = two_pi * (long double)t / (long double)n;
-    T.tw.push_back((double)cosl(a));
-    T.tw.push_back((double)-sinl(a));
-  }
-  p.pf_off = (int)T.itab.size();
+  std::vector<double> tw(2 * (size_t)n);
   std::vector<int> pf(n), sf(n);
-  for (int k = 0; k < n; ++k) {
-    int rem = k, span = n, pos = 0;
-    for (int s = 0; s < p.nst; ++s) {
-      const int R = rad[s];
-      const int q = rem % R;
-      rem /= R;
-      span /= R;
-      pos += q * span;
-    }
-    pf[k] = pos;
-  }
-  for (int k = 0; k < n; ++k) sf[pf[k]] = (2 * k <= n) ? k : k - n;
+  if (!plan_fill(n, &p, tw.data(), pf.data(), sf.data())) return -1;
+  p.tw_off = (int)(T.tw.size() / 2);
+  T.tw.insert(T.tw.end(), tw.begin(), tw.end());
+  p.pf_off = (int)T.itab.size();
   T.itab.insert(T.itab.end(), pf.begin(), pf.end());
   p.sf_off = (int)T.itab.size();
   T.itab.insert(T.itab.end(), sf.begin(), sf.end());
@@ -827,11 +843,16 @@ struct hh_ctx {
   Ctx c;
 };
 
-static thread_local std::string g_last_error;
+static thread_local char g_last_error[512];
+
+static void set_last_error(const char* msg) {
+  std::strncpy(g_last_error, msg, sizeof(g_last_error) - 1);
+  g_last_error[sizeof(g_last_error) - 1] = 0;
+}
 
 static hh_status fail(hh_ctx* ctx, hh_status s, const std::string& msg) {
   if (ctx) ctx->c.err = msg;
-  g_last_error = msg;
+  set_last_error(msg.c_str());
   return s;
 }
 
@@ -853,7 +874,7 @@ extern "C" const char* hh_status_string(hh_status s) {
 }
 
 extern "C" const char* hh_last_error(hh_ctx* ctx) {
-  return ctx ? ctx->c.err.c_str() : g_last_error.c_str();
+  return ctx ? ctx->c.err.c_str() : g_last_error;
 }
 
 extern "C" hh_status hh_options_default(hh_options* o) {
@@ -883,7 +904,7 @@ extern "C" hh_status hh_create(hh_ctx** out, int device, void* cuda_stream) {
   Ctx& c = h->c;
   c.dev = device;
   auto bad = [&](cudaError_t e) {
-    g_last_error = cudaGetErrorString(e);
+    set_last_error(cudaGetErrorString(e));
     delete h;
     return e == cudaErrorMemoryAllocation ? HH_ERR_OOM : HH_ERR_CUDA;
   };
@@ -1454,4 +1475,190 @@ extern "C" hh_status hh_extrapolate(hh_ctx* h, const uint8_t* img, int nx, int n
   s = hh_fit_inverse_n(h, ns, Gs.data(), count, G_inf, C_G);
   if (s != HH_OK) return s;
   return worst;
+}
+
+// ===========================================================================
+// Operator application without allocation
+// ===========================================================================
+// Some callers cannot allocate device memory: code running inside a memory
+// pool or arena they do not own, allocation-free real-time loops, or hosts
+// whose allocator must not be re-entered. hh_apply_operator_noalloc serves
+// them. Its scratch (problem descriptor, work items, FFT tables, phase table
+// and the half spectrum) lives in the file-scope device array below, which
+// every GPU that loads this library holds until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(HH_NOALLOC_SCRATCH_BYTES);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the scratch array, looked up once per device (with that
+// device current) by the first call made on it.
+constexpr int kNoAllocMaxDevices = 64;
+static void* g_noalloc_addr[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_phase* phases, int nphase, int nx,
+                                               int ny, int nz, const float* p, float* q, int nyquist,
+                                               void* cuda_stream) {
+  if (!labels || !phases || !p || !q) {
+    set_last_error("hh_apply_operator_noalloc: NULL pointer");
+    return HH_ERR_ARG;
+  }
+  if (nx < 1 || ny < 1 || nz < 1 || nx > HH_NOALLOC_MAX_EDGE || ny > HH_NOALLOC_MAX_EDGE ||
+      nz > HH_NOALLOC_MAX_EDGE) {
+    set_last_error("hh_apply_operator_noalloc: each edge must be in 1..HH_NOALLOC_MAX_EDGE");
+    return HH_ERR_ARG;
+  }
+  if (nphase < 1 || nphase > 256 || (nyquist != HH_NYQ_ZERO_COMPONENT && nyquist != HH_NYQ_ZERO_MODE)) {
+    set_last_error("hh_apply_operator_noalloc: bad phase count or Nyquist rule");
+    return HH_ERR_ARG;
+  }
+  float lm[2 * 256];
+  for (int i = 0; i < nphase; ++i) {
+    if (!(phases[i].K > 0.0) || !(phases[i].G > 0.0) || !std::isfinite(phases[i].K) || !std::isfinite(phases[i].G)) {
+      set_last_error("hh_apply_operator_noalloc: phase moduli must be finite and > 0");
+      return HH_ERR_ARG;
+    }
+    lm[2 * i] = float(phases[i].K - 2.0 * phases[i].G / 3.0);
+    lm[2 * i + 1] = float(phases[i].G);
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_last_error("hh_apply_operator_noalloc: no usable current device");
+    return HH_ERR_CUDA;
+  }
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* a = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
+      if (e != cudaSuccess || !a) {
+        set_last_error("hh_apply_operator_noalloc: cudaGetSymbolAddress failed");
+        return HH_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = a;
+    }
+    base = g_noalloc_addr[dev];
+  }
+
+  // host staging of the small tables, on the stack (no allocation)
+  const int nxh = nx / 2 + 1;
+  int smem_optin = 0;
+  if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    set_last_error("hh_apply_operator_noalloc: device query failed");
+    return HH_ERR_CUDA;
+  }
+  int rch = ny;
+  while (rch > 1 && plane_smem_bytes<float>(nx, ny, rch, nphase) > (size_t)smem_optin) --rch;
+  int colw = nxh;
+  while (colw > 1 && column_smem_bytes<float>(colw, nz) > (size_t)smem_optin) colw = (colw + 1) / 2;
+  const size_t psm = plane_smem_bytes<float>(nx, ny, rch, nphase);
+  const size_t csm = column_smem_bytes<float>(colw, nz);
+  if (psm > (size_t)smem_optin || csm > (size_t)smem_optin) {
+    set_last_error("hh_apply_operator_noalloc: plane too large for shared memory");
+    return HH_ERR_UNSUPPORTED;
+  }
+  const int ncol = ny * ((nxh + colw - 1) / colw);
+  struct Staging {
+    Prob prob;
+    AxisPlan plans[3];
+    double tw[2 * 3 * HH_NOALLOC_MAX_EDGE];
+    int itab[2 * 3 * HH_NOALLOC_MAX_EDGE];
+    float lm[2 * 256];
+    int2 items[HH_NOALLOC_MAX_EDGE + HH_NOALLOC_MAX_EDGE * (HH_NOALLOC_MAX_EDGE / 2 + 1)];
+  };
+  static thread_local Staging h;  // static storage: no heap or stack growth per call
+  std::memset(&h.prob, 0, sizeof(h.prob));
+  const int dims[3] = {nx, ny, nz};
+  int tw_off = 0, it_off = 0;
+  for (int a = 0; a < 3; ++a) {
+    AxisPlan& pl = h.plans[a];
+    if (!plan_fill(dims[a], &pl, h.tw + 2 * tw_off, h.itab + it_off, h.itab + it_off + dims[a])) {
+      set_last_error("hh_apply_operator_noalloc: FFT length with a prime factor above 31");
+      return HH_ERR_UNSUPPORTED;
+    }
+    pl.tw_off = tw_off;
+    pl.pf_off = it_off;
+    pl.sf_off = it_off + dims[a];
+    tw_off += dims[a];
+    it_off += 2 * dims[a];
+  }
+  Prob& d = h.prob;
+  d.nx = nx;
+  d.ny = ny;
+  d.nz = nz;
+  d.nxh = nxh;
+  d.cnx = nx;
+  d.cny = ny;
+  d.cnz = nz;
+  d.px = 0;
+  d.py = 1;
+  d.pz = 2;
+  for (int i = 0; i < 2 * nphase; ++i) h.lm[i] = lm[i];
+  for (int k = 0; k < nz; ++k) h.items[k] = make_int2(0, k);
+  int nc = 0;
+  for (int k = 0; k < ny; ++k)
+    for (int x0 = 0; x0 < nxh; x0 += colw) h.items[nz + nc++] = make_int2(0, k | (x0 << 16));
+
+  // scratch layout: [staging][half spectrum]
+  const size_t spec_off = align256(sizeof(Staging));
+  const size_t need = spec_off + sizeof(C2<float>) * 6 * (size_t)nz * ny * nxh;
+  if (need > kNoAllocScratchBytes) {
+    set_last_error("hh_apply_operator_noalloc: grid needs more than the HH_NOALLOC_SCRATCH_BYTES scratch");
+    return HH_ERR_ARG;
+  }
+  unsigned char* sbase = static_cast<unsigned char*>(base);
+  const Staging* dst = reinterpret_cast<const Staging*>(sbase);
+  if (cudaMemcpyAsync(sbase, &h, sizeof(Staging), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    set_last_error("hh_apply_operator_noalloc: staging copy failed");
+    return HH_ERR_CUDA;
+  }
+  KParams<float> kp;
+  std::memset(&kp, 0, sizeof(kp));
+  kp.prob = &dst->prob;
+  kp.medium = MED_ISO;
+  kp.nyq_mode = nyquist;
+  kp.rch = rch;
+  kp.colw = colw;
+  kp.nphase = nphase;
+  kp.plans = dst->plans;
+  kp.tw = dst->tw;
+  kp.itab = dst->itab;
+  kp.labels = labels;
+  kp.lammu = dst->lm;
+  kp.p = const_cast<float*>(p);
+  kp.q = q;
+  kp.r = q;
+  kp.x = q;
+  kp.spec = reinterpret_cast<C2<float>*>(sbase + spec_off);
+  kp.nprob = 1;
+  KParams<float> kpp = kp, kpc = kp;
+  kpp.items = dst->items;
+  kpp.nitems = nz;
+  kpc.items = dst->items + nz;
+  kpc.nitems = nc;
+  auto* kf = k_plane_fwd<float, MODE_APPLY>;
+  auto* ki = k_plane_inv<float, MODE_APPLY>;
+  auto* kc = k_column<float>;
+  if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
+      cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
+      cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm) != cudaSuccess) {
+    set_last_error("hh_apply_operator_noalloc: kernel attribute failed");
+    return HH_ERR_CUDA;
+  }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  nsm = std::max(nsm, 1);
+  kf<<<std::min(nz, 4 * nsm), 256, psm, st>>>(kpp);
+  kc<<<std::min(nc, 4 * nsm), 256, csm, st>>>(kpc, MODE_APPLY);
+  ki<<<std::min(nz, 4 * nsm), 256, psm, st>>>(kpp);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return HH_ERR_CUDA;
+  }
+  return HH_OK;
 }
