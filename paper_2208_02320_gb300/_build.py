@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libhh.so")
 SOURCES = [os.path.join(HERE, "csrc", "hh_host.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("hh_device.cuh", "hh_post.cuh")] + [
+DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("hh_device.cuh", "hh_post.cuh", "hh_fft2.cuh", "hh_ctmath.h")] + [
     os.path.join(ROOT, "include", "hh.h")]
 
 NVCC_FLAGS = [

@@ -59,7 +59,9 @@ constexpr int kMaxRadix = 31;
 // One transform length. Twiddles W_n[t] = exp(-2 pi i t / n) live in a shared
 // table of doubles at tw_off; pos_of_freq (natural frequency -> storage
 // position after the forward transform) and sfreq (storage position -> signed
-// frequency in (-n/2, n/2]) live in an int table.
+// frequency in (-n/2, n/2]) live in an int table. Lengths with a two-pass plan
+// (hh_fft2.cuh) keep natural order, so both tables are the identity map and
+// the signed frequency; other lengths use the staged transform below.
 struct AxisPlan {
   int n;
   int nst;
@@ -67,7 +69,7 @@ struct AxisPlan {
   int tw_off;
   int pf_off;
   int sf_off;
-  int pad;
+  int split;  // N1 of the two-pass plan (natural order in and out), 0: staged
 };
 
 // One (subimage, load case) solve.
@@ -92,7 +94,8 @@ struct PState {
   double sbar[6];  // sum over the core of C:(E + eps*) (final pass)
   double resid;    // final ||b - A x|| / ||b|| from the true residual
   double rt_best;  // smallest true <r, r> seen at a checkpoint
-  int iters, active, status, trueflag, homog, restarts, stall, pad1;
+  int iters, active, status, trueflag, homog, restarts, stall;
+  int pending;     // r <- r - alpha q, x <- x + alpha p not yet applied
 };
 
 enum : int { MED_ISO = 0, MED_ANISO = 1 };
@@ -109,7 +112,7 @@ struct KParams {
   int nitems;
   int medium;         // MED_ISO / MED_ANISO
   int nyq_mode;       // 0 component rule, 1 mode rule
-  int rch;            // rows per chunk in the plane passes
+  int pad0;
   int nphase;
   const AxisPlan* plans;
   const double* tw;   // interleaved (re, im) twiddles
@@ -272,10 +275,19 @@ __device__ __noinline__ void fft_stage_generic(C2<T>* base, const Lines& L, int 
   }
 }
 
+}  // namespace hh
+
+#include "hh_fft2.cuh"
+
+namespace hh {
+
 // In-place transform of a set of lines in shared memory (all threads of the
-// block take part; ends with __syncthreads()).
+// block take part; ends with __syncthreads()): the two-pass plan when the
+// length has one, else the staged transform (digit-reversed order between
+// forward and inverse).
 template <typename T, bool INV>
 __device__ __noinline__ void fft_lines(C2<T>* base, const Lines L, const AxisPlan& pl, const C2<T>* tw) {
+  if (pl.split && fft2_dispatch<T, INV>(base, L, pl.n, tw)) return;
   const int N = pl.n;
   int spans[kMaxStages];
   int s = N;
@@ -407,28 +419,33 @@ __device__ __forceinline__ void load_tw(C2<T>* dst, const double* tw, const Axis
 
 __device__ __forceinline__ int odd_pitch(int n) { return n | 1; }
 
-// Shared-memory layout of the plane passes (must match plane_smem_bytes on the host).
+// Shared-memory layout of the plane passes (must match plane_smem_bytes on the
+// host). The whole plane lives in S as three blocks of ny "pair rows", one
+// block per component pair (2 c2, 2 c2 + 1), with an odd pitch RP >= nx + 2.
+// In real space a pair row holds the packed complex row s_(2c2) + i s_(2c2+1)
+// (nx entries); after the x transform and the unpack it holds the two half
+// spectra [A_0 .. A_(nxh-1) | B_0 .. B_(nxh-1)], and the y transforms run
+// down its columns.
 template <typename T>
 struct PlaneSmem {
-  C2<T>* S;    // 6 * ny * nxh (component-major, rows of nxh)
-  C2<T>* Z;    // 3 * rch * PX
-  C2<T>* twx;  // nx
-  C2<T>* twy;  // ny
-  int* pfx;    // nx
-  T* lm;       // 2 * nphase
-  double* red; // 32 * 16
+  C2<T>* S;     // 3 * ny * RP
+  C2<T>* twx;   // nx
+  C2<T>* twy;   // ny
+  int* pfx;     // nx
+  T* lm;        // 2 * nphase
+  double* red;  // 32 * 4
 };
 
+__device__ __forceinline__ int pair_pitch(int nx) { return (nx + 2) | 1; }
+
 template <typename T>
-__device__ __forceinline__ PlaneSmem<T> plane_layout(char* base, int nx, int ny, int nxh, int rch, int nphase) {
+__device__ __forceinline__ PlaneSmem<T> plane_layout(char* base, int nx, int ny, int nphase) {
   PlaneSmem<T> s;
   size_t o = 0;
   s.red = reinterpret_cast<double*>(base + o);
-  o += 32 * 16 * sizeof(double);
+  o += 32 * 4 * sizeof(double);
   s.S = reinterpret_cast<C2<T>*>(base + o);
-  o += sizeof(C2<T>) * 6 * ny * nxh;
-  s.Z = reinterpret_cast<C2<T>*>(base + o);
-  o += sizeof(C2<T>) * 3 * rch * odd_pitch(nx);
+  o += sizeof(C2<T>) * 3 * ny * pair_pitch(nx);
   s.twx = reinterpret_cast<C2<T>*>(base + o);
   o += sizeof(C2<T>) * nx;
   s.twy = reinterpret_cast<C2<T>*>(base + o);
@@ -439,9 +456,107 @@ __device__ __forceinline__ PlaneSmem<T> plane_layout(char* base, int nx, int ny,
   return s;
 }
 
+// x-line and y-line views of the pair-row plane.
+__device__ __forceinline__ Lines plane_rows(int ny, int RP) { return Lines{3 * ny, 1 << 30, 0, RP, 1, false}; }
+__device__ __forceinline__ Lines plane_cols(int ny, int nxh, int RP) {
+  return Lines{6 * nxh, 2 * nxh, ny * RP, 1, RP, true};
+}
+// Position in S of spectrum component c at (ky position, kx).
+__device__ __forceinline__ int plane_spec_at(int c, int ky, int kx, int ny, int nxh, int RP) {
+  return ((c >> 1) * ny + ky) * RP + (c & 1) * nxh + kx;
+}
+
+constexpr int kPackPerThread = 4;
+
+// Split every transformed packed row Z = A + iB (A, B spectra of real rows)
+// into [A | B] in place, in rounds of whole rows (reads, barrier, writes).
+template <typename T>
+__device__ __forceinline__ void unpack_rows(C2<T>* S, int nrows, int RP, int nx, int nxh, const int* pfx) {
+  const int rpr = max(1, (kPackPerThread * (int)blockDim.x) / nxh);
+  for (int r0 = 0; r0 < nrows; r0 += rpr) {
+    const int tot = min(rpr, nrows - r0) * nxh;
+    C2<T> A[kPackPerThread], B[kPackPerThread];
+    int o[kPackPerThread];
+#pragma unroll
+    for (int i = 0; i < kPackPerThread; ++i) {
+      const int e = threadIdx.x + i * blockDim.x;
+      o[i] = -1;
+      if (e < tot) {
+        const int rr = e / nxh;
+        const int k = e - rr * nxh;
+        const C2<T>* R = S + (r0 + rr) * RP;
+        const C2<T> a = R[pfx[k]];
+        const C2<T> b = R[pfx[k == 0 ? 0 : nx - k]];
+        A[i] = mk<T>(T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y));
+        B[i] = mk<T>(T(0.5) * (a.y + b.y), T(-0.5) * (a.x - b.x));
+        o[i] = (r0 + rr) * RP + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPackPerThread; ++i)
+      if (o[i] >= 0) {
+        S[o[i]] = A[i];
+        S[o[i] + nxh] = B[i];
+      }
+    __syncthreads();
+  }
+}
+
+// Inverse of unpack_rows: [A | B] -> A + iB over the full row with the
+// Hermitian extension, at the transform's input positions pfx[k].
+template <typename T>
+__device__ __forceinline__ void pack_rows(C2<T>* S, int nrows, int RP, int nx, int nxh, const int* pfx) {
+  const int rpr = max(1, (kPackPerThread * (int)blockDim.x) / nx);
+  for (int r0 = 0; r0 < nrows; r0 += rpr) {
+    const int tot = min(rpr, nrows - r0) * nx;
+    C2<T> Z[kPackPerThread];
+    int o[kPackPerThread];
+#pragma unroll
+    for (int i = 0; i < kPackPerThread; ++i) {
+      const int e = threadIdx.x + i * blockDim.x;
+      o[i] = -1;
+      if (e < tot) {
+        const int rr = e / nx;
+        const int k = e - rr * nx;
+        const C2<T>* R = S + (r0 + rr) * RP;
+        C2<T> A, B;
+        if (k < nxh) {
+          A = R[k];
+          B = R[nxh + k];
+        } else {
+          A = R[nx - k];
+          B = R[nxh + nx - k];
+          A.y = -A.y;
+          B.y = -B.y;
+        }
+        Z[i] = mk<T>(A.x - B.y, A.y + B.x);
+        o[i] = (r0 + rr) * RP + pfx[k];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kPackPerThread; ++i)
+      if (o[i] >= 0) S[o[i]] = Z[i];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void plane_tables(const KParams<T>& P, const PlaneSmem<T>& sm, const AxisPlan& ax,
+                                             const AxisPlan& ay, int nx) {
+  load_tw<T>(sm.twx, P.tw, ax);
+  load_tw<T>(sm.twy, P.tw, ay);
+  for (int t = threadIdx.x; t < nx; t += blockDim.x) sm.pfx[t] = P.itab[ax.pf_off + t];
+  if (P.medium == MED_ISO)
+    for (int t = threadIdx.x; t < 2 * P.nphase; t += blockDim.x) sm.lm[t] = P.lammu[t];
+}
+
 // Plane pass (forward): constitutive law fused into the x and y transforms.
 //   MODE_RHS  : tau = C : E (E = unit load of the problem); partial <tau, tau>_F
-//   MODE_ITER : p <- r + beta p (stored), tau = C : p
+//   MODE_ITER : the deferred CG update of the previous iteration (when
+//               pending) r <- r - alpha q, x <- x + alpha p, then
+//               p <- r + beta p (all stored), tau = C : p; partial <r, r>_F
 //   MODE_TRUE : tau = C : (E + x)  (true residual r = -G*tau follows)
 //   MODE_APPLY: tau = C : p (p read only)
 // ---------------------------------------------------------------------------
@@ -461,109 +576,93 @@ __global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
     const Prob d = P.prob[w.x];
     const int z = w.y;
     const int nx = d.nx, ny = d.ny, nxh = d.nxh;
-    const int rch = min(P.rch, ny);
-    const int PX = odd_pitch(nx);
+    const int RP = pair_pitch(nx);
     const long long V = (long long)nx * ny * d.nz;
-    PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, nxh, rch, P.nphase);
+    PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, P.nphase);
     const AxisPlan ax = P.plans[d.px];
     const AxisPlan ay = P.plans[d.py];
-    load_tw<T>(sm.twx, P.tw, ax);
-    load_tw<T>(sm.twy, P.tw, ay);
-    for (int t = threadIdx.x; t < nx; t += blockDim.x) sm.pfx[t] = P.itab[ax.pf_off + t];
-    if (P.medium == MED_ISO)
-      for (int t = threadIdx.x; t < 2 * P.nphase; t += blockDim.x) sm.lm[t] = P.lammu[t];
-    const T beta = (MODE == MODE_ITER) ? T(P.st[w.x].beta) : T(0);
+    plane_tables<T>(P, sm, ax, ay, nx);
+    T alpha = T(0), beta = T(0);
+    bool pend = false;
+    if (MODE == MODE_ITER) {
+      const PState& s = P.st[w.x];
+      alpha = T(s.alpha);
+      beta = T(s.beta);
+      pend = s.pending != 0;
+    }
     __syncthreads();
 
     double acc[1] = {0.0};
     T* rr = P.r + d.fld_off;
     T* pp = P.p + d.fld_off;
-    const T* xx = P.x + d.fld_off;
+    T* xx = P.x + d.fld_off;
+    const T* qq = P.q + d.fld_off;
     const long long zoff = (long long)z * ny * nx;
     const T Ed = d.lc < 3 ? T(1) : T(0.5);
-
-    for (int y0 = 0; y0 < ny; y0 += rch) {
-      const int nr = min(rch, ny - y0);
-      // voxel phase: stress of the chunk rows into Z (pairs of components packed as complex)
-      for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
-        const int yy = v / nx;
-        const int x = v - yy * nx;
-        const int y = y0 + yy;
-        const long long vo = zoff + (long long)y * nx + x;
-        T e[6];
-        if (MODE == MODE_RHS) {
+    // voxel phase: stress of the whole plane into the pair rows
+    for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
+      const int y = v / nx;
+      const int x = v - y * nx;
+      const long long vo = zoff + v;
+      T e[6];
+      if (MODE == MODE_RHS) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) e[c] = T(0);
-          e[d.lc] = Ed;
-        } else if (MODE == MODE_ITER) {
+        for (int c = 0; c < 6; ++c) e[c] = T(0);
+        e[d.lc] = Ed;
+      } else if (MODE == MODE_ITER) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const T pv = rr[c * V + vo] + beta * pp[c * V + vo];
-            pp[c * V + vo] = pv;
-            e[c] = pv;
+        for (int c = 0; c < 6; ++c) {
+          const long long o = c * V + vo;
+          T rv = rr[o];
+          const T pv = pp[o];
+          if (pend) {
+            rv -= alpha * qq[o];
+            rr[o] = rv;
+            xx[o] = xx[o] + alpha * pv;
           }
-        } else if (MODE == MODE_TRUE) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
-          e[d.lc] += Ed;
-        } else {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
+          const T pn = rv + beta * pv;
+          pp[o] = pn;
+          e[c] = pn;
+          acc[0] += frob_w(c) * double(rv) * double(rv);
         }
-        T s[6];
-        if (P.medium == MED_ISO) {
-          const int lab = P.labels[d.med_off + vo];
-          stress_iso<T>(e, sm.lm[2 * lab], sm.lm[2 * lab + 1], s);
-        } else {
-          stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
-        }
-        if (MODE == MODE_RHS) {
+      } else if (MODE == MODE_TRUE) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) acc[0] += frob_w(c) * double(s[c]) * double(s[c]);
-        }
+        for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
+        e[d.lc] += Ed;
+      } else {
 #pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) sm.Z[(c2 * rch + yy) * PX + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
+        for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
       }
-      __syncthreads();
-      // x transforms of the packed rows
-      Lines Lx{3 * rch, 1 << 30, 0, PX, 1, false};
-      if (nr < rch) {
-        // ragged last chunk: only rows < nr of each component pair are valid
-        Lx.n = 3 * nr;
-        Lx.lpg = nr;
-        Lx.gstride = rch * PX;
+      T s[6];
+      if (P.medium == MED_ISO) {
+        const int lab = P.labels[d.med_off + vo];
+        stress_iso<T>(e, sm.lm[2 * lab], sm.lm[2 * lab + 1], s);
+      } else {
+        stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
       }
-      fft_lines<T, false>(sm.Z, Lx, ax, sm.twx);
-      // unpack the two real spectra of every packed row into S
-      for (int e = threadIdx.x; e < 3 * nr * nxh; e += blockDim.x) {
-        const int k = e % nxh;
-        const int l = e / nxh;
-        const int c2 = l / nr;
-        const int yy = l - c2 * nr;
-        const C2<T>* row = sm.Z + (c2 * rch + yy) * PX;
-        const C2<T> a = row[sm.pfx[k]];
-        const C2<T> b = row[sm.pfx[k == 0 ? 0 : nx - k]];
-        const C2<T> A = mk<T>(T(0.5) * (a.x + b.x), T(0.5) * (a.y - b.y));
-        const C2<T> B = mk<T>(T(0.5) * (a.y + b.y), T(-0.5) * (a.x - b.x));
-        sm.S[((2 * c2) * ny + y0 + yy) * nxh + k] = A;
-        sm.S[((2 * c2 + 1) * ny + y0 + yy) * nxh + k] = B;
+      if (MODE == MODE_RHS) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) acc[0] += frob_w(c) * double(s[c]) * double(s[c]);
       }
-      __syncthreads();
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * ny + y) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
     }
-    // y transforms of all 6 * nxh columns
-    Lines Ly{6 * nxh, nxh, ny * nxh, 1, nxh, true};
-    fft_lines<T, false>(sm.S, Ly, ay, sm.twy);
+    __syncthreads();
+    fft_lines<T, false>(sm.S, plane_rows(ny, RP), ax, sm.twx);
+    unpack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
+    fft_lines<T, false>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
     // store the plane of the spectrum: spec[c][z][kyp][kx]
     C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
     for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
       const int c = e / pl;
       const int rem = e - c * pl;
-      sp[((long long)c * d.nz + z) * pl + rem] = sm.S[e];
+      const int ky = rem / nxh;
+      sp[((long long)c * d.nz + z) * pl + rem] = sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)];
     }
-    if (MODE == MODE_RHS) {
+    if (MODE == MODE_RHS || MODE == MODE_ITER) {
       block_reduce<1>(acc, sm.red);
-      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 0] = acc[0];
+      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + (MODE == MODE_RHS ? 0 : 13)] = acc[0];
     }
     __syncthreads();
   }
@@ -640,7 +739,8 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
 // ---------------------------------------------------------------------------
 // Plane pass (inverse): inverse y and complex-to-real x transforms.
 //   MODE_RHS  : r = p = -q, x = 0, partial <r, r>_F
-//   MODE_ITER : store q, partial <p, q>_F
+//   MODE_ITER : store q; partials <p, q>_F, <r, q>_F, <q, q>_F (the next
+//               <r, r> follows from them without another pass)
 //   MODE_TRUE : r = -q (true residual), partial <r, r>_F
 //   MODE_APPLY: store q
 // ---------------------------------------------------------------------------
@@ -653,114 +753,95 @@ __global__ void __launch_bounds__(256) k_plane_inv(KParams<T> P) {
     const Prob d = P.prob[w.x];
     const int z = w.y;
     const int nx = d.nx, ny = d.ny, nxh = d.nxh;
-    const int rch = min(P.rch, ny);
-    const int PX = odd_pitch(nx);
+    const int RP = pair_pitch(nx);
     const long long V = (long long)nx * ny * d.nz;
-    PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, nxh, rch, P.nphase);
+    PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, P.nphase);
     const AxisPlan ax = P.plans[d.px];
     const AxisPlan ay = P.plans[d.py];
-    load_tw<T>(sm.twx, P.tw, ax);
-    load_tw<T>(sm.twy, P.tw, ay);
-    for (int t = threadIdx.x; t < nx; t += blockDim.x) sm.pfx[t] = P.itab[ax.pf_off + t];
+    plane_tables<T>(P, sm, ax, ay, nx);
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
     for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
       const int c = e / pl;
       const int rem = e - c * pl;
-      sm.S[e] = sp[((long long)c * d.nz + z) * pl + rem];
+      const int ky = rem / nxh;
+      sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)] = sp[((long long)c * d.nz + z) * pl + rem];
     }
     __syncthreads();
-    Lines Ly{6 * nxh, nxh, ny * nxh, 1, nxh, true};
-    fft_lines<T, true>(sm.S, Ly, ay, sm.twy);
+    fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
+    pack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
+    fft_lines<T, true>(sm.S, plane_rows(ny, RP), ax, sm.twx);
 
-    double acc[1] = {0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     const T invV = T(1) / T(V);
     T* rr = P.r + d.fld_off;
     T* pp = P.p + d.fld_off;
     T* qq = P.q + d.fld_off;
     T* xx = P.x + d.fld_off;
     const long long zoff = (long long)z * ny * nx;
-    for (int y0 = 0; y0 < ny; y0 += rch) {
-      const int nr = min(rch, ny - y0);
-      // pack A + iB with the Hermitian extension, into digit-reversed positions
-      for (int e = threadIdx.x; e < 3 * nr * nx; e += blockDim.x) {
-        const int k = e % nx;
-        const int l = e / nx;
-        const int c2 = l / nr;
-        const int yy = l - c2 * nr;
-        const int y = y0 + yy;
-        C2<T> A, B;
-        if (k < nxh) {
-          A = sm.S[((2 * c2) * ny + y) * nxh + k];
-          B = sm.S[((2 * c2 + 1) * ny + y) * nxh + k];
-        } else {
-          A = sm.S[((2 * c2) * ny + y) * nxh + (nx - k)];
-          B = sm.S[((2 * c2 + 1) * ny + y) * nxh + (nx - k)];
-          A.y = -A.y;
-          B.y = -B.y;
-        }
-        sm.Z[(c2 * rch + yy) * PX + sm.pfx[k]] = mk<T>(A.x - B.y, A.y + B.x);
-      }
-      __syncthreads();
-      Lines Lx{3 * rch, 1 << 30, 0, PX, 1, false};
-      if (nr < rch) {
-        Lx.n = 3 * nr;
-        Lx.lpg = nr;
-        Lx.gstride = rch * PX;
-      }
-      fft_lines<T, true>(sm.Z, Lx, ax, sm.twx);
-      for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
-        const int yy = v / nx;
-        const int x = v - yy * nx;
-        const long long vo = zoff + (long long)(y0 + yy) * nx + x;
-        T qv[6];
+    for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
+      const int y = v / nx;
+      const int x = v - y * nx;
+      const long long vo = zoff + v;
+      T qv[6];
 #pragma unroll
-        for (int c2 = 0; c2 < 3; ++c2) {
-          const C2<T> zz = sm.Z[(c2 * rch + yy) * PX + x];
-          qv[2 * c2] = zz.x * invV;
-          qv[2 * c2 + 1] = zz.y * invV;
-        }
-        if (MODE == MODE_RHS || MODE == MODE_TRUE) {
+      for (int c2 = 0; c2 < 3; ++c2) {
+        const C2<T> zz = sm.S[(c2 * ny + y) * RP + x];
+        qv[2 * c2] = zz.x * invV;
+        qv[2 * c2 + 1] = zz.y * invV;
+      }
+      if (MODE == MODE_RHS || MODE == MODE_TRUE) {
 #pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            const T rv = -qv[c];
-            rr[c * V + vo] = rv;
-            if (MODE == MODE_RHS) {
-              pp[c * V + vo] = rv;
-              xx[c * V + vo] = T(0);
-            }
-            acc[0] += frob_w(c) * double(rv) * double(rv);
+        for (int c = 0; c < 6; ++c) {
+          const T rv = -qv[c];
+          rr[c * V + vo] = rv;
+          if (MODE == MODE_RHS) {
+            pp[c * V + vo] = rv;
+            xx[c * V + vo] = T(0);
           }
-        } else if (MODE == MODE_ITER) {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) {
-            qq[c * V + vo] = qv[c];
-            acc[0] += frob_w(c) * double(pp[c * V + vo]) * double(qv[c]);
-          }
-        } else {
-#pragma unroll
-          for (int c = 0; c < 6; ++c) qq[c * V + vo] = qv[c];
+          acc[0] += frob_w(c) * double(rv) * double(rv);
         }
+      } else if (MODE == MODE_ITER) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const long long o = c * V + vo;
+          qq[o] = qv[c];
+          const double wq = frob_w(c) * double(qv[c]);
+          acc[0] += wq * double(pp[o]);
+          acc[1] += wq * double(rr[o]);
+          acc[2] += wq * double(qv[c]);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) qq[c * V + vo] = qv[c];
       }
-      __syncthreads();
     }
-    if (MODE != MODE_APPLY) {
-      block_reduce<1>(acc, sm.red);
-      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 12] = acc[0];
+    if (MODE == MODE_ITER) {
+      block_reduce<3>(acc, sm.red);
+      if (threadIdx.x == 0) {
+        double* pt = P.part + (long long)(d.plane0 + z) * 16;
+        pt[12] = acc[0];
+        pt[14] = acc[1];
+        pt[15] = acc[2];
+      }
+    } else if (MODE != MODE_APPLY) {
+      double a1[1] = {acc[0]};
+      block_reduce<1>(a1, sm.red);
+      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 12] = a1[0];
     }
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
-// CG update on one plane: r <- r - alpha q, x <- x + alpha p, partial <r, r>_F.
+// Deferred CG update of the problems that have one pending (before the true
+// residual, the averages, or a restart): r <- r - alpha q, x <- x + alpha p.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_update(KParams<T> P) {
-  __shared__ double red[32];
+__global__ void __launch_bounds__(256) k_flush(KParams<T> P) {
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
-    if (!P.st[w.x].active) continue;
+    if (!P.st[w.x].pending) continue;
     const Prob d = P.prob[w.x];
     const int z = w.y;
     const long long V = (long long)d.nx * d.ny * d.nz;
@@ -771,17 +852,12 @@ __global__ void __launch_bounds__(256) k_update(KParams<T> P) {
     T* xx = P.x + o0;
     const T* qq = P.q + o0;
     const T* pp = P.p + o0;
-    double acc[1] = {0.0};
-    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
-      const int c = e / pl;
-      const long long o = c * V + (e - c * pl);
-      const T rv = rr[o] - alpha * qq[o];
-      rr[o] = rv;
-      xx[o] = xx[o] + alpha * pp[o];
-      acc[0] += frob_w(c) * double(rv) * double(rv);
-    }
-    block_reduce<1>(acc, red);
-    if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 13] = acc[0];
+    for (int c = 0; c < 6; ++c)
+      for (int e = threadIdx.x; e < pl; e += blockDim.x) {
+        const long long o = c * V + e;
+        rr[o] = rr[o] - alpha * qq[o];
+        xx[o] = xx[o] + alpha * pp[o];
+      }
   }
 }
 
@@ -872,7 +948,7 @@ __global__ void k_scal_init(const Prob* prob, PState* st, const double* part, in
   s.homog = 0;
   s.restarts = 0;
   s.stall = 0;
-  s.pad1 = 0;
+  s.pending = 0;
   s.rt_best = rho;
   if (!isfinite(rho) || !isfinite(tt)) {
     s.active = 0;
@@ -884,12 +960,27 @@ __global__ void k_scal_init(const Prob* prob, PState* st, const double* part, in
   st[i] = s;
 }
 
-__global__ void k_scal_alpha(const Prob* prob, PState* st, const double* part, int nprob) {
+// One CG step after the inverse plane pass of iteration k. The plane passes
+// left <r_k, r_k> (slot 13, from the r that the forward pass formed), <p, q>,
+// <r, q> and <q, q> (slots 12, 14, 15). Then
+//   alpha = <r, r> / <p, q>,
+//   <r', r'> = <r, r> - 2 alpha <r, q> + alpha^2 <q, q>   (r' = r - alpha q),
+//   beta = <r', r'> / <r, r>,
+// and the vector updates r', x + alpha p are deferred to the next forward
+// plane pass (pending = 1). <r, r> comes from the stored r every iteration,
+// so the expansion does not accumulate rounding across iterations.
+__global__ void k_scal_step(const Prob* prob, PState* st, const double* part, int nprob, double tol,
+                            int max_iter, int fixed_iters) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nprob || !st[i].active) return;
-  const double pq = sum_parts(part, prob[i], 12);
+  const Prob d = prob[i];
   PState& s = st[i];
-  if (!isfinite(pq)) {
+  s.pending = 0;  // the forward pass of this iteration applied the previous update
+  const double rr = sum_parts(part, d, 13);
+  const double pq = sum_parts(part, d, 12);
+  const double rq = sum_parts(part, d, 14);
+  const double qq = sum_parts(part, d, 15);
+  if (!isfinite(rr) || !isfinite(pq) || !isfinite(rq) || !isfinite(qq)) {
     s.active = 0;
     s.status = ST_NONFINITE;
     return;
@@ -900,30 +991,27 @@ __global__ void k_scal_alpha(const Prob* prob, PState* st, const double* part, i
     s.active = 0;
     return;
   }
-  s.alpha = s.rho / pq;
+  const double alpha = rr / pq;
+  double rn = rr - 2.0 * alpha * rq + alpha * alpha * qq;
+  if (rn < 0.0) rn = 0.0;
+  s.alpha = alpha;
+  s.pending = 1;
+  s.iters += 1;
+  const bool conv = fixed_iters > 0 ? (s.iters >= fixed_iters) : (sqrt(rn) <= tol * sqrt(s.rho0));
+  s.rho_prev = rr;
+  s.rho = rn;
+  if (conv || rn == 0.0 || s.iters >= max_iter) {
+    s.active = 0;
+    if (!conv && rn != 0.0) s.status = ST_NOT_CONVERGED;
+    return;
+  }
+  s.beta = rn / rr;
 }
 
-__global__ void k_scal_beta(const Prob* prob, PState* st, const double* part, int nprob, double tol,
-                            int max_iter, int fixed_iters) {
+// After k_flush: no update is pending any more.
+__global__ void k_scal_clear(PState* st, int nprob) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nprob || !st[i].active) return;
-  const double rr = sum_parts(part, prob[i], 13);
-  PState& s = st[i];
-  s.iters += 1;
-  if (!isfinite(rr)) {
-    s.active = 0;
-    s.status = ST_NONFINITE;
-    return;
-  }
-  const bool conv = fixed_iters > 0 ? (s.iters >= fixed_iters) : (sqrt(rr) <= tol * sqrt(s.rho0));
-  s.rho_prev = s.rho;
-  s.rho = rr;
-  if (conv || rr == 0.0 || s.iters >= max_iter) {
-    s.active = 0;
-    if (!conv && rr != 0.0) s.status = ST_NOT_CONVERGED;
-    return;
-  }
-  s.beta = rr / s.rho_prev;
+  if (i < nprob) st[i].pending = 0;
 }
 
 // which = 0: flag the active problems (residual replacement);

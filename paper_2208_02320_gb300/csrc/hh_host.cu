@@ -54,11 +54,20 @@ static bool plan_fill(int n, AxisPlan* p, double* tw, int* pf, int* sf) {
   std::memset(p, 0, sizeof(*p));
   if (n < 1 || !factorize(n, p->rad, &p->nst)) return false;
   p->n = n;
+  p->split = fft2_split(n);
   const long double two_pi = 6.283185307179586476925286766559005768L;
   for (int t = 0; t < n; ++t) {
     const long double a = two_pi * (long double)t / (long double)n;
     tw[2 * t] = (double)cosl(a);
     tw[2 * t + 1] = (double)-sinl(a);
+  }
+  if (p->split) {
+    // two-pass plan: natural order in and out
+    for (int k = 0; k < n; ++k) {
+      pf[k] = k;
+      sf[k] = (2 * k <= n) ? k : k - n;
+    }
+    return true;
   }
   for (int k = 0; k < n; ++k) {
     int rem = k, span = n, pos = 0;
@@ -180,11 +189,9 @@ static hh_status upload_tables(Ctx& c) {
 }
 
 template <typename T>
-static size_t plane_smem_bytes(int nx, int ny, int rch, int nphase) {
-  const int nxh = nx / 2 + 1;
-  size_t o = 32 * 16 * sizeof(double);
-  o += sizeof(C2<T>) * 6 * (size_t)ny * nxh;
-  o += sizeof(C2<T>) * 3 * (size_t)rch * (nx | 1);
+static size_t plane_smem_bytes(int nx, int ny, int nphase) {
+  size_t o = 32 * 4 * sizeof(double);
+  o += sizeof(C2<T>) * 3 * (size_t)ny * (size_t)((nx + 2) | 1);
   o += sizeof(C2<T>) * (size_t)nx;
   o += sizeof(C2<T>) * (size_t)ny;
   o += sizeof(int) * (size_t)((nx + 3) & ~3);
@@ -207,7 +214,6 @@ static size_t smem_bucket(size_t bytes) {
     if (bytes <= k * 1024) return k * 1024;
   return bytes;
 }
-constexpr int kRowsPerChunk = 8;
 
 // ---------------------------------------------------------------------------
 // The batched solver.
@@ -283,12 +289,12 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     budget = (size_t)((fr + have) * 0.75);
   }
 
-  // shared memory: planes are processed kRowsPerChunk rows at a time, columns
-  // colw kx at a time; every box must fit the per-block limit
+  // shared memory: a whole plane per plane-pass block, colw kx columns per
+  // column-pass block; every box must fit the per-block limit
   const int colw = (sizeof(T) == 4) ? 16 : 8;
   for (int b = 0; b < nbox; ++b) {
     const int nx = bdim[3 * b], ny = bdim[3 * b + 1], nz = bdim[3 * b + 2];
-    if (plane_smem_bytes<T>(nx, ny, std::min(kRowsPerChunk, ny), nphase) > c.smem_optin ||
+    if (plane_smem_bytes<T>(nx, ny, nphase) > c.smem_optin ||
         column_smem_bytes<T>(colw, nz) > c.smem_optin) {
       c.err = "plane too large for shared memory";
       return HH_ERR_UNSUPPORTED;
@@ -301,7 +307,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   auto* ki_it = k_plane_inv<T, MODE_ITER>;
   auto* ki_tr = k_plane_inv<T, MODE_TRUE>;
   auto* kc = k_column<T>;
-  auto* ku = k_update<T>;
+  auto* ku = k_flush<T>;
   auto* ka = k_avg<T>;
   for (const void* f : {(const void*)kf_rhs, (const void*)kf_it, (const void*)kf_tr, (const void*)ki_rhs,
                         (const void*)ki_it, (const void*)ki_tr, (const void*)kc})
@@ -362,7 +368,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
         d.fld_off = fld_off;
         d.spc_off = spc_off;
-        const size_t pkey = smem_bucket(plane_smem_bytes<T>(nx, ny, std::min(kRowsPerChunk, ny), nphase));
+        const size_t pkey = smem_bucket(plane_smem_bytes<T>(nx, ny, nphase));
         const size_t ckey = smem_bucket(column_smem_bytes<T>(colw, nz));
         std::vector<int2>& pc = pclass[pkey];
         std::vector<int2>& cc = cclass[ckey];
@@ -457,7 +463,6 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kp.st = d_st;
     kp.medium = med.kind;
     kp.nyq_mode = o.nyquist;
-    kp.rch = kRowsPerChunk;
     kp.colw = colw;
     kp.nphase = std::max(nphase, 1);
     kp.plans = (const AxisPlan*)c.d_plans.p;
@@ -516,7 +521,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
 
     // profiling: events around the field kernels of the first iteration of every chunk
     const bool prof = o.profile != 0;
-    cudaEvent_t pev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
     if (prof)
       for (auto& e : pev) HH_CK(cudaEventCreate(&e));
     // external record nodes, so that the events are timed inside graph replays
@@ -524,6 +529,13 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       if (prof && m == 0) {
         if (cudaEventRecordWithFlags(pev[k], c.st, cudaEventRecordExternal) != cudaSuccess) (void)cudaGetLastError();
       }
+    };
+    // apply the deferred CG updates of every problem that has one
+    auto flush = [&]() {
+      ++c.launches;
+      ku<<<gu, threads, 0, c.st>>>(kpp);
+      ++c.launches;
+      k_scal_clear<<<gs, 128, 0, c.st>>>(d_st, np);
     };
     // true residual r = -G*(C:(E + x)) of the flagged problems
     auto true_pass = [&]() {
@@ -544,15 +556,10 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         plane_pass(ki_it, false);
         rec(m, 3);
         ++c.launches;
-        k_scal_alpha<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np);
-        rec(m, 4);
-        ++c.launches;
-        ku<<<gu, threads, 0, c.st>>>(kpp);
-        rec(m, 5);
-        ++c.launches;
-        k_scal_beta<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
+        k_scal_step<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
       }
       if (replace) {
+        flush();
         ++c.launches;
         k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 0);
         true_pass();
@@ -590,9 +597,11 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     // four field kernels: every field value read or written once
     const double Tb = sizeof(T);
     const double lab_b = (med.kind == MED_ISO) ? 1.0 : 21.0 * Tb;
-    const char* pnames[4] = {"plane_fwd", "column", "plane_inv", "update"};
-    const double pa[4] = {18.0 * Tb + lab_b, 0.0, 12.0 * Tb, 36.0 * Tb};
-    const double pb[4] = {2.0 * Tb, 4.0 * Tb, 2.0 * Tb, 0.0};
+    // (plane_fwd: r, q, p, x read, r, x, p written, label, half spectrum
+    // written; plane_inv: half spectrum read, p, r read, q written)
+    const char* pnames[3] = {"plane_fwd", "column", "plane_inv"};
+    const double pa[3] = {42.0 * Tb + lab_b, 0.0, 18.0 * Tb};
+    const double pb[3] = {2.0 * Tb, 4.0 * Tb, 2.0 * Tb};
     unsigned long long* h_vs = reinterpret_cast<unsigned long long*>(c.h_dbl);
     double act_v = 0.0, act_s = 0.0;
     bool sampled_pending = false;
@@ -604,8 +613,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       cudaError_t e = cudaStreamSynchronize(c.st);
       *out = c.h_int[0];
       if (e == cudaSuccess && prof && sampled_pending) {
-        const int pairs[4][2] = {{0, 1}, {1, 2}, {2, 3}, {4, 5}};
-        for (int k = 0; k < 4; ++k) {
+        const int pairs[3][2] = {{0, 1}, {1, 2}, {2, 3}};
+        for (int k = 0; k < 3; ++k) {
           float ms = 0.f;
           if (cudaEventElapsedTime(&ms, pev[pairs[k][0]], pev[pairs[k][1]]) == cudaSuccess) {
             Ctx::KStat& ks = c.prof[pnames[k]];
@@ -635,6 +644,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       if (nact == 0) {
         // every problem stopped on its recursive residual: check the true one
         if (final_rounds > o.max_restarts) break;
+        flush();
         ++c.launches;
         k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 1);
         true_pass();
@@ -659,8 +669,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       }
       if (prof) {
         sampled_pending = true;
-        const long long per[4] = {(long long)pcl.size(), (long long)ccl.size(), (long long)pcl.size(), 1};
-        for (int k = 0; k < 4; ++k) c.prof[pnames[k]].launches += chunk * per[k];
+        const long long per[3] = {(long long)pcl.size(), (long long)ccl.size(), (long long)pcl.size()};
+        for (int k = 0; k < 3; ++k) c.prof[pnames[k]].launches += chunk * per[k];
       }
       if (e != cudaSuccess) {
         c.err = std::string("launch: ") + cudaGetErrorString(e);
@@ -676,6 +686,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
 
     // ---- core averages from x
     {
+      flush();
       const int ga = grid_for<T>(c, (const void*)ka, threads, 0, kpp.nitems);
       ++c.launches;
       ka<<<ga, threads, 0, c.st>>>(kpp);
@@ -719,9 +730,7 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   const int nphase = (int)med.lam.size();
   const long long V = (long long)nx * ny * nz;
   const int nxh = nx / 2 + 1;
-  int rch = ny;
-  while (rch > 1 && plane_smem_bytes<T>(nx, ny, rch, nphase) > c.smem_optin) --rch;
-  const size_t psm = plane_smem_bytes<T>(nx, ny, rch, nphase);
+  const size_t psm = plane_smem_bytes<T>(nx, ny, nphase);
   int colw = nxh;
   while (colw > 1 && column_smem_bytes<T>(colw, nz) > c.smem_optin) colw = (colw + 1) / 2;
   const size_t csm = column_smem_bytes<T>(colw, nz);
@@ -787,7 +796,6 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   kp.prob = d_prob;
   kp.medium = med.kind;
   kp.nyq_mode = o.nyquist;
-  kp.rch = rch;
   kp.colw = colw;
   kp.nphase = std::max(nphase, 1);
   kp.plans = (const AxisPlan*)c.d_plans.p;
@@ -1550,11 +1558,9 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
     set_last_error("hh_apply_operator_noalloc: device query failed");
     return HH_ERR_CUDA;
   }
-  int rch = ny;
-  while (rch > 1 && plane_smem_bytes<float>(nx, ny, rch, nphase) > (size_t)smem_optin) --rch;
   int colw = nxh;
   while (colw > 1 && column_smem_bytes<float>(colw, nz) > (size_t)smem_optin) colw = (colw + 1) / 2;
-  const size_t psm = plane_smem_bytes<float>(nx, ny, rch, nphase);
+  const size_t psm = plane_smem_bytes<float>(nx, ny, nphase);
   const size_t csm = column_smem_bytes<float>(colw, nz);
   if (psm > (size_t)smem_optin || csm > (size_t)smem_optin) {
     set_last_error("hh_apply_operator_noalloc: plane too large for shared memory");
@@ -1620,7 +1626,6 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
   kp.prob = &dst->prob;
   kp.medium = MED_ISO;
   kp.nyq_mode = nyquist;
-  kp.rch = rch;
   kp.colw = colw;
   kp.nphase = nphase;
   kp.plans = dst->plans;
