@@ -1,5 +1,11 @@
-"""Compile libhh (the CUDA sources under csrc/) in-tree for sm_103a with nvcc."""
+"""Compile libhh (the CUDA sources under csrc/) in-tree for sm_103a with nvcc.
 
+The translation units are compiled in parallel as relocatable device code and
+linked into one shared library: the host/kernel unit hh_host.cu, and the
+two-pass transform table hh_fft2_inst.cu once per (precision, direction).
+"""
+
+import concurrent.futures
 import os
 import shutil
 import subprocess
@@ -7,15 +13,21 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libhh.so")
-SOURCES = [os.path.join(HERE, "csrc", "hh_host.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("hh_device.cuh", "hh_post.cuh", "hh_fft2.cuh", "hh_ctmath.h")] + [
-    os.path.join(ROOT, "include", "hh.h")]
+CSRC = os.path.join(HERE, "csrc")
+BUILD_DIR = os.path.join(HERE, "_build")
 
-NVCC_FLAGS = [
-    "-gencode", "arch=compute_103a,code=sm_103a",
-    "-O3", "-lineinfo", "-std=c++17",
-    "-Xcompiler", "-fPIC", "-shared",
-]
+# (source, object name, extra flags)
+UNITS = [("hh_host.cu", "hh_host.o", [])] + [
+    ("hh_fft2_inst.cu", "hh_fft2_%s.o" % name, ["-DHH_FFT2_T=%s" % t, "-DHH_FFT2_INV=%d" % inv,
+                                                  "-DHH_FFT2_NAME=fft2_%s" % name])
+    for name, t, inv in (("f32_fwd", "float", 0), ("f32_inv", "float", 1), ("f64_fwd", "double", 0),
+                         ("f64_inv", "double", 1))]
+DEPS = [os.path.join(CSRC, f) for f in ("hh_host.cu", "hh_fft2_inst.cu", "hh_device.cuh", "hh_post.cuh",
+                                        "hh_fftcore.cuh", "hh_fft2.cuh", "hh_ctmath.h")] + [
+    os.path.join(ROOT, "include", "hh.h"), os.path.abspath(__file__)]
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC"]
 
 
 def nvcc_path() -> str:
@@ -32,17 +44,34 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in DEPS)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def _run(cmd, verbose):
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + res.stdout + res.stderr)
+    return res.stdout + res.stderr
+
+
+def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     """Build libhh.so next to this file; returns its path."""
     if not force and up_to_date():
         return LIB
-    tmp = LIB + ".tmp"
-    cmd = [nvcc_path(), *NVCC_FLAGS, "-I" + os.path.join(ROOT, "include"), "-o", tmp, *SOURCES]
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    nvcc = nvcc_path()
+    inc = "-I" + os.path.join(ROOT, "include")
+    cmds, objs = [], []
+    for src, obj, flags in UNITS:
+        o = os.path.join(BUILD_DIR, obj)
+        objs.append(o)
+        cmds.append([nvcc, *NVCC_FLAGS, *extra, *flags, inc, "-c", "-o", o, os.path.join(CSRC, src)])
+    with concurrent.futures.ThreadPoolExecutor(max_workers=len(cmds)) as ex:
+        outs = [f.result() for f in [ex.submit(_run, c, verbose) for c in cmds]]
     if verbose:
-        print(" ".join(cmd))
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + res.stdout + res.stderr)
+        for out in outs:
+            print(out)
+    tmp = LIB + ".tmp"
+    _run([nvcc, *ARCH, "-rdc=true", "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs], verbose)
     os.replace(tmp, LIB)
     return LIB
 

@@ -149,6 +149,8 @@ def options(**kw) -> Options:
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp32": HH_FP32, "fp64": HH_FP64}[v]
+        if k == "scheme" and isinstance(v, str):
+            v = {"cg": HH_CG, "basic": HH_BASIC}[v]
         if k == "nyquist" and isinstance(v, str):
             v = {"component": HH_NYQ_ZERO_COMPONENT, "mode": HH_NYQ_ZERO_MODE}[v]
         setattr(o, k, v)

@@ -20,38 +20,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "hh_fftcore.cuh"
+
 namespace hh {
-
-template <typename T>
-struct alignas(2 * sizeof(T)) C2 {
-  T x, y;
-};
-
-template <typename T>
-__host__ __device__ __forceinline__ C2<T> mk(T a, T b) {
-  C2<T> r;
-  r.x = a;
-  r.y = b;
-  return r;
-}
-template <typename T>
-__device__ __forceinline__ C2<T> cadd(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T>
-__device__ __forceinline__ C2<T> csub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
-template <typename T>
-__device__ __forceinline__ C2<T> cmul(C2<T> a, C2<T> b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// a * conj(b)
-template <typename T>
-__device__ __forceinline__ C2<T> cmulc(C2<T> a, C2<T> b) {
-  return mk<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
-}
-// multiply by -i (forward) or +i (inverse)
-template <typename T, bool INV>
-__device__ __forceinline__ C2<T> rot(C2<T> a) {
-  return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
-}
 
 constexpr int kMaxStages = 16;
 constexpr int kMaxRadix = 31;
@@ -99,7 +70,7 @@ struct PState {
 };
 
 enum : int { MED_ISO = 0, MED_ANISO = 1 };
-enum : int { MODE_RHS = 0, MODE_ITER = 1, MODE_APPLY = 2, MODE_TRUE = 3 };
+enum : int { MODE_RHS = 0, MODE_ITER = 1, MODE_APPLY = 2, MODE_TRUE = 3, MODE_BASIC = 4 };
 enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NONFINITE = 2 };
 
 constexpr int kAvgParts = 12;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
@@ -132,65 +103,12 @@ struct KParams {
   int fixed_iters;
   int nprob;
   int colw;          // kx columns per column-pass item
+  // basic scheme: Green operator of the isotropic reference medium,
+  // Gamma0 = g0a (n (x) v + v (x) n) - g0b (n . v) n (x) n, v = tau n
+  T g0a, g0b;
+  double* cpart;     // per column item: sum h |P tau|^2_F, then Re tau^(0) (6)
 };
 
-// ---------------------------------------------------------------------------
-// Small DFTs of size R on registers (forward: exp(-2 pi i rq / R)).
-// ---------------------------------------------------------------------------
-template <typename T, int R, bool INV>
-__device__ __forceinline__ void small_dft(C2<T>* a, const C2<T>* tw, int N) {
-  if constexpr (R == 2) {
-    C2<T> t = a[0];
-    a[0] = cadd(t, a[1]);
-    a[1] = csub(t, a[1]);
-  } else if constexpr (R == 3) {
-    const T h = T(0.86602540378443864676);  // sqrt(3)/2
-    C2<T> s = cadd(a[1], a[2]);
-    C2<T> d = csub(a[1], a[2]);
-    C2<T> m = mk<T>(a[0].x - T(0.5) * s.x, a[0].y - T(0.5) * s.y);
-    a[0] = cadd(a[0], s);
-    // -i h d (forward) / +i h d (inverse)
-    C2<T> t = rot<T, INV>(mk<T>(h * d.x, h * d.y));
-    a[1] = cadd(m, t);
-    a[2] = csub(m, t);
-  } else if constexpr (R == 4) {
-    C2<T> s02 = cadd(a[0], a[2]);
-    C2<T> d02 = csub(a[0], a[2]);
-    C2<T> s13 = cadd(a[1], a[3]);
-    C2<T> d13 = rot<T, INV>(csub(a[1], a[3]));
-    a[0] = cadd(s02, s13);
-    a[2] = csub(s02, s13);
-    a[1] = cadd(d02, d13);
-    a[3] = csub(d02, d13);
-  } else {
-    C2<T> y[R];
-    const int st = N / R;
-#pragma unroll
-    for (int q = 0; q < R; ++q) {
-      C2<T> acc = a[0];
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C2<T> w = tw[((r * q) % R) * st];
-        if (INV) w.y = -w.y;
-        acc = cadd(acc, cmul(a[r], w));
-      }
-      y[q] = acc;
-    }
-#pragma unroll
-    for (int q = 0; q < R; ++q) a[q] = y[q];
-  }
-}
-
-// Lines addressed as off(l) = (l / lpg) * gstride + (l % lpg) * lstride, element
-// k of a line at off(l) + k * es.
-struct Lines {
-  int n;       // number of lines
-  int lpg;     // lines per group
-  int gstride;
-  int lstride;
-  int es;
-  bool fast;   // adjacent threads take adjacent lines (column access)
-};
 
 template <typename T, int R, bool INV>
 __device__ void fft_stage(C2<T>* base, const Lines& L, int N, int span, const C2<T>* tw) {
@@ -379,6 +297,33 @@ __device__ __forceinline__ void stress_aniso(const T (&e)[6], const T* c21, long
   }
 }
 
+// a (n_i v_j + v_i n_j) - b n_i n_j (n . v), v = t n, of one mode (6 complex
+// tensor components, in place); zero where the wave vector vanishes.
+template <typename T>
+__device__ __forceinline__ void green_mode(C2<T> (&t)[6], T x0, T x1, T x2, T a, T b) {
+  const T nn = x0 * x0 + x1 * x1 + x2 * x2;
+  if (!(nn > T(0))) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) t[c] = mk<T>(T(0), T(0));
+    return;
+  }
+  const T inv = T(1) / sqrt(nn);
+  const T n[3] = {x0 * inv, x1 * inv, x2 * inv};
+  // tensor: 0=11 1=22 2=33 3=23 4=13 5=12; (i, j) of each stored component
+  const int ci[6] = {0, 1, 2, 1, 0, 0}, cj[6] = {0, 1, 2, 2, 2, 1};
+  C2<T> v[3];
+  v[0] = mk<T>(t[0].x * n[0] + t[5].x * n[1] + t[4].x * n[2], t[0].y * n[0] + t[5].y * n[1] + t[4].y * n[2]);
+  v[1] = mk<T>(t[5].x * n[0] + t[1].x * n[1] + t[3].x * n[2], t[5].y * n[0] + t[1].y * n[1] + t[3].y * n[2]);
+  v[2] = mk<T>(t[4].x * n[0] + t[3].x * n[1] + t[2].x * n[2], t[4].y * n[0] + t[3].y * n[1] + t[2].y * n[2]);
+  const C2<T> sv = mk<T>(n[0] * v[0].x + n[1] * v[1].x + n[2] * v[2].x, n[0] * v[0].y + n[1] * v[1].y + n[2] * v[2].y);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const T ni = n[ci[c]], nj = n[cj[c]];
+    const C2<T> vi = v[ci[c]], vj = v[cj[c]];
+    t[c] = mk<T>(a * (ni * vj.x + vi.x * nj) - b * ni * nj * sv.x, a * (ni * vj.y + vi.y * nj) - b * ni * nj * sv.y);
+  }
+}
+
 // Projection of one mode (6 complex tensor components, in place).
 template <typename T>
 __device__ __forceinline__ void project_mode(C2<T> (&t)[6], T x0, T x1, T x2) {
@@ -559,10 +504,12 @@ __device__ __forceinline__ void plane_tables(const KParams<T>& P, const PlaneSme
 //               p <- r + beta p (all stored), tau = C : p; partial <r, r>_F
 //   MODE_TRUE : tau = C : (E + x)  (true residual r = -G*tau follows)
 //   MODE_APPLY: tau = C : p (p read only)
+//   MODE_BASIC: the pending fixed-point update x <- x - q, then
+//               tau = C : (E + x)  (basic scheme; x holds eps - E)
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ bool skip_problem(const PState* st, int pr, int mode) {
-  if (mode == MODE_ITER) return !st[pr].active;
+  if (mode == MODE_ITER || mode == MODE_BASIC) return !st[pr].active;
   if (mode == MODE_TRUE) return !st[pr].trueflag;
   return false;
 }
@@ -584,7 +531,7 @@ __global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
     plane_tables<T>(P, sm, ax, ay, nx);
     T alpha = T(0), beta = T(0);
     bool pend = false;
-    if (MODE == MODE_ITER) {
+    if (MODE == MODE_ITER || MODE == MODE_BASIC) {
       const PState& s = P.st[w.x];
       alpha = T(s.alpha);
       beta = T(s.beta);
@@ -629,6 +576,18 @@ __global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
         e[d.lc] += Ed;
+      } else if (MODE == MODE_BASIC) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+          const long long o = c * V + vo;
+          T xv = xx[o];
+          if (pend) {
+            xv -= qq[o];
+            xx[o] = xv;
+          }
+          e[c] = xv;
+        }
+        e[d.lc] += Ed;
       } else {
 #pragma unroll
         for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
@@ -672,9 +631,14 @@ __global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
 // Column pass: z transform, projection, inverse z transform for one ky.
 // `skip_mode` selects which problems take part (as in the plane passes).
 // ---------------------------------------------------------------------------
+//   skip_mode == MODE_BASIC: the basic scheme's step instead of the
+//   projection: the mode becomes Gamma0 tau, and the item leaves the partial
+//   sum of h |P tau|^2_F (h = 2 for the kx that stand for a conjugate pair)
+//   and, from the zero mode, Re tau^(0) for the equilibrium residual.
 template <typename T>
 __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
+  __shared__ double red[32 * 7];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
@@ -703,6 +667,7 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
     // projection of every (kz, kx) mode of this ky
     const int my = P.itab[ay.sf_off + kyp];
     const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
+    double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int e = threadIdx.x; e < nz * W; e += blockDim.x) {
       const int kxl = e % W;
       const int kx = kx0 + kxl;
@@ -721,9 +686,34 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
       C2<T> t[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) t[c] = tile[(c * nz + kzp) * W + kxl];
-      project_mode<T>(t, x0, x1, x2);
+      if (skip_mode == MODE_BASIC) {
+        C2<T> pt[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pt[c] = t[c];
+        project_mode<T>(pt, x0, x1, x2);
+        const double h = (kx == 0 || 2 * kx == nx) ? 1.0 : 2.0;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          acc[0] += h * frob_w(c) * (double(pt[c].x) * double(pt[c].x) + double(pt[c].y) * double(pt[c].y));
+        if (kx == 0 && my == 0 && mz == 0) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c) acc[1 + c] += double(t[c].x);
+        }
+        green_mode<T>(t, x0, x1, x2, P.g0a, P.g0b);
+      } else {
+        project_mode<T>(t, x0, x1, x2);
+      }
 #pragma unroll
       for (int c = 0; c < 6; ++c) tile[(c * nz + kzp) * W + kxl] = t[c];
+    }
+    if (skip_mode == MODE_BASIC) {
+      block_reduce<7>(acc, red);
+      if (threadIdx.x == 0) {
+        const int nxb = (nxh + P.colw - 1) / P.colw;
+        double* cp = P.cpart + (long long)(d.col0 + kyp * nxb + kx0 / P.colw) * 8;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) cp[k] = acc[k];
+      }
     }
     __syncthreads();
     fft_lines<T, true>(tile, Lz, az, twz);
@@ -742,7 +732,7 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
 //   MODE_ITER : store q; partials <p, q>_F, <r, q>_F, <q, q>_F (the next
 //               <r, r> follows from them without another pass)
 //   MODE_TRUE : r = -q (true residual), partial <r, r>_F
-//   MODE_APPLY: store q
+//   MODE_APPLY, MODE_BASIC: store q
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256) k_plane_inv(KParams<T> P) {
@@ -824,7 +814,7 @@ __global__ void __launch_bounds__(256) k_plane_inv(KParams<T> P) {
         pt[14] = acc[1];
         pt[15] = acc[2];
       }
-    } else if (MODE != MODE_APPLY) {
+    } else if (MODE != MODE_APPLY && MODE != MODE_BASIC) {
       double a1[1] = {acc[0]};
       block_reduce<1>(a1, sm.red);
       if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 12] = a1[0];
@@ -1006,6 +996,58 @@ __global__ void k_scal_step(const Prob* prob, PState* st, const double* part, in
     return;
   }
   s.beta = rn / rr;
+}
+
+// Basic scheme: fresh state, x = eps - E = 0 (set by the host).
+__global__ void k_scal_basic_init(PState* st, int nprob) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob) return;
+  PState s;
+  memset(&s, 0, sizeof(s));
+  s.rho0 = 1.0;
+  s.active = 1;
+  st[i] = s;
+}
+
+// Basic scheme, after the column pass of iteration k: the equilibrium
+// residual ||G*sigma|| / ||<sigma>|| (Frobenius norms over the box; by
+// Parseval sum h |P sigma^|^2 / sum_c w_c (Re sigma^_c(0))^2) of the current
+// strain decides; otherwise the update x <- x - Gamma0 * sigma that the
+// inverse pass stored in q is applied by the next forward pass.
+__global__ void k_scal_basic(const Prob* prob, PState* st, const double* cpart, int nprob, int colw, double tol,
+                             int max_iter, int fixed_iters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nprob || !st[i].active) return;
+  const Prob d = prob[i];
+  PState& s = st[i];
+  s.pending = 0;
+  const int nxb = (d.nxh + colw - 1) / colw;
+  const int n = d.ny * nxb;
+  double eq = 0.0, m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int j = 0; j < n; ++j) {
+    const double* cp = cpart + (long long)(d.col0 + j) * 8;
+    eq += cp[0];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) m[c] += cp[1 + c];
+  }
+  double den = 0.0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) den += frob_w(c) * m[c] * m[c];
+  const double res = den > 0.0 ? sqrt(eq / den) : 0.0;
+  if (!isfinite(res)) {
+    s.active = 0;
+    s.status = ST_NONFINITE;
+    return;
+  }
+  s.resid = res;
+  const bool stop = fixed_iters > 0 ? (s.iters >= fixed_iters) : (res <= tol);
+  if (stop || s.iters >= max_iter) {
+    s.active = 0;
+    if (!stop) s.status = ST_NOT_CONVERGED;
+    return;
+  }
+  s.iters += 1;
+  s.pending = 1;
 }
 
 // After k_flush: no update is pending any more.

@@ -11,12 +11,13 @@
 // (t1 k2 < N, no reduction needed). Each pass reads all of a round's elements
 // before any is written (a barrier between, and a round never splits a line),
 // so the transform is in place. Inverse transforms (INV) conjugate every
-// factor. Included by hh_device.cuh after the Lines and small_dft definitions.
+// factor.
 #pragma once
 
 #include <type_traits>
 
 #include "hh_ctmath.h"
+#include "hh_fftcore.cuh"
 
 namespace hh {
 
@@ -222,19 +223,21 @@ __device__ __noinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>*
   }
 }
 
-// Two-pass transform of length n if it has a plan; false otherwise (nothing done).
+// Two-pass transform of length n if it has a plan; false otherwise (nothing
+// done). One definition per (precision, direction), each instantiating the
+// whole table, lives in its own relocatable object (hh_fft2_inst.cu, built
+// four times) so the large instantiation set compiles in parallel.
+__device__ bool fft2_f32_fwd(C2<float>* base, const Lines L, int n, const C2<float>* tw);
+__device__ bool fft2_f32_inv(C2<float>* base, const Lines L, int n, const C2<float>* tw);
+__device__ bool fft2_f64_fwd(C2<double>* base, const Lines L, int n, const C2<double>* tw);
+__device__ bool fft2_f64_inv(C2<double>* base, const Lines L, int n, const C2<double>* tw);
+
 template <typename T, bool INV>
-__device__ __noinline__ bool fft2_dispatch(C2<T>* base, const Lines L, int n, const C2<T>* tw) {
-  switch (n) {
-#define HH_F2_CALL(N, A, B)                 \
-  case N:                                   \
-    fft2_lines<T, A, B, INV>(base, L, tw); \
-    return true;
-    HH_FFT2_TABLE(HH_F2_CALL)
-#undef HH_F2_CALL
-    default:
-      return false;
-  }
+__device__ __forceinline__ bool fft2_dispatch(C2<T>* base, const Lines L, int n, const C2<T>* tw) {
+  if constexpr (sizeof(T) == 4)
+    return INV ? fft2_f32_inv(base, L, n, tw) : fft2_f32_fwd(base, L, n, tw);
+  else
+    return INV ? fft2_f64_inv(base, L, n, tw) : fft2_f64_fwd(base, L, n, tw);
 }
 
 }  // namespace hh

@@ -309,8 +309,10 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   auto* kc = k_column<T>;
   auto* ku = k_flush<T>;
   auto* ka = k_avg<T>;
+  auto* kf_b = k_plane_fwd<T, MODE_BASIC>;
+  auto* ki_b = k_plane_inv<T, MODE_BASIC>;
   for (const void* f : {(const void*)kf_rhs, (const void*)kf_it, (const void*)kf_tr, (const void*)ki_rhs,
-                        (const void*)ki_it, (const void*)ki_tr, (const void*)kc})
+                        (const void*)ki_it, (const void*)ki_tr, (const void*)kc, (const void*)kf_b, (const void*)ki_b})
     HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
   const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
 
@@ -324,6 +326,18 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   if ((s = ensure(c, "lammu", lm.size() * sizeof(T), (void**)&d_lm)) != HH_OK) return s;
   HH_CK(cudaMemcpyAsync(d_lm, lm.data(), lm.size() * sizeof(T), cudaMemcpyHostToDevice, c.st));
 
+  // basic scheme: isotropic reference medium, given or the means of the
+  // extreme phase values of lambda and mu
+  const bool basic = o.scheme == HH_BASIC;
+  double lam0 = o.ref_lambda, mu0 = o.ref_mu;
+  if (basic && !(mu0 > 0.0 && lam0 + 2.0 * mu0 / 3.0 > 0.0)) {
+    if (med.kind != MED_ISO || nphase < 1) {
+      c.err = "the basic scheme on an anisotropic medium needs ref_lambda and ref_mu";
+      return HH_ERR_UNSUPPORTED;
+    }
+    lam0 = 0.5 * (*std::min_element(med.lam.begin(), med.lam.end()) + *std::max_element(med.lam.begin(), med.lam.end()));
+    mu0 = 0.5 * (*std::min_element(med.mu.begin(), med.mu.end()) + *std::max_element(med.mu.begin(), med.mu.end()));
+  }
   const double floor2 = (sizeof(T) == 4) ? 1e-12 : 1e-28;
   int b0 = 0;
   while (b0 < nbox) {
@@ -337,7 +351,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     std::vector<BoxReq> wboxes(boxes_in.begin() + b0, boxes_in.begin() + b1);
     std::vector<int2> pitems, citems, gitems;
     std::map<size_t, std::vector<int2>> pclass, cclass;  // launch classes by shared-memory size
-    long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0;
+    long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0, ccount = 0;
     for (int b = 0; b < nb; ++b) {
       const BoxReq& B = wboxes[b];
       const int nx = bdim[3 * (b0 + b)], ny = bdim[3 * (b0 + b) + 1], nz = bdim[3 * (b0 + b) + 2];
@@ -364,7 +378,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.lc = a;
         d.box = b0 + b;
         d.plane0 = (int)pitems.size();
-        d.col0 = (int)citems.size();
+        d.col0 = (int)ccount;
+        ccount += (long long)ny * ((nxh + colw - 1) / colw);
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
         d.fld_off = fld_off;
         d.spc_off = spc_off;
@@ -425,6 +440,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     if ((s = ensure(c, "x", fld_off * sizeof(T), (void**)&d_x)) != HH_OK) return s;
     if ((s = ensure(c, "spec", spc_off * sizeof(C2<T>), (void**)&d_spec)) != HH_OK) return s;
     if ((s = ensure(c, "part", pitems.size() * 16 * sizeof(double), (void**)&d_part)) != HH_OK) return s;
+    double* d_cpart = nullptr;
+    if (basic && (s = ensure(c, "cpart", std::max<long long>(ccount, 1) * 8 * sizeof(double), (void**)&d_cpart)) != HH_OK)
+      return s;
     if ((s = ensure(c, "flag", 64, (void**)&d_flag)) != HH_OK) return s;
     HH_CK(cudaMemcpyAsync(d_prob, probs.data(), np * sizeof(Prob), cudaMemcpyHostToDevice, c.st));
     HH_CK(cudaMemcpyAsync(d_pit, pitems.data(), pitems.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st));
@@ -480,6 +498,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kp.tol = o.tol;
     kp.max_iter = o.max_iter;
     kp.fixed_iters = o.fixed_iters;
+    kp.g0a = T(1.0 / (2.0 * mu0));
+    kp.g0b = T((lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0)));
+    kp.cpart = d_cpart;
     kp.nprob = np;
     KParams<T> kpp = kp;
     kpp.items = d_pit;
@@ -511,182 +532,250 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     const int gu = grid_for<T>(c, (const void*)ku, threads, 0, kpp.nitems);
     const int gs = (np + 127) / 128;
 
-    // ---- right-hand side b = -G*(C:E), r = p = b, x = 0
-    plane_pass(kf_rhs, true);
-    column_pass(MODE_RHS);
-    plane_pass(ki_rhs, false);
-    ++c.launches;
-    k_scal_init<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, floor2);
-    HH_CK(cudaGetLastError());
-
-    // profiling: events around the field kernels of the first iteration of every chunk
-    const bool prof = o.profile != 0;
-    cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
-    if (prof)
-      for (auto& e : pev) HH_CK(cudaEventCreate(&e));
-    // external record nodes, so that the events are timed inside graph replays
-    auto rec = [&](int m, int k) {
-      if (prof && m == 0) {
-        if (cudaEventRecordWithFlags(pev[k], c.st, cudaEventRecordExternal) != cudaSuccess) (void)cudaGetLastError();
-      }
-    };
-    // apply the deferred CG updates of every problem that has one
-    auto flush = [&]() {
-      ++c.launches;
-      ku<<<gu, threads, 0, c.st>>>(kpp);
-      ++c.launches;
-      k_scal_clear<<<gs, 128, 0, c.st>>>(d_st, np);
-    };
-    // true residual r = -G*(C:(E + x)) of the flagged problems
-    auto true_pass = [&]() {
-      plane_pass(kf_tr, true);
-      column_pass(MODE_TRUE);
-      plane_pass(ki_tr, false);
-    };
-    // ---- iterations, in chunks captured as CUDA graphs; residual
-    //      replacement at the end of every chunk (when enabled)
+    hh_status rs = HH_OK;
     const int chunk = std::max(1, o.check_every);
-    auto launch_chunk = [&]() {
-      for (int m = 0; m < chunk; ++m) {
-        rec(m, 0);
-        plane_pass(kf_it, true);
-        rec(m, 1);
-        column_pass(MODE_ITER);
-        rec(m, 2);
-        plane_pass(ki_it, false);
-        rec(m, 3);
-        ++c.launches;
-        k_scal_step<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
-      }
-      if (replace) {
-        flush();
-        ++c.launches;
-        k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 0);
-        true_pass();
-        ++c.launches;
-        k_scal_replace<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.fixed_iters);
-      }
-    };
-    cudaGraphExec_t exec = nullptr;
-    long long chunk_kernels = 0;
-    if (o.use_graphs) {
-      cudaGraph_t g = nullptr;
-      HH_CK(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
-      const long long l0 = c.launches;
-      launch_chunk();
-      chunk_kernels = c.launches - l0;
-      c.launches = l0;
-      cudaError_t ce = cudaStreamEndCapture(c.st, &g);
-      if (ce != cudaSuccess) {
-        c.err = std::string("graph capture: ") + cudaGetErrorString(ce);
-        return HH_ERR_CUDA;
-      }
-      ce = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      if (ce != cudaSuccess) {
-        c.err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
-        return HH_ERR_CUDA;
-      }
-    }
     const long long max_chunks =
         ((long long)(o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) / chunk + 2) * (o.max_restarts + 2);
-    long long chunks = 0;
-    int final_rounds = 0;
-    hh_status rs = HH_OK;
-    // algorithmic bytes per voxel (a) and per half-spectrum element (b) of the
-    // four field kernels: every field value read or written once
-    const double Tb = sizeof(T);
-    const double lab_b = (med.kind == MED_ISO) ? 1.0 : 21.0 * Tb;
-    // (plane_fwd: r, q, p, x read, r, x, p written, label, half spectrum
-    // written; plane_inv: half spectrum read, p, r read, q written)
-    const char* pnames[3] = {"plane_fwd", "column", "plane_inv"};
-    const double pa[3] = {42.0 * Tb + lab_b, 0.0, 18.0 * Tb};
-    const double pb[3] = {2.0 * Tb, 4.0 * Tb, 2.0 * Tb};
-    unsigned long long* h_vs = reinterpret_cast<unsigned long long*>(c.h_dbl);
-    double act_v = 0.0, act_s = 0.0;
-    bool sampled_pending = false;
-    auto count_active = [&](int* out) -> cudaError_t {
+    if (basic) {
+      // ---- basic scheme (Moulinec-Suquet fixed point): x = eps - E = 0, then
+      //      per iteration sigma = C:(E + x), residual, x <- x - Gamma0 * sigma
+      HH_CK(cudaMemsetAsync(d_x, 0, fld_off * sizeof(T), c.st));
       ++c.launches;
-      k_count_active<<<1, 256, 0, c.st>>>(d_st, d_prob, np, d_flag, reinterpret_cast<unsigned long long*>(d_flag + 4));
-      cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
-      cudaMemcpyAsync(h_vs, d_flag + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.st);
-      cudaError_t e = cudaStreamSynchronize(c.st);
-      *out = c.h_int[0];
-      if (e == cudaSuccess && prof && sampled_pending) {
-        const int pairs[3][2] = {{0, 1}, {1, 2}, {2, 3}};
-        for (int k = 0; k < 3; ++k) {
-          float ms = 0.f;
-          if (cudaEventElapsedTime(&ms, pev[pairs[k][0]], pev[pairs[k][1]]) == cudaSuccess) {
-            Ctx::KStat& ks = c.prof[pnames[k]];
-            ks.sampled += 1;
-            ks.ms += ms;
-            ks.bytes += pa[k] * act_v + pb[k] * act_s;
-          } else {
-            (void)cudaGetLastError();  // profiling is best effort; keep the error state clean
-          }
+      k_scal_basic_init<<<gs, 128, 0, c.st>>>(d_st, np);
+      HH_CK(cudaGetLastError());
+      auto basic_chunk = [&]() {
+        for (int m = 0; m < chunk; ++m) {
+          plane_pass(kf_b, true);
+          column_pass(MODE_BASIC);
+          plane_pass(ki_b, false);
+          ++c.launches;
+          k_scal_basic<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_cpart, np, colw, o.tol, o.max_iter, o.fixed_iters);
         }
-        sampled_pending = false;
+      };
+      cudaGraphExec_t bexec = nullptr;
+      long long bk = 0;
+      if (o.use_graphs) {
+        cudaGraph_t g = nullptr;
+        HH_CK(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = c.launches;
+        basic_chunk();
+        bk = c.launches - l0;
+        c.launches = l0;
+        cudaError_t ce = cudaStreamEndCapture(c.st, &g);
+        if (ce == cudaSuccess) {
+          ce = cudaGraphInstantiate(&bexec, g, 0);
+          cudaGraphDestroy(g);
+        }
+        if (ce != cudaSuccess) {
+          c.err = std::string("graph: ") + cudaGetErrorString(ce);
+          return HH_ERR_CUDA;
+        }
       }
-      if (e == cudaSuccess) {
-        act_v = double(h_vs[0]);
-        act_s = double(h_vs[1]);
-      }
-      return e;
-    };
-    while (true) {
-      int nact = 0;
-      cudaError_t e = count_active(&nact);
-      if (e != cudaSuccess) {
-        c.err = std::string("solve: ") + cudaGetErrorString(e);
-        rs = HH_ERR_CUDA;
-        break;
-      }
-      if (nact == 0) {
-        // every problem stopped on its recursive residual: check the true one
-        if (final_rounds > o.max_restarts) break;
-        flush();
+      for (long long chunks = 0;; ++chunks) {
         ++c.launches;
-        k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 1);
-        true_pass();
-        ++c.launches;
-        k_scal_true_final<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, 2.0, o.max_restarts, o.max_iter,
-                                                 o.fixed_iters);
-        ++final_rounds;
-        if ((e = count_active(&nact)) != cudaSuccess) {
+        k_count_active<<<1, 256, 0, c.st>>>(d_st, d_prob, np, d_flag,
+                                            reinterpret_cast<unsigned long long*>(d_flag + 4));
+        cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+        cudaError_t e = cudaStreamSynchronize(c.st);
+        if (e != cudaSuccess) {
           c.err = std::string("solve: ") + cudaGetErrorString(e);
           rs = HH_ERR_CUDA;
           break;
         }
-        if (nact == 0) break;
+        if (c.h_int[0] == 0 || chunks >= max_chunks) break;
+        if (bexec) {
+          e = cudaGraphLaunch(bexec, c.st);
+          c.launches += bk;
+        } else {
+          basic_chunk();
+          e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+          c.err = std::string("launch: ") + cudaGetErrorString(e);
+          rs = HH_ERR_CUDA;
+          break;
+        }
       }
-      if (chunks >= max_chunks) break;
-      if (exec) {
-        e = cudaGraphLaunch(exec, c.st);
-        c.launches += chunk_kernels;
-      } else {
+      if (bexec) cudaGraphExecDestroy(bexec);
+    } else {
+      // ---- right-hand side b = -G*(C:E), r = p = b, x = 0
+      plane_pass(kf_rhs, true);
+      column_pass(MODE_RHS);
+      plane_pass(ki_rhs, false);
+      ++c.launches;
+      k_scal_init<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, floor2);
+      HH_CK(cudaGetLastError());
+
+      // profiling: events around the field kernels of the first iteration of every chunk
+      const bool prof = o.profile != 0;
+      cudaEvent_t pev[4] = {nullptr, nullptr, nullptr, nullptr};
+      if (prof)
+        for (auto& e : pev) HH_CK(cudaEventCreate(&e));
+      // external record nodes, so that the events are timed inside graph replays
+      auto rec = [&](int m, int k) {
+        if (prof && m == 0) {
+          if (cudaEventRecordWithFlags(pev[k], c.st, cudaEventRecordExternal) != cudaSuccess) (void)cudaGetLastError();
+        }
+      };
+      // apply the deferred CG updates of every problem that has one
+      auto flush = [&]() {
+        ++c.launches;
+        ku<<<gu, threads, 0, c.st>>>(kpp);
+        ++c.launches;
+        k_scal_clear<<<gs, 128, 0, c.st>>>(d_st, np);
+      };
+      // true residual r = -G*(C:(E + x)) of the flagged problems
+      auto true_pass = [&]() {
+        plane_pass(kf_tr, true);
+        column_pass(MODE_TRUE);
+        plane_pass(ki_tr, false);
+      };
+      // ---- iterations, in chunks captured as CUDA graphs; residual
+      //      replacement at the end of every chunk (when enabled)
+      auto launch_chunk = [&]() {
+        for (int m = 0; m < chunk; ++m) {
+          rec(m, 0);
+          plane_pass(kf_it, true);
+          rec(m, 1);
+          column_pass(MODE_ITER);
+          rec(m, 2);
+          plane_pass(ki_it, false);
+          rec(m, 3);
+          ++c.launches;
+          k_scal_step<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
+        }
+        if (replace) {
+          flush();
+          ++c.launches;
+          k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 0);
+          true_pass();
+          ++c.launches;
+          k_scal_replace<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.fixed_iters);
+        }
+      };
+      cudaGraphExec_t exec = nullptr;
+      long long chunk_kernels = 0;
+      if (o.use_graphs) {
+        cudaGraph_t g = nullptr;
+        HH_CK(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+        const long long l0 = c.launches;
         launch_chunk();
-        e = cudaGetLastError();
+        chunk_kernels = c.launches - l0;
+        c.launches = l0;
+        cudaError_t ce = cudaStreamEndCapture(c.st, &g);
+        if (ce != cudaSuccess) {
+          c.err = std::string("graph capture: ") + cudaGetErrorString(ce);
+          return HH_ERR_CUDA;
+        }
+        ce = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+          c.err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
+          return HH_ERR_CUDA;
+        }
       }
-      if (prof) {
-        sampled_pending = true;
-        const long long per[3] = {(long long)pcl.size(), (long long)ccl.size(), (long long)pcl.size()};
-        for (int k = 0; k < 3; ++k) c.prof[pnames[k]].launches += chunk * per[k];
+      long long chunks = 0;
+      int final_rounds = 0;
+      // algorithmic bytes per voxel (a) and per half-spectrum element (b) of the
+      // four field kernels: every field value read or written once
+      const double Tb = sizeof(T);
+      const double lab_b = (med.kind == MED_ISO) ? 1.0 : 21.0 * Tb;
+      // (plane_fwd: r, q, p, x read, r, x, p written, label, half spectrum
+      // written; plane_inv: half spectrum read, p, r read, q written)
+      const char* pnames[3] = {"plane_fwd", "column", "plane_inv"};
+      const double pa[3] = {42.0 * Tb + lab_b, 0.0, 18.0 * Tb};
+      const double pb[3] = {2.0 * Tb, 4.0 * Tb, 2.0 * Tb};
+      unsigned long long* h_vs = reinterpret_cast<unsigned long long*>(c.h_dbl);
+      double act_v = 0.0, act_s = 0.0;
+      bool sampled_pending = false;
+      auto count_active = [&](int* out) -> cudaError_t {
+        ++c.launches;
+        k_count_active<<<1, 256, 0, c.st>>>(d_st, d_prob, np, d_flag, reinterpret_cast<unsigned long long*>(d_flag + 4));
+        cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+        cudaMemcpyAsync(h_vs, d_flag + 4, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c.st);
+        cudaError_t e = cudaStreamSynchronize(c.st);
+        *out = c.h_int[0];
+        if (e == cudaSuccess && prof && sampled_pending) {
+          const int pairs[3][2] = {{0, 1}, {1, 2}, {2, 3}};
+          for (int k = 0; k < 3; ++k) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pev[pairs[k][0]], pev[pairs[k][1]]) == cudaSuccess) {
+              Ctx::KStat& ks = c.prof[pnames[k]];
+              ks.sampled += 1;
+              ks.ms += ms;
+              ks.bytes += pa[k] * act_v + pb[k] * act_s;
+            } else {
+              (void)cudaGetLastError();  // profiling is best effort; keep the error state clean
+            }
+          }
+          sampled_pending = false;
+        }
+        if (e == cudaSuccess) {
+          act_v = double(h_vs[0]);
+          act_s = double(h_vs[1]);
+        }
+        return e;
+      };
+      while (true) {
+        int nact = 0;
+        cudaError_t e = count_active(&nact);
+        if (e != cudaSuccess) {
+          c.err = std::string("solve: ") + cudaGetErrorString(e);
+          rs = HH_ERR_CUDA;
+          break;
+        }
+        if (nact == 0) {
+          // every problem stopped on its recursive residual: check the true one
+          if (final_rounds > o.max_restarts) break;
+          flush();
+          ++c.launches;
+          k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 1);
+          true_pass();
+          ++c.launches;
+          k_scal_true_final<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, 2.0, o.max_restarts, o.max_iter,
+                                                   o.fixed_iters);
+          ++final_rounds;
+          if ((e = count_active(&nact)) != cudaSuccess) {
+            c.err = std::string("solve: ") + cudaGetErrorString(e);
+            rs = HH_ERR_CUDA;
+            break;
+          }
+          if (nact == 0) break;
+        }
+        if (chunks >= max_chunks) break;
+        if (exec) {
+          e = cudaGraphLaunch(exec, c.st);
+          c.launches += chunk_kernels;
+        } else {
+          launch_chunk();
+          e = cudaGetLastError();
+        }
+        if (prof) {
+          sampled_pending = true;
+          const long long per[3] = {(long long)pcl.size(), (long long)ccl.size(), (long long)pcl.size()};
+          for (int k = 0; k < 3; ++k) c.prof[pnames[k]].launches += chunk * per[k];
+        }
+        if (e != cudaSuccess) {
+          c.err = std::string("launch: ") + cudaGetErrorString(e);
+          rs = HH_ERR_CUDA;
+          break;
+        }
+        ++chunks;
       }
-      if (e != cudaSuccess) {
-        c.err = std::string("launch: ") + cudaGetErrorString(e);
-        rs = HH_ERR_CUDA;
-        break;
-      }
-      ++chunks;
+      if (exec) cudaGraphExecDestroy(exec);
+      for (auto& e : pev)
+        if (e) cudaEventDestroy(e);
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    for (auto& e : pev)
-      if (e) cudaEventDestroy(e);
     if (rs != HH_OK) return rs;
 
     // ---- core averages from x
     {
-      flush();
+      if (!basic) {
+        ++c.launches;
+        ku<<<gu, threads, 0, c.st>>>(kpp);
+        ++c.launches;
+        k_scal_clear<<<gs, 128, 0, c.st>>>(d_st, np);
+      }
       const int ga = grid_for<T>(c, (const void*)ka, threads, 0, kpp.nitems);
       ++c.launches;
       ka<<<ga, threads, 0, c.st>>>(kpp);
@@ -987,7 +1076,7 @@ static hh_status check_opts(hh_ctx* h, const hh_options* o) {
   if (!(o->tol > 0.0) && o->fixed_iters <= 0) return fail(h, HH_ERR_ARG, "tol must be > 0");
   if (o->max_iter < 1 || o->fixed_iters < 0) return fail(h, HH_ERR_ARG, "bad iteration limits");
   if (o->nyquist != HH_NYQ_ZERO_COMPONENT && o->nyquist != HH_NYQ_ZERO_MODE) return fail(h, HH_ERR_ARG, "bad nyquist");
-  if (o->scheme != HH_CG) return fail(h, HH_ERR_UNSUPPORTED, "only the conjugate-gradient scheme is built");
+  if (o->scheme != HH_CG && o->scheme != HH_BASIC) return fail(h, HH_ERR_ARG, "bad scheme");
   if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1)
     return fail(h, HH_ERR_ARG, "bad check_every, replace or max_restarts");
   return HH_OK;
@@ -1158,7 +1247,9 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   one[0].cnz = Cz;
   Stats st2;
   BoxRes* d_res2;
-  if ((s = run_boxes_p(h, o, m2, one, &d_res2, st2)) != HH_OK) return s;
+  hh_options o2 = o;
+  o2.scheme = HH_CG;  // the basic scheme is a mode of the subimage (level-1) solves
+  if ((s = run_boxes_p(h, o2, m2, one, &d_res2, st2)) != HH_OK) return s;
   BoxRes R;
   double am[4];
   HH_CK(cudaMemcpyAsync(&R, d_res2, sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));

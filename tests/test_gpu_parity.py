@@ -315,3 +315,51 @@ def test_error_paths(ctx):
     lab = synth.grf_two_phase(n=8, ell=2.0, seed=2)
     r = ctx.homogenize_direct(lab, synth.PHASES_SOLID_PORE, max_iter=3)
     assert r["status"] == B.HH_WARN_NOT_CONVERGED and r["iters_max"] == 3
+
+
+# ----------------------------------------------- A5-alt basic scheme -------
+
+def _ref_medium(ph):
+    ph = np.asarray(ph, dtype=np.float64)
+    lam = ph[:, 0] - 2.0 * ph[:, 1] / 3.0
+    return 0.5 * (lam.min() + lam.max()), 0.5 * (ph[:, 1].min() + ph[:, 1].max())
+
+
+@pytest.mark.parametrize("shape", [(9, 10, 11), (16, 18, 12)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_basic_fixed_iterations_parity(ctx, shape, precision, tol):
+    lab = RNG.integers(0, 3, size=shape).astype(np.uint8)
+    ph = synth.PHASES_APPENDIX_B
+    got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=12, scheme="basic")
+    ref = O.homogenize_box(O.IsoMedium.from_labels(lab, ph), (slice(None),) * 3, fixed_iters=12, scheme="basic",
+                           ref=_ref_medium(ph))
+    assert np.all(got["iters"] == 12)
+    assert rel(got["Sigma"][0], ref["Sigma"]) < tol
+    assert rel(got["C"][0], ref["C"]) < tol
+    assert rel(got["resid"][0], ref["resid"]) < (1e-8 if precision == "fp64" else 1e-3)
+
+
+@pytest.mark.parametrize("precision,solver_tol,tol", [("fp64", 1e-9, 1e-7), ("fp32", 2e-6, 5e-5)])
+def test_basic_converges_to_the_cg_solution(ctx, precision, solver_tol, tol):
+    img = synth.grf_two_phase(n=14, ell=2.0, porosity=0.35, seed=3)
+    ph = synth.PHASES_APPENDIX_B
+    got = ctx.homogenize_direct(img, ph, precision=precision, tol=solver_tol, scheme="basic", max_iter=5000)
+    ref = O.homogenize_direct(img, ph, tol=1e-12)
+    assert got["status"] == 0 and got["resid_max"] <= solver_tol
+    assert rel(got["C"], ref["C"]) < tol
+
+
+def test_basic_explicit_reference_and_anisotropic_medium(ctx):
+    shape = (6, 7, 8)
+    C = rand_spd_field(shape, RNG)
+    from paper_2208_02320_gb300 import HHError
+    from paper_2208_02320_gb300 import binding as B
+    with pytest.raises(HHError) as e:
+        ctx.homogenize_aniso(c21_of(C), scheme="basic")
+    assert e.value.status == B.HH_ERR_UNSUPPORTED
+    ev = np.linalg.eigvalsh(np.moveaxis(C.reshape(6, 6, -1), -1, 0) * np.outer(O.MANDEL, O.MANDEL))
+    mu0 = 0.25 * (ev.min() + ev.max())  # 2 mu0 = mean of the extreme Mandel eigenvalues
+    got = ctx.homogenize_aniso(c21_of(C), precision="fp64", tol=1e-10, scheme="basic", ref_lambda=0.0, ref_mu=mu0,
+                               max_iter=20000)
+    cg = ctx.homogenize_aniso(c21_of(C), precision="fp64", tol=1e-11)
+    assert rel(got["C"], cg["C"]) < 1e-7
