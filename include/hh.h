@@ -47,7 +47,9 @@ typedef int hh_status;
 #define HH_FP32 0                 /* FP32 fields and FFTs, FP64 scalars and averages */
 #define HH_FP64 1                 /* FP64 everywhere */
 #define HH_CG 0                   /* conjugate gradients (Appendix A) */
-#define HH_BASIC 1                /* basic fixed point with an isotropic reference medium */
+#define HH_BASIC 1                /* basic fixed point with an isotropic reference medium
+                                     (Moulinec-Suquet, cited in Appendix A) for the subimage
+                                     and direct solves; the level-2 solve always uses CG */
 #define HH_NYQ_ZERO_COMPONENT 0   /* even N: Nyquist wave-vector component set to 0 */
 #define HH_NYQ_ZERO_MODE 1        /* even N: projection zero on every Nyquist mode */
 
@@ -60,12 +62,17 @@ typedef struct {
 
 typedef struct {
     int precision;        /* HH_FP32 (default) or HH_FP64 */
-    double tol;           /* stop when ||r|| <= tol ||b|| (Frobenius norm), default 1e-6 */
+    double tol;           /* HH_CG: stop when ||r|| <= tol ||b|| (Frobenius norm);
+                             HH_BASIC: stop when the equilibrium residual
+                             ||G*sigma|| / ||<sigma>|| <= tol; default 1e-6 */
     int max_iter;         /* per load case, default 20000 */
     int scheme;           /* HH_CG (default) or HH_BASIC */
     int nyquist;          /* HH_NYQ_ZERO_COMPONENT (default) or HH_NYQ_ZERO_MODE */
     int fixed_iters;      /* > 0: run exactly this many iterations, ignore tol (parity runs) */
-    double ref_lambda;    /* HH_BASIC reference medium; <= 0: mean of the extreme phase values */
+    double ref_lambda;    /* HH_BASIC reference medium (Lame lambda, mu, GPa). When ref_mu <= 0
+                             or lambda + 2 mu / 3 <= 0: the means of the smallest and largest
+                             phase lambda and mu (isotropic phases only; an anisotropic
+                             medium with no valid reference returns HH_ERR_UNSUPPORTED) */
     double ref_mu;
     int64_t workspace_bytes; /* device workspace budget for batched solves; 0 = 3/4 of free memory */
     int use_graphs;       /* 1 (default): capture the iteration loop in CUDA graphs */

@@ -27,6 +27,11 @@ DEPS = [os.path.join(CSRC, f) for f in ("hh_host.cu", "hh_fft2_inst.cu", "hh_dev
     os.path.join(ROOT, "include", "hh.h"), os.path.abspath(__file__)]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Relocatable device code: a kernel's register count after linking is the
+# largest over everything it calls, so one cap for every unit keeps the
+# transform functions from setting the occupancy of the field kernels
+# (80 registers: three 256-thread blocks per SM).
+MAX_REGS = 80
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC"]
 
 
@@ -53,27 +58,29 @@ def _run(cmd, verbose):
     return res.stdout + res.stderr
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Build libhh.so next to this file; returns its path."""
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=(), max_regs: int = MAX_REGS, lib: str = LIB,
+          build_dir: str = BUILD_DIR) -> str:
+    """Build libhh.so next to this file (or at `lib`); returns its path."""
+    if not force and lib == LIB and up_to_date():
         return LIB
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = nvcc_path()
     inc = "-I" + os.path.join(ROOT, "include")
     cmds, objs = [], []
     for src, obj, flags in UNITS:
-        o = os.path.join(BUILD_DIR, obj)
+        o = os.path.join(build_dir, obj)
         objs.append(o)
-        cmds.append([nvcc, *NVCC_FLAGS, *extra, *flags, inc, "-c", "-o", o, os.path.join(CSRC, src)])
+        cmds.append([nvcc, *NVCC_FLAGS, "-maxrregcount=%d" % max_regs, *extra, *flags, inc, "-c", "-o", o,
+                     os.path.join(CSRC, src)])
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(cmds)) as ex:
         outs = [f.result() for f in [ex.submit(_run, c, verbose) for c in cmds]]
     if verbose:
         for out in outs:
             print(out)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     _run([nvcc, *ARCH, "-rdc=true", "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs], verbose)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -73,7 +73,10 @@ enum : int { MED_ISO = 0, MED_ANISO = 1 };
 enum : int { MODE_RHS = 0, MODE_ITER = 1, MODE_APPLY = 2, MODE_TRUE = 3, MODE_BASIC = 4 };
 enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NONFINITE = 2 };
 
-constexpr int kAvgParts = 12;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
+constexpr int kAvgParts = 12;
+// Resident 256-thread blocks per SM the plane and column passes are compiled
+// for (a register budget of 80 per thread).
+constexpr int kFieldBlocksPerSM = 3;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
 
 template <typename T>
 struct KParams {
@@ -515,7 +518,7 @@ __device__ __forceinline__ bool skip_problem(const PState* st, int pr, int mode)
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(256) k_plane_fwd(KParams<T> P) {
 //   sum of h |P tau|^2_F (h = 2 for the kx that stand for a conjugate pair)
 //   and, from the zero mode, Re tau^(0) for the equilibrium residual.
 template <typename T>
-__global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
   __shared__ double red[32 * 7];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
@@ -735,7 +738,7 @@ __global__ void __launch_bounds__(256) k_column(KParams<T> P, int skip_mode) {
 //   MODE_APPLY, MODE_BASIC: store q
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256) k_plane_inv(KParams<T> P) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
