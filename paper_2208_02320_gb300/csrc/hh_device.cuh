@@ -75,8 +75,11 @@ enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NONFINITE = 2 };
 
 constexpr int kAvgParts = 12;
 // Resident 256-thread blocks per SM the plane and column passes are compiled
-// for (a register budget of 80 per thread).
-constexpr int kFieldBlocksPerSM = 3;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
+// for (3: a register budget of 80 per thread; 4: 64).
+#ifndef HH_FIELD_BLOCKS_PER_SM
+#define HH_FIELD_BLOCKS_PER_SM 3
+#endif
+constexpr int kFieldBlocksPerSM = HH_FIELD_BLOCKS_PER_SM;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
 
 template <typename T>
 struct KParams {
