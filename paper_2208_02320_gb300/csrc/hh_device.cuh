@@ -644,7 +644,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
 template <typename T>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
-  __shared__ double red[32 * 7];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
@@ -656,6 +655,8 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     C2<T>* tile = reinterpret_cast<C2<T>*>(smem);
     C2<T>* twz = tile + 6 * nz * P.colw;
     int* sfz = reinterpret_cast<int*>(twz + nz);
+    double* red = reinterpret_cast<double*>(
+        smem + ((sizeof(C2<T>) * (6 * nz * P.colw + nz) + sizeof(int) * nz + 7) & ~size_t(7)));  // 32 * 7
     const AxisPlan az = P.plans[d.pz];
     const AxisPlan ay = P.plans[d.py];
     load_tw<T>(twz, P.tw, az);

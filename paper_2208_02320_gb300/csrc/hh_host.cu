@@ -202,6 +202,8 @@ static size_t plane_smem_bytes(int nx, int ny, int nphase) {
 template <typename T>
 static size_t column_smem_bytes(int colw, int nz) {
   size_t o = sizeof(C2<T>) * 6 * (size_t)nz * colw + sizeof(C2<T>) * nz + sizeof(int) * nz;
+  o = (o + 7) & ~size_t(7);
+  o += 32 * 7 * sizeof(double);  // block reduction of the basic scheme's residual partials
   return (o + 15) & ~size_t(15);
 }
 
