@@ -42,7 +42,8 @@ typedef int hh_status;
 #define HH_ERR_NONFINITE (-4)     /* NaN/Inf in a CG scalar */
 #define HH_ERR_DEVICE_TIMEOUT (-5)/* a bounded device-side wait ran out */
 #define HH_ERR_BAD_STIFFNESS (-6) /* a stiffness that is not symmetric positive definite */
-#define HH_ERR_UNSUPPORTED (-7)   /* FFT length with a prime factor above 31, or plane too large */
+#define HH_ERR_UNSUPPORTED (-7)   /* FFT length with a prime factor above 31, or a row or z
+                                     column too long for shared memory */
 
 #define HH_FP32 0                 /* FP32 fields and FFTs, FP64 scalars and averages */
 #define HH_FP64 1                 /* FP64 everywhere */
@@ -83,6 +84,10 @@ typedef struct {
                              2 tol (default 4) */
     int profile;          /* 1: time the field kernels of the first iteration of every
                              chunk with CUDA events (read with hh_profile_read) */
+    int plane_smem_limit; /* largest shared-memory footprint (bytes) of a whole-plane
+                             block; a subimage whose xy plane needs more takes the
+                             row/column streaming passes (x rows and y columns
+                             through HBM). 0 (default): the device's per-block limit */
 } hh_options;
 
 typedef struct {

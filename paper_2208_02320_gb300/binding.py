@@ -46,6 +46,7 @@ class Options(ctypes.Structure):
         ("replace", ctypes.c_int),
         ("max_restarts", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("plane_smem_limit", ctypes.c_int),
     ]
 
 

@@ -50,8 +50,11 @@ struct Prob {
   int px, py, pz;                    // plan index per axis
   int lc;                            // load case 0..5
   int box;                           // subimage index in the request
-  int plane0;                        // first plane item of this problem
+  int plane0;                        // first (problem, z) item of this problem
   int col0;                          // first column item of this problem
+  int part0;                         // first partial-sum row of its field-pass items
+  int npi;                           // field-pass items: nz, or nz * row chunks when streaming
+  int rows;                          // rows per row-streaming item; 0: whole planes
   int pad;
   long long med_off;                 // iso: byte offset of labels; aniso: element offset of C21
   long long fld_off;                 // element offset of r, p, q (6 V each)
@@ -109,6 +112,7 @@ struct KParams {
   int fixed_iters;
   int nprob;
   int colw;          // kx columns per column-pass item
+  int ycw;           // kx columns per y-column item (row-streaming problems)
   // basic scheme: Green operator of the isotropic reference medium,
   // Gamma0 = g0a (n (x) v + v (x) n) - g0b (n . v) n (x) n, v = tau n
   T g0a, g0b;
@@ -495,9 +499,9 @@ __device__ __forceinline__ void pack_rows(C2<T>* S, int nrows, int RP, int nx, i
 
 template <typename T>
 __device__ __forceinline__ void plane_tables(const KParams<T>& P, const PlaneSmem<T>& sm, const AxisPlan& ax,
-                                             const AxisPlan& ay, int nx) {
+                                             const AxisPlan& ay, int nx, bool with_y = true) {
   load_tw<T>(sm.twx, P.tw, ax);
-  load_tw<T>(sm.twy, P.tw, ay);
+  if (with_y) load_tw<T>(sm.twy, P.tw, ay);
   for (int t = threadIdx.x; t < nx; t += blockDim.x) sm.pfx[t] = P.itab[ax.pf_off + t];
   if (P.medium == MED_ISO)
     for (int t = threadIdx.x; t < 2 * P.nphase; t += blockDim.x) sm.lm[t] = P.lammu[t];
@@ -520,6 +524,89 @@ __device__ __forceinline__ bool skip_problem(const PState* st, int pr, int mode)
   return false;
 }
 
+// Per-item CG scalars of the forward pass.
+template <typename T, int MODE>
+struct FwdScal {
+  T alpha = T(0), beta = T(0);
+  bool pend = false;
+  __device__ __forceinline__ explicit FwdScal(const PState& s) {
+    if (MODE == MODE_ITER || MODE == MODE_BASIC) {
+      alpha = T(s.alpha);
+      beta = T(s.beta);
+      pend = s.pending != 0;
+    }
+  }
+};
+
+// One voxel of the forward pass: the mode's strain (with the vector updates
+// it stores), its stress s, and the mode's partial sum.
+template <typename T, int MODE>
+__device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
+                                          const FwdScal<T, MODE>& k, const T* lm, T (&s)[6], double& acc) {
+  T* rr = P.r + d.fld_off;
+  T* pp = P.p + d.fld_off;
+  T* xx = P.x + d.fld_off;
+  const T* qq = P.q + d.fld_off;
+  const T Ed = d.lc < 3 ? T(1) : T(0.5);
+  T e[6];
+  if (MODE == MODE_RHS) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = T(0);
+    e[d.lc] = Ed;
+  } else if (MODE == MODE_ITER) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const long long o = c * V + vo;
+      T rv = rr[o];
+      const T pv = pp[o];
+      if (k.pend) {
+        rv -= k.alpha * qq[o];
+        rr[o] = rv;
+        xx[o] = xx[o] + k.alpha * pv;
+      }
+      const T pn = rv + k.beta * pv;
+      pp[o] = pn;
+      e[c] = pn;
+      acc += frob_w(c) * double(rv) * double(rv);
+    }
+  } else if (MODE == MODE_TRUE) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
+    e[d.lc] += Ed;
+  } else if (MODE == MODE_BASIC) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const long long o = c * V + vo;
+      T xv = xx[o];
+      if (k.pend) {
+        xv -= qq[o];
+        xx[o] = xv;
+      }
+      e[c] = xv;
+    }
+    e[d.lc] += Ed;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
+  }
+  if (P.medium == MED_ISO) {
+    const int lab = P.labels[d.med_off + vo];
+    stress_iso<T>(e, lm[2 * lab], lm[2 * lab + 1], s);
+  } else {
+    stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
+  }
+  if (MODE == MODE_RHS) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc += frob_w(c) * double(s[c]) * double(s[c]);
+  }
+}
+
+// Partial-sum slot the forward pass of a mode writes (-1: none).
+template <int MODE>
+__device__ __forceinline__ int fwd_slot() {
+  return MODE == MODE_RHS ? 0 : (MODE == MODE_ITER ? 13 : -1);
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
@@ -535,80 +622,17 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     const AxisPlan ax = P.plans[d.px];
     const AxisPlan ay = P.plans[d.py];
     plane_tables<T>(P, sm, ax, ay, nx);
-    T alpha = T(0), beta = T(0);
-    bool pend = false;
-    if (MODE == MODE_ITER || MODE == MODE_BASIC) {
-      const PState& s = P.st[w.x];
-      alpha = T(s.alpha);
-      beta = T(s.beta);
-      pend = s.pending != 0;
-    }
+    const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
 
     double acc[1] = {0.0};
-    T* rr = P.r + d.fld_off;
-    T* pp = P.p + d.fld_off;
-    T* xx = P.x + d.fld_off;
-    const T* qq = P.q + d.fld_off;
     const long long zoff = (long long)z * ny * nx;
-    const T Ed = d.lc < 3 ? T(1) : T(0.5);
     // voxel phase: stress of the whole plane into the pair rows
     for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
       const int y = v / nx;
       const int x = v - y * nx;
-      const long long vo = zoff + v;
-      T e[6];
-      if (MODE == MODE_RHS) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = T(0);
-        e[d.lc] = Ed;
-      } else if (MODE == MODE_ITER) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const long long o = c * V + vo;
-          T rv = rr[o];
-          const T pv = pp[o];
-          if (pend) {
-            rv -= alpha * qq[o];
-            rr[o] = rv;
-            xx[o] = xx[o] + alpha * pv;
-          }
-          const T pn = rv + beta * pv;
-          pp[o] = pn;
-          e[c] = pn;
-          acc[0] += frob_w(c) * double(rv) * double(rv);
-        }
-      } else if (MODE == MODE_TRUE) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
-        e[d.lc] += Ed;
-      } else if (MODE == MODE_BASIC) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const long long o = c * V + vo;
-          T xv = xx[o];
-          if (pend) {
-            xv -= qq[o];
-            xx[o] = xv;
-          }
-          e[c] = xv;
-        }
-        e[d.lc] += Ed;
-      } else {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
-      }
       T s[6];
-      if (P.medium == MED_ISO) {
-        const int lab = P.labels[d.med_off + vo];
-        stress_iso<T>(e, sm.lm[2 * lab], sm.lm[2 * lab + 1], s);
-      } else {
-        stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
-      }
-      if (MODE == MODE_RHS) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) acc[0] += frob_w(c) * double(s[c]) * double(s[c]);
-      }
+      fwd_voxel<T, MODE>(P, d, V, zoff + v, k, sm.lm, s, acc[0]);
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * ny + y) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
     }
@@ -625,9 +649,101 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
       const int ky = rem / nxh;
       sp[((long long)c * d.nz + z) * pl + rem] = sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)];
     }
-    if (MODE == MODE_RHS || MODE == MODE_ITER) {
+    if (fwd_slot<MODE>() >= 0) {
       block_reduce<1>(acc, sm.red);
-      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + (MODE == MODE_RHS ? 0 : 13)] = acc[0];
+      if (threadIdx.x == 0) P.part[(long long)(d.part0 + z) * 16 + fwd_slot<MODE>()] = acc[0];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row-streaming forward pass, for planes too large for one block: rows
+// y0 .. y0 + nr of plane z (item w.y = z | y0 << 16), the constitutive law
+// fused into the x transform; the half-spectrum rows go to spec in natural y
+// order and k_ycols does the y transform.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_fwd(KParams<T> P) {
+  extern __shared__ __align__(16) char smem[];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (skip_problem<T>(P.st, w.x, MODE)) continue;
+    const Prob d = P.prob[w.x];
+    const int z = w.y & 0xffff, y0 = w.y >> 16;
+    const int nx = d.nx, ny = d.ny, nxh = d.nxh, R = d.rows;
+    const int nr = min(R, ny - y0);
+    const int RP = pair_pitch(nx);
+    const long long V = (long long)nx * ny * d.nz;
+    PlaneSmem<T> sm = plane_layout<T>(smem, nx, R, P.nphase);
+    const AxisPlan ax = P.plans[d.px];
+    plane_tables<T>(P, sm, ax, ax, nx, false);
+    const FwdScal<T, MODE> k(P.st[w.x]);
+    __syncthreads();
+
+    double acc[1] = {0.0};
+    const long long off0 = ((long long)z * ny + y0) * nx;
+    for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
+      const int yy = v / nx;
+      const int x = v - yy * nx;
+      T s[6];
+      fwd_voxel<T, MODE>(P, d, V, off0 + v, k, sm.lm, s, acc[0]);
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * R + yy) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
+    }
+    __syncthreads();
+    fft_lines<T, false>(sm.S, Lines{3 * nr, nr, R * RP, RP, 1, false}, ax, sm.twx);
+    unpack_rows<T>(sm.S, 3 * R, RP, nx, nxh, sm.pfx);
+    C2<T>* sp = P.spec + d.spc_off;
+    const int rl = nr * nxh;
+    for (int e = threadIdx.x; e < 6 * rl; e += blockDim.x) {
+      const int c = e / rl;
+      const int rem = e - c * rl;
+      const int yy = rem / nxh;
+      sp[(((long long)c * d.nz + z) * ny + y0) * nxh + rem] = sm.S[plane_spec_at(c, yy, rem - yy * nxh, R, nxh, RP)];
+    }
+    if (fwd_slot<MODE>() >= 0) {
+      block_reduce<1>(acc, sm.red);
+      const int nch = (ny + R - 1) / R;
+      if (threadIdx.x == 0) P.part[(long long)(d.part0 + z * nch + y0 / R) * 16 + fwd_slot<MODE>()] = acc[0];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y transforms of row-streaming problems: W = ycw kx columns of plane z
+// (item w.y = z | kx0 << 16), forward or inverse, in place in spec.
+// ---------------------------------------------------------------------------
+template <typename T, bool INV>
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_ycols(KParams<T> P, int skip_mode) {
+  extern __shared__ __align__(16) char smem[];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
+    const Prob d = P.prob[w.x];
+    const int z = w.y & 0xffff, kx0 = w.y >> 16;
+    const int ny = d.ny, nxh = d.nxh;
+    const int W = min(P.ycw, nxh - kx0);
+    C2<T>* tile = reinterpret_cast<C2<T>*>(smem);
+    C2<T>* twy = tile + 6 * ny * P.ycw;
+    const AxisPlan ay = P.plans[d.py];
+    load_tw<T>(twy, P.tw, ay);
+    C2<T>* sp = P.spec + d.spc_off + (long long)z * ny * nxh + kx0;
+    const long long cstride = (long long)d.nz * ny * nxh;
+    for (int e = threadIdx.x; e < 6 * ny * W; e += blockDim.x) {
+      const int kx = e % W;
+      const int cy = e / W;  // c * ny + y
+      const int c = cy / ny;
+      tile[e] = sp[c * cstride + (long long)(cy - c * ny) * nxh + kx];
+    }
+    __syncthreads();
+    fft_lines<T, INV>(tile, Lines{6 * W, W, ny * W, 1, W, true}, ay, twy);
+    for (int e = threadIdx.x; e < 6 * ny * W; e += blockDim.x) {
+      const int kx = e % W;
+      const int cy = e / W;
+      const int c = cy / ny;
+      sp[c * cstride + (long long)(cy - c * ny) * nxh + kx] = tile[e];
     }
     __syncthreads();
   }
@@ -741,6 +857,60 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
 //   MODE_TRUE : r = -q (true residual), partial <r, r>_F
 //   MODE_APPLY, MODE_BASIC: store q
 // ---------------------------------------------------------------------------
+// One voxel of the inverse pass: q = (transformed value) / V and the mode's
+// stores and partial sums (acc: MODE_ITER <p,q>, <r,q>, <q,q>; RHS/TRUE <r,r>).
+template <typename T, int MODE>
+__device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
+                                          const T (&qv)[6], double (&acc)[3]) {
+  T* rr = P.r + d.fld_off;
+  T* pp = P.p + d.fld_off;
+  T* qq = P.q + d.fld_off;
+  T* xx = P.x + d.fld_off;
+  if (MODE == MODE_RHS || MODE == MODE_TRUE) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const T rv = -qv[c];
+      rr[c * V + vo] = rv;
+      if (MODE == MODE_RHS) {
+        pp[c * V + vo] = rv;
+        xx[c * V + vo] = T(0);
+      }
+      acc[0] += frob_w(c) * double(rv) * double(rv);
+    }
+  } else if (MODE == MODE_ITER) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const long long o = c * V + vo;
+      qq[o] = qv[c];
+      const double wq = frob_w(c) * double(qv[c]);
+      acc[0] += wq * double(pp[o]);
+      acc[1] += wq * double(rr[o]);
+      acc[2] += wq * double(qv[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) qq[c * V + vo] = qv[c];
+  }
+}
+
+// Partial sums of the inverse pass of one item into row `row` of P.part.
+template <typename T, int MODE>
+__device__ __forceinline__ void inv_partials(const KParams<T>& P, long long row, double (&acc)[3], double* red) {
+  if (MODE == MODE_ITER) {
+    block_reduce<3>(acc, red);
+    if (threadIdx.x == 0) {
+      double* pt = P.part + row * 16;
+      pt[12] = acc[0];
+      pt[14] = acc[1];
+      pt[15] = acc[2];
+    }
+  } else if (MODE != MODE_APPLY && MODE != MODE_BASIC) {
+    double a1[1] = {acc[0]};
+    block_reduce<1>(a1, red);
+    if (threadIdx.x == 0) P.part[row * 16 + 12] = a1[0];
+  }
+}
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
@@ -771,15 +941,10 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
 
     double acc[3] = {0.0, 0.0, 0.0};
     const T invV = T(1) / T(V);
-    T* rr = P.r + d.fld_off;
-    T* pp = P.p + d.fld_off;
-    T* qq = P.q + d.fld_off;
-    T* xx = P.x + d.fld_off;
     const long long zoff = (long long)z * ny * nx;
     for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
       const int y = v / nx;
       const int x = v - y * nx;
-      const long long vo = zoff + v;
       T qv[6];
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) {
@@ -787,45 +952,61 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
         qv[2 * c2] = zz.x * invV;
         qv[2 * c2 + 1] = zz.y * invV;
       }
-      if (MODE == MODE_RHS || MODE == MODE_TRUE) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const T rv = -qv[c];
-          rr[c * V + vo] = rv;
-          if (MODE == MODE_RHS) {
-            pp[c * V + vo] = rv;
-            xx[c * V + vo] = T(0);
-          }
-          acc[0] += frob_w(c) * double(rv) * double(rv);
-        }
-      } else if (MODE == MODE_ITER) {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          const long long o = c * V + vo;
-          qq[o] = qv[c];
-          const double wq = frob_w(c) * double(qv[c]);
-          acc[0] += wq * double(pp[o]);
-          acc[1] += wq * double(rr[o]);
-          acc[2] += wq * double(qv[c]);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < 6; ++c) qq[c * V + vo] = qv[c];
-      }
+      inv_voxel<T, MODE>(P, d, V, zoff + v, qv, acc);
     }
-    if (MODE == MODE_ITER) {
-      block_reduce<3>(acc, sm.red);
-      if (threadIdx.x == 0) {
-        double* pt = P.part + (long long)(d.plane0 + z) * 16;
-        pt[12] = acc[0];
-        pt[14] = acc[1];
-        pt[15] = acc[2];
-      }
-    } else if (MODE != MODE_APPLY && MODE != MODE_BASIC) {
-      double a1[1] = {acc[0]};
-      block_reduce<1>(a1, sm.red);
-      if (threadIdx.x == 0) P.part[(long long)(d.plane0 + z) * 16 + 12] = a1[0];
+    inv_partials<T, MODE>(P, d.part0 + z, acc, sm.red);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Row-streaming inverse pass: rows y0 .. y0 + nr of plane z after the
+// inverse y transform (k_ycols), complex-to-real x transform, voxel phase.
+// ---------------------------------------------------------------------------
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_inv(KParams<T> P) {
+  extern __shared__ __align__(16) char smem[];
+  for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
+    const int2 w = P.items[it];
+    if (skip_problem<T>(P.st, w.x, MODE)) continue;
+    const Prob d = P.prob[w.x];
+    const int z = w.y & 0xffff, y0 = w.y >> 16;
+    const int nx = d.nx, ny = d.ny, nxh = d.nxh, R = d.rows;
+    const int nr = min(R, ny - y0);
+    const int RP = pair_pitch(nx);
+    const long long V = (long long)nx * ny * d.nz;
+    PlaneSmem<T> sm = plane_layout<T>(smem, nx, R, P.nphase);
+    const AxisPlan ax = P.plans[d.px];
+    plane_tables<T>(P, sm, ax, ax, nx, false);
+    const C2<T>* sp = P.spec + d.spc_off;
+    const int rl = nr * nxh;
+    for (int e = threadIdx.x; e < 6 * rl; e += blockDim.x) {
+      const int c = e / rl;
+      const int rem = e - c * rl;
+      const int yy = rem / nxh;
+      sm.S[plane_spec_at(c, yy, rem - yy * nxh, R, nxh, RP)] = sp[(((long long)c * d.nz + z) * ny + y0) * nxh + rem];
     }
+    __syncthreads();
+    pack_rows<T>(sm.S, 3 * R, RP, nx, nxh, sm.pfx);
+    fft_lines<T, true>(sm.S, Lines{3 * nr, nr, R * RP, RP, 1, false}, ax, sm.twx);
+
+    double acc[3] = {0.0, 0.0, 0.0};
+    const T invV = T(1) / T(V);
+    const long long off0 = ((long long)z * ny + y0) * nx;
+    for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
+      const int yy = v / nx;
+      const int x = v - yy * nx;
+      T qv[6];
+#pragma unroll
+      for (int c2 = 0; c2 < 3; ++c2) {
+        const C2<T> zz = sm.S[(c2 * R + yy) * RP + x];
+        qv[2 * c2] = zz.x * invV;
+        qv[2 * c2 + 1] = zz.y * invV;
+      }
+      inv_voxel<T, MODE>(P, d, V, off0 + v, qv, acc);
+    }
+    const int nch = (ny + R - 1) / R;
+    inv_partials<T, MODE>(P, d.part0 + z * nch + y0 / R, acc, sm.red);
     __syncthreads();
   }
 }
@@ -916,7 +1097,7 @@ __global__ void __launch_bounds__(256) k_avg(KParams<T> P) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double sum_parts(const double* part, const Prob& d, int slot) {
   double a = 0.0;
-  for (int z = 0; z < d.nz; ++z) a += part[(long long)(d.plane0 + z) * 16 + slot];
+  for (int i = 0; i < d.npi; ++i) a += part[(long long)(d.part0 + i) * 16 + slot];
   return a;
 }
 
@@ -1146,10 +1327,15 @@ __global__ void k_scal_avg(const Prob* prob, PState* st, const double* part, int
   if (i >= nprob) return;
   const Prob d = prob[i];
   PState& s = st[i];
-#pragma unroll
+  // k_avg leaves one row of partials per (problem, z) item
   for (int c = 0; c < 6; ++c) {
-    s.xbar[c] = sum_parts(part, d, c);
-    s.sbar[c] = sum_parts(part, d, 6 + c);
+    double a = 0.0, b = 0.0;
+    for (int z = 0; z < d.nz; ++z) {
+      a += part[(long long)(d.plane0 + z) * 16 + c];
+      b += part[(long long)(d.plane0 + z) * 16 + 6 + c];
+    }
+    s.xbar[c] = a;
+    s.sbar[c] = b;
   }
 }
 

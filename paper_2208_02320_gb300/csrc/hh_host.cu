@@ -207,6 +207,17 @@ static size_t column_smem_bytes(int colw, int nz) {
   return (o + 15) & ~size_t(15);
 }
 
+// Row-streaming passes: R rows of a plane per block; y columns: W kx columns.
+template <typename T>
+static size_t rows_smem_bytes(int nx, int R, int nphase) {
+  return plane_smem_bytes<T>(nx, R, nphase);
+}
+template <typename T>
+static size_t ycol_smem_bytes(int ny, int W) {
+  return (sizeof(C2<T>) * (6 * (size_t)ny * W + ny) + 15) & ~size_t(15);
+}
+constexpr size_t kStreamSmem = 48 * 1024;  // per-block target of the streaming passes
+
 // Launch classes: shared-memory footprints are rounded up to these sizes and
 // every class gets its own launch, so small subimages are not held to the
 // occupancy of the largest one.
@@ -291,17 +302,35 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     budget = (size_t)((fr + have) * 0.75);
   }
 
-  // shared memory: a whole plane per plane-pass block, colw kx columns per
-  // column-pass block; every box must fit the per-block limit
-  const int colw = (sizeof(T) == 4) ? 16 : 8;
+  // shared memory: a whole plane per plane-pass block when it fits the plane
+  // limit, else R rows per block and W kx columns per y-column block (row
+  // streaming); colw kx columns per column-pass block
+  const size_t plane_lim = o.plane_smem_limit > 0 ? std::min<size_t>(o.plane_smem_limit, c.smem_optin) : c.smem_optin;
+  int colw = (sizeof(T) == 4) ? 16 : 8;
+  int ycw = 16;
+  const size_t stream_target = std::min(kStreamSmem, plane_lim);
   for (int b = 0; b < nbox; ++b) {
     const int nx = bdim[3 * b], ny = bdim[3 * b + 1], nz = bdim[3 * b + 2];
-    if (plane_smem_bytes<T>(nx, ny, nphase) > c.smem_optin ||
-        column_smem_bytes<T>(colw, nz) > c.smem_optin) {
-      c.err = "plane too large for shared memory";
+    while (colw > 1 && column_smem_bytes<T>(colw, nz) > c.smem_optin) colw /= 2;
+    if (plane_smem_bytes<T>(nx, ny, nphase) > plane_lim) {
+      while (ycw > 1 && ycol_smem_bytes<T>(ny, ycw) > std::max(stream_target, ycol_smem_bytes<T>(ny, 1))) ycw /= 2;
+      if (rows_smem_bytes<T>(nx, 1, nphase) > c.smem_optin || ycol_smem_bytes<T>(ny, 1) > c.smem_optin) {
+        c.err = "row or y column too long for shared memory";
+        return HH_ERR_UNSUPPORTED;
+      }
+    }
+    if (column_smem_bytes<T>(colw, nz) > c.smem_optin) {
+      c.err = "z column too long for shared memory";
       return HH_ERR_UNSUPPORTED;
     }
   }
+  // rows per streaming item: as many as fit the streaming target
+  auto stream_rows = [&](int nx, int ny) {
+    int R = 1;
+    while (R < ny && rows_smem_bytes<T>(nx, R + 1, nphase) <= std::max(stream_target, rows_smem_bytes<T>(nx, 1, nphase)))
+      ++R;
+    return R;
+  };
   auto* kf_rhs = k_plane_fwd<T, MODE_RHS>;
   auto* kf_it = k_plane_fwd<T, MODE_ITER>;
   auto* kf_tr = k_plane_fwd<T, MODE_TRUE>;
@@ -313,8 +342,31 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   auto* ka = k_avg<T>;
   auto* kf_b = k_plane_fwd<T, MODE_BASIC>;
   auto* ki_b = k_plane_inv<T, MODE_BASIC>;
-  for (const void* f : {(const void*)kf_rhs, (const void*)kf_it, (const void*)kf_tr, (const void*)ki_rhs,
-                        (const void*)ki_it, (const void*)ki_tr, (const void*)kc, (const void*)kf_b, (const void*)ki_b})
+  using KFn = void (*)(KParams<T>);
+  // forward / inverse kernels per mode: whole planes and row streaming
+  auto kfwd = [&](int mode, bool rows) -> KFn {
+    switch (mode) {
+      case MODE_RHS: return rows ? k_rows_fwd<T, MODE_RHS> : kf_rhs;
+      case MODE_ITER: return rows ? k_rows_fwd<T, MODE_ITER> : kf_it;
+      case MODE_TRUE: return rows ? k_rows_fwd<T, MODE_TRUE> : kf_tr;
+      default: return rows ? k_rows_fwd<T, MODE_BASIC> : kf_b;
+    }
+  };
+  auto kinv = [&](int mode, bool rows) -> KFn {
+    switch (mode) {
+      case MODE_RHS: return rows ? k_rows_inv<T, MODE_RHS> : ki_rhs;
+      case MODE_ITER: return rows ? k_rows_inv<T, MODE_ITER> : ki_it;
+      case MODE_TRUE: return rows ? k_rows_inv<T, MODE_TRUE> : ki_tr;
+      default: return rows ? k_rows_inv<T, MODE_BASIC> : ki_b;
+    }
+  };
+  auto* kyf = k_ycols<T, false>;
+  auto* kyi = k_ycols<T, true>;
+  for (int m : {MODE_RHS, MODE_ITER, MODE_TRUE, MODE_BASIC})
+    for (bool rows : {false, true})
+      for (KFn f : {kfwd(m, rows), kinv(m, rows)})
+        HH_CK(cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
+  for (const void* f : {(const void*)kc, (const void*)kyf, (const void*)kyi})
     HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
   const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
 
@@ -352,8 +404,10 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     std::vector<Prob> probs(np);
     std::vector<BoxReq> wboxes(boxes_in.begin() + b0, boxes_in.begin() + b1);
     std::vector<int2> pitems, citems, gitems;
-    std::map<size_t, std::vector<int2>> pclass, cclass;  // launch classes by shared-memory size
-    long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0, ccount = 0;
+    // launch classes by shared-memory size: whole planes, streaming rows,
+    // streaming y columns, z columns
+    std::map<size_t, std::vector<int2>> pclass, rclass, yclass, cclass;
+    long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0, ccount = 0, prow = 0;
     for (int b = 0; b < nb; ++b) {
       const BoxReq& B = wboxes[b];
       const int nx = bdim[3 * (b0 + b)], ny = bdim[3 * (b0 + b) + 1], nz = bdim[3 * (b0 + b) + 2];
@@ -385,14 +439,29 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
         d.fld_off = fld_off;
         d.spc_off = spc_off;
-        const size_t pkey = smem_bucket(plane_smem_bytes<T>(nx, ny, nphase));
-        const size_t ckey = smem_bucket(column_smem_bytes<T>(colw, nz));
-        std::vector<int2>& pc = pclass[pkey];
-        std::vector<int2>& cc = cclass[ckey];
-        for (int k = 0; k < nz; ++k) {
-          pitems.push_back(make_int2(6 * b + a, k));
-          pc.push_back(make_int2(6 * b + a, k));
+        const int pr = 6 * b + a;
+        for (int k = 0; k < nz; ++k) pitems.push_back(make_int2(pr, k));
+        d.part0 = (int)prow;
+        if (plane_smem_bytes<T>(nx, ny, nphase) <= plane_lim) {
+          d.rows = 0;
+          d.npi = nz;
+          std::vector<int2>& pc = pclass[smem_bucket(plane_smem_bytes<T>(nx, ny, nphase))];
+          for (int k = 0; k < nz; ++k) pc.push_back(make_int2(pr, k));
+        } else {
+          const int R = stream_rows(nx, ny);
+          const int nch = (ny + R - 1) / R;
+          d.rows = R;
+          d.npi = nz * nch;
+          std::vector<int2>& rc = rclass[smem_bucket(rows_smem_bytes<T>(nx, R, nphase))];
+          std::vector<int2>& yc = yclass[smem_bucket(ycol_smem_bytes<T>(ny, ycw))];
+          for (int k = 0; k < nz; ++k) {
+            for (int j = 0; j < nch; ++j) rc.push_back(make_int2(pr, k | ((j * R) << 16)));
+            for (int x0 = 0; x0 < nxh; x0 += ycw) yc.push_back(make_int2(pr, k | (x0 << 16)));
+          }
         }
+        prow += d.npi;
+        const size_t ckey = smem_bucket(column_smem_bytes<T>(colw, nz));
+        std::vector<int2>& cc = cclass[ckey];
         for (int k = 0; k < ny; ++k)
           for (int x0 = 0; x0 < nxh; x0 += colw) cc.push_back(make_int2(6 * b + a, k | (x0 << 16)));
         fld_off += 6 * V;
@@ -407,18 +476,21 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       long long off;
       int n;
       int grid_f, grid_i;
+      bool rows;
     };
-    std::vector<Cls> pcl, ccl;
+    std::vector<Cls> pcl, ycl, ccl;
     citems.clear();
     std::vector<int2> clsitems;
-    for (auto& kv : pclass) {
-      pcl.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0});
-      clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
-    }
-    for (auto& kv : cclass) {
-      ccl.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0});
-      clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
-    }
+    auto add_classes = [&](std::map<size_t, std::vector<int2>>& m, std::vector<Cls>& out, bool rows) {
+      for (auto& kv : m) {
+        out.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows});
+        clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
+      }
+    };
+    add_classes(pclass, pcl, false);
+    add_classes(rclass, pcl, true);
+    add_classes(yclass, ycl, false);
+    add_classes(cclass, ccl, false);
     citems = clsitems;
     // ---- device buffers
     Prob* d_prob;
@@ -441,7 +513,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     if ((s = ensure(c, "q", fld_off * sizeof(T), (void**)&d_q)) != HH_OK) return s;
     if ((s = ensure(c, "x", fld_off * sizeof(T), (void**)&d_x)) != HH_OK) return s;
     if ((s = ensure(c, "spec", spc_off * sizeof(C2<T>), (void**)&d_spec)) != HH_OK) return s;
-    if ((s = ensure(c, "part", pitems.size() * 16 * sizeof(double), (void**)&d_part)) != HH_OK) return s;
+    if ((s = ensure(c, "part", std::max<size_t>(pitems.size(), prow) * 16 * sizeof(double), (void**)&d_part)) !=
+        HH_OK)
+      return s;
     double* d_cpart = nullptr;
     if (basic && (s = ensure(c, "cpart", std::max<long long>(ccount, 1) * 8 * sizeof(double), (void**)&d_cpart)) != HH_OK)
       return s;
@@ -484,6 +558,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kp.medium = med.kind;
     kp.nyq_mode = o.nyquist;
     kp.colw = colw;
+    kp.ycw = ycw;
     kp.nphase = std::max(nphase, 1);
     kp.plans = (const AxisPlan*)c.d_plans.p;
     kp.tw = (const double*)c.d_tw.p;
@@ -508,9 +583,10 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kpp.items = d_pit;
     kpp.nitems = (int)pitems.size();
     for (Cls& k : pcl) {
-      k.grid_f = grid_for<T>(c, (const void*)kf_it, threads, k.smem, k.n);
-      k.grid_i = grid_for<T>(c, (const void*)ki_it, threads, k.smem, k.n);
+      k.grid_f = grid_for<T>(c, (const void*)kfwd(MODE_ITER, k.rows), threads, k.smem, k.n);
+      k.grid_i = grid_for<T>(c, (const void*)kinv(MODE_ITER, k.rows), threads, k.smem, k.n);
     }
+    for (Cls& k : ycl) k.grid_f = k.grid_i = grid_for<T>(c, (const void*)kyf, threads, k.smem, k.n);
     for (Cls& k : ccl) k.grid_f = grid_for<T>(c, (const void*)kc, threads, k.smem, k.n);
     auto cls_params = [&](const Cls& k) {
       KParams<T> q = kp;
@@ -519,10 +595,26 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       return q;
     };
     // one launch per class for the plane and column passes
-    auto plane_pass = [&](auto kern, bool fwd) {
+    // forward pass of a mode: whole planes and streaming rows, then the
+    // streaming problems' y transforms; the inverse pass in reverse order
+    auto fwd_pass = [&](int mode) {
       for (const Cls& k : pcl) {
         ++c.launches;
-        kern<<<fwd ? k.grid_f : k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
+        kfwd(mode, k.rows)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k));
+      }
+      for (const Cls& k : ycl) {
+        ++c.launches;
+        kyf<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
+      }
+    };
+    auto inv_pass = [&](int mode) {
+      for (const Cls& k : ycl) {
+        ++c.launches;
+        kyi<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k), mode);
+      }
+      for (const Cls& k : pcl) {
+        ++c.launches;
+        kinv(mode, k.rows)<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
       }
     };
     auto column_pass = [&](int mode) {
@@ -547,9 +639,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       HH_CK(cudaGetLastError());
       auto basic_chunk = [&]() {
         for (int m = 0; m < chunk; ++m) {
-          plane_pass(kf_b, true);
+          fwd_pass(MODE_BASIC);
           column_pass(MODE_BASIC);
-          plane_pass(ki_b, false);
+          inv_pass(MODE_BASIC);
           ++c.launches;
           k_scal_basic<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_cpart, np, colw, o.tol, o.max_iter, o.fixed_iters);
         }
@@ -601,9 +693,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       if (bexec) cudaGraphExecDestroy(bexec);
     } else {
       // ---- right-hand side b = -G*(C:E), r = p = b, x = 0
-      plane_pass(kf_rhs, true);
+      fwd_pass(MODE_RHS);
       column_pass(MODE_RHS);
-      plane_pass(ki_rhs, false);
+      inv_pass(MODE_RHS);
       ++c.launches;
       k_scal_init<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, floor2);
       HH_CK(cudaGetLastError());
@@ -628,20 +720,20 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       };
       // true residual r = -G*(C:(E + x)) of the flagged problems
       auto true_pass = [&]() {
-        plane_pass(kf_tr, true);
+        fwd_pass(MODE_TRUE);
         column_pass(MODE_TRUE);
-        plane_pass(ki_tr, false);
+        inv_pass(MODE_TRUE);
       };
       // ---- iterations, in chunks captured as CUDA graphs; residual
       //      replacement at the end of every chunk (when enabled)
       auto launch_chunk = [&]() {
         for (int m = 0; m < chunk; ++m) {
           rec(m, 0);
-          plane_pass(kf_it, true);
+          fwd_pass(MODE_ITER);
           rec(m, 1);
           column_pass(MODE_ITER);
           rec(m, 2);
-          plane_pass(ki_it, false);
+          inv_pass(MODE_ITER);
           rec(m, 3);
           ++c.launches;
           k_scal_step<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.max_iter, o.fixed_iters);
@@ -754,7 +846,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         }
         if (prof) {
           sampled_pending = true;
-          const long long per[3] = {(long long)pcl.size(), (long long)ccl.size(), (long long)pcl.size()};
+          const long long per[3] = {(long long)(pcl.size() + ycl.size()), (long long)ccl.size(),
+                                    (long long)(pcl.size() + ycl.size())};
           for (int k = 0; k < 3; ++k) c.prof[pnames[k]].launches += chunk * per[k];
         }
         if (e != cudaSuccess) {

@@ -363,3 +363,39 @@ def test_basic_explicit_reference_and_anisotropic_medium(ctx):
                                max_iter=20000)
     cg = ctx.homogenize_aniso(c21_of(C), precision="fp64", tol=1e-11)
     assert rel(got["C"], cg["C"]) < 1e-7
+
+
+# ------------------------------------------- A10 row-streaming passes ------
+
+@pytest.mark.parametrize("shape,limit", [((10, 26, 28), 6000), ((7, 33, 20), 3000), ((9, 12, 45), 9000)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_streaming_rows_fixed_iterations_parity(ctx, shape, limit, precision, tol):
+    """Planes above the shared-memory limit take the row/column streaming
+    passes (several row chunks with a ragged last one, ragged y-column tiles)."""
+    lab = RNG.integers(0, 3, size=shape).astype(np.uint8)
+    ph = synth.PHASES_SOLID_CLAY_PORE
+    got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=12,
+                              plane_smem_limit=limit)
+    ref = O.homogenize_box(O.IsoMedium.from_labels(lab, ph), (slice(None),) * 3, fixed_iters=12)
+    assert np.all(got["iters"] == 12)
+    assert rel(got["Sigma"][0], ref["Sigma"]) < tol
+    assert rel(got["C"][0], ref["C"]) < tol
+
+
+def test_streaming_and_whole_plane_agree_converged(ctx):
+    img = synth.grf_two_phase(n=24, ell=3.0, porosity=0.3, seed=11)
+    ph = synth.PHASES_APPENDIX_B
+    a = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-10)
+    b = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-10, plane_smem_limit=8000)
+    assert rel(b["C"], a["C"]) < 1e-9
+    c = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-9, plane_smem_limit=8000, scheme="basic",
+                              max_iter=5000)
+    assert rel(c["C"], a["C"]) < 1e-7
+
+
+def test_streaming_anisotropic_level2_parity(ctx):
+    shape = (6, 14, 10)
+    C = rand_spd_field(shape, RNG)
+    got = ctx.homogenize_aniso(c21_of(C), precision="fp64", fixed_iters=10, plane_smem_limit=2500)
+    ref = O.homogenize_box(O.AnisoMedium(C), (slice(None),) * 3, fixed_iters=10)
+    assert rel(got["C"], ref["C"]) < 1e-10
