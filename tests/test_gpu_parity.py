@@ -328,7 +328,7 @@ def _ref_medium(ph):
 @pytest.mark.parametrize("shape", [(9, 10, 11), (16, 18, 12)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
 def test_basic_fixed_iterations_parity(ctx, shape, precision, tol):
-    lab = RNG.integers(0, 3, size=shape).astype(np.uint8)
+    lab = RNG.integers(0, 2, size=shape).astype(np.uint8)
     ph = synth.PHASES_APPENDIX_B
     got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=12, scheme="basic")
     ref = O.homogenize_box(O.IsoMedium.from_labels(lab, ph), (slice(None),) * 3, fixed_iters=12, scheme="basic",
