@@ -131,7 +131,8 @@ def measured_peaks():
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("hh_device.cuh", "hh_fft2.cuh", "hh_ctmath.h", "hh_post.cuh", "hh_host.cu"):
+    for f in ("hh_device.cuh", "hh_fftcore.cuh", "hh_fft2.cuh", "hh_fft2_inst.cu", "hh_ctmath.h", "hh_post.cuh",
+              "hh_host.cu"):
         with open(os.path.join(ROOT, "paper_2208_02320_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
