@@ -30,8 +30,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Relocatable device code: a kernel's register count after linking is the
 # largest over everything it calls, so one cap for every unit keeps the
 # transform functions from setting the occupancy of the field kernels
-# (80 registers: three 256-thread blocks per SM).
-MAX_REGS = 80
+# (64 registers: four 256-thread blocks per SM, matching the launch bounds).
+MAX_REGS = 64
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC"]
 
 

@@ -76,13 +76,13 @@ enum : int { MED_ISO = 0, MED_ANISO = 1 };
 enum : int { MODE_RHS = 0, MODE_ITER = 1, MODE_APPLY = 2, MODE_TRUE = 3, MODE_BASIC = 4 };
 enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NONFINITE = 2 };
 
-constexpr int kAvgParts = 12;
+constexpr int kAvgParts = 12;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
 // Resident 256-thread blocks per SM the plane and column passes are compiled
-// for (3: a register budget of 80 per thread; 4: 64).
+// for (4: a register budget of 64 per thread; 3: 80).
 #ifndef HH_FIELD_BLOCKS_PER_SM
-#define HH_FIELD_BLOCKS_PER_SM 3
+#define HH_FIELD_BLOCKS_PER_SM 4
 #endif
-constexpr int kFieldBlocksPerSM = HH_FIELD_BLOCKS_PER_SM;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
+constexpr int kFieldBlocksPerSM = HH_FIELD_BLOCKS_PER_SM;
 
 template <typename T>
 struct KParams {
@@ -272,6 +272,39 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], double* red) {
 }
 
 __device__ __forceinline__ double frob_w(int c) { return c < 3 ? 1.0 : 2.0; }
+
+// Per-thread accumulator of a sum of products with FP64-level accuracy. In
+// FP32 it keeps an unevaluated sum hi + lo of two floats: each product a b is
+// split exactly into p + e (p = fl(a b), e = fma(a, b, -p)), p is added to hi
+// with Knuth's two-sum (hi + p = s + t exactly) and the error terms t + e go
+// to lo. The FP64 pipe of this GPU runs at a small fraction of the FP32 rate,
+// so per-element FP64 arithmetic is avoided; the thread's total is converted
+// to FP64 once, for the block reduction. The _rn intrinsics keep the compiler
+// from contracting the two-sum into fused multiply-adds.
+template <typename T>
+struct DotAcc {
+  double v = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { v = fma(double(a), double(b), v); }
+  __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(t, e));
+  }
+  __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
+};
+
+// Weighted Frobenius product term of stored component c (weights 1, 1, 1, 2, 2, 2).
+template <typename T>
+__device__ __forceinline__ T frob_t(int c, T b) { return c < 3 ? b : T(2) * b; }
 
 // ---------------------------------------------------------------------------
 // Constitutive law (Section 4): isotropic sigma = lam tr(eps) I + 2 mu eps, or
@@ -542,7 +575,7 @@ struct FwdScal {
 // it stores), its stress s, and the mode's partial sum.
 template <typename T, int MODE>
 __device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
-                                          const FwdScal<T, MODE>& k, const T* lm, T (&s)[6], double& acc) {
+                                          const FwdScal<T, MODE>& k, const T* lm, T (&s)[6], DotAcc<T>& acc) {
   T* rr = P.r + d.fld_off;
   T* pp = P.p + d.fld_off;
   T* xx = P.x + d.fld_off;
@@ -567,7 +600,7 @@ __device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, lo
       const T pn = rv + k.beta * pv;
       pp[o] = pn;
       e[c] = pn;
-      acc += frob_w(c) * double(rv) * double(rv);
+      acc.add(rv, frob_t(c, rv));
     }
   } else if (MODE == MODE_TRUE) {
 #pragma unroll
@@ -597,7 +630,7 @@ __device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, lo
   }
   if (MODE == MODE_RHS) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) acc += frob_w(c) * double(s[c]) * double(s[c]);
+    for (int c = 0; c < 6; ++c) acc.add(s[c], frob_t(c, s[c]));
   }
 }
 
@@ -625,14 +658,14 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
 
-    double acc[1] = {0.0};
+    DotAcc<T> dot;
     const long long zoff = (long long)z * ny * nx;
     // voxel phase: stress of the whole plane into the pair rows
     for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
       const int y = v / nx;
       const int x = v - y * nx;
       T s[6];
-      fwd_voxel<T, MODE>(P, d, V, zoff + v, k, sm.lm, s, acc[0]);
+      fwd_voxel<T, MODE>(P, d, V, zoff + v, k, sm.lm, s, dot);
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * ny + y) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
     }
@@ -650,6 +683,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
       sp[((long long)c * d.nz + z) * pl + rem] = sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)];
     }
     if (fwd_slot<MODE>() >= 0) {
+      double acc[1] = {dot.value()};
       block_reduce<1>(acc, sm.red);
       if (threadIdx.x == 0) P.part[(long long)(d.part0 + z) * 16 + fwd_slot<MODE>()] = acc[0];
     }
@@ -681,13 +715,13 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_fwd(KParams<T> 
     const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
 
-    double acc[1] = {0.0};
+    DotAcc<T> dot;
     const long long off0 = ((long long)z * ny + y0) * nx;
     for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {
       const int yy = v / nx;
       const int x = v - yy * nx;
       T s[6];
-      fwd_voxel<T, MODE>(P, d, V, off0 + v, k, sm.lm, s, acc[0]);
+      fwd_voxel<T, MODE>(P, d, V, off0 + v, k, sm.lm, s, dot);
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * R + yy) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
     }
@@ -703,6 +737,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_fwd(KParams<T> 
       sp[(((long long)c * d.nz + z) * ny + y0) * nxh + rem] = sm.S[plane_spec_at(c, yy, rem - yy * nxh, R, nxh, RP)];
     }
     if (fwd_slot<MODE>() >= 0) {
+      double acc[1] = {dot.value()};
       block_reduce<1>(acc, sm.red);
       const int nch = (ny + R - 1) / R;
       if (threadIdx.x == 0) P.part[(long long)(d.part0 + z * nch + y0 / R) * 16 + fwd_slot<MODE>()] = acc[0];
@@ -753,11 +788,11 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_ycols(KParams<T> P, 
 // Column pass: z transform, projection, inverse z transform for one ky.
 // `skip_mode` selects which problems take part (as in the plane passes).
 // ---------------------------------------------------------------------------
-//   skip_mode == MODE_BASIC: the basic scheme's step instead of the
+//   BASIC: the basic scheme's step instead of the
 //   projection: the mode becomes Gamma0 tau, and the item leaves the partial
 //   sum of h |P tau|^2_F (h = 2 for the kx that stand for a conjugate pair)
 //   and, from the zero mode, Re tau^(0) for the equilibrium residual.
-template <typename T>
+template <typename T, bool BASIC>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
@@ -809,7 +844,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       C2<T> t[6];
 #pragma unroll
       for (int c = 0; c < 6; ++c) t[c] = tile[(c * nz + kzp) * W + kxl];
-      if (skip_mode == MODE_BASIC) {
+      if (BASIC) {
         C2<T> pt[6];
 #pragma unroll
         for (int c = 0; c < 6; ++c) pt[c] = t[c];
@@ -829,7 +864,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
 #pragma unroll
       for (int c = 0; c < 6; ++c) tile[(c * nz + kzp) * W + kxl] = t[c];
     }
-    if (skip_mode == MODE_BASIC) {
+    if (BASIC) {
       block_reduce<7>(acc, red);
       if (threadIdx.x == 0) {
         const int nxb = (nxh + P.colw - 1) / P.colw;
@@ -861,7 +896,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
 // stores and partial sums (acc: MODE_ITER <p,q>, <r,q>, <q,q>; RHS/TRUE <r,r>).
 template <typename T, int MODE>
 __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
-                                          const T (&qv)[6], double (&acc)[3]) {
+                                          const T (&qv)[6], DotAcc<T> (&acc)[3]) {
   T* rr = P.r + d.fld_off;
   T* pp = P.p + d.fld_off;
   T* qq = P.q + d.fld_off;
@@ -875,17 +910,17 @@ __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, lo
         pp[c * V + vo] = rv;
         xx[c * V + vo] = T(0);
       }
-      acc[0] += frob_w(c) * double(rv) * double(rv);
+      acc[0].add(rv, frob_t(c, rv));
     }
   } else if (MODE == MODE_ITER) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const long long o = c * V + vo;
       qq[o] = qv[c];
-      const double wq = frob_w(c) * double(qv[c]);
-      acc[0] += wq * double(pp[o]);
-      acc[1] += wq * double(rr[o]);
-      acc[2] += wq * double(qv[c]);
+      const T wq = frob_t(c, qv[c]);
+      acc[0].add(pp[o], wq);
+      acc[1].add(rr[o], wq);
+      acc[2].add(qv[c], wq);
     }
   } else {
 #pragma unroll
@@ -895,7 +930,9 @@ __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, lo
 
 // Partial sums of the inverse pass of one item into row `row` of P.part.
 template <typename T, int MODE>
-__device__ __forceinline__ void inv_partials(const KParams<T>& P, long long row, double (&acc)[3], double* red) {
+__device__ __forceinline__ void inv_partials(const KParams<T>& P, long long row, const DotAcc<T> (&dot)[3],
+                                             double* red) {
+  double acc[3] = {dot[0].value(), dot[1].value(), dot[2].value()};
   if (MODE == MODE_ITER) {
     block_reduce<3>(acc, red);
     if (threadIdx.x == 0) {
@@ -939,7 +976,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     pack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
     fft_lines<T, true>(sm.S, plane_rows(ny, RP), ax, sm.twx);
 
-    double acc[3] = {0.0, 0.0, 0.0};
+    DotAcc<T> acc[3];
     const T invV = T(1) / T(V);
     const long long zoff = (long long)z * ny * nx;
     for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
@@ -990,7 +1027,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_inv(KParams<T> 
     pack_rows<T>(sm.S, 3 * R, RP, nx, nxh, sm.pfx);
     fft_lines<T, true>(sm.S, Lines{3 * nr, nr, R * RP, RP, 1, false}, ax, sm.twx);
 
-    double acc[3] = {0.0, 0.0, 0.0};
+    DotAcc<T> acc[3];
     const T invV = T(1) / T(V);
     const long long off0 = ((long long)z * ny + y0) * nx;
     for (int v = threadIdx.x; v < nr * nx; v += blockDim.x) {

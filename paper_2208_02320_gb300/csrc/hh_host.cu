@@ -337,7 +337,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   auto* ki_rhs = k_plane_inv<T, MODE_RHS>;
   auto* ki_it = k_plane_inv<T, MODE_ITER>;
   auto* ki_tr = k_plane_inv<T, MODE_TRUE>;
-  auto* kc = k_column<T>;
+  auto* kc = k_column<T, false>;
+  auto* kcb = k_column<T, true>;
   auto* ku = k_flush<T>;
   auto* ka = k_avg<T>;
   auto* kf_b = k_plane_fwd<T, MODE_BASIC>;
@@ -366,7 +367,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     for (bool rows : {false, true})
       for (KFn f : {kfwd(m, rows), kinv(m, rows)})
         HH_CK(cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
-  for (const void* f : {(const void*)kc, (const void*)kyf, (const void*)kyi})
+  for (const void* f : {(const void*)kc, (const void*)kcb, (const void*)kyf, (const void*)kyi})
     HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
   const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
 
@@ -620,7 +621,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     auto column_pass = [&](int mode) {
       for (const Cls& k : ccl) {
         ++c.launches;
-        kc<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
+        (mode == MODE_BASIC ? kcb : kc)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
       }
     };
     const int gu = grid_for<T>(c, (const void*)ku, threads, 0, kpp.nitems);
@@ -1001,7 +1002,7 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   kpc.nitems = (int)cit.size();
   auto* kf = k_plane_fwd<T, MODE_APPLY>;
   auto* ki = k_plane_inv<T, MODE_APPLY>;
-  auto* kc = k_column<T>;
+  auto* kc = k_column<T, false>;
   HH_CK(cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
   HH_CK(cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm));
   HH_CK(cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
@@ -1832,7 +1833,7 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
   kpc.nitems = nc;
   auto* kf = k_plane_fwd<float, MODE_APPLY>;
   auto* ki = k_plane_inv<float, MODE_APPLY>;
-  auto* kc = k_column<float>;
+  auto* kc = k_column<float, false>;
   if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
       cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
       cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm) != cudaSuccess) {
