@@ -302,6 +302,16 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
+// L2 prefetch of a byte range by all threads of the block (one request per
+// 128-byte line). The field passes issue the next item's loads this way before
+// transforming the current one, so its global reads overlap the transform.
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+__device__ __forceinline__ void prefetch_range(const void* base, long long bytes) {
+  const char* b = reinterpret_cast<const char*>(base);
+  for (long long off = (long long)threadIdx.x * 128; off < bytes; off += (long long)blockDim.x * 128)
+    prefetch_l2(b + off);
+}
+
 // Weighted Frobenius product term of stored component c (weights 1, 1, 1, 2, 2, 2).
 template <typename T>
 __device__ __forceinline__ T frob_t(int c, T b) { return c < 3 ? b : T(2) * b; }
@@ -576,54 +586,71 @@ struct FwdScal {
 template <typename T, int MODE>
 __device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
                                           const FwdScal<T, MODE>& k, const T* lm, T (&s)[6], DotAcc<T>& acc) {
-  T* rr = P.r + d.fld_off;
-  T* pp = P.p + d.fld_off;
-  T* xx = P.x + d.fld_off;
-  const T* qq = P.q + d.fld_off;
+  T* __restrict__ rr = P.r + d.fld_off + vo;
+  T* __restrict__ pp = P.p + d.fld_off + vo;
+  T* __restrict__ xx = P.x + d.fld_off + vo;
+  const T* __restrict__ qq = P.q + d.fld_off + vo;
   const T Ed = d.lc < 3 ? T(1) : T(0.5);
+  // every load of the voxel is issued before any store, so the loads of all
+  // six components are in flight together
+  int lab = 0;
+  if (P.medium == MED_ISO) lab = P.labels[d.med_off + vo];
   T e[6];
   if (MODE == MODE_RHS) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) e[c] = T(0);
     e[d.lc] = Ed;
   } else if (MODE == MODE_ITER) {
+    T rv[6], pv[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const long long o = c * V + vo;
-      T rv = rr[o];
-      const T pv = pp[o];
-      if (k.pend) {
-        rv -= k.alpha * qq[o];
-        rr[o] = rv;
-        xx[o] = xx[o] + k.alpha * pv;
+      rv[c] = rr[c * V];
+      pv[c] = pp[c * V];
+    }
+    if (k.pend) {
+      T qv[6], xv[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        qv[c] = qq[c * V];
+        xv[c] = xx[c * V];
       }
-      const T pn = rv + k.beta * pv;
-      pp[o] = pn;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        rv[c] -= k.alpha * qv[c];
+        rr[c * V] = rv[c];
+        xx[c * V] = xv[c] + k.alpha * pv[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const T pn = rv[c] + k.beta * pv[c];
+      pp[c * V] = pn;
       e[c] = pn;
-      acc.add(rv, frob_t(c, rv));
+      acc.add(rv[c], frob_t(c, rv[c]));
     }
   } else if (MODE == MODE_TRUE) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = xx[c * V + vo];
+    for (int c = 0; c < 6; ++c) e[c] = xx[c * V];
     e[d.lc] += Ed;
   } else if (MODE == MODE_BASIC) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      const long long o = c * V + vo;
-      T xv = xx[o];
-      if (k.pend) {
-        xv -= qq[o];
-        xx[o] = xv;
+    for (int c = 0; c < 6; ++c) e[c] = xx[c * V];
+    if (k.pend) {
+      T qv[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) qv[c] = qq[c * V];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        e[c] -= qv[c];
+        xx[c * V] = e[c];
       }
-      e[c] = xv;
     }
     e[d.lc] += Ed;
   } else {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) e[c] = pp[c * V + vo];
+    for (int c = 0; c < 6; ++c) e[c] = pp[c * V];
   }
   if (P.medium == MED_ISO) {
-    const int lab = P.labels[d.med_off + vo];
     stress_iso<T>(e, lm[2 * lab], lm[2 * lab + 1], s);
   } else {
     stress_aniso<T>(e, P.c21 + d.med_off, V, vo, s);
@@ -668,6 +695,19 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
       fwd_voxel<T, MODE>(P, d, V, zoff + v, k, sm.lm, s, dot);
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * ny + y) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
+    }
+    if (MODE == MODE_ITER && it + gridDim.x < P.nitems) {
+      // the fields of this block's next plane
+      const int2 wn = P.items[it + gridDim.x];
+      if (!skip_problem<T>(P.st, wn.x, MODE)) {
+        const Prob& dn = P.prob[wn.x];
+        const long long Vn = (long long)dn.nx * dn.ny * dn.nz;
+        const long long pln = (long long)dn.nx * dn.ny;
+        const long long o = dn.fld_off + (long long)wn.y * pln;
+        for (int c = 0; c < 6; ++c)
+          for (const T* f : {P.r, P.p, P.q, P.x}) prefetch_range(f + o + c * Vn, pln * (long long)sizeof(T));
+        if (P.medium == MED_ISO) prefetch_range(P.labels + dn.med_off + (long long)wn.y * pln, pln);
+      }
     }
     __syncthreads();
     fft_lines<T, false>(sm.S, plane_rows(ny, RP), ax, sm.twx);
@@ -819,6 +859,20 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       const int cz = e / W;  // c * nz + z
       tile[e] = sp[(long long)cz * pl + kyp * nxh + kx0 + kx];
     }
+    if (it + gridDim.x < P.nitems) {
+      // the spectrum segments of this block's next item
+      const int2 wn = P.items[it + gridDim.x];
+      if (!skip_problem<T>(P.st, wn.x, skip_mode)) {
+        const Prob& dn = P.prob[wn.x];
+        const int Wn = min(P.colw, dn.nxh - (wn.y >> 16));
+        const long long pln = (long long)dn.ny * dn.nxh;
+        const C2<T>* b = P.spec + dn.spc_off + (long long)(wn.y & 0xffff) * dn.nxh + (wn.y >> 16);
+        for (int cz = threadIdx.x; cz < 6 * dn.nz; cz += blockDim.x) {
+          prefetch_l2(b + cz * pln);
+          prefetch_l2(b + cz * pln + Wn - 1);
+        }
+      }
+    }
     __syncthreads();
     Lines Lz{6 * W, W, nz * W, 1, W, true};
     fft_lines<T, false>(tile, Lz, az, twz);
@@ -897,34 +951,39 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
 template <typename T, int MODE>
 __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
                                           const T (&qv)[6], DotAcc<T> (&acc)[3]) {
-  T* rr = P.r + d.fld_off;
-  T* pp = P.p + d.fld_off;
-  T* qq = P.q + d.fld_off;
-  T* xx = P.x + d.fld_off;
+  T* __restrict__ rr = P.r + d.fld_off + vo;
+  T* __restrict__ pp = P.p + d.fld_off + vo;
+  T* __restrict__ qq = P.q + d.fld_off + vo;
+  T* __restrict__ xx = P.x + d.fld_off + vo;
   if (MODE == MODE_RHS || MODE == MODE_TRUE) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const T rv = -qv[c];
-      rr[c * V + vo] = rv;
+      rr[c * V] = rv;
       if (MODE == MODE_RHS) {
-        pp[c * V + vo] = rv;
-        xx[c * V + vo] = T(0);
+        pp[c * V] = rv;
+        xx[c * V] = T(0);
       }
       acc[0].add(rv, frob_t(c, rv));
     }
   } else if (MODE == MODE_ITER) {
+    T pv[6], rv[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const long long o = c * V + vo;
-      qq[o] = qv[c];
+      pv[c] = pp[c * V];
+      rv[c] = rr[c * V];
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      qq[c * V] = qv[c];
       const T wq = frob_t(c, qv[c]);
-      acc[0].add(pp[o], wq);
-      acc[1].add(rr[o], wq);
+      acc[0].add(pv[c], wq);
+      acc[1].add(rv[c], wq);
       acc[2].add(qv[c], wq);
     }
   } else {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) qq[c * V + vo] = qv[c];
+    for (int c = 0; c < 6; ++c) qq[c * V] = qv[c];
   }
 }
 
@@ -970,6 +1029,22 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
       const int rem = e - c * pl;
       const int ky = rem / nxh;
       sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)] = sp[((long long)c * d.nz + z) * pl + rem];
+    }
+    if (MODE == MODE_ITER) {
+      // p and r of this plane (read after the transforms), and the spectrum
+      // plane of this block's next item
+      const long long pln = (long long)nx * ny;
+      for (int c = 0; c < 6; ++c)
+        for (const T* f : {P.p, P.r}) prefetch_range(f + d.fld_off + (long long)z * pln + c * V, pln * (long long)sizeof(T));
+      if (it + gridDim.x < P.nitems) {
+        const int2 wn = P.items[it + gridDim.x];
+        if (!skip_problem<T>(P.st, wn.x, MODE)) {
+          const Prob& dn = P.prob[wn.x];
+          const long long spn = (long long)dn.ny * dn.nxh;
+          for (int c = 0; c < 6; ++c)
+            prefetch_range(P.spec + dn.spc_off + ((long long)c * dn.nz + wn.y) * spn, spn * (long long)sizeof(C2<T>));
+        }
+      }
     }
     __syncthreads();
     fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
