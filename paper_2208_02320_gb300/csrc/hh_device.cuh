@@ -55,7 +55,7 @@ struct Prob {
   int part0;                         // first partial-sum row of its field-pass items
   int npi;                           // field-pass items: nz, or nz * row chunks when streaming
   int rows;                          // rows per row-streaming item; 0: whole planes
-  int pad;
+  int cw;                            // spectrum columns (ky, kx) per column-pass item
   long long med_off;                 // iso: byte offset of labels; aniso: element offset of C21
   long long fld_off;                 // element offset of r, p, q (6 V each)
   long long spc_off;                 // complex offset of the spectrum (6 nz ny nxh)
@@ -111,7 +111,6 @@ struct KParams {
   int max_iter;
   int fixed_iters;
   int nprob;
-  int colw;          // kx columns per column-pass item
   int ycw;           // kx columns per y-column item (row-streaming problems)
   // basic scheme: Green operator of the isotropic reference medium,
   // Gamma0 = g0a (n (x) v + v (x) n) - g0b (n . v) n (x) n, v = tau n
@@ -824,8 +823,38 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_ycols(KParams<T> P, 
   }
 }
 
+// Shared-memory layout of the column pass (must match column_smem_bytes on
+// the host): W-column tile of the six components, z twiddles, the signed
+// z and y frequencies, and the block-reduction buffer.
+template <typename T>
+struct ColumnSmem {
+  C2<T>* tile;  // 6 * nz * cw
+  C2<T>* twz;   // nz
+  int* sfz;     // nz
+  int* sfy;     // ny
+  double* red;  // 32 * 7
+};
+
+template <typename T>
+__device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int nz, int ny) {
+  ColumnSmem<T> s;
+  size_t o = 0;
+  s.tile = reinterpret_cast<C2<T>*>(base + o);
+  o += sizeof(C2<T>) * 6 * (size_t)nz * cw;
+  s.twz = reinterpret_cast<C2<T>*>(base + o);
+  o += sizeof(C2<T>) * nz;
+  s.sfz = reinterpret_cast<int*>(base + o);
+  o += sizeof(int) * nz;
+  s.sfy = reinterpret_cast<int*>(base + o);
+  o += sizeof(int) * ny;
+  o = (o + 7) & ~size_t(7);
+  s.red = reinterpret_cast<double*>(base + o);
+  return s;
+}
+
 // ---------------------------------------------------------------------------
-// Column pass: z transform, projection, inverse z transform for one ky.
+// Column pass: z transform, projection, inverse z transform for cw
+// consecutive spectrum columns j = ky position * nxh + kx of one problem.
 // `skip_mode` selects which problems take part (as in the plane passes).
 // ---------------------------------------------------------------------------
 //   BASIC: the basic scheme's step instead of the
@@ -839,53 +868,49 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
     const Prob d = P.prob[w.x];
-    const int kyp = w.y & 0xffff;
-    const int kx0 = w.y >> 16;
+    const int j0 = w.y;  // first spectrum column: j = ky position * nxh + kx
     const int nx = d.nx, ny = d.ny, nz = d.nz, nxh = d.nxh;
-    const int W = min(P.colw, nxh - kx0);  // kx columns of this item
-    C2<T>* tile = reinterpret_cast<C2<T>*>(smem);
-    C2<T>* twz = tile + 6 * nz * P.colw;
-    int* sfz = reinterpret_cast<int*>(twz + nz);
-    double* red = reinterpret_cast<double*>(
-        smem + ((sizeof(C2<T>) * (6 * nz * P.colw + nz) + sizeof(int) * nz + 7) & ~size_t(7)));  // 32 * 7
+    const int pl = ny * nxh;
+    const int W = min(d.cw, pl - j0);  // columns of this item, contiguous in every (c, z) plane
+    ColumnSmem<T> sm = column_layout<T>(smem, d.cw, nz, ny);
     const AxisPlan az = P.plans[d.pz];
     const AxisPlan ay = P.plans[d.py];
-    load_tw<T>(twz, P.tw, az);
-    for (int t = threadIdx.x; t < nz; t += blockDim.x) sfz[t] = P.itab[az.sf_off + t];
-    C2<T>* sp = P.spec + d.spc_off;
-    const int pl = ny * nxh;
+    load_tw<T>(sm.twz, P.tw, az);
+    for (int t = threadIdx.x; t < nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
+    for (int t = threadIdx.x; t < ny; t += blockDim.x) sm.sfy[t] = P.itab[ay.sf_off + t];
+    C2<T>* sp = P.spec + d.spc_off + j0;
     for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
-      const int kx = e % W;
+      const int jl = e % W;
       const int cz = e / W;  // c * nz + z
-      tile[e] = sp[(long long)cz * pl + kyp * nxh + kx0 + kx];
+      sm.tile[e] = sp[(long long)cz * pl + jl];
     }
     if (it + gridDim.x < P.nitems) {
       // the spectrum segments of this block's next item
       const int2 wn = P.items[it + gridDim.x];
       if (!skip_problem<T>(P.st, wn.x, skip_mode)) {
         const Prob& dn = P.prob[wn.x];
-        const int Wn = min(P.colw, dn.nxh - (wn.y >> 16));
         const long long pln = (long long)dn.ny * dn.nxh;
-        const C2<T>* b = P.spec + dn.spc_off + (long long)(wn.y & 0xffff) * dn.nxh + (wn.y >> 16);
-        for (int cz = threadIdx.x; cz < 6 * dn.nz; cz += blockDim.x) {
-          prefetch_l2(b + cz * pln);
-          prefetch_l2(b + cz * pln + Wn - 1);
-        }
+        const int Wn = (int)min((long long)dn.cw, pln - wn.y);
+        const C2<T>* b = P.spec + dn.spc_off + wn.y;
+        for (int cz = threadIdx.x; cz < 6 * dn.nz; cz += blockDim.x)
+          for (int o = 0; o < Wn; o += 128 / (int)sizeof(C2<T>)) prefetch_l2(b + cz * pln + o);
       }
     }
     __syncthreads();
-    Lines Lz{6 * W, W, nz * W, 1, W, true};
-    fft_lines<T, false>(tile, Lz, az, twz);
-    // projection of every (kz, kx) mode of this ky
-    const int my = P.itab[ay.sf_off + kyp];
-    const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
+    const Lines Lz{6 * W, W, nz * W, 1, W, true};
+    fft_lines<T, false>(sm.tile, Lz, az, sm.twz);
+    // projection (or the basic scheme's Green operator) of every mode
     double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int e = threadIdx.x; e < nz * W; e += blockDim.x) {
-      const int kxl = e % W;
-      const int kx = kx0 + kxl;
+      const int jl = e % W;
       const int kzp = e / W;
-      const int mz = sfz[kzp];
+      const int j = j0 + jl;
+      const int kyp = j / nxh;
+      const int kx = j - kyp * nxh;
+      const int my = sm.sfy[kyp];
+      const int mz = sm.sfz[kzp];
       const bool nyq_x = (nx % 2 == 0) && (2 * kx == nx);
+      const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
       const bool nyq_z = (nz % 2 == 0) && (2 * mz == nz);
       T x0 = T(kx) / T(nx), x1 = T(my) / T(ny), x2 = T(mz) / T(nz);
       if (P.nyq_mode == 0) {
@@ -897,7 +922,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       }
       C2<T> t[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) t[c] = tile[(c * nz + kzp) * W + kxl];
+      for (int c = 0; c < 6; ++c) t[c] = sm.tile[(c * nz + kzp) * W + jl];
       if (BASIC) {
         C2<T> pt[6];
 #pragma unroll
@@ -916,23 +941,22 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
         project_mode<T>(t, x0, x1, x2);
       }
 #pragma unroll
-      for (int c = 0; c < 6; ++c) tile[(c * nz + kzp) * W + kxl] = t[c];
+      for (int c = 0; c < 6; ++c) sm.tile[(c * nz + kzp) * W + jl] = t[c];
     }
     if (BASIC) {
-      block_reduce<7>(acc, red);
+      block_reduce<7>(acc, sm.red);
       if (threadIdx.x == 0) {
-        const int nxb = (nxh + P.colw - 1) / P.colw;
-        double* cp = P.cpart + (long long)(d.col0 + kyp * nxb + kx0 / P.colw) * 8;
+        double* cp = P.cpart + (long long)(d.col0 + j0 / d.cw) * 8;
 #pragma unroll
         for (int k = 0; k < 7; ++k) cp[k] = acc[k];
       }
     }
     __syncthreads();
-    fft_lines<T, true>(tile, Lz, az, twz);
+    fft_lines<T, true>(sm.tile, Lz, az, sm.twz);
     for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
-      const int kx = e % W;
+      const int jl = e % W;
       const int cz = e / W;
-      sp[(long long)cz * pl + kyp * nxh + kx0 + kx] = tile[e];
+      sp[(long long)cz * pl + jl] = sm.tile[e];
     }
     __syncthreads();
   }
@@ -1314,15 +1338,14 @@ __global__ void k_scal_basic_init(PState* st, int nprob) {
 // Parseval sum h |P sigma^|^2 / sum_c w_c (Re sigma^_c(0))^2) of the current
 // strain decides; otherwise the update x <- x - Gamma0 * sigma that the
 // inverse pass stored in q is applied by the next forward pass.
-__global__ void k_scal_basic(const Prob* prob, PState* st, const double* cpart, int nprob, int colw, double tol,
+__global__ void k_scal_basic(const Prob* prob, PState* st, const double* cpart, int nprob, double tol,
                              int max_iter, int fixed_iters) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nprob || !st[i].active) return;
   const Prob d = prob[i];
   PState& s = st[i];
   s.pending = 0;
-  const int nxb = (d.nxh + colw - 1) / colw;
-  const int n = d.ny * nxb;
+  const int n = (d.ny * d.nxh + d.cw - 1) / d.cw;
   double eq = 0.0, m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = 0; j < n; ++j) {
     const double* cp = cpart + (long long)(d.col0 + j) * 8;

@@ -139,7 +139,7 @@ template <typename T, int N1, int N2, bool INV>
 __device__ __noinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>* tw) {
   const int nthr = blockDim.x;
   if constexpr (N2 > 1) {
-    constexpr int P = 1;  // (line, t1) pairs per thread per round
+    constexpr int P = N2 <= 2 ? 4 : (N2 <= 4 ? 2 : 1);  // (line, t1) pairs per thread per round
     const int lpr = (P * nthr) / N1;    // whole lines per round
     for (int l0 = 0; l0 < L.n; l0 += lpr) {
       const int nl = min(lpr, L.n - l0);
@@ -182,7 +182,7 @@ __device__ __noinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>*
     }
   }
   {
-    constexpr int P = 1;  // (line, k2) pairs per thread per round
+    constexpr int P = N1 <= 2 ? 4 : (N1 <= 4 ? 2 : 1);  // (line, k2) pairs per thread per round
     const int lpr = (P * nthr) / N2;
     for (int l0 = 0; l0 < L.n; l0 += lpr) {
       const int nl = min(lpr, L.n - l0);

@@ -200,11 +200,22 @@ static size_t plane_smem_bytes(int nx, int ny, int nphase) {
 }
 
 template <typename T>
-static size_t column_smem_bytes(int colw, int nz) {
-  size_t o = sizeof(C2<T>) * 6 * (size_t)nz * colw + sizeof(C2<T>) * nz + sizeof(int) * nz;
+static size_t column_smem_bytes(int cw, int nz, int ny) {
+  size_t o = sizeof(C2<T>) * (6 * (size_t)nz * cw + nz) + sizeof(int) * ((size_t)nz + ny);
   o = (o + 7) & ~size_t(7);
   o += 32 * 7 * sizeof(double);  // block reduction of the basic scheme's residual partials
   return (o + 15) & ~size_t(15);
+}
+constexpr size_t kColumnSmem = 48 * 1024;  // per-block target of the column pass
+
+// Spectrum columns per column-pass item: the widest power of two up to 32
+// (FP32) or 16 (FP64) whose tile fits the column target, else what fits at all.
+template <typename T>
+static int column_width(int nz, int ny, size_t optin) {
+  int cw = sizeof(T) == 4 ? 32 : 16;
+  while (cw > 1 && column_smem_bytes<T>(cw, nz, ny) > kColumnSmem) cw /= 2;
+  while (cw > 1 && column_smem_bytes<T>(cw, nz, ny) > optin) cw /= 2;
+  return cw;
 }
 
 // Row-streaming passes: R rows of a plane per block; y columns: W kx columns.
@@ -304,14 +315,12 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
 
   // shared memory: a whole plane per plane-pass block when it fits the plane
   // limit, else R rows per block and W kx columns per y-column block (row
-  // streaming); colw kx columns per column-pass block
+  // streaming); column_width() spectrum columns per column-pass block
   const size_t plane_lim = o.plane_smem_limit > 0 ? std::min<size_t>(o.plane_smem_limit, c.smem_optin) : c.smem_optin;
-  int colw = (sizeof(T) == 4) ? 16 : 8;
   int ycw = 16;
   const size_t stream_target = std::min(kStreamSmem, plane_lim);
   for (int b = 0; b < nbox; ++b) {
     const int nx = bdim[3 * b], ny = bdim[3 * b + 1], nz = bdim[3 * b + 2];
-    while (colw > 1 && column_smem_bytes<T>(colw, nz) > c.smem_optin) colw /= 2;
     if (plane_smem_bytes<T>(nx, ny, nphase) > plane_lim) {
       while (ycw > 1 && ycol_smem_bytes<T>(ny, ycw) > std::max(stream_target, ycol_smem_bytes<T>(ny, 1))) ycw /= 2;
       if (rows_smem_bytes<T>(nx, 1, nphase) > c.smem_optin || ycol_smem_bytes<T>(ny, 1) > c.smem_optin) {
@@ -319,7 +328,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         return HH_ERR_UNSUPPORTED;
       }
     }
-    if (column_smem_bytes<T>(colw, nz) > c.smem_optin) {
+    if (column_smem_bytes<T>(1, nz, ny) > c.smem_optin) {
       c.err = "z column too long for shared memory";
       return HH_ERR_UNSUPPORTED;
     }
@@ -435,8 +444,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.lc = a;
         d.box = b0 + b;
         d.plane0 = (int)pitems.size();
+        d.cw = column_width<T>(nz, ny, c.smem_optin);
         d.col0 = (int)ccount;
-        ccount += (long long)ny * ((nxh + colw - 1) / colw);
+        ccount += ((long long)ny * nxh + d.cw - 1) / d.cw;
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
         d.fld_off = fld_off;
         d.spc_off = spc_off;
@@ -461,10 +471,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
           }
         }
         prow += d.npi;
-        const size_t ckey = smem_bucket(column_smem_bytes<T>(colw, nz));
+        const size_t ckey = smem_bucket(column_smem_bytes<T>(d.cw, nz, ny));
         std::vector<int2>& cc = cclass[ckey];
-        for (int k = 0; k < ny; ++k)
-          for (int x0 = 0; x0 < nxh; x0 += colw) cc.push_back(make_int2(6 * b + a, k | (x0 << 16)));
+        for (int j0 = 0; j0 < ny * nxh; j0 += d.cw) cc.push_back(make_int2(6 * b + a, j0));
         fld_off += 6 * V;
         spc_off += 6LL * nz * ny * nxh;
       }
@@ -558,7 +567,6 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kp.st = d_st;
     kp.medium = med.kind;
     kp.nyq_mode = o.nyquist;
-    kp.colw = colw;
     kp.ycw = ycw;
     kp.nphase = std::max(nphase, 1);
     kp.plans = (const AxisPlan*)c.d_plans.p;
@@ -644,7 +652,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
           column_pass(MODE_BASIC);
           inv_pass(MODE_BASIC);
           ++c.launches;
-          k_scal_basic<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_cpart, np, colw, o.tol, o.max_iter, o.fixed_iters);
+          k_scal_basic<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_cpart, np, o.tol, o.max_iter, o.fixed_iters);
         }
       };
       cudaGraphExec_t bexec = nullptr;
@@ -916,9 +924,8 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   const long long V = (long long)nx * ny * nz;
   const int nxh = nx / 2 + 1;
   const size_t psm = plane_smem_bytes<T>(nx, ny, nphase);
-  int colw = nxh;
-  while (colw > 1 && column_smem_bytes<T>(colw, nz) > c.smem_optin) colw = (colw + 1) / 2;
-  const size_t csm = column_smem_bytes<T>(colw, nz);
+  const int colw = column_width<T>(nz, ny, c.smem_optin);
+  const size_t csm = column_smem_bytes<T>(colw, nz, ny);
   if (psm > c.smem_optin || csm > c.smem_optin) {
     c.err = "plane too large for shared memory";
     return HH_ERR_UNSUPPORTED;
@@ -935,10 +942,11 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   d.px = px;
   d.py = py;
   d.pz = pz;
+  d.cw = colw;
+  d.npi = nz;
   std::vector<int2> pit, cit;
   for (int k = 0; k < nz; ++k) pit.push_back(make_int2(0, k));
-  for (int k = 0; k < ny; ++k)
-    for (int x0 = 0; x0 < nxh; x0 += colw) cit.push_back(make_int2(0, k | (x0 << 16)));
+  for (int j0 = 0; j0 < ny * nxh; j0 += colw) cit.push_back(make_int2(0, j0));
   Prob* d_prob;
   int2 *d_pit, *d_cit;
   T *d_p, *d_q, *d_c21 = nullptr, *d_lm;
@@ -981,7 +989,6 @@ static hh_status apply_operator(Ctx& c, const hh_options& o, const Medium& med, 
   kp.prob = d_prob;
   kp.medium = med.kind;
   kp.nyq_mode = o.nyquist;
-  kp.colw = colw;
   kp.nphase = std::max(nphase, 1);
   kp.plans = (const AxisPlan*)c.d_plans.p;
   kp.tw = (const double*)c.d_tw.p;
@@ -1745,15 +1752,14 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
     set_last_error("hh_apply_operator_noalloc: device query failed");
     return HH_ERR_CUDA;
   }
-  int colw = nxh;
-  while (colw > 1 && column_smem_bytes<float>(colw, nz) > (size_t)smem_optin) colw = (colw + 1) / 2;
+  const int colw = column_width<float>(nz, ny, (size_t)smem_optin);
   const size_t psm = plane_smem_bytes<float>(nx, ny, nphase);
-  const size_t csm = column_smem_bytes<float>(colw, nz);
+  const size_t csm = column_smem_bytes<float>(colw, nz, ny);
   if (psm > (size_t)smem_optin || csm > (size_t)smem_optin) {
     set_last_error("hh_apply_operator_noalloc: plane too large for shared memory");
     return HH_ERR_UNSUPPORTED;
   }
-  const int ncol = ny * ((nxh + colw - 1) / colw);
+  const int ncol = (ny * nxh + colw - 1) / colw;
   struct Staging {
     Prob prob;
     AxisPlan plans[3];
@@ -1791,9 +1797,10 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
   d.pz = 2;
   for (int i = 0; i < 2 * nphase; ++i) h.lm[i] = lm[i];
   for (int k = 0; k < nz; ++k) h.items[k] = make_int2(0, k);
+  d.cw = colw;
+  d.npi = nz;
   int nc = 0;
-  for (int k = 0; k < ny; ++k)
-    for (int x0 = 0; x0 < nxh; x0 += colw) h.items[nz + nc++] = make_int2(0, k | (x0 << 16));
+  for (int j0 = 0; j0 < ny * nxh; j0 += colw) h.items[nz + nc++] = make_int2(0, j0);
 
   // scratch layout: [staging][half spectrum]
   const size_t spec_off = align256(sizeof(Staging));
@@ -1813,7 +1820,6 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
   kp.prob = &dst->prob;
   kp.medium = MED_ISO;
   kp.nyq_mode = nyquist;
-  kp.colw = colw;
   kp.nphase = nphase;
   kp.plans = dst->plans;
   kp.tw = dst->tw;
