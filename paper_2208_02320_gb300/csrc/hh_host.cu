@@ -232,10 +232,14 @@ constexpr size_t kStreamSmem = 48 * 1024;  // per-block target of the streaming 
 // Launch classes: shared-memory footprints are rounded up to these sizes and
 // every class gets its own launch, so small subimages are not held to the
 // occupancy of the largest one.
+// The field kernels run at most kFieldBlocksPerSM blocks per SM (register
+// bound), so footprints are grouped by the blocks per SM their shared memory
+// allows (228 KB per SM, 1 KB reserved per block): one launch per tier, with
+// the tier's largest footprint.
 static size_t smem_bucket(size_t bytes) {
-  static const size_t kb[] = {12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128, 160, 192, 227};
-  for (size_t k : kb)
-    if (bytes <= k * 1024) return k * 1024;
+  const size_t per_sm = 228 * 1024, reserve = 1024;
+  for (int nb = kFieldBlocksPerSM; nb > 1; --nb)
+    if (bytes <= per_sm / nb - reserve) return per_sm / nb - reserve;
   return bytes;
 }
 
@@ -491,8 +495,15 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     std::vector<Cls> pcl, ycl, ccl;
     citems.clear();
     std::vector<int2> clsitems;
+    // within a launch, the largest problems first (shortest tail)
+    auto by_size = [&](const int2& a, const int2& b) {
+      const Prob& pa = probs[a.x];
+      const Prob& pb = probs[b.x];
+      return (long long)pa.nx * pa.ny * pa.nz > (long long)pb.nx * pb.ny * pb.nz;
+    };
     auto add_classes = [&](std::map<size_t, std::vector<int2>>& m, std::vector<Cls>& out, bool rows) {
       for (auto& kv : m) {
+        std::stable_sort(kv.second.begin(), kv.second.end(), by_size);
         out.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows});
         clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
       }
