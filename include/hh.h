@@ -228,6 +228,54 @@ hh_status hh_fit_inverse_n(hh_ctx *ctx, const int *ns, const double *M, int coun
                            double *M_inf, double *C);
 
 /* ---------------------------------------------------------------------------
+ * Subimage surrogate (not in the paper; a learned shortcut for the first
+ * hierarchical level). A small 3D CNN maps a cube of phase labels (0, 1, 2;
+ * edge `edge`, x fastest) to the 21 upper-triangle components of its
+ * effective Voigt stiffness (row-major i <= j, engineering shear), divided by
+ * a caller-chosen scale. Layers: one-hot(3) -> conv3^3 3->16 -> ReLU ->
+ * conv 16->32 stride 2 -> ReLU -> conv 32->64 stride 2 -> ReLU -> conv 64->64
+ * -> ReLU -> mean pool -> fc 64->128 -> ReLU -> fc 128->21; zero padding 1.
+ * Parameters are one flat FP32 vector of hh_cnn_num_params() values: per conv
+ * layer W[tap][ci][co] (tap = (kz*3+ky)*3+kx) then bias[co]; per fc layer
+ * W[in][out] then bias[out]. The convolutions run on BF16 tensor cores with
+ * FP32 accumulation. All buffers below are host memory owned by the caller;
+ * errors: HH_ERR_ARG (count < 1, edge outside 8..256, NULL pointers),
+ * HH_ERR_OOM, HH_ERR_CUDA. */
+int64_t hh_cnn_num_params(void);
+
+/* Network outputs out[count][21] for `count` cubes labels[count][edge^3]. */
+hh_status hh_cnn_forward(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+                         const float *params, float *out);
+
+/* Mean squared error over the count x 21 outputs against targets[count][21]
+ * (*loss) and its gradient with respect to the parameters (grad[n_params]). */
+hh_status hh_cnn_loss_grad(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+                           const float *params, const float *targets, double *loss, float *grad);
+
+/* Trains one network from `init` with Adam (lr, beta 0.9/0.999, eps 1e-8) on
+ * minibatches of `batch` cubes (whole batches of a seeded permutation per
+ * epoch) and writes the final parameters to params_out. loss_history
+ * (epochs values, may be NULL) receives each epoch's mean training loss. */
+hh_status hh_surrogate_train(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+                             const float *targets, const float *init, int epochs, int batch,
+                             double lr, uint64_t seed, float *params_out, double *loss_history);
+
+/* Predictions of an ensemble (params[ensemble][n_params]) in GPa:
+ * out[count][ensemble][21] = network output * scale. */
+hh_status hh_surrogate_predict(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+                               const float *params, int ensemble, double scale, float *out);
+
+/* The gate: accept[i] = 1 when every member's Voigt-projected K and G lie in
+ * the cube's own Reuss..Voigt bounds of the phase moduli (from its phase
+ * fractions), the relative spread (max - min) / mean over the members of K
+ * and of G is <= spread, and the members' mean stiffness is positive
+ * definite; else 0 (the cube goes to the FFT solver). c21[count][21]
+ * receives the members' mean. members[count][ensemble][21] in GPa. */
+hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+                            const hh_phase *phases, int nphase, const float *members,
+                            int ensemble, double spread, int *accept, double *c21);
+
+/* ---------------------------------------------------------------------------
  * Operator application without allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (code
  * that runs inside a memory pool or arena it does not own, allocation-free

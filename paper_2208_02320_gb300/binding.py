@@ -117,6 +117,12 @@ _SIGNATURES = {
     "hh_profile_read": (_I, [_P, _P, _I, _P]),
     "hh_profile_reset": (_I, [_P]),
     "hh_apply_operator_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _I, _P]),
+    "hh_cnn_num_params": (ctypes.c_int64, []),
+    "hh_cnn_forward": (_I, [_P, _P, _I, _I, _P, _P]),
+    "hh_cnn_loss_grad": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
+    "hh_surrogate_train": (_I, [_P, _P, _I, _I, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
+    "hh_surrogate_predict": (_I, [_P, _P, _I, _I, _P, _I, _D, _P]),
+    "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
 }
 
 _lib = None
@@ -346,6 +352,67 @@ class Context:
         s = self._lib.hh_fit_inverse_n(self._h, _ptr(nsa), _ptr(Ma), len(nsa), ctypes.byref(mi), ctypes.byref(c))
         self._check(s, "hh_fit_inverse_n", allow_warn=False)
         return mi.value, c.value
+
+    # ----- subimage surrogate (3D CNN, BF16 tensor cores) -----
+    def cnn_num_params(self) -> int:
+        return int(self._lib.hh_cnn_num_params())
+
+    @staticmethod
+    def _cubes(labels):
+        lab = np.ascontiguousarray(labels, dtype=np.uint8)
+        if lab.ndim == 3:
+            lab = lab[None]
+        assert lab.ndim == 4 and lab.shape[1] == lab.shape[2] == lab.shape[3], "cubes [count][e][e][e]"
+        return lab, lab.shape[0], lab.shape[1]
+
+    def cnn_forward(self, labels, params):
+        lab, n, e = self._cubes(labels)
+        th = np.ascontiguousarray(params, dtype=np.float32)
+        out = np.zeros((n, 21), dtype=np.float32)
+        self._check(self._lib.hh_cnn_forward(self._h, _ptr(lab), n, e, _ptr(th), _ptr(out)), "hh_cnn_forward",
+                    allow_warn=False)
+        return out
+
+    def cnn_loss_grad(self, labels, params, targets):
+        lab, n, e = self._cubes(labels)
+        th = np.ascontiguousarray(params, dtype=np.float32)
+        tg = np.ascontiguousarray(targets, dtype=np.float32).reshape(n, 21)
+        loss = ctypes.c_double()
+        grad = np.zeros(th.size, dtype=np.float32)
+        self._check(self._lib.hh_cnn_loss_grad(self._h, _ptr(lab), n, e, _ptr(th), _ptr(tg), ctypes.byref(loss),
+                                               _ptr(grad)), "hh_cnn_loss_grad", allow_warn=False)
+        return loss.value, grad
+
+    def surrogate_train(self, labels, targets, init, epochs=10, batch=32, lr=1e-3, seed=0):
+        lab, n, e = self._cubes(labels)
+        tg = np.ascontiguousarray(targets, dtype=np.float32).reshape(n, 21)
+        th0 = np.ascontiguousarray(init, dtype=np.float32)
+        out = np.zeros(th0.size, dtype=np.float32)
+        hist = np.zeros(epochs)
+        self._check(self._lib.hh_surrogate_train(self._h, _ptr(lab), n, e, _ptr(tg), _ptr(th0), int(epochs),
+                                                 int(batch), float(lr), int(seed), _ptr(out), _ptr(hist)),
+                    "hh_surrogate_train", allow_warn=False)
+        return out, hist
+
+    def surrogate_predict(self, labels, params_ensemble, scale):
+        lab, n, e = self._cubes(labels)
+        th = np.ascontiguousarray(params_ensemble, dtype=np.float32)
+        ens = th.shape[0] if th.ndim == 2 else 1
+        out = np.zeros((n, ens, 21), dtype=np.float32)
+        self._check(self._lib.hh_surrogate_predict(self._h, _ptr(lab), n, e, _ptr(th), ens, float(scale), _ptr(out)),
+                    "hh_surrogate_predict", allow_warn=False)
+        return out
+
+    def surrogate_gate(self, labels, phases, members, spread=0.01):
+        lab, n, e = self._cubes(labels)
+        ph, nph = _phases(phases)
+        mem = np.ascontiguousarray(members, dtype=np.float32)
+        ens = mem.shape[1]
+        acc = np.zeros(n, dtype=np.int32)
+        c21 = np.zeros((n, 21))
+        self._check(self._lib.hh_surrogate_gate(self._h, _ptr(lab), n, e, ph, nph, _ptr(mem), ens, float(spread),
+                                                _ptr(acc), _ptr(c21)), "hh_surrogate_gate", allow_warn=False)
+        return acc.astype(bool), c21
 
     def profile(self) -> dict:
         arr = (KernelStat * 64)()

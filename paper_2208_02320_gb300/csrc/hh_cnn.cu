@@ -1,0 +1,867 @@
+// Subimage surrogate network (not in the paper): a small 3D CNN that maps a
+// subimage's phase labels to the 21 upper-triangle components of its effective
+// Voigt stiffness, trained on GPU with the library's own kernels, and the gate
+// that decides whether the ensemble's prediction stands in for an FFT solve.
+//
+//   input   one-hot of the labels 0, 1, 2 (3 channels, cube of edge D)
+//   conv1   3 -> 16, 3x3x3, stride 1, zero padding 1, bias, ReLU
+//   conv2  16 -> 32, stride 2, ReLU
+//   conv3  32 -> 64, stride 2, ReLU
+//   conv4  64 -> 64, stride 1, ReLU
+//   pool    mean over the voxels -> 64;  fc1 64 -> 128, ReLU;  fc2 128 -> 21
+//
+// Activations are channels-last BF16 ([sample][z][y][x][c]); weights are FP32
+// master copies with BF16 copies for the convolutions; every sum accumulates in
+// FP32. conv1 reads the labels directly (a one-hot input turns its contraction
+// into a lookup of the weight row of each neighbour's label). conv2..conv4,
+// their data gradients and their weight gradients are implicit GEMMs on the
+// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate) with the operands
+// gathered from the activations (no im2col buffer).
+//
+// Parameter layout (flat FP32): per conv layer W[tap][ci][co] with
+// tap = (kz * 3 + ky) * 3 + kx, then bias[co]; per fully connected layer
+// W[in][out], then bias[out]; layers in order.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hh.h"
+#include "hh_internal.h"
+
+namespace hh {
+namespace cnn {
+
+using bf16 = __nv_bfloat16;
+
+struct ConvSpec {
+  int ci, co, stride;
+};
+constexpr ConvSpec kConv[4] = {{3, 16, 1}, {16, 32, 2}, {32, 64, 2}, {64, 64, 1}};
+constexpr int kFc[2][2] = {{64, 128}, {128, 21}};
+constexpr int kOut = 21;
+constexpr int kPoolC = 64;
+constexpr int kHid = 128;
+
+struct Offsets {
+  long long w[6], b[6], total;
+};
+inline Offsets offsets() {
+  Offsets o;
+  long long p = 0;
+  for (int i = 0; i < 4; ++i) {
+    o.w[i] = p;
+    p += 27LL * kConv[i].ci * kConv[i].co;
+    o.b[i] = p;
+    p += kConv[i].co;
+  }
+  for (int i = 0; i < 2; ++i) {
+    o.w[4 + i] = p;
+    p += (long long)kFc[i][0] * kFc[i][1];
+    o.b[4 + i] = p;
+    p += kFc[i][1];
+  }
+  o.total = p;
+  return o;
+}
+
+__host__ __device__ inline int out_size(int n, int s) { return (n + 2 - 3) / s + 1; }
+
+// ---------------------------------------------------------------------------
+// conv1 on the labels: y[m][co] = relu(b[co] + sum_tap W1[tap][label(m + tap - 1)][co]).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_conv1_fwd(const uint8_t* lab, int B, int D, const float* W1, const float* b1,
+                                                   bf16* Y) {
+  __shared__ float w[27 * 3 * 16 + 16];
+  for (int t = threadIdx.x; t < 27 * 3 * 16; t += blockDim.x) w[t] = W1[t];
+  for (int t = threadIdx.x; t < 16; t += blockDim.x) w[27 * 3 * 16 + t] = b1[t];
+  __syncthreads();
+  const long long V = (long long)D * D * D;
+  const long long M = (long long)B * V;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
+    const long long n = m / V;
+    const int v = (int)(m - n * V);
+    const int z = v / (D * D), y = (v / D) % D, x = v % D;
+    float acc[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) acc[c] = w[27 * 3 * 16 + c];
+    for (int kz = 0; kz < 3; ++kz) {
+      const int iz = z + kz - 1;
+      if (iz < 0 || iz >= D) continue;
+      for (int ky = 0; ky < 3; ++ky) {
+        const int iy = y + ky - 1;
+        if (iy < 0 || iy >= D) continue;
+        for (int kx = 0; kx < 3; ++kx) {
+          const int ix = x + kx - 1;
+          if (ix < 0 || ix >= D) continue;
+          const int l = lab[n * V + ((long long)iz * D + iy) * D + ix];
+          if (l >= 3) continue;
+          const float* wr = w + (((kz * 3 + ky) * 3 + kx) * 3 + l) * 16;
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] += wr[c];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) Y[m * 16 + c] = __float2bfloat16(fmaxf(acc[c], 0.f));
+  }
+}
+
+// conv1 weight gradient: dW1[tap][l][co] += sum over voxels m whose neighbour at
+// tap has label l of dZ1[m][co] (shared-memory partial sums, then global atomics).
+__global__ void __launch_bounds__(256) k_conv1_wgrad(const uint8_t* lab, int B, int D, const bf16* dZ, float* dW1) {
+  __shared__ float acc[27 * 3 * 16];
+  for (int t = threadIdx.x; t < 27 * 3 * 16; t += blockDim.x) acc[t] = 0.f;
+  __syncthreads();
+  const long long V = (long long)D * D * D;
+  const long long M = (long long)B * V;
+  for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
+    const long long n = m / V;
+    const int v = (int)(m - n * V);
+    const int z = v / (D * D), y = (v / D) % D, x = v % D;
+    float g[16];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+      g[c] = __bfloat162float(dZ[m * 16 + c]);
+      any |= g[c] != 0.f;
+    }
+    if (!any) continue;
+    for (int tap = 0; tap < 27; ++tap) {
+      const int iz = z + tap / 9 - 1, iy = y + (tap / 3) % 3 - 1, ix = x + tap % 3 - 1;
+      if (iz < 0 || iz >= D || iy < 0 || iy >= D || ix < 0 || ix >= D) continue;
+      const int l = lab[n * V + ((long long)iz * D + iy) * D + ix];
+      if (l >= 3) continue;
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        if (g[c] != 0.f) atomicAdd(&acc[(tap * 3 + l) * 16 + c], g[c]);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 27 * 3 * 16; t += blockDim.x)
+    if (acc[t] != 0.f) atomicAdd(&dW1[t], acc[t]);
+}
+
+// Bias gradient: db[c] += sum over rows of dZ[m][c] (C channels).
+__global__ void __launch_bounds__(256) k_bias_grad(const bf16* dZ, long long M, int C, float* db) {
+  __shared__ float acc[64];
+  for (int t = threadIdx.x; t < C; t += blockDim.x) acc[t] = 0.f;
+  __syncthreads();
+  const int c = threadIdx.x % C;
+  const int rows_per = blockDim.x / C;
+  float a = 0.f;
+  if ((int)threadIdx.x < rows_per * C)
+    for (long long m = blockIdx.x * (long long)rows_per + threadIdx.x / C; m < M; m += (long long)gridDim.x * rows_per)
+      a += __bfloat162float(dZ[m * C + c]);
+  atomicAdd(&acc[c], a);
+  __syncthreads();
+  for (int t = threadIdx.x; t < C; t += blockDim.x) atomicAdd(&db[t], acc[t]);
+}
+
+// ---------------------------------------------------------------------------
+// Implicit GEMM C[M][N] = sum_k A(m, k) B(k, n) on the BF16 tensor cores.
+// Block tile 64 x 64, k step 32, 4 warps of 32 x 32 (2 x 4 mma tiles of
+// 16 x 8). The operands are gathered through Op::a / Op::b into shared memory;
+// Op::store receives each FP32 result. blockIdx.z splits K (Op::store then
+// accumulates with atomics).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <class Op>
+__global__ void __launch_bounds__(128) k_igemm(Op op, long long M, int N, long long K, long long kper) {
+  __shared__ bf16 As[64][40];
+  __shared__ bf16 Bs[32][72];
+  const long long m0 = (long long)blockIdx.x * 64;
+  const int n0 = blockIdx.y * 64;
+  const long long kb = (long long)blockIdx.z * kper;
+  const long long ke = min(K, kb + kper);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (long long k0 = kb; k0 < ke; k0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += 128) {
+      const int r = e >> 5, c = e & 31;
+      As[r][c] = (m0 + r < M && k0 + c < ke) ? op.a(m0 + r, k0 + c) : zero;
+      const int kr = e >> 6, nc = e & 63;
+      Bs[kr][nc] = (k0 + kr < ke && n0 + nc < N) ? op.b(k0 + kr, n0 + nc) : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 32; kk += 16) {
+      uint32_t a[2][4], b[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + 16 * i + g, c = kk + 2 * t;
+        a[i][0] = pack2(As[r][c], As[r][c + 1]);
+        a[i][1] = pack2(As[r + 8][c], As[r + 8][c + 1]);
+        a[i][2] = pack2(As[r][c + 8], As[r][c + 9]);
+        a[i][3] = pack2(As[r + 8][c + 8], As[r + 8][c + 9]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = wn + 8 * j + g, k = kk + 2 * t;
+        b[j][0] = pack2(Bs[k][n], Bs[k + 1][n]);
+        b[j][1] = pack2(Bs[k + 8][n], Bs[k + 9][n]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const long long m = m0 + wm + 16 * i + g + (q >= 2 ? 8 : 0);
+        const int n = n0 + wn + 8 * j + 2 * t + (q & 1);
+        if (m < M && n < N) op.store(m, n, acc[i][j][q]);
+      }
+}
+
+// Geometry of one convolution layer (cubes): input edge Di, output edge Do.
+struct Geo {
+  int Di, Do, ci, co, s;
+};
+
+// Input value feeding output voxel m (sample-major) at reduction index
+// k = tap * ci + c, or 0 in the zero padding.
+__device__ __forceinline__ bf16 gather_in(const bf16* X, const Geo& g, long long m, long long k) {
+  const long long V = (long long)g.Do * g.Do * g.Do;
+  const long long n = m / V;
+  const int v = (int)(m - n * V);
+  const int tap = (int)(k / g.ci), c = (int)(k - (long long)tap * g.ci);
+  const int iz = (v / (g.Do * g.Do)) * g.s + tap / 9 - 1;
+  const int iy = ((v / g.Do) % g.Do) * g.s + (tap / 3) % 3 - 1;
+  const int ix = (v % g.Do) * g.s + tap % 3 - 1;
+  if (iz < 0 || iz >= g.Di || iy < 0 || iy >= g.Di || ix < 0 || ix >= g.Di) return __float2bfloat16(0.f);
+  return X[((((n * g.Di + iz) * g.Di + iy) * g.Di) + ix) * g.ci + c];
+}
+
+// Forward: Y[m][o] = relu(b[o] + sum_k gather_in(m, k) W[k][o]).
+struct OpFwd {
+  const bf16* X;
+  const bf16* W;
+  const float* bias;
+  bf16* Y;
+  Geo g;
+  __device__ bf16 a(long long m, long long k) const { return gather_in(X, g, m, k); }
+  __device__ bf16 b(long long k, int n) const { return W[k * g.co + n]; }
+  __device__ void store(long long m, int n, float v) const {
+    Y[m * g.co + n] = __float2bfloat16(fmaxf(v + bias[n], 0.f));
+  }
+};
+
+// Data gradient masked by the ReLU of the layer's input:
+// dZin[m][c] = [X[m][c] > 0] sum_{tap, o} dZ[out(m, tap)][o] W[tap][c][o],
+// out(m, tap) = (in(m) + 1 - k) / s where that divides exactly and lands inside.
+struct OpDgrad {
+  const bf16* dZ;
+  const bf16* W;
+  const bf16* X;
+  bf16* dZin;
+  Geo g;
+  __device__ bf16 a(long long m, long long k) const {
+    const long long V = (long long)g.Di * g.Di * g.Di;
+    const long long n = m / V;
+    const int v = (int)(m - n * V);
+    const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
+    int q[3] = {v / (g.Di * g.Di) + 1 - tap / 9, (v / g.Di) % g.Di + 1 - (tap / 3) % 3, v % g.Di + 1 - tap % 3};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (q[d] < 0 || q[d] % g.s) return __float2bfloat16(0.f);
+      q[d] /= g.s;
+      if (q[d] >= g.Do) return __float2bfloat16(0.f);
+    }
+    return dZ[((((n * g.Do + q[0]) * g.Do + q[1]) * g.Do) + q[2]) * g.co + o];
+  }
+  __device__ bf16 b(long long k, int c) const {
+    const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
+    return W[((long long)tap * g.ci + c) * g.co + o];
+  }
+  __device__ void store(long long m, int c, float v) const {
+    const long long i = m * g.ci + c;
+    dZin[i] = __float2bfloat16(__bfloat162float(X[i]) > 0.f ? v : 0.f);
+  }
+};
+
+// Weight gradient: dW[k][o] += sum_m gather_in(m, k) dZ[m][o] (rows = k).
+struct OpWgrad {
+  const bf16* X;
+  const bf16* dZ;
+  float* dW;
+  Geo g;
+  __device__ bf16 a(long long k, long long m) const { return gather_in(X, g, m, k); }
+  __device__ bf16 b(long long m, int o) const { return dZ[m * g.co + o]; }
+  __device__ void store(long long k, int o, float v) const { atomicAdd(&dW[k * g.co + o], v); }
+};
+
+// ---------------------------------------------------------------------------
+// Head: mean pool, fc1 + ReLU, fc2 (one block per sample, FP32).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_head_fwd(const bf16* Y4, int V4, const float* W5, const float* b5,
+                                                  const float* W6, const float* b6, float* h0, float* h1,
+                                                  float* out) {
+  __shared__ float s0[kPoolC], s1[kHid], part[128];
+  const int n = blockIdx.x;
+  const bf16* y = Y4 + (long long)n * V4 * kPoolC;
+  // pool: thread t sums channel t % 64 over voxels of parity t / 64
+  {
+    const int c = threadIdx.x % kPoolC, h = threadIdx.x / kPoolC;
+    float a = 0.f;
+    for (int v = h; v < V4; v += 2) a += __bfloat162float(y[(long long)v * kPoolC + c]);
+    part[threadIdx.x] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < kPoolC) s0[threadIdx.x] = (part[threadIdx.x] + part[threadIdx.x + kPoolC]) / float(V4);
+  __syncthreads();
+  if (threadIdx.x < kHid) {
+    float a = b5[threadIdx.x];
+    for (int i = 0; i < kPoolC; ++i) a += s0[i] * W5[i * kHid + threadIdx.x];
+    s1[threadIdx.x] = fmaxf(a, 0.f);
+  }
+  __syncthreads();
+  if (threadIdx.x < kOut) {
+    float a = b6[threadIdx.x];
+    for (int i = 0; i < kHid; ++i) a += s1[i] * W6[i * kOut + threadIdx.x];
+    out[n * kOut + threadIdx.x] = a;
+  }
+  if (threadIdx.x < kPoolC) h0[n * kPoolC + threadIdx.x] = s0[threadIdx.x];
+  if (threadIdx.x < kHid) h1[n * kHid + threadIdx.x] = s1[threadIdx.x];
+}
+
+// Loss gradient and head backward: dout = 2 (out - t) / (B * 21); fc2 and fc1
+// weight and bias gradients (atomics over the batch); dZ4 = dpool masked by
+// conv4's ReLU. loss_part[n] = |out - t|^2.
+__global__ void __launch_bounds__(128) k_head_bwd(const bf16* Y4, int V4, int B, const float* W5, const float* W6,
+                                                  const float* h0, const float* h1, const float* out,
+                                                  const float* tgt, float* dW5, float* db5, float* dW6, float* db6,
+                                                  bf16* dZ4, double* loss_part) {
+  __shared__ float dout[kOut], dh1[kHid], dh0[kPoolC];
+  const int n = blockIdx.x;
+  if (threadIdx.x < kOut) {
+    const float r = out[n * kOut + threadIdx.x] - tgt[n * kOut + threadIdx.x];
+    dout[threadIdx.x] = 2.f * r / float(B * kOut);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    for (int i = 0; i < kOut; ++i) {
+      const double r = (double)out[n * kOut + i] - (double)tgt[n * kOut + i];
+      l += r * r;
+    }
+    loss_part[n] = l;
+  }
+  for (int e = threadIdx.x; e < kHid * kOut; e += blockDim.x) {
+    const int i = e / kOut, j = e % kOut;
+    atomicAdd(&dW6[e], h1[n * kHid + i] * dout[j]);
+  }
+  if (threadIdx.x < kOut) atomicAdd(&db6[threadIdx.x], dout[threadIdx.x]);
+  if (threadIdx.x < kHid) {
+    float a = 0.f;
+    for (int j = 0; j < kOut; ++j) a += W6[threadIdx.x * kOut + j] * dout[j];
+    dh1[threadIdx.x] = h1[n * kHid + threadIdx.x] > 0.f ? a : 0.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPoolC * kHid; e += blockDim.x) {
+    const int i = e / kHid, j = e % kHid;
+    atomicAdd(&dW5[e], h0[n * kPoolC + i] * dh1[j]);
+  }
+  if (threadIdx.x < kHid) atomicAdd(&db5[threadIdx.x], dh1[threadIdx.x]);
+  if (threadIdx.x < kPoolC) {
+    float a = 0.f;
+    for (int j = 0; j < kHid; ++j) a += W5[threadIdx.x * kHid + j] * dh1[j];
+    dh0[threadIdx.x] = a / float(V4);
+  }
+  __syncthreads();
+  const bf16* y = Y4 + (long long)n * V4 * kPoolC;
+  bf16* dz = dZ4 + (long long)n * V4 * kPoolC;
+  for (int e = threadIdx.x; e < V4 * kPoolC; e += blockDim.x)
+    dz[e] = __float2bfloat16(__bfloat162float(y[e]) > 0.f ? dh0[e % kPoolC] : 0.f);
+}
+
+// Adam (Kingma and Ba) with bias correction; refreshes the BF16 weight copy.
+__global__ void k_adam(float* theta, const float* grad, float* m, float* v, long long n, float lr, float c1, float c2,
+                       bf16* theta16) {
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float g = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * g;
+    const float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const float th = theta[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    theta[i] = th;
+    theta16[i] = __float2bfloat16(th);
+  }
+}
+
+__global__ void k_to_bf16(const float* a, bf16* b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16(a[i]);
+}
+
+// Scale the network outputs (normalised stiffness) to GPa.
+__global__ void k_scale(const float* a, float s, float* b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = a[i] * s;
+}
+
+// ---------------------------------------------------------------------------
+// Gate: one block per subimage. Phase fractions -> Reuss and Voigt bounds of
+// K and G; each member's Voigt-projected K, G must lie inside; the relative
+// spread (max - min) / mean of K and of G must be <= spread; the mean
+// stiffness must be positive definite (Cholesky, FP64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kg_of(const double* c21, double& K, double& G) {
+  // upper-triangle index of (i, j), i <= j
+  auto at = [&](int i, int j) { return c21[i * 6 - i * (i - 1) / 2 + (j - i)]; };
+  K = (at(0, 0) + at(1, 1) + at(2, 2) + 2.0 * (at(0, 1) + at(0, 2) + at(1, 2))) / 9.0;
+  G = (at(0, 0) + at(1, 1) + at(2, 2) - (at(0, 1) + at(0, 2) + at(1, 2)) + 3.0 * (at(3, 3) + at(4, 4) + at(5, 5))) /
+      15.0;
+}
+
+__global__ void __launch_bounds__(256) k_gate(const uint8_t* lab, long long V, const double* ph, int nphase,
+                                              const float* members, int E, double spread, int* accept,
+                                              double* c21_out) {
+  __shared__ unsigned int cnt[256];
+  const int n = blockIdx.x;
+  for (int t = threadIdx.x; t < 256; t += blockDim.x) cnt[t] = 0;
+  __syncthreads();
+  for (long long v = threadIdx.x; v < V; v += blockDim.x) atomicAdd(&cnt[lab[n * V + v]], 1u);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double sKf = 0, sKr = 0, sGf = 0, sGr = 0;
+  bool badlab = false;
+  for (int p = 0; p < 256; ++p) {
+    if (!cnt[p]) continue;
+    if (p >= nphase) {
+      badlab = true;
+      break;
+    }
+    const double f = double(cnt[p]) / double(V);
+    sKf += f * ph[2 * p];
+    sKr += f / ph[2 * p];
+    sGf += f * ph[2 * p + 1];
+    sGr += f / ph[2 * p + 1];
+  }
+  const double KV = sKf, KR = 1.0 / sKr, GV = sGf, GR = 1.0 / sGr;
+  double mean[21];
+  for (int i = 0; i < 21; ++i) mean[i] = 0.0;
+  double Kmin = 1e300, Kmax = -1e300, Gmin = 1e300, Gmax = -1e300, Ks = 0, Gs = 0;
+  bool ok = !badlab;
+  for (int e = 0; e < E; ++e) {
+    double c[21];
+    for (int i = 0; i < 21; ++i) {
+      c[i] = members[((long long)n * E + e) * 21 + i];
+      mean[i] += c[i] / E;
+    }
+    double K, G;
+    kg_of(c, K, G);
+    ok = ok && K >= KR && K <= KV && G >= GR && G <= GV;
+    Kmin = fmin(Kmin, K);
+    Kmax = fmax(Kmax, K);
+    Gmin = fmin(Gmin, G);
+    Gmax = fmax(Gmax, G);
+    Ks += K / E;
+    Gs += G / E;
+  }
+  ok = ok && (Kmax - Kmin) <= spread * Ks && (Gmax - Gmin) <= spread * Gs;
+  // Cholesky of the mean (Voigt form; same definiteness as the Mandel form)
+  double A[6][6];
+  for (int i = 0, t = 0; i < 6; ++i)
+    for (int j = i; j < 6; ++j, ++t) A[i][j] = A[j][i] = mean[t];
+  for (int j = 0; j < 6 && ok; ++j) {
+    double d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    if (!(d > 0.0)) {
+      ok = false;
+      break;
+    }
+    d = sqrt(d);
+    A[j][j] = d;
+    for (int i = j + 1; i < 6; ++i) {
+      double s = A[i][j];
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s / d;
+    }
+  }
+  accept[n] = ok ? 1 : 0;
+  for (int i = 0; i < 21; ++i) c21_out[(long long)n * 21 + i] = mean[i];
+}
+
+// ---------------------------------------------------------------------------
+// Host side: device workspace of one batch and the passes over it.
+// ---------------------------------------------------------------------------
+#define CNN_CK(x)                                                                          \
+  do {                                                                                     \
+    cudaError_t e_ = (x);                                                                  \
+    if (e_ != cudaSuccess) {                                                               \
+      err = std::string(#x) + ": " + cudaGetErrorString(e_);                               \
+      return HH_ERR_CUDA;                                                                  \
+    }                                                                                      \
+  } while (0)
+
+struct Net {
+  cudaStream_t st = nullptr;
+  int B = 0, D = 0;
+  int dims[5] = {0, 0, 0, 0, 0};  // edge before conv1 .. after conv4
+  Offsets off;
+  std::string err;
+  std::vector<void*> allocs;
+  float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  bf16* theta16 = nullptr;
+  uint8_t* lab = nullptr;
+  bf16* act[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // act[i]: output of conv i (1-based)
+  bf16* dact[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // gradient at conv i's output (pre-ReLU)
+  float *h0 = nullptr, *h1 = nullptr, *out = nullptr, *tgt = nullptr;
+  double* loss_part = nullptr;
+  long long launches = 0;
+
+  ~Net() {
+    for (void* p : allocs) cudaFree(p);
+  }
+  template <typename T>
+  hh_status alloc(T** p, long long n) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, std::max<long long>(n, 1) * sizeof(T)) != cudaSuccess) {
+      (void)cudaGetLastError();
+      err = "device allocation failed";
+      return HH_ERR_OOM;
+    }
+    allocs.push_back(q);
+    *p = reinterpret_cast<T*>(q);
+    return HH_OK;
+  }
+
+  hh_status init(cudaStream_t s, int batch, int edge, bool train) {
+    st = s;
+    B = batch;
+    D = edge;
+    off = offsets();
+    dims[0] = D;
+    for (int i = 0; i < 4; ++i) dims[i + 1] = out_size(dims[i], kConv[i].stride);
+    hh_status r;
+    if ((r = alloc(&theta, off.total)) || (r = alloc(&theta16, off.total)) ||
+        (r = alloc(&lab, (long long)B * D * D * D)) || (r = alloc(&h0, (long long)B * kPoolC)) ||
+        (r = alloc(&h1, (long long)B * kHid)) || (r = alloc(&out, (long long)B * kOut)) ||
+        (r = alloc(&tgt, (long long)B * kOut)) || (r = alloc(&loss_part, B)))
+      return r;
+    for (int i = 1; i <= 4; ++i) {
+      const long long n = (long long)B * dims[i] * dims[i] * dims[i] * kConv[i - 1].co;
+      if ((r = alloc(&act[i], n))) return r;
+      if (train && (r = alloc(&dact[i], n))) return r;
+    }
+    if (train && ((r = alloc(&grad, off.total)) || (r = alloc(&m, off.total)) || (r = alloc(&v, off.total))))
+      return r;
+    return HH_OK;
+  }
+
+  hh_status set_params(const float* host) {
+    CNN_CK(cudaMemcpyAsync(theta, host, off.total * sizeof(float), cudaMemcpyHostToDevice, st));
+    ++launches;
+    k_to_bf16<<<256, 256, 0, st>>>(theta, theta16, off.total);
+    CNN_CK(cudaGetLastError());
+    return HH_OK;
+  }
+
+  template <class Op>
+  hh_status gemm(const Op& op, long long M, int N, long long K, int splits = 1) {
+    const long long kper = ((K + splits - 1) / splits + 31) / 32 * 32;
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)splits);
+    ++launches;
+    k_igemm<Op><<<grid, 128, 0, st>>>(op, M, N, K, kper);
+    CNN_CK(cudaGetLastError());
+    return HH_OK;
+  }
+
+  Geo geo(int i) const { return Geo{dims[i], dims[i + 1], kConv[i].ci, kConv[i].co, kConv[i].stride}; }
+
+  // forward of nb <= B samples already in lab
+  hh_status forward(int nb) {
+    const long long V1 = (long long)dims[1] * dims[1] * dims[1];
+    ++launches;
+    k_conv1_fwd<<<(unsigned)std::min<long long>(4096, (nb * V1 + 255) / 256), 256, 0, st>>>(
+        lab, nb, D, theta + off.w[0], theta + off.b[0], act[1]);
+    CNN_CK(cudaGetLastError());
+    for (int i = 1; i < 4; ++i) {
+      const Geo g = geo(i);
+      const long long M = (long long)nb * g.Do * g.Do * g.Do;
+      OpFwd op{act[i], theta16 + off.w[i], theta + off.b[i], act[i + 1], g};
+      hh_status r = gemm(op, M, g.co, 27LL * g.ci);
+      if (r) return r;
+    }
+    const int V4 = dims[4] * dims[4] * dims[4];
+    ++launches;
+    k_head_fwd<<<nb, 128, 0, st>>>(act[4], V4, theta + off.w[4], theta + off.b[4], theta + off.w[5],
+                                   theta + off.b[5], h0, h1, out);
+    CNN_CK(cudaGetLastError());
+    return HH_OK;
+  }
+
+  // gradients of the batch loss into grad (zeroed here); needs tgt
+  hh_status backward(int nb) {
+    CNN_CK(cudaMemsetAsync(grad, 0, off.total * sizeof(float), st));
+    const int V4 = dims[4] * dims[4] * dims[4];
+    ++launches;
+    k_head_bwd<<<nb, 128, 0, st>>>(act[4], V4, nb, theta + off.w[4], theta + off.w[5], h0, h1, out, tgt,
+                                   grad + off.w[4], grad + off.b[4], grad + off.w[5], grad + off.b[5], dact[4],
+                                   loss_part);
+    CNN_CK(cudaGetLastError());
+    for (int i = 3; i >= 1; --i) {
+      const Geo g = geo(i);
+      const long long Mo = (long long)nb * g.Do * g.Do * g.Do;
+      const long long Mi = (long long)nb * g.Di * g.Di * g.Di;
+      // weight and bias gradients of conv i+1 (0-based i)
+      const int splits = (int)std::min<long long>(64, std::max<long long>(1, Mo / 4096));
+      OpWgrad ow{act[i], dact[i + 1], grad + off.w[i], g};
+      hh_status r = gemm(ow, 27LL * g.ci, g.co, Mo, splits);
+      if (r) return r;
+      ++launches;
+      k_bias_grad<<<(unsigned)std::min<long long>(1024, (Mo + 63) / 64), 256, 0, st>>>(dact[i + 1], Mo, g.co,
+                                                                                      grad + off.b[i]);
+      CNN_CK(cudaGetLastError());
+      // gradient at the layer's input, masked by the previous ReLU
+      OpDgrad od{dact[i + 1], theta16 + off.w[i], act[i], dact[i], g};
+      if ((r = gemm(od, Mi, g.ci, 27LL * g.co))) return r;
+    }
+    const long long V1 = (long long)dims[1] * dims[1] * dims[1];
+    ++launches;
+    k_conv1_wgrad<<<(unsigned)std::min<long long>(2048, (nb * V1 + 255) / 256), 256, 0, st>>>(lab, nb, D, dact[1],
+                                                                                            grad + off.w[0]);
+    CNN_CK(cudaGetLastError());
+    ++launches;
+    k_bias_grad<<<(unsigned)std::min<long long>(1024, (nb * V1 + 63) / 64), 256, 0, st>>>(dact[1], nb * V1, 16,
+                                                                                         grad + off.b[0]);
+    CNN_CK(cudaGetLastError());
+    return HH_OK;
+  }
+};
+
+hh_status check_geometry(hh_ctx* h, int count, int edge) {
+  if (count < 1 || edge < 8 || edge > 256) return ctx_fail(h, HH_ERR_ARG, "surrogate: count >= 1, 8 <= edge <= 256");
+  return HH_OK;
+}
+
+}  // namespace cnn
+}  // namespace hh
+
+using namespace hh;
+using namespace hh::cnn;
+
+extern "C" int64_t hh_cnn_num_params(void) { return offsets().total; }
+
+extern "C" hh_status hh_cnn_forward(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* params,
+                                   float* out) {
+  if (!h || !labels || !params || !out) return HH_ERR_ARG;
+  hh_status s = check_geometry(h, count, edge);
+  if (s) return s;
+  if ((s = ctx_enter(h))) return s;
+  const int B = std::min(count, 64);
+  Net net;
+  if ((s = net.init(ctx_stream(h), B, edge, false)) || (s = net.set_params(params)))
+    return ctx_fail(h, s, net.err.c_str());
+  const long long V = (long long)edge * edge * edge;
+  for (int b0 = 0; b0 < count; b0 += B) {
+    const int nb = std::min(B, count - b0);
+    if (cudaMemcpyAsync(net.lab, labels + b0 * V, nb * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
+        (s = net.forward(nb)) ||
+        cudaMemcpyAsync(out + (long long)b0 * kOut, net.out, (long long)nb * kOut * sizeof(float),
+                        cudaMemcpyDeviceToHost, net.st) != cudaSuccess)
+      return ctx_fail(h, s ? s : HH_ERR_CUDA, net.err.empty() ? "surrogate forward: copy failed" : net.err.c_str());
+  }
+  if (cudaStreamSynchronize(net.st) != cudaSuccess) return ctx_fail(h, HH_ERR_CUDA, "surrogate forward failed");
+  return HH_OK;
+}
+
+extern "C" hh_status hh_cnn_loss_grad(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* params,
+                                     const float* targets, double* loss, float* grad) {
+  if (!h || !labels || !params || !targets || !loss || !grad) return HH_ERR_ARG;
+  hh_status s = check_geometry(h, count, edge);
+  if (s) return s;
+  if ((s = ctx_enter(h))) return s;
+  Net net;
+  if ((s = net.init(ctx_stream(h), count, edge, true)) || (s = net.set_params(params)))
+    return ctx_fail(h, s, net.err.c_str());
+  const long long V = (long long)edge * edge * edge;
+  std::vector<double> lp(count);
+  if (cudaMemcpyAsync(net.lab, labels, count * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
+      cudaMemcpyAsync(net.tgt, targets, (long long)count * kOut * sizeof(float), cudaMemcpyHostToDevice, net.st) !=
+          cudaSuccess)
+    return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients: copy failed");
+  if ((s = net.forward(count)) || (s = net.backward(count))) return ctx_fail(h, s, net.err.c_str());
+  if (cudaMemcpyAsync(grad, net.grad, net.off.total * sizeof(float), cudaMemcpyDeviceToHost, net.st) != cudaSuccess ||
+      cudaMemcpyAsync(lp.data(), net.loss_part, count * sizeof(double), cudaMemcpyDeviceToHost, net.st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(net.st) != cudaSuccess)
+    return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients failed");
+  double l = 0.0;
+  for (double x : lp) l += x;
+  *loss = l / (double(count) * kOut);
+  return HH_OK;
+}
+
+// Host shuffle: SplitMix64 stream (Steele, Lea and Flood 2014) driving a
+// Fisher-Yates permutation.
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+extern "C" hh_status hh_surrogate_train(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* targets,
+                                       const float* init, int epochs, int batch, double lr, uint64_t seed,
+                                       float* params_out, double* loss_history) {
+  if (!h || !labels || !targets || !init || !params_out || epochs < 1 || batch < 1 || !(lr > 0.0))
+    return HH_ERR_ARG;
+  hh_status s = check_geometry(h, count, edge);
+  if (s) return s;
+  if ((s = ctx_enter(h))) return s;
+  const int B = std::min(batch, count);
+  Net net;
+  if ((s = net.init(ctx_stream(h), B, edge, true)) || (s = net.set_params(init)))
+    return ctx_fail(h, s, net.err.c_str());
+  const long long V = (long long)edge * edge * edge;
+  uint8_t* all_lab = nullptr;
+  float* all_tgt = nullptr;
+  if ((s = net.alloc(&all_lab, (long long)count * V)) || (s = net.alloc(&all_tgt, (long long)count * kOut)))
+    return ctx_fail(h, s, net.err.c_str());
+  if (cudaMemcpyAsync(all_lab, labels, count * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
+      cudaMemcpyAsync(all_tgt, targets, (long long)count * kOut * sizeof(float), cudaMemcpyHostToDevice, net.st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(net.m, 0, net.off.total * sizeof(float), net.st) != cudaSuccess ||
+      cudaMemsetAsync(net.v, 0, net.off.total * sizeof(float), net.st) != cudaSuccess)
+    return ctx_fail(h, HH_ERR_CUDA, "surrogate training: setup failed");
+  std::vector<int> perm(count);
+  for (int i = 0; i < count; ++i) perm[i] = i;
+  uint64_t rs = seed;
+  std::vector<double> lp(B);
+  long long step = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = count - 1; i > 0; --i) std::swap(perm[i], perm[(int)(splitmix64(rs) % (uint64_t)(i + 1))]);
+    double ep_loss = 0.0;
+    long long ep_n = 0;
+    for (int b0 = 0; b0 + B <= count; b0 += B) {  // whole batches only
+      for (int j = 0; j < B; ++j) {
+        const int k = perm[b0 + j];
+        if (cudaMemcpyAsync(net.lab + j * V, all_lab + k * V, V, cudaMemcpyDeviceToDevice, net.st) != cudaSuccess ||
+            cudaMemcpyAsync(net.tgt + j * kOut, all_tgt + (long long)k * kOut, kOut * sizeof(float),
+                            cudaMemcpyDeviceToDevice, net.st) != cudaSuccess)
+          return ctx_fail(h, HH_ERR_CUDA, "surrogate training: batch copy failed");
+      }
+      if ((s = net.forward(B)) || (s = net.backward(B))) return ctx_fail(h, s, net.err.c_str());
+      ++step;
+      const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
+      k_adam<<<256, 256, 0, net.st>>>(net.theta, net.grad, net.m, net.v, net.off.total, (float)lr, c1, c2,
+                                      net.theta16);
+      ++net.launches;
+      if (cudaGetLastError() != cudaSuccess) return ctx_fail(h, HH_ERR_CUDA, "surrogate training: adam failed");
+      if (loss_history) {
+        if (cudaMemcpyAsync(lp.data(), net.loss_part, B * sizeof(double), cudaMemcpyDeviceToHost, net.st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(net.st) != cudaSuccess)
+          return ctx_fail(h, HH_ERR_CUDA, "surrogate training failed");
+        for (double x : lp) ep_loss += x;
+        ep_n += B;
+      }
+    }
+    if (loss_history) loss_history[ep] = ep_n ? ep_loss / (double(ep_n) * kOut) : 0.0;
+  }
+  if (cudaMemcpyAsync(params_out, net.theta, net.off.total * sizeof(float), cudaMemcpyDeviceToHost, net.st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(net.st) != cudaSuccess)
+    return ctx_fail(h, HH_ERR_CUDA, "surrogate training failed");
+  return HH_OK;
+}
+
+extern "C" hh_status hh_surrogate_predict(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* params,
+                                         int ensemble, double scale, float* out) {
+  if (!h || !labels || !params || !out || ensemble < 1 || !(scale > 0.0)) return HH_ERR_ARG;
+  hh_status s = check_geometry(h, count, edge);
+  if (s) return s;
+  const long long np = offsets().total;
+  std::vector<float> tmp((size_t)count * kOut);
+  for (int e = 0; e < ensemble; ++e) {
+    if ((s = hh_cnn_forward(h, labels, count, edge, params + e * np, tmp.data()))) return s;
+    for (int i = 0; i < count; ++i)
+      for (int j = 0; j < kOut; ++j) out[((long long)i * ensemble + e) * kOut + j] = float(tmp[(size_t)i * kOut + j] * scale);
+  }
+  return HH_OK;
+}
+
+extern "C" hh_status hh_surrogate_gate(hh_ctx* h, const uint8_t* labels, int count, int edge, const hh_phase* phases,
+                                      int nphase, const float* members, int ensemble, double spread, int* accept,
+                                      double* c21) {
+  if (!h || !labels || !phases || nphase < 1 || nphase > 256 || !members || ensemble < 1 || !accept || !c21 ||
+      !(spread >= 0.0))
+    return HH_ERR_ARG;
+  hh_status s = check_geometry(h, count, edge);
+  if (s) return s;
+  for (int i = 0; i < nphase; ++i)
+    if (!(phases[i].K > 0.0) || !(phases[i].G > 0.0)) return ctx_fail(h, HH_ERR_ARG, "surrogate gate: phase moduli");
+  if ((s = ctx_enter(h))) return s;
+  const cudaStream_t st = ctx_stream(h);
+  const long long V = (long long)edge * edge * edge;
+  uint8_t* d_lab = nullptr;
+  double *d_ph = nullptr, *d_c = nullptr;
+  float* d_mem = nullptr;
+  int* d_acc = nullptr;
+  std::vector<double> ph(2 * nphase);
+  for (int i = 0; i < nphase; ++i) {
+    ph[2 * i] = phases[i].K;
+    ph[2 * i + 1] = phases[i].G;
+  }
+  hh_status r = HH_OK;
+  if (cudaMalloc(&d_lab, count * V) != cudaSuccess || cudaMalloc(&d_ph, ph.size() * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&d_mem, (size_t)count * ensemble * kOut * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&d_acc, count * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&d_c, (size_t)count * kOut * sizeof(double)) != cudaSuccess) {
+    (void)cudaGetLastError();
+    r = ctx_fail(h, HH_ERR_OOM, "surrogate gate: device allocation failed");
+  } else if (cudaMemcpyAsync(d_lab, labels, count * V, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+             cudaMemcpyAsync(d_ph, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+             cudaMemcpyAsync(d_mem, members, (size_t)count * ensemble * kOut * sizeof(float), cudaMemcpyHostToDevice,
+                             st) != cudaSuccess) {
+    r = ctx_fail(h, HH_ERR_CUDA, "surrogate gate: copy failed");
+  } else {
+    k_gate<<<count, 256, 0, st>>>(d_lab, V, d_ph, nphase, d_mem, ensemble, spread, d_acc, d_c);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(accept, d_acc, count * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(c21, d_c, (size_t)count * kOut * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      r = ctx_fail(h, HH_ERR_CUDA, "surrogate gate failed");
+  }
+  cudaFree(d_lab);
+  cudaFree(d_ph);
+  cudaFree(d_mem);
+  cudaFree(d_acc);
+  cudaFree(d_c);
+  return r;
+}

@@ -15,6 +15,7 @@
 #include "hh.h"
 #include "hh_device.cuh"
 #include "hh_post.cuh"
+#include "hh_internal.h"
 
 namespace hh {
 
@@ -1172,6 +1173,14 @@ static hh_status enter(hh_ctx* h) {
 }
 
 // Stop the device timer of a call and fill the counters of its result.
+// Bridge for the surrogate unit (hh_internal.h).
+namespace hh {
+int ctx_device(hh_ctx* h) { return h->c.dev; }
+cudaStream_t ctx_stream(hh_ctx* h) { return h->c.st; }
+hh_status ctx_fail(hh_ctx* h, hh_status s, const char* msg) { return fail(h, s, msg); }
+hh_status ctx_enter(hh_ctx* h) { return enter(h); }
+}  // namespace hh
+
 static hh_status finish(hh_ctx* h, hh_status s, hh_result* out) {
   Ctx& c = h->c;
   if (s < 0) return s;

@@ -1,0 +1,151 @@
+"""The subimage surrogate on the GPU (through the C ABI) against the FP64 CNN
+oracle, its training, its gate, and what it gains over the FFT solver.
+
+Tolerances: the network computes in BF16 with FP32 accumulation, so the
+forward output and the gradient agree with the FP64 oracle to a relative 2e-2
+and 5e-2 (norm-wise per layer); the gate's decisions agree exactly.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cnn_oracle as N
+
+pytestmark = pytest.mark.gpu
+
+SCALE = 100.0  # GPa: targets are C21 / SCALE
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a CUDA device")
+    from paper_2208_02320_gb300 import Context, _build
+    _build.build()
+    c = Context(0)
+    yield c
+    c.close()
+
+
+def _params(seed):
+    theta = N.init_params(synth.uniform01(seed, 1, N.n_params()))
+    # small nonzero biases so that every gradient path is exercised
+    p = N.unflatten(theta)
+    for name, _ in N.layer_shapes():
+        if name.endswith(".b"):
+            p[name] = 0.05 * (synth.uniform01(seed, 2, p[name].size).reshape(p[name].shape) - 0.5)
+    return N.flatten(p)
+
+
+def _cubes(count, edge, seed, nphase=3):
+    out = []
+    for i in range(count):
+        f = synth.gaussian_random_field((edge,) * 3, 2.0, seed, stream=i)
+        q = np.quantile(f, [0.2, 0.35]) if nphase == 3 else np.quantile(f, [0.3])
+        out.append(np.digitize(f, q).astype(np.uint8) if nphase == 3 else (f > q[0]).astype(np.uint8))
+    return np.stack(out)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+def test_num_params(ctx):
+    assert ctx.cnn_num_params() == N.n_params()
+
+
+@pytest.mark.parametrize("edge", [8, 16, 20])
+def test_forward_parity_with_oracle(ctx, edge):
+    theta = _params(11)
+    labs = _cubes(3, edge, seed=5)
+    got = ctx.cnn_forward(labs, theta.astype(np.float32))
+    ref = np.stack([N.forward(theta, l)[0] for l in labs])
+    assert _rel(got, ref) < 2e-2
+
+
+def test_gradient_parity_with_oracle(ctx):
+    theta = _params(12)
+    labs = _cubes(2, 16, seed=6)
+    tg = synth.uniform01(7, 0, 2 * N.NOUT).reshape(2, N.NOUT)
+    loss, grad = ctx.cnn_loss_grad(labs, theta.astype(np.float32), tg.astype(np.float32))
+    rloss, rgrad, _ = N.batch_loss_and_grad(theta, list(labs), tg)
+    assert abs(loss - rloss) <= 2e-2 * rloss
+    o = 0
+    for name, shape in N.layer_shapes():
+        n = int(np.prod(shape))
+        assert _rel(grad[o:o + n], rgrad[o:o + n]) < 5e-2, name
+        o += n
+
+
+def test_gate_matches_oracle(ctx):
+    rng = np.random.default_rng(3)
+    labs = _cubes(6, 8, seed=8, nphase=2)
+    ph = synth.PHASES_APPENDIX_B
+    members = []
+    for l in labs:
+        KR, KV, GR, GV = N.phase_bounds(l, ph)
+        K0, G0 = rng.uniform(KR, KV), rng.uniform(GR, GV)
+        lam = K0 - 2 * G0 / 3
+        C = np.zeros((6, 6))
+        C[:3, :3] = lam
+        C[np.arange(3), np.arange(3)] += 2 * G0
+        C[np.arange(3, 6), np.arange(3, 6)] = G0
+        c21 = C[np.triu_indices(6)]
+        members.append([c21 * (1 + rng.uniform(-0.008, 0.008)) for _ in range(4)])
+    members = np.array(members)
+    members[1, 2] *= 1.5  # spread and bounds break
+    members[4, :, 0] = -50.0  # not positive definite
+    acc, mean = ctx.surrogate_gate(labs, ph, members.astype(np.float32), spread=0.01)
+    for i, l in enumerate(labs):
+        ok, m = N.gate(members[i].astype(np.float32).astype(np.float64), l, ph, 0.01)
+        assert bool(acc[i]) == ok, i
+        assert np.allclose(mean[i], m, rtol=1e-6)
+    assert acc.sum() >= 3 and not acc[1] and not acc[4]
+
+
+def _fft_labels(ctx, labs, ph):
+    n, e = labs.shape[0], labs.shape[1]
+    img = labs.reshape(n * e, e, e)  # stacked along z; one box per cube
+    boxes = np.array([[0, 0, i * e, e, e, e, 0] for i in range(n)], dtype=np.int32)
+    r = ctx.solve_subimages(img, ph, boxes, precision="fp32", tol=1e-5)
+    iu = np.triu_indices(6)
+    Cs = 0.5 * (r["C"] + np.swapaxes(r["C"], 1, 2))
+    return np.stack([c[iu] for c in Cs])
+
+
+def test_training_and_what_the_surrogate_gains(ctx):
+    """Trains a 2-member ensemble on FFT-labelled cubes, then compares, on
+    held-out cubes from the same generator, the ensemble+gate against the FFT
+    solver: the accepted predictions' K and G errors and the time per cube."""
+    ph = synth.PHASES_APPENDIX_B
+    edge = 16
+    train = _cubes(160, edge, seed=21, nphase=2)
+    test = _cubes(48, edge, seed=22, nphase=2)
+    y_train = _fft_labels(ctx, train, ph)
+    members = []
+    for m in range(2):
+        th, hist = ctx.surrogate_train(train, (y_train / SCALE).astype(np.float32),
+                                       _params(30 + m).astype(np.float32), epochs=40, batch=16, lr=2e-3, seed=m)
+        assert hist[-1] < 0.2 * hist[0], hist
+        members.append(th)
+    members = np.stack(members)
+    t0 = time.perf_counter()
+    pred = ctx.surrogate_predict(test, members, SCALE)
+    acc, mean = ctx.surrogate_gate(test, ph, pred, spread=0.05)
+    t_sur = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    y_test = _fft_labels(ctx, test, ph)
+    t_fft = time.perf_counter() - t0
+    errs = []
+    for i in np.flatnonzero(acc):
+        Kp, Gp = N.moduli_voigt(N.c21_to_full(mean[i]))
+        Kt, Gt = N.moduli_voigt(N.c21_to_full(y_test[i]))
+        errs.append(max(abs(Kp - Kt) / Kt, abs(Gp - Gt) / Gt))
+    print(f"accepted {acc.sum()}/{len(acc)}, max K/G error of accepted {max(errs) if errs else None}, "
+          f"surrogate {t_sur:.3f} s vs FFT {t_fft:.3f} s")
+    assert acc.sum() >= len(acc) // 4
+    assert max(errs) < 0.05
