@@ -252,9 +252,10 @@ hh_status hh_cnn_forward(hh_ctx *ctx, const uint8_t *labels, int count, int edge
 hh_status hh_cnn_loss_grad(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
                            const float *params, const float *targets, double *loss, float *grad);
 
-/* Trains one network from `init` with Adam (lr, beta 0.9/0.999, eps 1e-8) on
- * minibatches of `batch` cubes (whole batches of a seeded permutation per
- * epoch) and writes the final parameters to params_out. loss_history
+/* Trains one network from `init` with Adam (beta 0.9/0.999, eps 1e-8; step
+ * size lr with cosine decay to 0 over the run) on minibatches of `batch`
+ * cubes (whole batches of a seeded permutation per epoch) and writes the
+ * final parameters to params_out. loss_history
  * (epochs values, may be NULL) receives each epoch's mean training loss. */
 hh_status hh_surrogate_train(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
                              const float *targets, const float *init, int epochs, int batch,

@@ -764,6 +764,7 @@ extern "C" hh_status hh_surrogate_train(hh_ctx* h, const uint8_t* labels, int co
   uint64_t rs = seed;
   std::vector<double> lp(B);
   long long step = 0;
+  const long long total_steps = (long long)epochs * (count / B);
   for (int ep = 0; ep < epochs; ++ep) {
     for (int i = count - 1; i > 0; --i) std::swap(perm[i], perm[(int)(splitmix64(rs) % (uint64_t)(i + 1))]);
     double ep_loss = 0.0;
@@ -777,9 +778,11 @@ extern "C" hh_status hh_surrogate_train(hh_ctx* h, const uint8_t* labels, int co
           return ctx_fail(h, HH_ERR_CUDA, "surrogate training: batch copy failed");
       }
       if ((s = net.forward(B)) || (s = net.backward(B))) return ctx_fail(h, s, net.err.c_str());
+      // cosine decay of the step size over the whole run
+      const double lr_t = 0.5 * lr * (1.0 + cos(3.14159265358979323846 * double(step) / double(total_steps)));
       ++step;
       const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
-      k_adam<<<256, 256, 0, net.st>>>(net.theta, net.grad, net.m, net.v, net.off.total, (float)lr, c1, c2,
+      k_adam<<<256, 256, 0, net.st>>>(net.theta, net.grad, net.m, net.v, net.off.total, (float)lr_t, c1, c2,
                                       net.theta16);
       ++net.launches;
       if (cudaGetLastError() != cudaSuccess) return ctx_fail(h, HH_ERR_CUDA, "surrogate training: adam failed");

@@ -88,14 +88,14 @@ def test_gate_matches_oracle(ctx):
     members = []
     for l in labs:
         KR, KV, GR, GV = N.phase_bounds(l, ph)
-        K0, G0 = rng.uniform(KR, KV), rng.uniform(GR, GV)
+        K0, G0 = KR + (KV - KR) * rng.uniform(0.1, 0.9), GR + (GV - GR) * rng.uniform(0.1, 0.9)
         lam = K0 - 2 * G0 / 3
         C = np.zeros((6, 6))
         C[:3, :3] = lam
         C[np.arange(3), np.arange(3)] += 2 * G0
         C[np.arange(3, 6), np.arange(3, 6)] = G0
         c21 = C[np.triu_indices(6)]
-        members.append([c21 * (1 + rng.uniform(-0.008, 0.008)) for _ in range(4)])
+        members.append([c21 * (1 + rng.uniform(-0.003, 0.003)) for _ in range(4)])
     members = np.array(members)
     members[1, 2] *= 1.5  # spread and bounds break
     members[4, :, 0] = -50.0  # not positive definite
@@ -118,34 +118,36 @@ def _fft_labels(ctx, labs, ph):
 
 
 def test_training_and_what_the_surrogate_gains(ctx):
-    """Trains a 2-member ensemble on FFT-labelled cubes, then compares, on
+    """Trains a 4-member ensemble on FFT-labelled cubes, then compares, on
     held-out cubes from the same generator, the ensemble+gate against the FFT
     solver: the accepted predictions' K and G errors and the time per cube."""
     ph = synth.PHASES_APPENDIX_B
     edge = 16
-    train = _cubes(160, edge, seed=21, nphase=2)
+    train = _cubes(320, edge, seed=21, nphase=2)
     test = _cubes(48, edge, seed=22, nphase=2)
     y_train = _fft_labels(ctx, train, ph)
     members = []
-    for m in range(2):
+    for m in range(4):
         th, hist = ctx.surrogate_train(train, (y_train / SCALE).astype(np.float32),
-                                       _params(30 + m).astype(np.float32), epochs=40, batch=16, lr=2e-3, seed=m)
-        assert hist[-1] < 0.2 * hist[0], hist
+                                       _params(30 + m).astype(np.float32), epochs=150, batch=16, lr=2e-3, seed=m)
+        assert hist[-1] < 0.05 * hist[0], hist
         members.append(th)
     members = np.stack(members)
     t0 = time.perf_counter()
     pred = ctx.surrogate_predict(test, members, SCALE)
-    acc, mean = ctx.surrogate_gate(test, ph, pred, spread=0.05)
+    acc, mean = ctx.surrogate_gate(test, ph, pred, spread=0.03)
     t_sur = time.perf_counter() - t0
     t0 = time.perf_counter()
     y_test = _fft_labels(ctx, test, ph)
     t_fft = time.perf_counter() - t0
-    errs = []
-    for i in np.flatnonzero(acc):
+    errs = np.zeros(len(acc))
+    for i in range(len(acc)):
         Kp, Gp = N.moduli_voigt(N.c21_to_full(mean[i]))
         Kt, Gt = N.moduli_voigt(N.c21_to_full(y_test[i]))
-        errs.append(max(abs(Kp - Kt) / Kt, abs(Gp - Gt) / Gt))
-    print(f"accepted {acc.sum()}/{len(acc)}, max K/G error of accepted {max(errs) if errs else None}, "
-          f"surrogate {t_sur:.3f} s vs FFT {t_fft:.3f} s")
+        errs[i] = max(abs(Kp - Kt) / Kt, abs(Gp - Gt) / Gt)
+    print(f"accepted {acc.sum()}/{len(acc)}; K/G error: accepted max {errs[acc].max() if acc.any() else None}, "
+          f"rejected median {np.median(errs[~acc]) if (~acc).any() else None}; "
+          f"surrogate {t_sur:.3f} s vs FFT {t_fft:.3f} s for {len(acc)} cubes")
     assert acc.sum() >= len(acc) // 4
-    assert max(errs) < 0.05
+    assert errs[acc].max() < 0.05
+    assert t_sur < t_fft
