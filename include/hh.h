@@ -276,6 +276,22 @@ hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, int e
                             const hh_phase *phases, int nphase, const float *members,
                             int ensemble, double spread, int *accept, double *c21);
 
+/* Two-level scheme on a partition (as hh_homogenize_partition) where every
+ * unbuffered cubic subimage (b = 0, edge 8..256) is first offered to the
+ * surrogate ensemble (params[ensemble][n_params], outputs * scale = GPa) and
+ * its gate (spread as in hh_surrogate_gate): accepted subimages take the
+ * ensemble's mean stiffness (raised to the stiffness floor like FFT results)
+ * and skip the FFT solve; every other subimage is solved by the FFT solver
+ * with `opt`. out->n_surrogate_accepted counts the accepted ones;
+ * accepted[nbox] (may be NULL) flags them. out->device_ms covers the FFT
+ * solves, the assembly and level 2, not the network's inference. */
+hh_status hh_homogenize_partition_surrogate(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
+                                            int img_on_device, const hh_phase *phases, int nphase,
+                                            const int32_t *boxes, int nbox, int unit, const float *params,
+                                            int ensemble, double scale, double spread,
+                                            const hh_options *opt, hh_result *out, double *per_sub_C,
+                                            int *accepted);
+
 /* ---------------------------------------------------------------------------
  * Operator application without allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (code

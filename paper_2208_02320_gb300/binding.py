@@ -123,6 +123,8 @@ _SIGNATURES = {
     "hh_surrogate_train": (_I, [_P, _P, _I, _I, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
     "hh_surrogate_predict": (_I, [_P, _P, _I, _I, _P, _I, _D, _P]),
     "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
+    "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _P,
+                                               _P, _P, _P]),
 }
 
 _lib = None
@@ -413,6 +415,29 @@ class Context:
         self._check(self._lib.hh_surrogate_gate(self._h, _ptr(lab), n, e, ph, nph, _ptr(mem), ens, float(spread),
                                                 _ptr(acc), _ptr(c21)), "hh_surrogate_gate", allow_warn=False)
         return acc.astype(bool), c21
+
+    def homogenize_partition_surrogate(self, img, phases, boxes, params_ensemble, unit=None, scale=100.0,
+                                       spread=0.01, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        bx = np.ascontiguousarray(boxes, dtype=np.int32).reshape(-1, 7)
+        th = np.ascontiguousarray(params_ensemble, dtype=np.float32)
+        ens = th.shape[0] if th.ndim == 2 else 1
+        if unit is None:
+            unit = int(np.gcd.reduce(bx[:, 3:6].ravel()))
+        o = options(**opt)
+        r = Result()
+        nb = len(bx)
+        Cb = np.zeros((nb, 6, 6))
+        acc = np.zeros(nb, dtype=np.int32)
+        s = self._lib.hh_homogenize_partition_surrogate(self._h, p, nx, ny, nz, dev, ph, nph, _ptr(bx), nb, int(unit),
+                                                        _ptr(th), ens, float(scale), float(spread), ctypes.byref(o),
+                                                        ctypes.byref(r), _ptr(Cb), _ptr(acc))
+        self._check(s, "hh_homogenize_partition_surrogate")
+        d = r.as_dict()
+        d.update(C_boxes=Cb, accepted=acc.astype(bool))
+        return d
 
     def profile(self) -> dict:
         arr = (KernelStat * 64)()

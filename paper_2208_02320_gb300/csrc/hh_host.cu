@@ -1328,15 +1328,31 @@ static hh_status parse_boxes(hh_ctx* h, const int32_t* boxes, int nbox, int nx, 
   return HH_OK;
 }
 
-// level 1 + assembly + level 2 on a validated tiling partition
+// level 1 + assembly + level 2 on a validated tiling partition. Subimages
+// listed in acc_idx take the stiffness acc_c21 (21 values each, accepted
+// surrogate predictions) instead of an FFT solve.
 static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, const std::vector<BoxReq>& boxes, int unit,
-                                   const int* reg, hh_result* out, double* per_sub_C, int* per_sub_iters) {
+                                   const int* reg, hh_result* out, double* per_sub_C, int* per_sub_iters,
+                                   const std::vector<int>* acc_idx = nullptr,
+                                   const std::vector<double>* acc_c21 = nullptr) {
   Ctx& c = h->c;
   hh_status s;
   Stats st1;
-  BoxRes* d_res;
-  if ((s = run_boxes_p(h, o, m, boxes, &d_res, st1)) != HH_OK) return s;
+  BoxRes* d_res = nullptr;
   const int nbox = (int)boxes.size();
+  const int nacc = acc_idx ? (int)acc_idx->size() : 0;
+  std::vector<int> rest;  // subimages that the FFT solver homogenizes
+  if (nacc) {
+    std::vector<char> is_acc(nbox, 0);
+    for (int i : *acc_idx) is_acc[i] = 1;
+    for (int i = 0; i < nbox; ++i)
+      if (!is_acc[i]) rest.push_back(i);
+    std::vector<BoxReq> rb;
+    for (int i : rest) rb.push_back(boxes[i]);
+    if (!rb.empty() && (s = run_boxes_p(h, o, m, rb, &d_res, st1)) != HH_OK) return s;
+  } else if ((s = run_boxes_p(h, o, m, boxes, &d_res, st1)) != HH_OK) {
+    return s;
+  }
   // assembly of the intermediate image (FP64)
   const int Cx = reg[3], Cy = reg[4], Cz = reg[5];
   const long long Vc = (long long)Cx * Cy * Cz;
@@ -1346,7 +1362,26 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   BoxRes* d_res1;
   // keep level-1 results: move them out of the buffer the level-2 solve reuses
   if ((s = ensure(c, "boxres1", nbox * sizeof(BoxRes), (void**)&d_res1)) != HH_OK) return s;
-  HH_CK(cudaMemcpyAsync(d_res1, d_res, nbox * sizeof(BoxRes), cudaMemcpyDeviceToDevice, c.st));
+  if (!nacc) {
+    HH_CK(cudaMemcpyAsync(d_res1, d_res, nbox * sizeof(BoxRes), cudaMemcpyDeviceToDevice, c.st));
+  } else {
+    int *d_pos, *d_acc;
+    double* d_pc;
+    if ((s = ensure(c, "surr_pos", std::max<size_t>(rest.size(), 1) * sizeof(int), (void**)&d_pos)) != HH_OK ||
+        (s = ensure(c, "surr_idx", nacc * sizeof(int), (void**)&d_acc)) != HH_OK ||
+        (s = ensure(c, "surr_c21", nacc * 21 * sizeof(double), (void**)&d_pc)) != HH_OK)
+      return s;
+    if (!rest.empty()) {
+      HH_CK(cudaMemcpyAsync(d_pos, rest.data(), rest.size() * sizeof(int), cudaMemcpyHostToDevice, c.st));
+      ++c.launches;
+      k_scatter_res<<<((int)rest.size() + 127) / 128, 128, 0, c.st>>>(d_res, d_pos, (int)rest.size(), d_res1);
+    }
+    HH_CK(cudaMemcpyAsync(d_acc, acc_idx->data(), nacc * sizeof(int), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_pc, acc_c21->data(), nacc * 21 * sizeof(double), cudaMemcpyHostToDevice, c.st));
+    ++c.launches;
+    k_accept_pred<<<(nacc + 127) / 128, 128, 0, c.st>>>(d_pc, d_acc, nacc, d_res1, m.floor);
+    HH_CK(cudaGetLastError());
+  }
   if ((s = ensure(c, "coarse", 21 * Vc * sizeof(double), (void**)&d_c21)) != HH_OK) return s;
   if ((s = ensure(c, "aboxes", nbox * sizeof(BoxReq), (void**)&d_boxes)) != HH_OK) return s;
   if ((s = ensure(c, "am", 4 * sizeof(double), (void**)&d_am)) != HH_OK) return s;
@@ -1393,6 +1428,7 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   out->K_am = am[0];
   out->G_am = am[1];
   out->n_subimages = nbox;
+  out->n_surrogate_accepted = nacc;
   out->n_clipped = (int)am[3];
   for (int b = 0; b < (int)all.size(); ++b) {
     if (per_sub_C) std::memcpy(per_sub_C + 36 * b, all[b].C, 36 * sizeof(double));
@@ -1460,6 +1496,66 @@ extern "C" hh_status hh_homogenize_partition(hh_ctx* h, const uint8_t* img, int 
   m.Nz = nz;
   if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
   return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, per_sub_iters), out);
+}
+
+extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz,
+                                                       int on_dev, const hh_phase* phases, int nphase,
+                                                       const int32_t* boxes, int nbox, int unit, const float* params,
+                                                       int ensemble, double scale, double spread,
+                                                       const hh_options* opt, hh_result* out, double* per_sub_C,
+                                                       int* accepted) {
+  if (!h || !out || !params || ensemble < 1 || !(scale > 0.0) || !(spread >= 0.0))
+    return fail(h, HH_ERR_ARG, "NULL context, output or parameters, or bad ensemble/scale/spread");
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  Medium m;
+  if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
+  std::vector<BoxReq> bx;
+  if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
+  int reg[6];
+  if ((s = check_tiling(h, bx, unit, nx, ny, nz, reg)) != HH_OK) return s;
+  // candidates: unbuffered cubic subimages, grouped by edge
+  std::map<int, std::vector<int>> groups;
+  for (int i = 0; i < nbox; ++i)
+    if (bx[i].b == 0 && bx[i].cnx == bx[i].cny && bx[i].cnx == bx[i].cnz && bx[i].cnx >= 8 && bx[i].cnx <= 256)
+      groups[bx[i].cnx].push_back(i);
+  std::vector<int> acc_idx;
+  std::vector<double> acc_c21;
+  for (auto& kv : groups) {
+    const int e = kv.first;
+    const std::vector<int>& ids = kv.second;
+    const long long V = (long long)e * e * e;
+    std::vector<int32_t> rows;
+    for (int i : ids) rows.insert(rows.end(), boxes + 7 * i, boxes + 7 * i + 7);
+    std::vector<uint8_t> lab(ids.size() * V);
+    std::vector<float> pred(ids.size() * (size_t)ensemble * 21);
+    std::vector<int> ok(ids.size());
+    std::vector<double> c21(ids.size() * 21);
+    if ((s = hh_extract_subimages(h, img, nx, ny, nz, on_dev, rows.data(), (int)ids.size(), lab.data(),
+                                  (int64_t)lab.size())) != HH_OK ||
+        (s = hh_surrogate_predict(h, lab.data(), (int)ids.size(), e, params, ensemble, scale, pred.data())) !=
+            HH_OK ||
+        (s = hh_surrogate_gate(h, lab.data(), (int)ids.size(), e, phases, nphase, pred.data(), ensemble, spread,
+                               ok.data(), c21.data())) != HH_OK)
+      return s;
+    for (size_t j = 0; j < ids.size(); ++j)
+      if (ok[j]) {
+        acc_idx.push_back(ids[j]);
+        acc_c21.insert(acc_c21.end(), c21.begin() + 21 * j, c21.begin() + 21 * j + 21);
+      }
+  }
+  if (accepted) {
+    std::memset(accepted, 0, nbox * sizeof(int));
+    for (int i : acc_idx) accepted[i] = 1;
+  }
+  if ((s = enter(h)) != HH_OK) return s;
+  m.kind = MED_ISO;
+  m.Nx = nx;
+  m.Ny = ny;
+  m.Nz = nz;
+  if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
+  return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, nullptr, &acc_idx, &acc_c21), out);
 }
 
 extern "C" hh_status hh_homogenize_hierarchical(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,

@@ -218,6 +218,30 @@ __global__ void k_finalize(const Prob* prob, const PState* st, int nbox, BoxRes*
   out[box_base + b] = R;
 }
 
+// Level-1 results of the subimages whose surrogate prediction was accepted:
+// C = sym(C) = the predicted stiffness (21 upper-triangle values, FP64), its
+// moduli, and the same projection onto the stiffness floor as FFT results.
+__global__ void k_accept_pred(const double* c21, const int* idx, int n, BoxRes* res, double floor) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  BoxRes R;
+  memset(&R, 0, sizeof(R));
+  for (int a = 0, t = 0; a < 6; ++a)
+    for (int b = a; b < 6; ++b, ++t) {
+      R.C[a * 6 + b] = R.C[b * 6 + a] = c21[(long long)i * 21 + t];
+      R.Csym[a * 6 + b] = R.Csym[b * 6 + a] = c21[(long long)i * 21 + t];
+    }
+  moduli(R.Csym, &R.K, &R.G, &R.KR, &R.GR);
+  R.clipped = clip_spd6(R.Csym, floor, R.Cspd) ? 1 : 0;
+  res[idx[i]] = R;
+}
+
+// res[pos[i]] = src[i] (FFT results of the remaining subimages into place).
+__global__ void k_scatter_res(const BoxRes* src, const int* pos, int n, BoxRes* res) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) res[pos[i]] = src[i];
+}
+
 // Assembly (Section 3): each box fills its block of unit-size coarse cells
 // with the 21 upper-triangle entries of sym(C_R) (component-major, FP64).
 __global__ void k_assemble(const BoxReq* boxes, const BoxRes* res, int nbox, int unit, int rx, int ry, int rz, int Cx,

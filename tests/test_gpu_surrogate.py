@@ -117,22 +117,30 @@ def _fft_labels(ctx, labs, ph):
     return np.stack([c[iu] for c in Cs])
 
 
-def test_training_and_what_the_surrogate_gains(ctx):
-    """Trains a 4-member ensemble on FFT-labelled cubes, then compares, on
-    held-out cubes from the same generator, the ensemble+gate against the FFT
-    solver: the accepted predictions' K and G errors and the time per cube."""
+@pytest.fixture(scope="module")
+def trained(ctx):
+    """A 4-member ensemble trained on FFT-labelled two-phase cubes (edge 16)."""
     ph = synth.PHASES_APPENDIX_B
-    edge = 16
-    train = _cubes(320, edge, seed=21, nphase=2)
-    test = _cubes(48, edge, seed=22, nphase=2)
+    train = _cubes(320, 16, seed=21, nphase=2)
     y_train = _fft_labels(ctx, train, ph)
-    members = []
+    members, hists = [], []
     for m in range(4):
         th, hist = ctx.surrogate_train(train, (y_train / SCALE).astype(np.float32),
                                        _params(30 + m).astype(np.float32), epochs=150, batch=16, lr=2e-3, seed=m)
-        assert hist[-1] < 0.05 * hist[0], hist
         members.append(th)
-    members = np.stack(members)
+        hists.append(hist)
+    return np.stack(members), hists
+
+
+def test_training_and_what_the_surrogate_gains(ctx, trained):
+    """On held-out cubes from the training generator, the ensemble + gate
+    against the FFT solver: the accepted predictions' K and G errors and the
+    time for the same cubes."""
+    members, hists = trained
+    for hist in hists:
+        assert hist[-1] < 0.05 * hist[0], hist
+    ph = synth.PHASES_APPENDIX_B
+    test = _cubes(48, 16, seed=22, nphase=2)
     t0 = time.perf_counter()
     pred = ctx.surrogate_predict(test, members, SCALE)
     acc, mean = ctx.surrogate_gate(test, ph, pred, spread=0.03)
@@ -151,3 +159,29 @@ def test_training_and_what_the_surrogate_gains(ctx):
     assert acc.sum() >= len(acc) // 4
     assert errs[acc].max() < 0.05
     assert t_sur < t_fft
+
+
+def test_hierarchical_with_surrogate(ctx, trained):
+    """Two-level homogenization of a 64^3 image cut into 16^3 cubes, with the
+    surrogate standing in for the accepted cubes, against the same partition
+    solved entirely by the FFT solver."""
+    members, _ = trained
+    ph = synth.PHASES_APPENDIX_B
+    f = synth.gaussian_random_field((64, 64, 64), 2.0, 23, stream=0)
+    img = (f > np.quantile(f, 0.3)).astype(np.uint8)
+    boxes = synth.uniform_partition(64, 16, 0)
+    t0 = time.perf_counter()
+    ref = ctx.homogenize_partition(img, ph, boxes, unit=16, precision="fp32", tol=1e-5)
+    t_fft = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    got = ctx.homogenize_partition_surrogate(img, ph, boxes, members, unit=16, scale=SCALE, spread=0.03,
+                                             precision="fp32", tol=1e-5)
+    t_sur = time.perf_counter() - t0
+    n_acc = int(got["accepted"].sum())
+    print(f"HH with surrogate: {n_acc}/{len(boxes)} accepted, K {got['K']:.4f} vs {ref['K']:.4f}, "
+          f"G {got['G']:.4f} vs {ref['G']:.4f}; {t_sur:.3f} s vs {t_fft:.3f} s")
+    assert got["n_surrogate_accepted"] == n_acc > 0
+    # rejected cubes are solved exactly as without the surrogate
+    rej = ~got["accepted"]
+    assert np.abs(got["C_boxes"][rej] - ref["C_boxes"][rej]).max() <= 1e-6 * np.abs(ref["C_boxes"]).max()
+    assert abs(got["K"] - ref["K"]) / ref["K"] < 0.02 and abs(got["G"] - ref["G"]) / ref["G"] < 0.02
