@@ -76,7 +76,8 @@ class Result(ctypes.Structure):
         return dict(C=np.array(self.C).reshape(6, 6), C_sym=np.array(self.C_sym).reshape(6, 6),
                     K=self.K, G=self.G, K_reuss=self.K_reuss, G_reuss=self.G_reuss,
                     K_am=self.K_am, G_am=self.G_am, iters_max=self.iters_max,
-                    n_subimages=self.n_subimages, n_clipped=self.n_clipped, resid_max=self.resid_max,
+                    n_subimages=self.n_subimages, n_surrogate_accepted=self.n_surrogate_accepted,
+                    n_clipped=self.n_clipped, resid_max=self.resid_max,
                     voxel_iters=self.voxel_iters, kernel_launches=self.kernel_launches,
                     device_ms=self.device_ms, status=self.status)
 
