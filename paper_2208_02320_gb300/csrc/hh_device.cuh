@@ -669,6 +669,7 @@ __device__ __forceinline__ int fwd_slot() {
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
+  int tab_px = -1, tab_py = -1;  // plans whose tables are in shared memory
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, MODE)) continue;
@@ -680,7 +681,11 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, P.nphase);
     const AxisPlan ax = P.plans[d.px];
     const AxisPlan ay = P.plans[d.py];
-    plane_tables<T>(P, sm, ax, ay, nx);
+    if (d.px != tab_px || d.py != tab_py) {  // same plans: same layout, tables still in place
+      plane_tables<T>(P, sm, ax, ay, nx);
+      tab_px = d.px;
+      tab_py = d.py;
+    }
     const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
 
@@ -864,6 +869,7 @@ __device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int n
 template <typename T, bool BASIC>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
+  int tab_pz = -1, tab_py = -1;  // plans whose tables are in shared memory
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
@@ -875,9 +881,13 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     ColumnSmem<T> sm = column_layout<T>(smem, d.cw, nz, ny);
     const AxisPlan az = P.plans[d.pz];
     const AxisPlan ay = P.plans[d.py];
-    load_tw<T>(sm.twz, P.tw, az);
-    for (int t = threadIdx.x; t < nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
-    for (int t = threadIdx.x; t < ny; t += blockDim.x) sm.sfy[t] = P.itab[ay.sf_off + t];
+    if (d.pz != tab_pz || d.py != tab_py) {  // same plans: same layout (cw follows nz, ny)
+      load_tw<T>(sm.twz, P.tw, az);
+      for (int t = threadIdx.x; t < nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
+      for (int t = threadIdx.x; t < ny; t += blockDim.x) sm.sfy[t] = P.itab[ay.sf_off + t];
+      tab_pz = d.pz;
+      tab_py = d.py;
+    }
     C2<T>* sp = P.spec + d.spc_off + j0;
     for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
       const int jl = e % W;
@@ -1034,6 +1044,7 @@ __device__ __forceinline__ void inv_partials(const KParams<T>& P, long long row,
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
+  int tab_px = -1, tab_py = -1;  // plans whose tables are in shared memory
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, MODE)) continue;
@@ -1045,7 +1056,11 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, P.nphase);
     const AxisPlan ax = P.plans[d.px];
     const AxisPlan ay = P.plans[d.py];
-    plane_tables<T>(P, sm, ax, ay, nx);
+    if (d.px != tab_px || d.py != tab_py) {
+      plane_tables<T>(P, sm, ax, ay, nx);
+      tab_px = d.px;
+      tab_py = d.py;
+    }
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
     for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
