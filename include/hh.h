@@ -88,6 +88,10 @@ typedef struct {
                              block; a subimage whose xy plane needs more takes the
                              row/column streaming passes (x rows and y columns
                              through HBM). 0 (default): the device's per-block limit */
+    int autotune;         /* 1 (default): the column pass's width (spectrum columns per
+                             block) is chosen per subimage shape by timing the
+                             candidates once per context; 0: a fixed rule. The width
+                             changes no result, only the speed */
 } hh_options;
 
 typedef struct {

@@ -47,6 +47,7 @@ class Options(ctypes.Structure):
         ("max_restarts", ctypes.c_int),
         ("profile", ctypes.c_int),
         ("plane_smem_limit", ctypes.c_int),
+        ("autotune", ctypes.c_int),
     ]
 
 

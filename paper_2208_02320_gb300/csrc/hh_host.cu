@@ -141,6 +141,7 @@ struct Ctx {
     double ms = 0.0, bytes = 0.0;
   };
   std::map<std::string, KStat> prof;
+  std::map<long long, int> col_tune;  // autotuned column-pass width per (precision, shape)
 };
 
 #define HH_CK(call)                                                         \
@@ -273,6 +274,95 @@ static int grid_for(Ctx& c, const void* kern, int threads, size_t smem, int nite
   long long g = (long long)nb * c.nsm;
   if (g > nitems) g = nitems;
   return (int)std::max<long long>(g, 1);
+}
+
+// Autotuner: the spectrum columns per column-pass block for one subimage
+// shape, chosen by timing the column pass on a scratch batch of that shape
+// (8 problems, zero spectrum) for the widths that fit, once per context. The
+// width changes no arithmetic (every z line is transformed and projected the
+// same way), only the speed.
+template <typename T>
+static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool enabled) {
+  const int rule = column_width<T>(nz, ny, c.smem_optin);
+  if (!enabled) return rule;
+  const long long key = ((long long)sizeof(T) << 48) | ((long long)nz << 32) | ((long long)ny << 16) | nx;
+  auto it = c.col_tune.find(key);
+  if (it != c.col_tune.end()) return it->second;
+  const int nxh = nx / 2 + 1, np = 8;
+  const long long pl = (long long)ny * nxh;
+  C2<T>* d_spec = nullptr;
+  Prob* d_prob = nullptr;
+  int2* d_items = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = rule;
+  float best_ms = 1e30f;
+  bool ok = ensure(c, "tune_spec", np * 6 * nz * pl * sizeof(C2<T>), (void**)&d_spec) == HH_OK &&
+            ensure(c, "tune_prob", np * sizeof(Prob), (void**)&d_prob) == HH_OK &&
+            ensure(c, "tune_items", np * pl * sizeof(int2), (void**)&d_items) == HH_OK &&
+            cudaMemsetAsync(d_spec, 0, np * 6 * nz * pl * sizeof(C2<T>), c.st) == cudaSuccess &&
+            cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  auto* kc = k_column<T, false>;
+  ok = ok && cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)c.smem_optin) == cudaSuccess;
+  for (int cw : {rule / 2, rule, rule * 2}) {
+    if (!ok || cw < 1 || column_smem_bytes<T>(cw, nz, ny) > c.smem_optin) continue;
+    std::vector<Prob> probs(np);
+    std::vector<int2> items;
+    for (int i = 0; i < np; ++i) {
+      Prob& d = probs[i];
+      std::memset(&d, 0, sizeof(d));
+      d.nx = nx;
+      d.ny = ny;
+      d.nz = nz;
+      d.nxh = nxh;
+      d.px = c.tab.index[nx];
+      d.py = c.tab.index[ny];
+      d.pz = c.tab.index[nz];
+      d.cw = cw;
+      d.spc_off = (long long)i * 6 * nz * pl;
+      for (int j0 = 0; j0 < pl; j0 += cw) items.push_back(make_int2(i, j0));
+    }
+    if (cudaMemcpyAsync(d_prob, probs.data(), np * sizeof(Prob), cudaMemcpyHostToDevice, c.st) != cudaSuccess ||
+        cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, c.st) !=
+            cudaSuccess) {
+      ok = false;
+      break;
+    }
+    KParams<T> kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.prob = d_prob;
+    kp.items = d_items;
+    kp.nitems = (int)items.size();
+    kp.nyq_mode = nyq_mode;
+    kp.plans = (const AxisPlan*)c.d_plans.p;
+    kp.tw = (const double*)c.d_tw.p;
+    kp.itab = (const int*)c.d_itab.p;
+    kp.spec = d_spec;
+    const size_t smem = column_smem_bytes<T>(cw, nz, ny);
+    const int grid = grid_for<T>(c, (const void*)kc, 256, smem, kp.nitems);
+    kc<<<grid, 256, smem, c.st>>>(kp, MODE_APPLY);
+    cudaEventRecord(e0, c.st);
+    for (int r = 0; r < 3; ++r) kc<<<grid, 256, smem, c.st>>>(kp, MODE_APPLY);
+    cudaEventRecord(e1, c.st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    c.launches += 4;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cw;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (!ok) {
+    (void)cudaGetLastError();
+    return rule;
+  }
+  c.col_tune[key] = best;
+  return best;
 }
 
 // Solve the six load cases of every box; per-box results land in d_res[box].
@@ -449,7 +539,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.lc = a;
         d.box = b0 + b;
         d.plane0 = (int)pitems.size();
-        d.cw = column_width<T>(nz, ny, c.smem_optin);
+        d.cw = tuned_column_width<T>(c, nx, ny, nz, o.nyquist, o.autotune != 0);
         d.col0 = (int)ccount;
         ccount += ((long long)ny * nxh + d.cw - 1) / d.cw;
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
@@ -1102,6 +1192,7 @@ extern "C" hh_status hh_options_default(hh_options* o) {
   o->check_every = 32;
   o->replace = -1;
   o->max_restarts = 4;
+  o->autotune = 1;
   return HH_OK;
 }
 

@@ -399,3 +399,13 @@ def test_streaming_anisotropic_level2_parity(ctx):
     got = ctx.homogenize_aniso(c21_of(C), precision="fp64", fixed_iters=10, plane_smem_limit=2500)
     ref = O.homogenize_box(O.AnisoMedium(C), (slice(None),) * 3, fixed_iters=10)
     assert rel(got["C"], ref["C"]) < 1e-10
+
+
+# --------------------------------------------------------- P1 autotuner ------
+
+def test_autotuned_column_width_changes_no_result(ctx):
+    img = synth.boolean_spheres(n=96, seed=5)
+    boxes = synth.uneven_partition(N=96, counts=((16, 3), (24, 1), (24, 1)), bmax=8, seed=9)[:12]
+    a = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=0)
+    b = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=1)
+    assert np.array_equal(a["C"], b["C"]) and np.array_equal(a["iters"], b["iters"])
