@@ -301,16 +301,6 @@ struct DotAcc<float> {
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
 
-// L2 prefetch of a byte range by all threads of the block (one request per
-// 128-byte line). The field passes issue the next item's loads this way before
-// transforming the current one, so its global reads overlap the transform.
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-__device__ __forceinline__ void prefetch_range(const void* base, long long bytes) {
-  const char* b = reinterpret_cast<const char*>(base);
-  for (long long off = (long long)threadIdx.x * 128; off < bytes; off += (long long)blockDim.x * 128)
-    prefetch_l2(b + off);
-}
-
 // Weighted Frobenius product term of stored component c (weights 1, 1, 1, 2, 2, 2).
 template <typename T>
 __device__ __forceinline__ T frob_t(int c, T b) { return c < 3 ? b : T(2) * b; }
@@ -700,19 +690,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) sm.S[(c2 * ny + y) * RP + x] = mk<T>(s[2 * c2], s[2 * c2 + 1]);
     }
-    if (MODE == MODE_ITER && it + gridDim.x < P.nitems) {
-      // the fields of this block's next plane
-      const int2 wn = P.items[it + gridDim.x];
-      if (!skip_problem<T>(P.st, wn.x, MODE)) {
-        const Prob& dn = P.prob[wn.x];
-        const long long Vn = (long long)dn.nx * dn.ny * dn.nz;
-        const long long pln = (long long)dn.nx * dn.ny;
-        const long long o = dn.fld_off + (long long)wn.y * pln;
-        for (int c = 0; c < 6; ++c)
-          for (const T* f : {P.r, P.p, P.q, P.x}) prefetch_range(f + o + c * Vn, pln * (long long)sizeof(T));
-        if (P.medium == MED_ISO) prefetch_range(P.labels + dn.med_off + (long long)wn.y * pln, pln);
-      }
-    }
     __syncthreads();
     fft_lines<T, false>(sm.S, plane_rows(ny, RP), ax, sm.twx);
     unpack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
@@ -894,18 +871,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       const int cz = e / W;  // c * nz + z
       sm.tile[e] = sp[(long long)cz * pl + jl];
     }
-    if (it + gridDim.x < P.nitems) {
-      // the spectrum segments of this block's next item
-      const int2 wn = P.items[it + gridDim.x];
-      if (!skip_problem<T>(P.st, wn.x, skip_mode)) {
-        const Prob& dn = P.prob[wn.x];
-        const long long pln = (long long)dn.ny * dn.nxh;
-        const int Wn = (int)min((long long)dn.cw, pln - wn.y);
-        const C2<T>* b = P.spec + dn.spc_off + wn.y;
-        for (int cz = threadIdx.x; cz < 6 * dn.nz; cz += blockDim.x)
-          for (int o = 0; o < Wn; o += 128 / (int)sizeof(C2<T>)) prefetch_l2(b + cz * pln + o);
-      }
-    }
     __syncthreads();
     const Lines Lz{6 * W, W, nz * W, 1, W, true};
     fft_lines<T, false>(sm.tile, Lz, az, sm.twz);
@@ -1068,22 +1033,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
       const int rem = e - c * pl;
       const int ky = rem / nxh;
       sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)] = sp[((long long)c * d.nz + z) * pl + rem];
-    }
-    if (MODE == MODE_ITER) {
-      // p and r of this plane (read after the transforms), and the spectrum
-      // plane of this block's next item
-      const long long pln = (long long)nx * ny;
-      for (int c = 0; c < 6; ++c)
-        for (const T* f : {P.p, P.r}) prefetch_range(f + d.fld_off + (long long)z * pln + c * V, pln * (long long)sizeof(T));
-      if (it + gridDim.x < P.nitems) {
-        const int2 wn = P.items[it + gridDim.x];
-        if (!skip_problem<T>(P.st, wn.x, MODE)) {
-          const Prob& dn = P.prob[wn.x];
-          const long long spn = (long long)dn.ny * dn.nxh;
-          for (int c = 0; c < 6; ++c)
-            prefetch_range(P.spec + dn.spc_off + ((long long)c * dn.nz + wn.y) * spn, spn * (long long)sizeof(C2<T>));
-        }
-      }
     }
     __syncthreads();
     fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
