@@ -213,8 +213,7 @@ namespace hh {
 // length has one, else the staged transform (digit-reversed order between
 // forward and inverse).
 template <typename T, bool INV>
-__device__ __noinline__ void fft_lines(C2<T>* base, const Lines L, const AxisPlan& pl, const C2<T>* tw) {
-  if (pl.split && fft2_dispatch<T, INV>(base, L, pl.n, tw)) return;
+__device__ __noinline__ void fft_lines_staged(C2<T>* base, const Lines L, const AxisPlan& pl, const C2<T>* tw) {
   const int N = pl.n;
   int spans[kMaxStages];
   int s = N;
@@ -234,6 +233,14 @@ __device__ __noinline__ void fft_lines(C2<T>* base, const Lines L, const AxisPla
     }
     __syncthreads();
   }
+}
+
+// The transform of a set of lines: the two-pass plan (one call into the
+// transform unit) when the length has one, else the staged transform.
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_lines(C2<T>* base, const Lines L, const AxisPlan& pl, const C2<T>* tw) {
+  if (pl.split && fft2_dispatch<T, INV>(base, L, pl.n, tw)) return;
+  fft_lines_staged<T, INV>(base, L, pl, tw);
 }
 
 // ---------------------------------------------------------------------------

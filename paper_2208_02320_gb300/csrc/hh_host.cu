@@ -512,6 +512,14 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     // launch classes by shared-memory size: whole planes, streaming rows,
     // streaming y columns, z columns
     std::map<size_t, std::vector<int2>> pclass, rclass, yclass, cclass;
+    // largest footprint in each class: the launch asks for no more, so small
+    // planes leave the SM's remaining shared memory to L1
+    std::map<size_t, size_t> pneed, rneed, yneed, cneed;
+    auto need = [](std::map<size_t, size_t>& m, size_t key, size_t bytes) {
+      size_t& v = m[key];
+      v = std::max(v, (bytes + 1023) & ~size_t(1023));
+      return key;
+    };
     long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0, ccount = 0, prow = 0;
     for (int b = 0; b < nb; ++b) {
       const BoxReq& B = wboxes[b];
@@ -551,22 +559,25 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         if (plane_smem_bytes<T>(nx, ny, nphase) <= plane_lim) {
           d.rows = 0;
           d.npi = nz;
-          std::vector<int2>& pc = pclass[smem_bucket(plane_smem_bytes<T>(nx, ny, nphase))];
+          const size_t pb = plane_smem_bytes<T>(nx, ny, nphase);
+          std::vector<int2>& pc = pclass[need(pneed, smem_bucket(pb), pb)];
           for (int k = 0; k < nz; ++k) pc.push_back(make_int2(pr, k));
         } else {
           const int R = stream_rows(nx, ny);
           const int nch = (ny + R - 1) / R;
           d.rows = R;
           d.npi = nz * nch;
-          std::vector<int2>& rc = rclass[smem_bucket(rows_smem_bytes<T>(nx, R, nphase))];
-          std::vector<int2>& yc = yclass[smem_bucket(ycol_smem_bytes<T>(ny, ycw))];
+          const size_t rb = rows_smem_bytes<T>(nx, R, nphase), yb = ycol_smem_bytes<T>(ny, ycw);
+          std::vector<int2>& rc = rclass[need(rneed, smem_bucket(rb), rb)];
+          std::vector<int2>& yc = yclass[need(yneed, smem_bucket(yb), yb)];
           for (int k = 0; k < nz; ++k) {
             for (int j = 0; j < nch; ++j) rc.push_back(make_int2(pr, k | ((j * R) << 16)));
             for (int x0 = 0; x0 < nxh; x0 += ycw) yc.push_back(make_int2(pr, k | (x0 << 16)));
           }
         }
         prow += d.npi;
-        const size_t ckey = smem_bucket(column_smem_bytes<T>(d.cw, nz, ny));
+        const size_t cb = column_smem_bytes<T>(d.cw, nz, ny);
+        const size_t ckey = need(cneed, smem_bucket(cb), cb);
         std::vector<int2>& cc = cclass[ckey];
         for (int j0 = 0; j0 < ny * nxh; j0 += d.cw) cc.push_back(make_int2(6 * b + a, j0));
         fld_off += 6 * V;
@@ -592,17 +603,18 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       const Prob& pb = probs[b.x];
       return (long long)pa.nx * pa.ny * pa.nz > (long long)pb.nx * pb.ny * pb.nz;
     };
-    auto add_classes = [&](std::map<size_t, std::vector<int2>>& m, std::vector<Cls>& out, bool rows) {
+    auto add_classes = [&](std::map<size_t, std::vector<int2>>& m, std::map<size_t, size_t>& nd, std::vector<Cls>& out,
+                           bool rows) {
       for (auto& kv : m) {
         std::stable_sort(kv.second.begin(), kv.second.end(), by_size);
-        out.push_back({kv.first, (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows});
+        out.push_back({nd[kv.first], (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows});
         clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
       }
     };
-    add_classes(pclass, pcl, false);
-    add_classes(rclass, pcl, true);
-    add_classes(yclass, ycl, false);
-    add_classes(cclass, ccl, false);
+    add_classes(pclass, pneed, pcl, false);
+    add_classes(rclass, rneed, pcl, true);
+    add_classes(yclass, yneed, ycl, false);
+    add_classes(cclass, cneed, ccl, false);
     citems = clsitems;
     // ---- device buffers
     Prob* d_prob;
