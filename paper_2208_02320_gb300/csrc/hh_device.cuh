@@ -853,7 +853,7 @@ __device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int n
 template <typename T, bool BASIC>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
-  int tab_pz = -1, tab_py = -1;  // plans whose tables are in shared memory
+  int tab_pz = -1, tab_py = -1, tab_cw = -1;  // layout whose tables are in shared memory
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
     if (skip_problem<T>(P.st, w.x, skip_mode)) continue;
@@ -865,12 +865,13 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     ColumnSmem<T> sm = column_layout<T>(smem, d.cw, nz, ny);
     const AxisPlan az = P.plans[d.pz];
     const AxisPlan ay = P.plans[d.py];
-    if (d.pz != tab_pz || d.py != tab_py) {  // same plans: same layout (cw follows nz, ny)
+    if (d.pz != tab_pz || d.py != tab_py || d.cw != tab_cw) {  // same plans and width: same layout
       load_tw<T>(sm.twz, P.tw, az);
       for (int t = threadIdx.x; t < nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
       for (int t = threadIdx.x; t < ny; t += blockDim.x) sm.sfy[t] = P.itab[ay.sf_off + t];
       tab_pz = d.pz;
       tab_py = d.py;
+      tab_cw = d.cw;
     }
     C2<T>* sp = P.spec + d.spc_off + j0;
     for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
