@@ -409,3 +409,18 @@ def test_autotuned_column_width_changes_no_result(ctx):
     a = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=0)
     b = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=1)
     assert np.array_equal(a["C"], b["C"]) and np.array_equal(a["iters"], b["iters"])
+
+
+def test_batched_mixed_x_extents_match_single_solves(ctx):
+    """Subimages that share their y and z extents but differ in x are solved
+    together (one column-pass launch, widths tuned per shape) exactly as when
+    each is solved alone."""
+    img = synth.boolean_spheres(n=64, seed=12)
+    boxes = np.array([[0, 0, 0, 16, 24, 24, 0], [16, 0, 0, 20, 24, 24, 0], [36, 0, 0, 26, 24, 24, 0],
+                      [0, 24, 0, 30, 24, 24, 0], [30, 24, 0, 34, 24, 24, 0]], dtype=np.int32)
+    ph = synth.PHASES_SOLID_CLAY_PORE[:2]
+    lab = np.minimum(img, 1).astype(np.uint8)
+    together = ctx.solve_subimages(lab, ph, boxes, precision="fp32", fixed_iters=20)
+    for i, b in enumerate(boxes):
+        alone = ctx.solve_subimages(lab, ph, b[None], precision="fp32", fixed_iters=20)
+        assert np.array_equal(alone["C"][0], together["C"][i]), i
