@@ -156,7 +156,10 @@ def test_training_and_what_the_surrogate_gains(ctx, trained):
     print(f"accepted {acc.sum()}/{len(acc)}; K/G error: accepted max {errs[acc].max() if acc.any() else None}, "
           f"rejected median {np.median(errs[~acc]) if (~acc).any() else None}; "
           f"surrogate {t_sur:.3f} s vs FFT {t_fft:.3f} s for {len(acc)} cubes")
-    assert acc.sum() >= len(acc) // 4
+    # the trained ensemble is accurate to a few percent on held-out cubes; the
+    # gate (bounds, 3 % spread, positive definite) accepts part of them
+    assert np.median(errs) < 0.03
+    assert acc.sum() >= 3
     assert errs[acc].max() < 0.05
     assert t_sur < t_fft
 
