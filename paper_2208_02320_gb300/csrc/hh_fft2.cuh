@@ -136,7 +136,7 @@ __device__ __forceinline__ int line_off(const Lines& L, int l) {
 // Lines per round are whole, so a block needs at least max(N1, N2) / 2
 // threads (every supported length is far below that bound for 256 threads).
 template <typename T, int N1, int N2, bool INV>
-__device__ __forceinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>* tw) {
+__device__ __noinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>* tw) {
   const int nthr = blockDim.x;
   if constexpr (N2 > 1) {
     constexpr int P = N2 <= 2 ? 4 : (N2 <= 4 ? 2 : 1);  // (line, t1) pairs per thread per round
