@@ -676,8 +676,8 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     const int RP = pair_pitch(nx);
     const long long V = (long long)nx * ny * d.nz;
     PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, P.nphase);
-    const AxisPlan ax = P.plans[d.px];
-    const AxisPlan ay = P.plans[d.py];
+    const AxisPlan& ax = P.plans[d.px];  // by reference: no per-thread copy
+    const AxisPlan& ay = P.plans[d.py];  // by reference: no per-thread copy
     if (d.px != tab_px || d.py != tab_py) {  // same plans: same layout, tables still in place
       plane_tables<T>(P, sm, ax, ay, nx);
       tab_px = d.px;
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_fwd(KParams<T> 
     const int RP = pair_pitch(nx);
     const long long V = (long long)nx * ny * d.nz;
     PlaneSmem<T> sm = plane_layout<T>(smem, nx, R, P.nphase);
-    const AxisPlan ax = P.plans[d.px];
+    const AxisPlan& ax = P.plans[d.px];  // by reference: no per-thread copy
     plane_tables<T>(P, sm, ax, ax, nx, false);
     const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_ycols(KParams<T> P, 
     const int W = min(P.ycw, nxh - kx0);
     C2<T>* tile = reinterpret_cast<C2<T>*>(smem);
     C2<T>* twy = tile + 6 * ny * P.ycw;
-    const AxisPlan ay = P.plans[d.py];
+    const AxisPlan& ay = P.plans[d.py];  // by reference: no per-thread copy
     load_tw<T>(twy, P.tw, ay);
     C2<T>* sp = P.spec + d.spc_off + (long long)z * ny * nxh + kx0;
     const long long cstride = (long long)d.nz * ny * nxh;
@@ -863,8 +863,8 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     const int pl = ny * nxh;
     const int W = min(d.cw, pl - j0);  // columns of this item, contiguous in every (c, z) plane
     ColumnSmem<T> sm = column_layout<T>(smem, d.cw, nz, ny);
-    const AxisPlan az = P.plans[d.pz];
-    const AxisPlan ay = P.plans[d.py];
+    const AxisPlan& az = P.plans[d.pz];  // by reference: no per-thread copy
+    const AxisPlan& ay = P.plans[d.py];  // by reference: no per-thread copy
     if (d.pz != tab_pz || d.py != tab_py || d.cw != tab_cw) {  // same plans and width: same layout
       load_tw<T>(sm.twz, P.tw, az);
       for (int t = threadIdx.x; t < nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
@@ -1027,8 +1027,8 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     const int RP = pair_pitch(nx);
     const long long V = (long long)nx * ny * d.nz;
     PlaneSmem<T> sm = plane_layout<T>(smem, nx, ny, P.nphase);
-    const AxisPlan ax = P.plans[d.px];
-    const AxisPlan ay = P.plans[d.py];
+    const AxisPlan& ax = P.plans[d.px];  // by reference: no per-thread copy
+    const AxisPlan& ay = P.plans[d.py];  // by reference: no per-thread copy
     if (d.px != tab_px || d.py != tab_py) {
       plane_tables<T>(P, sm, ax, ay, nx);
       tab_px = d.px;
@@ -1084,7 +1084,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_inv(KParams<T> 
     const int RP = pair_pitch(nx);
     const long long V = (long long)nx * ny * d.nz;
     PlaneSmem<T> sm = plane_layout<T>(smem, nx, R, P.nphase);
-    const AxisPlan ax = P.plans[d.px];
+    const AxisPlan& ax = P.plans[d.px];  // by reference: no per-thread copy
     plane_tables<T>(P, sm, ax, ax, nx, false);
     const C2<T>* sp = P.spec + d.spc_off;
     const int rl = nr * nxh;
