@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-rows", type=int, default=6)
+    ap.add_argument("--fp64-compare", type=int, default=0,
+                    help="also solve the first N rows of the last timed tile in FP64 (plain CG, no residual "
+                         "replacement) and report time and K, G differences")
     return ap.parse_args()
 
 
@@ -328,6 +331,17 @@ def run_gb300(args):
         "roofline": roof,
     }
     line["cpu_baseline"] = cpu_baseline(img, ph, slabs[0], args.cpu_seconds) if ws == 1 else None
+    if args.fp64_compare > 0 and ws == 1:
+        sl = slabs[(args.warmup + args.steps - 1) % len(slabs)]
+        ys = np.unique(sl[:, 1])[:args.fp64_compare]
+        sub = sl[np.isin(sl[:, 1], ys)]
+        r32 = ctx.homogenize_partition(dimg, ph, sub, unit=8, precision="fp32", tol=args.tol)
+        r64 = ctx.homogenize_partition(dimg, ph, sub, unit=8, precision="fp64", tol=args.tol)
+        line["fp64_compare"] = {
+            "cores": int(len(sub)), "fp32_ms": r32["device_ms"], "fp64_ms": r64["device_ms"],
+            "speedup_fp32": r64["device_ms"] / max(r32["device_ms"], 1e-9),
+            "K_rel_diff": abs(r32["K"] - r64["K"]) / r64["K"], "G_rel_diff": abs(r32["G"] - r64["G"]) / r64["G"],
+            "iters_max": [r32["iters_max"], r64["iters_max"]]}
     print(json.dumps(line))
 
 
