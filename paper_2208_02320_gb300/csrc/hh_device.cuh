@@ -112,7 +112,6 @@ struct KParams {
   int fixed_iters;
   int nprob;
   int ycw;           // kx columns per y-column item (row-streaming problems)
-  int stage_pr;      // inverse pass (MODE_ITER): p and r of the plane staged in shared memory
   // basic scheme: Green operator of the isotropic reference medium,
   // Gamma0 = g0a (n (x) v + v (x) n) - g0b (n . v) n (x) n, v = tau n
   T g0a, g0b;
@@ -429,7 +428,6 @@ struct PlaneSmem {
   int* pfx;     // nx
   T* lm;        // 2 * nphase
   double* red;  // 32 * 4
-  T* stage;     // 12 * ny * nx when the inverse pass stages p and r (after lm, 16-byte aligned)
 };
 
 __device__ __forceinline__ int pair_pitch(int nx) { return (nx + 2) | 1; }
@@ -449,21 +447,8 @@ __device__ __forceinline__ PlaneSmem<T> plane_layout(char* base, int nx, int ny,
   s.pfx = reinterpret_cast<int*>(base + o);
   o += sizeof(int) * ((nx + 3) & ~3);
   s.lm = reinterpret_cast<T*>(base + o);
-  o += sizeof(T) * 2 * nphase;
-  o = (o + 15) & ~size_t(15);
-  s.stage = reinterpret_cast<T*>(base + o);
   return s;
 }
-
-// Asynchronous 4- or 8-byte global -> shared copy (cp.async, completion by
-// cp_async_wait_all, visibility by a barrier).
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem_dst, const void* gmem_src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // x-line and y-line views of the pair-row plane.
 __device__ __forceinline__ Lines plane_rows(int ny, int RP) { return Lines{3 * ny, 1 << 30, 0, RP, 1, false}; }
@@ -1057,27 +1042,10 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
       const int ky = rem / nxh;
       sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)] = sp[((long long)c * d.nz + z) * pl + rem];
     }
-    const bool staged = MODE == MODE_ITER && P.stage_pr;
-    const int pl2 = nx * ny;
-    if (staged) {
-      // p and r of this plane arrive in shared memory while the plane transforms
-      const long long o0 = d.fld_off + (long long)z * pl2;
-      for (int e = threadIdx.x; e < 6 * pl2; e += blockDim.x) {
-        const int c = e / pl2;
-        const long long g = o0 + c * V + (e - c * pl2);
-        cp_async<sizeof(T)>(sm.stage + e, P.p + g);
-        cp_async<sizeof(T)>(sm.stage + 6 * pl2 + e, P.r + g);
-      }
-      cp_async_commit();
-    }
     __syncthreads();
     fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
     pack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
     fft_lines<T, true>(sm.S, plane_rows(ny, RP), ax, sm.twx);
-    if (staged) {
-      cp_async_wait_all();
-      __syncthreads();
-    }
 
     DotAcc<T> acc[3];
     const T invV = T(1) / T(V);
@@ -1092,19 +1060,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
         qv[2 * c2] = zz.x * invV;
         qv[2 * c2 + 1] = zz.y * invV;
       }
-      if (staged) {
-        T* __restrict__ qq = P.q + d.fld_off + zoff + v;
-#pragma unroll
-        for (int c = 0; c < 6; ++c) {
-          qq[c * V] = qv[c];
-          const T wq = frob_t(c, qv[c]);
-          acc[0].add(sm.stage[c * pl2 + v], wq);
-          acc[1].add(sm.stage[(6 + c) * pl2 + v], wq);
-          acc[2].add(qv[c], wq);
-        }
-      } else {
-        inv_voxel<T, MODE>(P, d, V, zoff + v, qv, acc);
-      }
+      inv_voxel<T, MODE>(P, d, V, zoff + v, qv, acc);
     }
     inv_partials<T, MODE>(P, d.part0 + z, acc, sm.red);
     __syncthreads();

@@ -514,7 +514,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     std::map<size_t, std::vector<int2>> pclass, rclass, yclass, cclass;
     // largest footprint in each class: the launch asks for no more, so small
     // planes leave the SM's remaining shared memory to L1
-    std::map<size_t, size_t> pneed, rneed, yneed, cneed, sneed;
+    std::map<size_t, size_t> pneed, rneed, yneed, cneed;
     auto need = [](std::map<size_t, size_t>& m, size_t key, size_t bytes) {
       size_t& v = m[key];
       v = std::max(v, (bytes + 1023) & ~size_t(1023));
@@ -559,14 +559,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         if (plane_smem_bytes<T>(nx, ny, nphase) <= plane_lim) {
           d.rows = 0;
           d.npi = nz;
-          // planes whose p, r staging area (inverse pass) keeps the tier form
-          // their own class (odd key) that stages
           const size_t pb = plane_smem_bytes<T>(nx, ny, nphase);
-          const size_t sb = ((pb + 15) & ~size_t(15)) + 12 * sizeof(T) * (size_t)nx * ny;
-          const bool stage = smem_bucket(sb) == smem_bucket(pb) && sb <= c.smem_optin;
-          const size_t key = smem_bucket(pb) + (stage ? 1 : 0);
-          std::vector<int2>& pc = pclass[need(pneed, key, pb)];
-          if (stage) need(sneed, key, sb);
+          std::vector<int2>& pc = pclass[need(pneed, smem_bucket(pb), pb)];
           for (int k = 0; k < nz; ++k) pc.push_back(make_int2(pr, k));
         } else {
           const int R = stream_rows(nx, ny);
@@ -599,8 +593,6 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       int n;
       int grid_f, grid_i;
       bool rows;
-      size_t smem_i;  // inverse launch: with the p, r staging area when it fits the same tier
-      int stage;
     };
     std::vector<Cls> pcl, ycl, ccl;
     citems.clear();
@@ -615,12 +607,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
                            bool rows) {
       for (auto& kv : m) {
         std::stable_sort(kv.second.begin(), kv.second.end(), by_size);
-        Cls k{nd[kv.first], (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows, nd[kv.first], 0};
-        if (&m == &pclass && (kv.first & 1)) {
-          k.smem_i = sneed[kv.first];
-          k.stage = 1;
-        }
-        out.push_back(k);
+        out.push_back({nd[kv.first], (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows});
         clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
       }
     };
@@ -720,7 +707,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     kpp.nitems = (int)pitems.size();
     for (Cls& k : pcl) {
       k.grid_f = grid_for<T>(c, (const void*)kfwd(MODE_ITER, k.rows), threads, k.smem, k.n);
-      k.grid_i = grid_for<T>(c, (const void*)kinv(MODE_ITER, k.rows), threads, k.smem_i, k.n);
+      k.grid_i = grid_for<T>(c, (const void*)kinv(MODE_ITER, k.rows), threads, k.smem, k.n);
     }
     for (Cls& k : ycl) k.grid_f = k.grid_i = grid_for<T>(c, (const void*)kyf, threads, k.smem, k.n);
     for (Cls& k : ccl) k.grid_f = grid_for<T>(c, (const void*)kc, threads, k.smem, k.n);
@@ -728,7 +715,6 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       KParams<T> q = kp;
       q.items = d_cit + k.off;
       q.nitems = k.n;
-      q.stage_pr = k.stage;
       return q;
     };
     // one launch per class for the plane and column passes
@@ -751,7 +737,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       }
       for (const Cls& k : pcl) {
         ++c.launches;
-        kinv(mode, k.rows)<<<k.grid_i, threads, k.smem_i, c.st>>>(cls_params(k));
+        kinv(mode, k.rows)<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
       }
     };
     auto column_pass = [&](int mode) {
