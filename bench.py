@@ -182,6 +182,12 @@ def cpu_baseline(img, ph, boxes, seconds: float):
                       f"{V} voxels), load case 11, {iters} iterations in {dt:.1f} s"}
 
 
+def tile_index(i: int, ws: int, rank: int, ntiles: int) -> int:
+    """Tile of step i on this rank: the ranks take consecutive tiles, so every
+    step of the job works on ws distinct tiles (weak scaling, no exchange)."""
+    return (i * ws + rank) % ntiles
+
+
 def dist_init():
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -251,7 +257,7 @@ def run_gb300(args):
     opt = dict(precision=args.precision, tol=args.tol, profile=1)
 
     def step(i, device=True):
-        sl = slabs[(i * ws + rank) % len(slabs)]
+        sl = slabs[tile_index(i, ws, rank, len(slabs))]
         src = dimg if device else img
         return ctx.homogenize_partition(src, ph, sl, unit=8, **opt)
 
@@ -302,7 +308,7 @@ def run_gb300(args):
                 "avg_launch_ms": st["sampled_ms"] / max(st["sampled"], 1), "peak_source": peak_src,
                 "kernels": {k: {"sampled": v["sampled"], "avg_ms": v["sampled_ms"] / max(v["sampled"], 1),
                                 "GBps": v["sampled_bytes"] / max(v["sampled_ms"], 1e-9) / 1e6} for k, v in prof.items()}}
-    nbox = sum(len(slabs[(i * ws + rank) % len(slabs)]) for i in range(args.warmup, args.warmup + args.steps))
+    nbox = sum(len(slabs[tile_index(i, ws, rank, len(slabs))]) for i in range(args.warmup, args.warmup + args.steps))
     value = units_sum / dev_s_max
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
