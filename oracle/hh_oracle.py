@@ -557,6 +557,61 @@ def homogenize_hierarchical(image, phases, boxes, unit, tol=1e-6, max_iter=20000
                 per_box=per_box, C_boxes=np.array(Cs), coarse=coarse, level2=res2, n_clipped=clipped)
 
 
+def uniform_boxes(shape, n: int, b: int) -> np.ndarray:
+    """Cubic cores of edge n tiling an image of the given (z, y, x) shape,
+    each with buffer b; rows (ox, oy, oz, nx, ny, nz, b), x fastest."""
+    Nz, Ny, Nx = shape
+    assert Nz % n == 0 and Ny % n == 0 and Nx % n == 0
+    return np.array([(i * n, j * n, k * n, n, n, n, b) for k in range(Nz // n) for j in range(Ny // n)
+                     for i in range(Nx // n)], dtype=np.int64)
+
+
+def extract_field(C: np.ndarray, box) -> np.ndarray:
+    """extract_box for a stiffness field (6, 6, Z, Y, X): the buffered box with
+    periodic wrap."""
+    ox, oy, oz, nx, ny, nz, b = (int(v) for v in box)
+    Nz, Ny, Nx = C.shape[2:]
+    iz = np.mod(np.arange(oz - b, oz + nz + b), Nz)
+    iy = np.mod(np.arange(oy - b, oy + ny + b), Ny)
+    ix = np.mod(np.arange(ox - b, ox + nx + b), Nx)
+    return C[:, :, iz[:, None, None], iy[None, :, None], ix[None, None, :]]
+
+
+def homogenize_multilevel(image, phases, levels, tol=1e-6, max_iter=20000, nyquist="component",
+                          fixed_iters=None):
+    """Hierarchical homogenization repeated over several levels (Section 3:
+    the renormalisation is applied repeatedly until the image is small).
+    levels = [(n1, b1), (n2, b2), ...]: level 1 cuts the label image into
+    n1-cubes with buffer b1 and assembles the symmetric stiffnesses (raised
+    to the stiffness floor) into a coarse anisotropic image; every further
+    level does the same to the previous coarse image with (n_k, b_k); the last
+    coarse image is solved whole."""
+    cmin = stiffness_floor(phases)
+    n1, b1 = levels[0]
+    Cs = []
+    for box in uniform_boxes(image.shape, n1, b1):
+        med = IsoMedium.from_labels(extract_box(image, box), phases)
+        r = homogenize_box(med, core_slices(box), tol, max_iter, nyquist, fixed_iters)
+        Cs.append(clip_spd(symmetrize(r["C"]), cmin))
+    coarse = assemble_coarse(image.shape, uniform_boxes(image.shape, n1, b1), Cs, n1)
+    coarses = [coarse]
+    for n, b in levels[1:]:
+        shape = coarse.shape[2:]
+        boxes = uniform_boxes(shape, n, b)
+        Cs = []
+        for box in boxes:
+            r = homogenize_box(AnisoMedium(extract_field(coarse, box)), core_slices(box), tol, max_iter, nyquist,
+                               fixed_iters)
+            Cs.append(clip_spd(symmetrize(r["C"]), cmin))
+        coarse = assemble_coarse(shape, boxes, Cs, n)
+        coarses.append(coarse)
+    res = homogenize_box(AnisoMedium(coarse), (slice(None),) * 3, tol, max_iter, nyquist, fixed_iters)
+    Ceff = symmetrize(res["C"])
+    K, G = moduli_voigt(Ceff)
+    KR, GR = moduli_reuss(Ceff)
+    return dict(C=res["C"], C_sym=Ceff, K=K, G=G, K_reuss=KR, G_reuss=GR, coarse=coarses)
+
+
 # --------------------------------------------------------------------------
 # Power law in 1/n and Richardson extrapolation (Section 5, Eq. fit_power_law).
 # --------------------------------------------------------------------------

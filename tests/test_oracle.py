@@ -546,3 +546,44 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(O, "FROB_W", np.array([1.0, 1, 1, 1, 1, 1]))
     with pytest.raises(AssertionError):
         test_homogeneous_isotropic_returns_phase_moduli_exactly()
+
+
+# ------------------------------------------------- multi-level renormalisation
+
+def test_multilevel_one_level_is_hierarchical():
+    img = synth.grf_two_phase(n=12, ell=2.0, porosity=0.3, seed=4)
+    ph = synth.PHASES_APPENDIX_B
+    a = O.homogenize_multilevel(img, ph, [(6, 1)], tol=1e-11)
+    b = O.homogenize_hierarchical(img, ph, O.uniform_boxes(img.shape, 6, 1), unit=6, tol=1e-11)
+    assert np.abs(a["C_sym"] - b["C_sym"]).max() < 1e-9 * np.abs(b["C_sym"]).max()
+
+
+def test_multilevel_unit_boxes_reproduce_the_direct_solve():
+    # one-voxel cores without buffer return the voxel's own stiffness at every
+    # level, so any number of such levels equals the direct solve
+    img = (RNG.random((4, 4, 4)) < 0.4).astype(np.uint8)
+    ph = synth.PHASES_APPENDIX_B
+    a = O.homogenize_multilevel(img, ph, [(1, 0), (1, 0), (1, 0)], tol=1e-12)
+    d = O.homogenize_direct(img, ph, tol=1e-12)
+    assert np.abs(a["C_sym"] - d["C_sym"]).max() < 1e-8 * np.abs(d["C_sym"]).max()
+
+
+def test_multilevel_laminate_exact_at_every_level():
+    # a laminate along z: every core is itself a laminate (odd edges, so no
+    # Nyquist mode is lost), its periodic solve is the exact layered (Backus)
+    # average, and Backus averages of groups of layers compose exactly
+    lab = synth.laminate((9, 9, 9), [0, 1, 1, 0, 0, 1, 1, 0, 1])
+    ph = synth.PHASES_APPENDIX_B
+    a = O.homogenize_multilevel(lab, ph, [(3, 0), (3, 0)], tol=1e-12)
+    d = O.homogenize_direct(lab, ph, tol=1e-12)
+    assert np.abs(a["C_sym"] - d["C_sym"]).max() < 1e-8 * np.abs(d["C_sym"]).max()
+
+
+def test_extract_field_wraps_like_extract_box():
+    C = RNG.standard_normal((6, 6, 5, 4, 3))
+    box = (2, 3, 4, 2, 1, 2, 1)
+    sub = O.extract_field(C, box)
+    lab = np.arange(60).reshape(5, 4, 3)
+    idx = O.extract_box(lab, box)
+    flat = C.reshape(6, 6, -1)
+    assert np.array_equal(sub, flat[:, :, idx])
