@@ -280,6 +280,20 @@ hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, int e
                             const hh_phase *phases, int nphase, const float *members,
                             int ensemble, double spread, int *accept, double *c21);
 
+/* Hierarchical homogenization over several levels (Section 3: the coarse
+ * image is renormalised again until it is small). Level 1 cuts the image
+ * into cubes of edge ns[0] with buffer bs[0] (as hh_homogenize_hierarchical);
+ * each further level l cuts the previous coarse anisotropic image into cubes
+ * of ns[l] coarse cells with buffer bs[l], solves them with the anisotropic
+ * medium and assembles their symmetric stiffnesses (raised to the stiffness
+ * floor) into the next coarse image; the last coarse image is solved whole
+ * by CG. Every ns[l] must divide the grid of its level. out receives the
+ * final stiffness, K and G (K_am, G_am and the per-subimage arrays are not
+ * filled). Errors as hh_homogenize_hierarchical. */
+hh_status hh_homogenize_multilevel(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz, int img_on_device,
+                                   const hh_phase *phases, int nphase, const int *ns, const int *bs,
+                                   int nlevels, const hh_options *opt, hh_result *out);
+
 /* Two-level scheme on a partition (as hh_homogenize_partition) where every
  * unbuffered cubic subimage (b = 0, edge 8..256) is first offered to the
  * surrogate ensemble (params[ensemble][n_params], outputs * scale = GPa) and

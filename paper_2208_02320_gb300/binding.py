@@ -125,6 +125,7 @@ _SIGNATURES = {
     "hh_surrogate_train": (_I, [_P, _P, _I, _I, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
     "hh_surrogate_predict": (_I, [_P, _P, _I, _I, _P, _I, _D, _P]),
     "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
+    "hh_homogenize_multilevel": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _P,
                                                _P, _P, _P]),
 }
@@ -417,6 +418,19 @@ class Context:
         self._check(self._lib.hh_surrogate_gate(self._h, _ptr(lab), n, e, ph, nph, _ptr(mem), ens, float(spread),
                                                 _ptr(acc), _ptr(c21)), "hh_surrogate_gate", allow_warn=False)
         return acc.astype(bool), c21
+
+    def homogenize_multilevel(self, img, phases, levels, **opt) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        ph, nph = _phases(phases)
+        ns = np.ascontiguousarray([lv[0] for lv in levels], dtype=np.int32)
+        bs = np.ascontiguousarray([lv[1] for lv in levels], dtype=np.int32)
+        o = options(**opt)
+        r = Result()
+        s = self._lib.hh_homogenize_multilevel(self._h, p, nx, ny, nz, dev, ph, nph, _ptr(ns), _ptr(bs), len(ns),
+                                               ctypes.byref(o), ctypes.byref(r))
+        self._check(s, "hh_homogenize_multilevel")
+        return r.as_dict()
 
     def homogenize_partition_surrogate(self, img, phases, boxes, params_ensemble, unit=None, scale=100.0,
                                        spread=0.01, **opt) -> dict:

@@ -526,7 +526,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       const int nx = bdim[3 * (b0 + b)], ny = bdim[3 * (b0 + b) + 1], nz = bdim[3 * (b0 + b) + 2];
       const long long V = (long long)nx * ny * nz;
       const int nxh = nx / 2 + 1;
-      wboxes[b].lab_off = lab_off;
+      wboxes[b].lab_off = (med.kind == MED_ISO) ? lab_off : c21_off;  // labels: bytes; stiffness: elements
       for (int k = 0; k < nz; ++k) gitems.push_back(make_int2(b, k));
       for (int a = 0; a < 6; ++a) {
         Prob& d = probs[6 * b + a];
@@ -658,10 +658,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       HH_CK(cudaGetLastError());
     } else {
       if ((s = ensure(c, "c21T", c21_off * sizeof(T), (void**)&d_c21)) != HH_OK) return s;
-      const long long V = c21_off / 21;
       ++c.launches;
-      k_c21_prepare<T><<<std::max(1, std::min<int>(c.nsm * 8, (int)((V + 255) / 256))), 256, 0, c.st>>>(
-          med.d_c21, d_c21, V, d_flag);
+      k_gather_c21<T><<<grid_for<T>(c, (const void*)k_gather_c21<T>, 256, 0, (int)gitems.size()), 256, 0, c.st>>>(
+          med.d_c21, med.Nx, med.Ny, med.Nz, d_boxes, d_git, (int)gitems.size(), d_c21, d_flag);
       HH_CK(cudaGetLastError());
     }
     HH_CK(cudaMemcpyAsync(c.h_int, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.st));
@@ -1659,6 +1658,119 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
   m.Nz = nz;
   if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
   return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, nullptr, &acc_idx, &acc_c21), out);
+}
+
+// Cubic cores of edge n tiling an nx x ny x nz grid (x fastest), buffer b.
+static std::vector<BoxReq> uniform_boxes(int nx, int ny, int nz, int n, int b) {
+  std::vector<BoxReq> out;
+  for (int k = 0; k < nz / n; ++k)
+    for (int j = 0; j < ny / n; ++j)
+      for (int i = 0; i < nx / n; ++i) {
+        BoxReq B;
+        std::memset(&B, 0, sizeof(B));
+        B.ox = i * n;
+        B.oy = j * n;
+        B.oz = k * n;
+        B.cnx = B.cny = B.cnz = n;
+        B.b = b;
+        out.push_back(B);
+      }
+  return out;
+}
+
+extern "C" hh_status hh_homogenize_multilevel(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,
+                                              const hh_phase* phases, int nphase, const int* ns, const int* bs,
+                                              int nlevels, const hh_options* opt, hh_result* out) {
+  if (!h || !out || !ns || !bs || nlevels < 1) return fail(h, HH_ERR_ARG, "NULL argument or nlevels < 1");
+  hh_status s;
+  if ((s = check_opts(h, opt)) != HH_OK) return s;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
+  int gx = nx, gy = ny, gz = nz;
+  for (int l = 0; l < nlevels; ++l) {
+    const int n = ns[l];
+    if (n < 1 || bs[l] < 0 || gx % n || gy % n || gz % n)
+      return fail(h, HH_ERR_ARG, "level " + std::to_string(l) + ": n must divide the grid, b >= 0");
+    gx /= n;
+    gy /= n;
+    gz /= n;
+  }
+  Medium m;
+  if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
+  if ((s = enter(h)) != HH_OK) return s;
+  Ctx& c = h->c;
+  m.kind = MED_ISO;
+  m.Nx = nx;
+  m.Ny = ny;
+  m.Nz = nz;
+  if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return finish(h, s, out);
+  Stats tot;
+  int cx = nx, cy = ny, cz = nz;  // grid of the current level
+  double* d_cur = nullptr;        // coarse stiffness image of the previous level
+  for (int l = 0; l < nlevels; ++l) {
+    const int n = ns[l];
+    std::vector<BoxReq> boxes = uniform_boxes(cx, cy, cz, n, bs[l]);
+    Medium ml = m;
+    if (l > 0) {
+      ml.kind = MED_ANISO;
+      ml.d_c21 = d_cur;
+      ml.Nx = cx;
+      ml.Ny = cy;
+      ml.Nz = cz;
+    }
+    Stats st;
+    BoxRes* d_res;
+    if ((s = run_boxes_p(h, *opt, ml, boxes, &d_res, st)) != HH_OK) return finish(h, s, out);
+    tot.iters_max = std::max(tot.iters_max, st.iters_max);
+    tot.resid_max = std::max(tot.resid_max, st.resid_max);
+    tot.voxel_iters += st.voxel_iters;
+    tot.worst = std::max(tot.worst, st.worst);
+    // assembly into the next coarse image (ping-pong buffers)
+    const int nbox = (int)boxes.size();
+    const int Cx = cx / n, Cy = cy / n, Cz = cz / n;
+    double* d_next;
+    BoxReq* d_boxes;
+    BoxRes* d_keep;
+    if ((s = ensure(c, (l & 1) ? "ml_b" : "ml_a", 21LL * Cx * Cy * Cz * sizeof(double), (void**)&d_next)) != HH_OK ||
+        (s = ensure(c, "ml_boxes", nbox * sizeof(BoxReq), (void**)&d_boxes)) != HH_OK ||
+        (s = ensure(c, "ml_res", nbox * sizeof(BoxRes), (void**)&d_keep)) != HH_OK)
+      return finish(h, s, out);
+    HH_CK(cudaMemcpyAsync(d_keep, d_res, nbox * sizeof(BoxRes), cudaMemcpyDeviceToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_boxes, boxes.data(), nbox * sizeof(BoxReq), cudaMemcpyHostToDevice, c.st));
+    ++c.launches;
+    k_assemble<<<nbox, 128, 0, c.st>>>(d_boxes, d_keep, nbox, n, 0, 0, 0, Cx, Cy, Cz, d_next);
+    HH_CK(cudaGetLastError());
+    d_cur = d_next;
+    cx = Cx;
+    cy = Cy;
+    cz = Cz;
+  }
+  // the last coarse image, solved whole (always by CG, like level 2)
+  Medium mf = m;
+  mf.kind = MED_ANISO;
+  mf.d_c21 = d_cur;
+  mf.Nx = cx;
+  mf.Ny = cy;
+  mf.Nz = cz;
+  std::vector<BoxReq> one = uniform_boxes(cx, cy, cz, 1, 0);
+  one.resize(1);
+  one[0].cnx = cx;
+  one[0].cny = cy;
+  one[0].cnz = cz;
+  hh_options of = *opt;
+  of.scheme = HH_CG;
+  Stats st;
+  BoxRes* d_res;
+  if ((s = run_boxes_p(h, of, mf, one, &d_res, st)) != HH_OK) return finish(h, s, out);
+  BoxRes R;
+  HH_CK(cudaMemcpyAsync(&R, d_res, sizeof(BoxRes), cudaMemcpyDeviceToHost, c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  tot.iters_max = std::max(tot.iters_max, st.iters_max);
+  tot.resid_max = std::max(tot.resid_max, st.resid_max);
+  tot.voxel_iters += st.voxel_iters;
+  tot.worst = std::max(tot.worst, st.worst);
+  std::memset(out, 0, sizeof(*out));
+  fill_result(out, R, tot);
+  return finish(h, out->status, out);
 }
 
 extern "C" hh_status hh_homogenize_hierarchical(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev,

@@ -305,6 +305,59 @@ __global__ void k_c21_prepare(const double* src, T* dst, long long V, int* bad) 
   }
 }
 
+// Extraction of buffered boxes from a stiffness field (21 upper-triangle
+// components, component-major over the whole Nx x Ny x Nz field, FP64) with
+// periodic wrap, into each box's own component-major block (element offset
+// boxes[b].lab_off) in the solver's precision, with the positive-definite
+// check of every voxel. One block per (box, z) item.
+template <typename T>
+__global__ void k_gather_c21(const double* src, int Nx, int Ny, int Nz, const BoxReq* boxes, const int2* items,
+                             int nitems, T* dst, int* bad) {
+  const long long Vs = (long long)Nx * Ny * Nz;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BoxReq B = boxes[w.x];
+    const int ex = B.cnx + 2 * B.b, ey = B.cny + 2 * B.b, ez = B.cnz + 2 * B.b;
+    const long long Vb = (long long)ex * ey * ez;
+    const int z = w.y;
+    const int sz = ((B.oz - B.b + z) % Nz + Nz) % Nz;
+    for (int v = threadIdx.x; v < ex * ey; v += blockDim.x) {
+      const int y = v / ex, x = v - (v / ex) * ex;
+      const int sy = ((B.oy - B.b + y) % Ny + Ny) % Ny;
+      const int sx = ((B.ox - B.b + x) % Nx + Nx) % Nx;
+      const long long s = ((long long)sz * Ny + sy) * Nx + sx;
+      const long long d = B.lab_off + (long long)z * ex * ey + v;
+      double A[6][6];
+      int k = 0;
+      for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j) {
+          const double val = src[k * Vs + s];
+          A[i][j] = val;
+          A[j][i] = val;
+          dst[d + k * Vb] = T(val);
+          ++k;
+        }
+      bool ok = true;
+      for (int j = 0; j < 6 && ok; ++j) {
+        double t = A[j][j];
+        for (int m = 0; m < j; ++m) t -= A[j][m] * A[j][m];
+        if (!(t > 0.0) || !isfinite(t)) {
+          ok = false;
+          break;
+        }
+        const double ljj = sqrt(t);
+        A[j][j] = ljj;
+        for (int i = j + 1; i < 6; ++i) {
+          double q = A[i][j];
+          for (int m = 0; m < j; ++m) q -= A[i][m] * A[j][m];
+          A[i][j] = q / ljj;
+        }
+      }
+      if (!ok) atomicOr(bad, 1);
+    }
+  }
+}
+
 // Core-volume-weighted means of subimage K and G (one block, fixed order).
 __global__ void k_am(const BoxRes* res, const BoxReq* boxes, int nbox, double* out3) {
   __shared__ double red[32 * 4];

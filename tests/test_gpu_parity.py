@@ -424,3 +424,25 @@ def test_batched_mixed_x_extents_match_single_solves(ctx):
     for i, b in enumerate(boxes):
         alone = ctx.solve_subimages(lab, ph, b[None], precision="fp32", fixed_iters=20)
         assert np.array_equal(alone["C"][0], together["C"][i]), i
+
+
+# ------------------------------------------- multi-level renormalisation ----
+
+@pytest.mark.parametrize("levels", [[(6, 1), (2, 0)], [(4, 0), (3, 1)], [(3, 1), (2, 1), (2, 0)]])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 5e-5)])
+def test_multilevel_parity(ctx, levels, precision, tol):
+    img = synth.grf_two_phase(n=24, ell=2.5, porosity=0.3, seed=13)
+    ph = synth.PHASES_APPENDIX_B
+    got = ctx.homogenize_multilevel(img, ph, levels, precision=precision,
+                                    tol=1e-11 if precision == "fp64" else 1e-6)
+    ref = O.homogenize_multilevel(img, ph, levels, tol=1e-12)
+    assert rel(got["C_sym"], ref["C_sym"]) < tol
+    assert abs(got["K"] - ref["K"]) / ref["K"] < tol and abs(got["G"] - ref["G"]) / ref["G"] < tol
+
+
+def test_multilevel_one_level_equals_hierarchical(ctx):
+    img = synth.grf_two_phase(n=24, ell=2.5, porosity=0.3, seed=14)
+    ph = synth.PHASES_SOLID_CLAY_PORE[:2]
+    a = ctx.homogenize_multilevel(img, ph, [(8, 2)], precision="fp64", tol=1e-10)
+    b = ctx.homogenize_hierarchical(img, ph, 8, 2, precision="fp64", tol=1e-10)
+    assert rel(a["C_sym"], b["C_sym"]) < 1e-12
