@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-rows", type=int, default=6)
+    ap.add_argument("--cost-scaling", type=int, default=0,
+                    help="1: also time single-subimage solves and whole hierarchical runs against the subimage "
+                         "edge n on a 120^3 crop (Section 3, Fig. 3) and fit power laws in n")
     ap.add_argument("--fp64-compare", type=int, default=0,
                     help="also solve the first N rows of the last timed tile in FP64 (plain CG, no residual "
                          "replacement) and report time and K, G differences")
@@ -348,7 +351,33 @@ def run_gb300(args):
             "speedup_fp32": r64["device_ms"] / max(r32["device_ms"], 1e-9),
             "K_rel_diff": abs(r32["K"] - r64["K"]) / r64["K"], "G_rel_diff": abs(r32["G"] - r64["G"]) / r64["G"],
             "iters_max": [r32["iters_max"], r64["iters_max"]]}
+    if args.cost_scaling and ws == 1:
+        line["cost_scaling"] = cost_scaling(ctx, img, ph, args.tol)
     print(json.dumps(line))
+
+
+def cost_scaling(ctx, img, ph, tol):
+    """Cost of one subimage solve t(n) and of the whole two-level run
+    T(n) = (N/n)^3 t(n) + level 2 on a fixed N^3 crop, against the subimage
+    edge n (no buffer), with least-squares exponents of t ~ n^a and T ~ n^b
+    (the paper's Fig. 3 reports a = 3.66 and b = a - 3 = 0.66 on its CPUs)."""
+    import numpy as np
+    N = 120
+    crop = np.ascontiguousarray(img[:N, :N, :N])
+    ns = [15, 20, 24, 30, 40, 60]
+    t1, tH, it1 = [], [], []
+    for n in ns:
+        box = np.array([[0, 0, 0, n, n, n, 0]], dtype=np.int32)
+        ctx.solve_subimages(crop, ph, box, precision="fp32", tol=tol)  # warm (autotuner, tables)
+        r = ctx.homogenize_partition(crop, ph, box, unit=n, precision="fp32", tol=tol)
+        t1.append(r["device_ms"])
+        it1.append(r["iters_max"])
+        ctx.homogenize_hierarchical(crop, ph, n, 0, precision="fp32", tol=tol)
+        tH.append(ctx.homogenize_hierarchical(crop, ph, n, 0, precision="fp32", tol=tol)["device_ms"])
+    a = float(np.polyfit(np.log(ns), np.log(t1), 1)[0])
+    b = float(np.polyfit(np.log(ns), np.log(tH), 1)[0])
+    return {"image": f"{N}^3 crop of the workload image, fp32, tol {tol}", "n": ns, "t_single_ms": t1,
+            "iters_single": it1, "t_hierarchical_ms": tH, "exponent_single": a, "exponent_hierarchical": b}
 
 
 def main():
