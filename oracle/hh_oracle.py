@@ -613,6 +613,70 @@ def homogenize_multilevel(image, phases, levels, tol=1e-6, max_iter=20000, nyqui
 
 
 # --------------------------------------------------------------------------
+# Correlation length (Section 2, Eq. eq_correlation) and the subimage size.
+# --------------------------------------------------------------------------
+
+def correlation_counts(image, pore_label: int, lmax: int):
+    """Pair counts of the material indicator M = [label != pore_label]
+    (mineral 1, pore 0) along x, y, z: count[a][l] = sum of M(v) M(v + l e_a)
+    over the voxel pairs that lie inside the image, l = 0..lmax (integers)."""
+    M = (np.asarray(image) != pore_label).astype(np.int64)
+    out = np.zeros((3, lmax + 1), dtype=np.int64)
+    for a, axis in enumerate((2, 1, 0)):  # x, y, z
+        n = M.shape[axis]
+        for l in range(min(lmax, n - 1) + 1):
+            lo = [slice(None)] * 3
+            hi = [slice(None)] * 3
+            lo[axis] = slice(0, n - l)
+            hi[axis] = slice(l, n)
+            out[a, l] = int(np.sum(M[tuple(lo)] * M[tuple(hi)]))
+    return out
+
+
+def correlation_function(image, pore_label: int, lmax: int):
+    """Corr_a(l) = (<M(v) M(v + l e_a)> - <M>^2) / (<M^2> - <M>^2), the pair
+    average over the pairs inside the image, <M> and <M^2> = <M> over all
+    voxels. Returns (3, lmax + 1)."""
+    M = (np.asarray(image) != pore_label)
+    m = float(M.mean())
+    counts = correlation_counts(image, pore_label, lmax)
+    corr = np.zeros((3, lmax + 1))
+    Nz, Ny, Nx = M.shape
+    for a, n in enumerate((Nx, Ny, Nz)):
+        other = M.size // n
+        for l in range(min(lmax, n - 1) + 1):
+            pairs = (n - l) * other
+            corr[a, l] = (counts[a, l] / pairs - m * m) / (m - m * m)
+    return corr
+
+
+def fit_correlation_length(corr_l):
+    """xi of the least-squares fit of exp(-l / xi) to corr(l) over l = 0 up to
+    the first l where corr drops below 0.05 (the paper's range of useful
+    correlation), by golden-section search on xi in (0.01, 1e4)."""
+    c = np.asarray(corr_l, dtype=np.float64)
+    below = np.flatnonzero(c < 0.05)
+    L = int(below[0]) if below.size else len(c) - 1
+    L = max(L, 1)
+    l = np.arange(L + 1, dtype=np.float64)
+    f = lambda lx: float(np.sum((c[:L + 1] - np.exp(-l / np.exp(lx))) ** 2))
+    a, b = np.log(0.01), np.log(1e4)
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    x1, x2 = b - g * (b - a), a + g * (b - a)
+    f1, f2 = f(x1), f(x2)
+    for _ in range(200):
+        if f1 < f2:
+            b, x2, f2 = x2, x1, f1
+            x1 = b - g * (b - a)
+            f1 = f(x1)
+        else:
+            a, x1, f1 = x1, x2, f2
+            x2 = a + g * (b - a)
+            f2 = f(x2)
+    return float(np.exp(0.5 * (a + b)))
+
+
+# --------------------------------------------------------------------------
 # Power law in 1/n and Richardson extrapolation (Section 5, Eq. fit_power_law).
 # --------------------------------------------------------------------------
 

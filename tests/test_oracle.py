@@ -587,3 +587,34 @@ def test_extract_field_wraps_like_extract_box():
     idx = O.extract_box(lab, box)
     flat = C.reshape(6, 6, -1)
     assert np.array_equal(sub, flat[:, :, idx])
+
+
+# ------------------------------------------------------ correlation length ----
+
+def test_correlation_counts_brute_force():
+    img = (RNG.random((5, 6, 7)) < 0.6).astype(np.uint8)
+    cnt = O.correlation_counts(img, 1, 4)
+    M = (img != 1).astype(int)
+    for l in range(5):
+        sx = sum(M[k, j, i] * M[k, j, i + l] for k in range(5) for j in range(6) for i in range(7 - l))
+        sy = sum(M[k, j, i] * M[k, j + l, i] for k in range(5) for j in range(6 - l) for i in range(7))
+        sz = sum(M[k, j, i] * M[k + l, j, i] for k in range(5 - l) for j in range(6) for i in range(7))
+        assert list(cnt[:, l]) == [sx, sy, sz]
+
+
+def test_correlation_function_special_values():
+    img = synth.grf_two_phase(n=20, ell=2.0, porosity=0.3, seed=9)
+    corr = O.correlation_function(img, 1, 8)
+    assert np.allclose(corr[:, 0], 1.0, atol=1e-12)  # Corr(0) = 1
+    # a laminate along z of period 4: pairs one period apart coincide
+    lab = synth.laminate((12, 5, 5), [0, 1, 1, 0] * 3)
+    cz = O.correlation_function(lab, 1, 4)[2]
+    assert abs(cz[4] - 1.0) < 1e-12
+    cx = O.correlation_function(lab, 1, 3)[0]  # uniform along x
+    assert np.allclose(cx, 1.0, atol=1e-12)
+
+
+def test_fit_recovers_an_exponential():
+    for xi in (2.5, 7.0, 13.1):
+        l = np.arange(60)
+        assert abs(O.fit_correlation_length(np.exp(-l / xi)) - xi) < 1e-6 * xi
