@@ -280,6 +280,20 @@ hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, int e
                             const hh_phase *phases, int nphase, const float *members,
                             int ensemble, double spread, int *accept, double *c21);
 
+/* Correlation length (Section 2, Eq. eq_correlation): with M = 1 on every
+ * voxel whose label is not pore_label (mineral) and 0 on the pore,
+ * counts[a][l] = sum of M(v) M(v + l e_a) over the voxel pairs inside the
+ * image (a = 0, 1, 2 for x, y, z; l = 0..lmax; exact integers),
+ * corr[a][l] = (<M M_l> - <M>^2) / (<M^2> - <M>^2) with the pair average over
+ * those pairs and <M> = <M^2> over all voxels, and xi[a] the least-squares
+ * fit of exp(-l / xi) to corr[a][0..L], L the first l where corr < 0.05. The
+ * paper takes subimages of at least 3 xi. Buffers counts[3][lmax+1],
+ * corr[3][lmax+1], xi[3] are host memory owned by the caller. Errors:
+ * HH_ERR_ARG (lmax outside 1..4096, pore_label outside 0..255, a dimension < 2),
+ * HH_ERR_CUDA. */
+hh_status hh_correlation(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz, int img_on_device,
+                         int pore_label, int lmax, int64_t *counts, double *corr, double *xi);
+
 /* Hierarchical homogenization over several levels (Section 3: the coarse
  * image is renormalised again until it is small). Level 1 cuts the image
  * into cubes of edge ns[0] with buffer bs[0] (as hh_homogenize_hierarchical);

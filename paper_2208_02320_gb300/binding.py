@@ -125,6 +125,7 @@ _SIGNATURES = {
     "hh_surrogate_train": (_I, [_P, _P, _I, _I, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
     "hh_surrogate_predict": (_I, [_P, _P, _I, _I, _P, _I, _D, _P]),
     "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
+    "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
     "hh_homogenize_multilevel": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _P,
                                                _P, _P, _P]),
@@ -418,6 +419,16 @@ class Context:
         self._check(self._lib.hh_surrogate_gate(self._h, _ptr(lab), n, e, ph, nph, _ptr(mem), ens, float(spread),
                                                 _ptr(acc), _ptr(c21)), "hh_surrogate_gate", allow_warn=False)
         return acc.astype(bool), c21
+
+    def correlation(self, img, pore_label: int, lmax: int) -> dict:
+        p, dev, keep = _u8(img)
+        nz, ny, nx = img.shape
+        counts = np.zeros((3, lmax + 1), dtype=np.int64)
+        corr = np.zeros((3, lmax + 1))
+        xi = np.zeros(3)
+        self._check(self._lib.hh_correlation(self._h, p, nx, ny, nz, dev, int(pore_label), int(lmax), _ptr(counts),
+                                             _ptr(corr), _ptr(xi)), "hh_correlation", allow_warn=False)
+        return dict(counts=counts, corr=corr, xi=xi, n_min=int(np.ceil(3.0 * xi.max())))
 
     def homogenize_multilevel(self, img, phases, levels, **opt) -> dict:
         p, dev, keep = _u8(img)

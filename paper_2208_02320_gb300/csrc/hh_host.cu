@@ -1660,6 +1660,92 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
   return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, nullptr, &acc_idx, &acc_c21), out);
 }
 
+// Least-squares fit of exp(-l / xi) to corr(0..L), L the first l with
+// corr(l) < 0.05 (at least 1), by golden-section search on log(xi) over
+// (0.01, 1e4); 200 steps.
+static double fit_xi(const double* corr, int n) {
+  int L = n - 1;
+  for (int l = 0; l < n; ++l)
+    if (corr[l] < 0.05) {
+      L = l;
+      break;
+    }
+  L = std::max(L, 1);
+  auto f = [&](double lx) {
+    const double xi = std::exp(lx);
+    double s = 0.0;
+    for (int l = 0; l <= L && l < n; ++l) {
+      const double r = corr[l] - std::exp(-double(l) / xi);
+      s += r * r;
+    }
+    return s;
+  };
+  double a = std::log(0.01), b = std::log(1e4);
+  const double g = (std::sqrt(5.0) - 1.0) / 2.0;
+  double x1 = b - g * (b - a), x2 = a + g * (b - a), f1 = f(x1), f2 = f(x2);
+  for (int it = 0; it < 200; ++it) {
+    if (f1 < f2) {
+      b = x2;
+      x2 = x1;
+      f2 = f1;
+      x1 = b - g * (b - a);
+      f1 = f(x1);
+    } else {
+      a = x1;
+      x1 = x2;
+      f1 = f2;
+      x2 = a + g * (b - a);
+      f2 = f(x2);
+    }
+  }
+  return std::exp(0.5 * (a + b));
+}
+
+extern "C" hh_status hh_correlation(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev, int pore_label,
+                                    int lmax, int64_t* counts, double* corr, double* xi) {
+  if (!h || !counts || !corr || !xi || lmax < 1 || lmax > 4096 || pore_label < 0 || pore_label > 255)
+    return fail(h, HH_ERR_ARG, "NULL output, lmax outside 1..4096 or pore label outside 0..255");
+  if (nx < 2 || ny < 2 || nz < 2) return fail(h, HH_ERR_ARG, "dims must be >= 2");
+  hh_status s;
+  if ((s = enter(h)) != HH_OK) return s;
+  Ctx& c = h->c;
+  const long long V = (long long)nx * ny * nz;
+  const uint8_t* d_img;
+  if ((s = stage_image(h, img, V, on_dev, &d_img)) != HH_OK) return s;
+  unsigned long long* d_cnt;
+  if ((s = ensure(c, "corr_counts", 3 * (lmax + 1) * sizeof(unsigned long long), (void**)&d_cnt)) != HH_OK) return s;
+  HH_CK(cudaMemsetAsync(d_cnt, 0, 3 * (lmax + 1) * sizeof(unsigned long long), c.st));
+  const int dims[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    const long long nline = V / dims[a];
+    const int grid = (int)std::min<long long>(8LL * c.nsm, (nline + 255) / 256);
+    ++c.launches;
+    k_corr_counts<<<std::max(grid, 1), 256, (lmax + 1) * sizeof(unsigned long long), c.st>>>(
+        d_img, nx, ny, nz, a, pore_label, lmax, d_cnt + a * (lmax + 1));
+    HH_CK(cudaGetLastError());
+  }
+  std::vector<unsigned long long> h_cnt(3 * (lmax + 1));
+  HH_CK(cudaMemcpyAsync(h_cnt.data(), d_cnt, h_cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c.st));
+  HH_CK(cudaStreamSynchronize(c.st));
+  // <M> over all voxels = the l = 0 count of any axis / V
+  const double m = double(h_cnt[0]) / double(V);
+  for (int a = 0; a < 3; ++a) {
+    const int n = dims[a];
+    const long long other = V / n;
+    const int nl = std::min(lmax, n - 1) + 1;
+    for (int l = 0; l <= lmax; ++l) {
+      counts[a * (lmax + 1) + l] = (int64_t)h_cnt[a * (lmax + 1) + l];
+      corr[a * (lmax + 1) + l] = (l < n && m > 0.0 && m < 1.0)
+                                     ? (double(h_cnt[a * (lmax + 1) + l]) / double((long long)(n - l) * other) - m * m) /
+                                           (m - m * m)
+                                     : 0.0;
+    }
+    xi[a] = (m > 0.0 && m < 1.0) ? fit_xi(corr + a * (lmax + 1), nl) : 0.0;
+  }
+  return HH_OK;
+}
+
 // Cubic cores of edge n tiling an nx x ny x nz grid (x fastest), buffer b.
 static std::vector<BoxReq> uniform_boxes(int nx, int ny, int nz, int n, int b) {
   std::vector<BoxReq> out;

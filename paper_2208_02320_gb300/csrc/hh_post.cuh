@@ -358,6 +358,42 @@ __global__ void k_gather_c21(const double* src, int Nx, int Ny, int Nz, const Bo
   }
 }
 
+// Two-point pair counts of the material indicator M = [label != pore] along
+// one axis (0 = x, 1 = y, 2 = z): counts[l] += sum of M(v) M(v + l e_axis)
+// over the pairs inside the image, l = 0..lmax. One thread per line along
+// the axis (adjacent threads take adjacent lines); per-block shared counts,
+// then one 64-bit atomic per l and block (integer sums: exact).
+__global__ void k_corr_counts(const uint8_t* lab, int Nx, int Ny, int Nz, int axis, int pore, int lmax,
+                              unsigned long long* counts) {
+  extern __shared__ unsigned long long cnt[];
+  for (int t = threadIdx.x; t <= lmax; t += blockDim.x) cnt[t] = 0ull;
+  __syncthreads();
+  const long long nline = axis == 0 ? (long long)Ny * Nz : (axis == 1 ? (long long)Nx * Nz : (long long)Nx * Ny);
+  const int n = axis == 0 ? Nx : (axis == 1 ? Ny : Nz);
+  const long long stride = axis == 0 ? 1 : (axis == 1 ? Nx : (long long)Nx * Ny);
+  for (long long line = blockIdx.x * (long long)blockDim.x + threadIdx.x; line < nline;
+       line += (long long)gridDim.x * blockDim.x) {
+    long long base;
+    if (axis == 0) {
+      base = line * Nx;  // line = z * Ny + y
+    } else if (axis == 1) {
+      const long long z = line / Nx, x = line - z * Nx;
+      base = z * Nx * Ny + x;
+    } else {
+      base = line;  // line = y * Nx + x
+    }
+    const uint8_t* p = lab + base;
+    for (int l = 0; l <= lmax && l < n; ++l) {
+      unsigned int c = 0;
+      for (int i = 0; i + l < n; ++i) c += (p[i * stride] != pore) & (p[(i + l) * stride] != pore);
+      if (c) atomicAdd(&cnt[l], (unsigned long long)c);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t <= lmax; t += blockDim.x)
+    if (cnt[t]) atomicAdd(&counts[t], cnt[t]);
+}
+
 // Core-volume-weighted means of subimage K and G (one block, fixed order).
 __global__ void k_am(const BoxRes* res, const BoxReq* boxes, int nbox, double* out3) {
   __shared__ double red[32 * 4];

@@ -446,3 +446,19 @@ def test_multilevel_one_level_equals_hierarchical(ctx):
     a = ctx.homogenize_multilevel(img, ph, [(8, 2)], precision="fp64", tol=1e-10)
     b = ctx.homogenize_hierarchical(img, ph, 8, 2, precision="fp64", tol=1e-10)
     assert rel(a["C_sym"], b["C_sym"]) < 1e-12
+
+
+# ------------------------------------------------------ correlation length ----
+
+@pytest.mark.parametrize("shape,lmax", [((36, 40, 48), 20), ((9, 7, 5), 12)])
+def test_correlation_parity(ctx, shape, lmax):
+    f = synth.gaussian_random_field(shape, 3.0, 17, stream=0)
+    img = np.digitize(f, np.quantile(f, [0.2, 0.5])).astype(np.uint8)  # labels 0, 1, 2
+    got = ctx.correlation(img, pore_label=2, lmax=lmax)
+    ref_counts = O.correlation_counts(img, 2, lmax)
+    assert np.array_equal(got["counts"], ref_counts)  # integer pair counts, bit-exact
+    ref_corr = O.correlation_function(img, 2, lmax)
+    assert np.abs(got["corr"] - ref_corr).max() < 1e-12
+    for a in range(3):
+        xi = O.fit_correlation_length(ref_corr[a, :min(lmax, img.shape[2 - a] - 1) + 1])
+        assert abs(got["xi"][a] - xi) <= 1e-6 * xi
