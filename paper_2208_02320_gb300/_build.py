@@ -29,12 +29,10 @@ DEPS = [os.path.join(CSRC, f) for f in ("hh_host.cu", "hh_cnn.cu", "hh_fft2_inst
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Relocatable device code: a kernel's register count after linking is the
-# largest over everything it calls, so every device function is capped at the
-# smallest budget of the field kernels that call it (48 registers: five
-# 256-thread blocks per SM); the field kernels themselves follow their launch
-# bounds (64 for the forward plane pass, 48 for the others).
-MAX_REGS = 48
-MAX_REGS_FFT = 48
+# largest over everything it calls, so one cap for every unit keeps the
+# transform functions from setting the occupancy of the field kernels
+# (64 registers: four 256-thread blocks per SM, matching the launch bounds).
+MAX_REGS = 64
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-rdc=true", "-Xcompiler", "-fPIC"]
 
 
@@ -62,7 +60,7 @@ def _run(cmd, verbose):
 
 
 def build(force: bool = False, verbose: bool = False, extra=(), max_regs: int = MAX_REGS, lib: str = LIB,
-          build_dir: str = BUILD_DIR, max_regs_fft: int = MAX_REGS_FFT) -> str:
+          build_dir: str = BUILD_DIR) -> str:
     """Build libhh.so next to this file (or at `lib`); returns its path."""
     if not force and lib == LIB and up_to_date():
         return LIB
@@ -73,8 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra=(), max_regs: int = 
     for src, obj, flags in UNITS:
         o = os.path.join(build_dir, obj)
         objs.append(o)
-        regs = max_regs if src != "hh_fft2_inst.cu" else min(max_regs, max_regs_fft)
-        cmds.append([nvcc, *NVCC_FLAGS, "-maxrregcount=%d" % regs, *extra, *flags, inc, "-c", "-o", o,
+        cmds.append([nvcc, *NVCC_FLAGS, "-maxrregcount=%d" % max_regs, *extra, *flags, inc, "-c", "-o", o,
                      os.path.join(CSRC, src)])
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(cmds)) as ex:
         outs = [f.result() for f in [ex.submit(_run, c, verbose) for c in cmds]]

@@ -77,18 +77,12 @@ enum : int { MODE_RHS = 0, MODE_ITER = 1, MODE_APPLY = 2, MODE_TRUE = 3, MODE_BA
 enum : int { ST_OK = 0, ST_NOT_CONVERGED = 1, ST_NONFINITE = 2 };
 
 constexpr int kAvgParts = 12;  // per plane item: core sums of eps* (6) and C:(E + eps*) (6)
-// Resident 256-thread blocks per SM the field passes are compiled for: the
-// forward plane pass at 4 (64 registers: its voxel phase keeps 24 loads in
-// flight), the inverse plane, column and streaming passes at 5 (48
-// registers); measured fastest on the sphere-pack workload.
+// Resident 256-thread blocks per SM the plane and column passes are compiled
+// for (4: a register budget of 64 per thread; 3: 80).
 #ifndef HH_FIELD_BLOCKS_PER_SM
 #define HH_FIELD_BLOCKS_PER_SM 4
 #endif
-#ifndef HH_FIELD2_BLOCKS_PER_SM
-#define HH_FIELD2_BLOCKS_PER_SM 5
-#endif
 constexpr int kFieldBlocksPerSM = HH_FIELD_BLOCKS_PER_SM;
-constexpr int kField2BlocksPerSM = HH_FIELD2_BLOCKS_PER_SM;
 
 template <typename T>
 struct KParams {
@@ -732,7 +726,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
 // order and k_ycols does the y transform.
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, kField2BlocksPerSM) k_rows_fwd(KParams<T> P) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_fwd(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
@@ -785,7 +779,7 @@ __global__ void __launch_bounds__(256, kField2BlocksPerSM) k_rows_fwd(KParams<T>
 // (item w.y = z | kx0 << 16), forward or inverse, in place in spec.
 // ---------------------------------------------------------------------------
 template <typename T, bool INV>
-__global__ void __launch_bounds__(256, kField2BlocksPerSM) k_ycols(KParams<T> P, int skip_mode) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_ycols(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
@@ -857,7 +851,7 @@ __device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int n
 //   sum of h |P tau|^2_F (h = 2 for the kx that stand for a conjugate pair)
 //   and, from the zero mode, Re tau^(0) for the equilibrium residual.
 template <typename T, bool BASIC>
-__global__ void __launch_bounds__(256, kField2BlocksPerSM) k_column(KParams<T> P, int skip_mode) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
   int tab_pz = -1, tab_py = -1, tab_cw = -1;  // layout whose tables are in shared memory
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
@@ -1021,7 +1015,7 @@ __device__ __forceinline__ void inv_partials(const KParams<T>& P, long long row,
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, kField2BlocksPerSM) k_plane_inv(KParams<T> P) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
   int tab_px = -1, tab_py = -1;  // plans whose tables are in shared memory
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
@@ -1078,7 +1072,7 @@ __global__ void __launch_bounds__(256, kField2BlocksPerSM) k_plane_inv(KParams<T
 // inverse y transform (k_ycols), complex-to-real x transform, voxel phase.
 // ---------------------------------------------------------------------------
 template <typename T, int MODE>
-__global__ void __launch_bounds__(256, kField2BlocksPerSM) k_rows_inv(KParams<T> P) {
+__global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_inv(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
   for (int it = blockIdx.x; it < P.nitems; it += gridDim.x) {
     const int2 w = P.items[it];
