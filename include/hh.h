@@ -314,15 +314,33 @@ hh_status hh_homogenize_multilevel(hh_ctx *ctx, const uint8_t *img, int nx, int 
  * its gate (spread as in hh_surrogate_gate): accepted subimages take the
  * ensemble's mean stiffness (raised to the stiffness floor like FFT results)
  * and skip the FFT solve; every other subimage is solved by the FFT solver
- * with `opt`. out->n_surrogate_accepted counts the accepted ones;
- * accepted[nbox] (may be NULL) flags them. out->device_ms covers the FFT
- * solves, the assembly and level 2, not the network's inference. */
+ * with `opt`.
+ *
+ * Audit: the FFT solver also checks a random sample of the accepted
+ * subimages. Accepted subimage i is audited when u_i < audit_fraction, where
+ * u_i is the top 53 bits (times 2^-53) of the i-th output (i from 0) of the
+ * SplitMix64 generator (Steele, Lea and Flood, 2014) seeded with audit_seed:
+ * u_i = mix(audit_seed + (i + 1) * 0x9E3779B97F4A7C15), mix(z) = z3 ^ (z3 >> 31)
+ * with z2 = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9 and
+ * z3 = (z2 ^ (z2 >> 27)) * 0x94D049BB133111EB (64-bit wrap-around). An
+ * audited subimage is solved by the FFT solver, which supplies its stiffness
+ * for the assembly, and audit_err[i] (may be NULL; -1 elsewhere) receives the
+ * ensemble mean's error against it: max(|K_p - K|/K, |G_p - G|/G) of the
+ * isotropic Voigt projections of the ensemble mean as gated and of the FFT
+ * solver's (C + C^T) / 2.
+ * audit_fraction 0 audits nothing, 1 every accepted subimage.
+ *
+ * accepted[nbox] (may be NULL): 0 rejected by the gate (or not a candidate),
+ * 1 accepted (the ensemble's stiffness is used), 2 accepted and audited.
+ * out->n_surrogate_accepted counts the subimages the gate accepted, audited
+ * ones included. out->device_ms covers the FFT solves, the assembly and
+ * level 2, not the network's inference. */
 hh_status hh_homogenize_partition_surrogate(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz,
                                             int img_on_device, const hh_phase *phases, int nphase,
                                             const int32_t *boxes, int nbox, int unit, const float *params,
-                                            int ensemble, double scale, double spread,
-                                            const hh_options *opt, hh_result *out, double *per_sub_C,
-                                            int *accepted);
+                                            int ensemble, double scale, double spread, double audit_fraction,
+                                            uint64_t audit_seed, const hh_options *opt, hh_result *out,
+                                            double *per_sub_C, int *accepted, double *audit_err);
 
 /* ---------------------------------------------------------------------------
  * Operator application without allocation. The paper has no counterpart: this

@@ -127,8 +127,8 @@ _SIGNATURES = {
     "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
     "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
     "hh_homogenize_multilevel": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
-    "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _P,
-                                               _P, _P, _P]),
+    "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _D,
+                                               ctypes.c_uint64, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -444,7 +444,11 @@ class Context:
         return r.as_dict()
 
     def homogenize_partition_surrogate(self, img, phases, boxes, params_ensemble, unit=None, scale=100.0,
-                                       spread=0.01, **opt) -> dict:
+                                       spread=0.01, audit=0.0, audit_seed=0, **opt) -> dict:
+        """accepted: the gate's decisions; audited: the accepted subimages the
+        FFT solver also solved (fraction `audit`, SplitMix64 draws seeded with
+        `audit_seed`); audit_err: the prediction's relative K/G error there
+        (NaN elsewhere)."""
         p, dev, keep = _u8(img)
         nz, ny, nx = img.shape
         ph, nph = _phases(phases)
@@ -458,12 +462,14 @@ class Context:
         nb = len(bx)
         Cb = np.zeros((nb, 6, 6))
         acc = np.zeros(nb, dtype=np.int32)
+        err = np.zeros(nb)
         s = self._lib.hh_homogenize_partition_surrogate(self._h, p, nx, ny, nz, dev, ph, nph, _ptr(bx), nb, int(unit),
-                                                        _ptr(th), ens, float(scale), float(spread), ctypes.byref(o),
-                                                        ctypes.byref(r), _ptr(Cb), _ptr(acc))
+                                                        _ptr(th), ens, float(scale), float(spread), float(audit),
+                                                        int(audit_seed) & (2**64 - 1), ctypes.byref(o),
+                                                        ctypes.byref(r), _ptr(Cb), _ptr(acc), _ptr(err))
         self._check(s, "hh_homogenize_partition_surrogate")
         d = r.as_dict()
-        d.update(C_boxes=Cb, accepted=acc.astype(bool))
+        d.update(C_boxes=Cb, accepted=acc > 0, audited=acc == 2, audit_err=np.where(acc == 2, err, np.nan))
         return d
 
     def profile(self) -> dict:

@@ -1600,14 +1600,35 @@ extern "C" hh_status hh_homogenize_partition(hh_ctx* h, const uint8_t* img, int 
   return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, per_sub_iters), out);
 }
 
+// The i-th draw (i from 0) of the SplitMix64 generator (Steele, Lea and
+// Flood, 2014) seeded with `seed`, as a double in [0, 1) from its top 53 bits.
+static double audit_draw(uint64_t seed, int i) {
+  uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Isotropic Voigt projection of a 6x6 Voigt stiffness: K = (C11 + C22 + C33 +
+// 2 (C12 + C13 + C23)) / 9, G = (C11 + C22 + C33 - C12 - C13 - C23 + 3 (C44 +
+// C55 + C66)) / 15.
+static void voigt_kg(const double* C, double* K, double* G) {
+  const double d = C[0] + C[7] + C[14], o = C[1] + C[2] + C[8], sh = C[21] + C[28] + C[35];
+  *K = (d + 2.0 * o) / 9.0;
+  *G = (d - o + 3.0 * sh) / 15.0;
+}
+
 extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz,
                                                        int on_dev, const hh_phase* phases, int nphase,
                                                        const int32_t* boxes, int nbox, int unit, const float* params,
                                                        int ensemble, double scale, double spread,
+                                                       double audit_fraction, uint64_t audit_seed,
                                                        const hh_options* opt, hh_result* out, double* per_sub_C,
-                                                       int* accepted) {
-  if (!h || !out || !params || ensemble < 1 || !(scale > 0.0) || !(spread >= 0.0))
-    return fail(h, HH_ERR_ARG, "NULL context, output or parameters, or bad ensemble/scale/spread");
+                                                       int* accepted, double* audit_err) {
+  if (!h || !out || !params || ensemble < 1 || !(scale > 0.0) || !(spread >= 0.0) ||
+      !(audit_fraction >= 0.0 && audit_fraction <= 1.0))
+    return fail(h, HH_ERR_ARG, "NULL context, output or parameters, or bad ensemble/scale/spread/audit fraction");
   hh_status s;
   if ((s = check_opts(h, opt)) != HH_OK) return s;
   if (nx < 1 || ny < 1 || nz < 1) return fail(h, HH_ERR_ARG, "dims must be >= 1");
@@ -1622,8 +1643,8 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
   for (int i = 0; i < nbox; ++i)
     if (bx[i].b == 0 && bx[i].cnx == bx[i].cny && bx[i].cnx == bx[i].cnz && bx[i].cnx >= 8 && bx[i].cnx <= 256)
       groups[bx[i].cnx].push_back(i);
-  std::vector<int> acc_idx;
-  std::vector<double> acc_c21;
+  std::vector<int> acc_idx, aud_idx;  // accepted: ensemble stiffness used; audited: FFT solve
+  std::vector<double> acc_c21, aud_c21;
   for (auto& kv : groups) {
     const int e = kv.first;
     const std::vector<int>& ids = kv.second;
@@ -1643,13 +1664,17 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
       return s;
     for (size_t j = 0; j < ids.size(); ++j)
       if (ok[j]) {
-        acc_idx.push_back(ids[j]);
-        acc_c21.insert(acc_c21.end(), c21.begin() + 21 * j, c21.begin() + 21 * j + 21);
+        const int i = ids[j];
+        std::vector<int>& to = audit_draw(audit_seed, i) < audit_fraction ? aud_idx : acc_idx;
+        std::vector<double>& c_to = &to == &aud_idx ? aud_c21 : acc_c21;
+        to.push_back(i);
+        c_to.insert(c_to.end(), c21.begin() + 21 * j, c21.begin() + 21 * j + 21);
       }
   }
   if (accepted) {
     std::memset(accepted, 0, nbox * sizeof(int));
     for (int i : acc_idx) accepted[i] = 1;
+    for (int i : aud_idx) accepted[i] = 2;
   }
   if ((s = enter(h)) != HH_OK) return s;
   m.kind = MED_ISO;
@@ -1657,7 +1682,31 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
   m.Ny = ny;
   m.Nz = nz;
   if ((s = stage_image(h, img, (long long)nx * ny * nz, on_dev, &m.d_img)) != HH_OK) return s;
-  return finish(h, hierarchical_core(h, *opt, m, bx, unit, reg, out, per_sub_C, nullptr, &acc_idx, &acc_c21), out);
+  // the audited subimages are solved by the FFT solver with the rejected ones
+  std::vector<double> Cb;
+  double* Cout = per_sub_C;
+  if (!Cout && audit_err && !aud_idx.empty()) {
+    Cb.resize((size_t)nbox * 36);
+    Cout = Cb.data();
+  }
+  s = hierarchical_core(h, *opt, m, bx, unit, reg, out, Cout, nullptr, &acc_idx, &acc_c21);
+  out->n_surrogate_accepted = (int)(acc_idx.size() + aud_idx.size());
+  if (audit_err && s >= 0) {
+    for (int i = 0; i < nbox; ++i) audit_err[i] = -1.0;
+    for (size_t j = 0; j < aud_idx.size(); ++j) {
+      const int i = aud_idx[j];
+      double P[36], F[36];
+      for (int a = 0, t = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b, ++t) P[6 * a + b] = P[6 * b + a] = aud_c21[21 * j + t];
+      for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) F[6 * a + b] = 0.5 * (Cout[36 * i + 6 * a + b] + Cout[36 * i + 6 * b + a]);
+      double Kp, Gp, Kf, Gf;
+      voigt_kg(P, &Kp, &Gp);
+      voigt_kg(F, &Kf, &Gf);
+      audit_err[i] = std::max(std::fabs(Kp - Kf) / Kf, std::fabs(Gp - Gf) / Gf);
+    }
+  }
+  return finish(h, s, out);
 }
 
 // Least-squares fit of exp(-l / xi) to corr(0..L), L the first l with

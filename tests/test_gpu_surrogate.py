@@ -164,15 +164,18 @@ def test_training_and_what_the_surrogate_gains(ctx, trained):
     assert t_sur < t_fft
 
 
-def test_hierarchical_with_surrogate(ctx, trained):
-    """Two-level homogenization of a 64^3 image cut into 16^3 cubes, with the
-    surrogate standing in for the accepted cubes, against the same partition
-    solved entirely by the FFT solver."""
+def _image64():
+    f = synth.gaussian_random_field((64, 64, 64), 2.0, 23, stream=0)
+    return (f > np.quantile(f, 0.3)).astype(np.uint8), synth.uniform_partition(64, 16, 0)
+
+
+@pytest.fixture(scope="module")
+def hierarchy(ctx, trained):
+    """A 64^3 image cut into 16^3 cubes, solved entirely by the FFT solver and
+    with the surrogate standing in for the accepted cubes (no audit)."""
     members, _ = trained
     ph = synth.PHASES_APPENDIX_B
-    f = synth.gaussian_random_field((64, 64, 64), 2.0, 23, stream=0)
-    img = (f > np.quantile(f, 0.3)).astype(np.uint8)
-    boxes = synth.uniform_partition(64, 16, 0)
+    img, boxes = _image64()
     t0 = time.perf_counter()
     ref = ctx.homogenize_partition(img, ph, boxes, unit=16, precision="fp32", tol=1e-5)
     t_fft = time.perf_counter() - t0
@@ -180,6 +183,14 @@ def test_hierarchical_with_surrogate(ctx, trained):
     got = ctx.homogenize_partition_surrogate(img, ph, boxes, members, unit=16, scale=SCALE, spread=0.03,
                                              precision="fp32", tol=1e-5)
     t_sur = time.perf_counter() - t0
+    return ref, got, t_fft, t_sur
+
+
+def test_hierarchical_with_surrogate(hierarchy):
+    """Two-level homogenization with the surrogate standing in for the
+    accepted cubes, against the same partition solved entirely by the FFT
+    solver."""
+    ref, got, t_fft, t_sur = hierarchy
     n_acc = int(got["accepted"].sum())
     print(f"HH with surrogate: {n_acc}/{len(boxes)} accepted, K {got['K']:.4f} vs {ref['K']:.4f}, "
           f"G {got['G']:.4f} vs {ref['G']:.4f}; {t_sur:.3f} s vs {t_fft:.3f} s")
@@ -204,3 +215,56 @@ def test_hierarchical_with_surrogate(ctx, trained):
     assert eK <= s + 1e-3 and eG <= s + 1e-3
     # and the accepted cubes keep it at the held-out accuracy of the ensemble
     assert eK < 0.05 and eG < 0.05
+
+
+def _audit_draw(seed, i):
+    """The audit's i-th draw: SplitMix64 (seeded with `seed`) output i, top
+    53 bits times 2^-53 (the generator is pinned to its published outputs in
+    tests/test_synth.py)."""
+    return float(synth.splitmix64(seed, [i])[0] >> np.uint64(11)) * 2.0 ** -53
+
+
+def test_surrogate_audit(ctx, trained, hierarchy):
+    """The FFT audit of accepted predictions: every accepted cube (fraction 1)
+    and a seeded half of them (fraction 0.5). Audited cubes take the FFT
+    stiffness, and their reported error is the ensemble mean's Voigt K/G
+    error against it."""
+    members, _ = trained
+    ref, got0, _, _ = hierarchy
+    ph = synth.PHASES_APPENDIX_B
+    img, boxes = _image64()
+    scale_C = np.abs(ref["C_boxes"]).max()
+    # the ensemble's gated mean for every cube, for the expected audit errors
+    cubes = np.stack([img[z:z + dz, y:y + dy, x:x + dx] for x, y, z, dx, dy, dz, _ in boxes])
+    acc, mean = ctx.surrogate_gate(cubes, ph, ctx.surrogate_predict(cubes, members, SCALE), spread=0.03)
+    assert np.array_equal(acc.astype(bool), got0["accepted"])
+
+    def expected_err(i):
+        Kp, Gp = N.moduli_voigt(N.c21_to_full(mean[i]))
+        Cf = 0.5 * (ref["C_boxes"][i] + ref["C_boxes"][i].T)
+        Kf, Gf = N.moduli_voigt(Cf)
+        return max(abs(Kp - Kf) / Kf, abs(Gp - Gf) / Gf)
+
+    full = ctx.homogenize_partition_surrogate(img, ph, boxes, members, unit=16, scale=SCALE, spread=0.03,
+                                              audit=1.0, audit_seed=5, precision="fp32", tol=1e-5)
+    assert np.array_equal(full["audited"], got0["accepted"]) and np.array_equal(full["accepted"], got0["accepted"])
+    assert full["n_surrogate_accepted"] == int(got0["accepted"].sum())
+    # every cube solved by the FFT solver: the all-FFT result
+    assert np.abs(full["C_boxes"] - ref["C_boxes"]).max() <= 1e-6 * scale_C
+    assert abs(full["K"] - ref["K"]) <= 1e-6 * ref["K"] and abs(full["G"] - ref["G"]) <= 1e-6 * ref["G"]
+    for i in np.flatnonzero(full["audited"]):
+        assert abs(full["audit_err"][i] - expected_err(i)) <= 1e-6, i
+    assert np.isnan(full["audit_err"][~full["audited"]]).all()
+
+    half = ctx.homogenize_partition_surrogate(img, ph, boxes, members, unit=16, scale=SCALE, spread=0.03,
+                                              audit=0.5, audit_seed=12345, precision="fp32", tol=1e-5)
+    want = np.array([bool(a) and _audit_draw(12345, i) < 0.5 for i, a in enumerate(got0["accepted"])])
+    assert np.array_equal(half["audited"], want)
+    assert np.array_equal(half["accepted"], got0["accepted"])
+    kept = got0["accepted"] & ~want
+    assert np.abs(half["C_boxes"][kept] - got0["C_boxes"][kept]).max(initial=0.0) <= 1e-9 * scale_C
+    assert np.abs(half["C_boxes"][~kept] - ref["C_boxes"][~kept]).max() <= 1e-6 * scale_C
+    for i in np.flatnonzero(want):
+        assert abs(half["audit_err"][i] - expected_err(i)) <= 1e-6, i
+    print(f"audit: {int(want.sum())}/{int(got0['accepted'].sum())} accepted cubes audited, "
+          f"max error {np.nanmax(half['audit_err']) if want.any() else None}")
