@@ -192,7 +192,7 @@ def test_hierarchical_with_surrogate(hierarchy):
     solver."""
     ref, got, t_fft, t_sur = hierarchy
     n_acc = int(got["accepted"].sum())
-    print(f"HH with surrogate: {n_acc}/{len(boxes)} accepted, K {got['K']:.4f} vs {ref['K']:.4f}, "
+    print(f"HH with surrogate: {n_acc}/{len(got['accepted'])} accepted, K {got['K']:.4f} vs {ref['K']:.4f}, "
           f"G {got['G']:.4f} vs {ref['G']:.4f}; {t_sur:.3f} s vs {t_fft:.3f} s")
     assert got["n_surrogate_accepted"] == n_acc > 0
     # rejected cubes are solved exactly as without the surrogate
