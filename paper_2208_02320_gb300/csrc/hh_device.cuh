@@ -462,6 +462,26 @@ __device__ __forceinline__ int plane_spec_at(int c, int ky, int kx, int ny, int 
 
 constexpr int kPackPerThread = 4;
 
+// Global-to-shared copy of n elements, dst[sidx(e)] = src[gidx(e)], with
+// kCopyBatch loads in flight per thread: a batch's loads are issued before
+// its stores, so a block keeps several HBM requests per thread outstanding
+// instead of one.
+constexpr int kCopyBatch = 4;
+template <typename V, typename GI, typename SI>
+__device__ __forceinline__ void copy_batched(V* __restrict__ dst, const V* __restrict__ src, int n, GI gidx,
+                                             SI sidx) {
+  const int stride = blockDim.x;
+  int e = threadIdx.x;
+  for (; e + (kCopyBatch - 1) * stride < n; e += kCopyBatch * stride) {
+    V v[kCopyBatch];
+#pragma unroll
+    for (int u = 0; u < kCopyBatch; ++u) v[u] = src[gidx(e + u * stride)];
+#pragma unroll
+    for (int u = 0; u < kCopyBatch; ++u) dst[sidx(e + u * stride)] = v[u];
+  }
+  for (; e < n; e += stride) dst[sidx(e)] = src[gidx(e)];
+}
+
 // Split every transformed packed row Z = A + iB (A, B spectra of real rows)
 // into [A | B] in place, in rounds of whole rows (reads, barrier, writes).
 template <typename T>
@@ -874,11 +894,13 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       tab_cw = d.cw;
     }
     C2<T>* sp = P.spec + d.spc_off + j0;
-    for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
-      const int jl = e % W;
-      const int cz = e / W;  // c * nz + z
-      sm.tile[e] = sp[(long long)cz * pl + jl];
-    }
+    copy_batched(
+        sm.tile, sp, 6 * nz * W,
+        [=](int e) {
+          const int cz = e / W;  // c * nz + z
+          return (long long)cz * pl + (e - cz * W);
+        },
+        [](int e) { return e; });
     __syncthreads();
     const Lines Lz{6 * W, W, nz * W, 1, W, true};
     fft_lines<T, false>(sm.tile, Lz, az, sm.twz);
@@ -1036,12 +1058,19 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     }
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
-    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
-      const int c = e / pl;
-      const int rem = e - c * pl;
-      const int ky = rem / nxh;
-      sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)] = sp[((long long)c * d.nz + z) * pl + rem];
-    }
+    const long long zpl = (long long)z * pl, cpl = (long long)d.nz * pl;
+    copy_batched(
+        sm.S, sp, 6 * pl,
+        [=](int e) {
+          const int c = e / pl;
+          return c * cpl + zpl + (e - c * pl);
+        },
+        [=](int e) {
+          const int c = e / pl;
+          const int rem = e - c * pl;
+          const int ky = rem / nxh;
+          return plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP);
+        });
     __syncthreads();
     fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
     pack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
