@@ -89,7 +89,8 @@ def test_full_size_tile_against_oracle_and_bounds(ctx):
     # accuracy is judged by the oracle samples below.
     print(f"status {r['status']}, resid_max {r['resid_max']:.2e}, iters_max {r['iters_max']}")
     assert r["status"] in (0, 1) and r["resid_max"] < 1e-3 and r["n_subimages"] == 180
-    assert (r["iters_boxes"] > 0).all() and (r["iters_boxes"] < 20000).all()
+    # a core without pore voxels has a zero right-hand side: 0 iterations
+    assert (r["iters_boxes"] >= 0).all() and (r["iters_boxes"] < 20000).all()
     Ceff = 0.5 * (r["C"] + r["C"].T)
     assert np.abs(r["C"] - r["C"].T).max() <= 1e-3 * np.abs(Ceff).max()
     assert np.linalg.eigvalsh(Ceff).min() > 0.0
