@@ -35,7 +35,10 @@ extern "C" {
 
 typedef int hh_status;
 #define HH_OK 0
-#define HH_WARN_NOT_CONVERGED 1   /* a solve hit max_iter; results filled, resid_max reported */
+#define HH_WARN_NOT_CONVERGED 1   /* a load case stopped with its true residual above 2 tol:
+                                     max_iter reached, or its restarts spent or no longer
+                                     reducing the residual (the FP32 floor at high phase
+                                     contrast); results filled, resid_max reported */
 #define HH_ERR_ARG (-1)           /* invalid argument (dims, labels, moduli, partition, options) */
 #define HH_ERR_OOM (-2)           /* device or pinned allocation failed */
 #define HH_ERR_CUDA (-3)          /* a CUDA runtime call failed */
