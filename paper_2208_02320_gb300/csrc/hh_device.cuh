@@ -462,25 +462,25 @@ __device__ __forceinline__ int plane_spec_at(int c, int ky, int kx, int ny, int 
 
 constexpr int kPackPerThread = 4;
 
-// Global-to-shared copy of n elements, dst[sidx(e)] = src[gidx(e)], with
-// kCopyBatch loads in flight per thread: a batch's loads are issued before
-// its stores, so a block keeps several HBM requests per thread outstanding
-// instead of one.
-constexpr int kCopyBatch = 4;
+// Global-to-shared copy of n elements, dst[sidx(e)] = src[gidx(e)], by
+// asynchronous element copies (cp.async, sm_80 and later): every copy of a
+// thread is in flight at once and none is staged through registers. The
+// caller waits with copy_async_wait() before its barrier. Elements are 8 or
+// 16 bytes, aligned to their size at both ends.
 template <typename V, typename GI, typename SI>
-__device__ __forceinline__ void copy_batched(V* __restrict__ dst, const V* __restrict__ src, int n, GI gidx,
-                                             SI sidx) {
-  const int stride = blockDim.x;
-  int e = threadIdx.x;
-  for (; e + (kCopyBatch - 1) * stride < n; e += kCopyBatch * stride) {
-    V v[kCopyBatch];
-#pragma unroll
-    for (int u = 0; u < kCopyBatch; ++u) v[u] = src[gidx(e + u * stride)];
-#pragma unroll
-    for (int u = 0; u < kCopyBatch; ++u) dst[sidx(e + u * stride)] = v[u];
+__device__ __forceinline__ void copy_async(V* dst, const V* src, int n, GI gidx, SI sidx) {
+  static_assert(sizeof(V) == 8 || sizeof(V) == 16, "8- or 16-byte elements");
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + sidx(e));
+    const V* g = src + gidx(e);
+    if constexpr (sizeof(V) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(g) : "memory");
+    else
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
   }
-  for (; e < n; e += stride) dst[sidx(e)] = src[gidx(e)];
 }
+
+__device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Split every transformed packed row Z = A + iB (A, B spectra of real rows)
 // into [A | B] in place, in rounds of whole rows (reads, barrier, writes).
@@ -894,13 +894,14 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       tab_cw = d.cw;
     }
     C2<T>* sp = P.spec + d.spc_off + j0;
-    copy_batched(
+    copy_async(
         sm.tile, sp, 6 * nz * W,
         [=](int e) {
           const int cz = e / W;  // c * nz + z
           return (long long)cz * pl + (e - cz * W);
         },
         [](int e) { return e; });
+    copy_async_wait();
     __syncthreads();
     const Lines Lz{6 * W, W, nz * W, 1, W, true};
     fft_lines<T, false>(sm.tile, Lz, az, sm.twz);
@@ -1059,7 +1060,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
     const long long zpl = (long long)z * pl, cpl = (long long)d.nz * pl;
-    copy_batched(
+    copy_async(
         sm.S, sp, 6 * pl,
         [=](int e) {
           const int c = e / pl;
@@ -1071,6 +1072,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
           const int ky = rem / nxh;
           return plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP);
         });
+    copy_async_wait();
     __syncthreads();
     fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
     pack_rows<T>(sm.S, 3 * ny, RP, nx, nxh, sm.pfx);
