@@ -273,6 +273,22 @@ hh_status hh_surrogate_train(hh_ctx *ctx, const uint8_t *labels, int count, int 
 hh_status hh_surrogate_predict(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
                                const float *params, int ensemble, double scale, float *out);
 
+/* Ensemble files. hh_surrogate_save writes params[ensemble][n_params]
+ * (n_params = hh_cnn_num_params()) and the output scale to `path`; the file
+ * is little-endian: the 8 bytes "HHSURR01", int32 ensemble, int32 0,
+ * int64 n_params, float64 scale, uint64 FNV-1a (64-bit) hash of the
+ * parameter bytes, then the FP32 parameters. hh_surrogate_load reads it back
+ * bit for bit into params (capacity = floats available) and sets *ensemble
+ * and *scale; with params NULL it only reads the header and sets both, so
+ * the caller can size the buffer. Host-only calls (no context, no GPU).
+ * Errors (text via hh_last_error(NULL)): HH_ERR_ARG for NULL pointers,
+ * ensemble < 1, a scale that is not finite and > 0, a file that cannot be
+ * opened, written or read, a wrong magic, n_params or length, a hash that
+ * does not match, or a capacity below ensemble * n_params. */
+hh_status hh_surrogate_save(const char *path, const float *params, int ensemble, double scale);
+hh_status hh_surrogate_load(const char *path, float *params, int64_t capacity, int *ensemble,
+                            double *scale);
+
 /* The gate: accept[i] = 1 when every member's Voigt-projected K and G lie in
  * the cube's own Reuss..Voigt bounds of the phase moduli (from its phase
  * fractions), the relative spread (max - min) / mean over the members of K

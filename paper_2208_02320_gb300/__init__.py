@@ -5,4 +5,4 @@ this package only builds it and marshals arguments through ctypes
 (`binding`). Nothing here computes on the CPU.
 """
 
-from .binding import Context, HHError, load, options  # noqa: F401
+from .binding import Context, HHError, load, options, surrogate_load, surrogate_save  # noqa: F401

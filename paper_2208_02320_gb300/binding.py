@@ -125,6 +125,8 @@ _SIGNATURES = {
     "hh_surrogate_train": (_I, [_P, _P, _I, _I, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
     "hh_surrogate_predict": (_I, [_P, _P, _I, _I, _P, _I, _D, _P]),
     "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
+    "hh_surrogate_save": (_I, [ctypes.c_char_p, _P, _I, _D]),
+    "hh_surrogate_load": (_I, [ctypes.c_char_p, _P, ctypes.c_int64, _P, _P]),
     "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
     "hh_homogenize_multilevel": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _D,
@@ -194,6 +196,32 @@ def _phases(phases):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def surrogate_save(path: str, params_ensemble, scale: float) -> None:
+    """Write an ensemble (params[ensemble][n_params] FP32) and its output
+    scale to an ensemble file (hh_surrogate_save; no GPU needed)."""
+    lib = load()
+    th = np.ascontiguousarray(params_ensemble, dtype=np.float32)
+    ens = th.shape[0] if th.ndim == 2 else 1
+    if th.size != ens * lib.hh_cnn_num_params():
+        raise ValueError("params_ensemble must hold ensemble x hh_cnn_num_params() values")
+    s = lib.hh_surrogate_save(os.fsencode(path), _ptr(th), ens, float(scale))
+    if s != HH_OK:
+        raise HHError(s, lib.hh_last_error(None).decode())
+
+
+def surrogate_load(path: str):
+    """(params[ensemble][n_params] FP32, scale) from an ensemble file."""
+    lib = load()
+    ens, sc = ctypes.c_int(), ctypes.c_double()
+    s = lib.hh_surrogate_load(os.fsencode(path), None, 0, ctypes.byref(ens), ctypes.byref(sc))
+    if s == HH_OK:
+        th = np.zeros((ens.value, lib.hh_cnn_num_params()), dtype=np.float32)
+        s = lib.hh_surrogate_load(os.fsencode(path), _ptr(th), th.size, ctypes.byref(ens), ctypes.byref(sc))
+    if s != HH_OK:
+        raise HHError(s, lib.hh_last_error(None).decode())
+    return th, sc.value
 
 
 class Context:

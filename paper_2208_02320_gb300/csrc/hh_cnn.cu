@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -867,4 +868,109 @@ extern "C" hh_status hh_surrogate_gate(hh_ctx* h, const uint8_t* labels, int cou
   cudaFree(d_acc);
   cudaFree(d_c);
   return r;
+}
+
+// ---------------------------------------------------------------------------
+// Ensemble files (host only). Fields are written byte by byte in
+// little-endian order, so the file is the same on every host.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr char kSurrMagic[8] = {'H', 'H', 'S', 'U', 'R', 'R', '0', '1'};
+constexpr size_t kSurrHeader = 8 + 4 + 4 + 8 + 8 + 8;
+
+// FNV-1a, 64-bit (Fowler, Noll and Vo): offset basis 0xcbf29ce484222325,
+// prime 0x100000001b3.
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+void put_le(unsigned char* dst, uint64_t v, int bytes) {
+  for (int i = 0; i < bytes; ++i) dst[i] = (unsigned char)(v >> (8 * i));
+}
+
+uint64_t get_le(const unsigned char* src, int bytes) {
+  uint64_t v = 0;
+  for (int i = 0; i < bytes; ++i) v |= (uint64_t)src[i] << (8 * i);
+  return v;
+}
+
+// The parameters as little-endian bytes (FP32 bit patterns).
+std::vector<unsigned char> params_bytes(const float* params, size_t n) {
+  std::vector<unsigned char> b(4 * n);
+  for (size_t i = 0; i < n; ++i) {
+    uint32_t u;
+    std::memcpy(&u, params + i, 4);
+    put_le(b.data() + 4 * i, u, 4);
+  }
+  return b;
+}
+
+}  // namespace
+
+extern "C" hh_status hh_surrogate_save(const char* path, const float* params, int ensemble, double scale) {
+  if (!path || !params || ensemble < 1 || !(scale > 0.0) || !std::isfinite(scale))
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_save: NULL path or params, ensemble < 1 or bad scale");
+  const int64_t np = hh_cnn_num_params();
+  const std::vector<unsigned char> body = params_bytes(params, (size_t)ensemble * (size_t)np);
+  unsigned char head[kSurrHeader];
+  std::memcpy(head, kSurrMagic, 8);
+  put_le(head + 8, (uint32_t)ensemble, 4);
+  put_le(head + 12, 0, 4);
+  put_le(head + 16, (uint64_t)np, 8);
+  uint64_t sb;
+  std::memcpy(&sb, &scale, 8);
+  put_le(head + 24, sb, 8);
+  put_le(head + 32, fnv1a64(body.data(), body.size()), 8);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return ctx_fail(nullptr, HH_ERR_ARG, (std::string("hh_surrogate_save: cannot open ") + path).c_str());
+  const bool ok = std::fwrite(head, 1, kSurrHeader, f) == kSurrHeader &&
+                  std::fwrite(body.data(), 1, body.size(), f) == body.size();
+  if (std::fclose(f) != 0 || !ok)
+    return ctx_fail(nullptr, HH_ERR_ARG, (std::string("hh_surrogate_save: cannot write ") + path).c_str());
+  return HH_OK;
+}
+
+extern "C" hh_status hh_surrogate_load(const char* path, float* params, int64_t capacity, int* ensemble,
+                                       double* scale) {
+  if (!path || !ensemble || !scale)
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_load: NULL path, ensemble or scale");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return ctx_fail(nullptr, HH_ERR_ARG, (std::string("hh_surrogate_load: cannot open ") + path).c_str());
+  unsigned char head[kSurrHeader];
+  const bool got_head = std::fread(head, 1, kSurrHeader, f) == kSurrHeader;
+  const int64_t np = hh_cnn_num_params();
+  const int ens = got_head ? (int)(uint32_t)get_le(head + 8, 4) : 0;
+  if (!got_head || std::memcmp(head, kSurrMagic, 8) != 0 || (int64_t)get_le(head + 16, 8) != np || ens < 1) {
+    std::fclose(f);
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_load: not an ensemble file of this network");
+  }
+  double sc;
+  const uint64_t sb = get_le(head + 24, 8);
+  std::memcpy(&sc, &sb, 8);
+  const size_t n = (size_t)ens * (size_t)np;
+  std::vector<unsigned char> body(4 * n);
+  const bool got_body = std::fread(body.data(), 1, body.size(), f) == body.size();
+  unsigned char extra;
+  const bool at_end = std::fread(&extra, 1, 1, f) == 0;
+  std::fclose(f);
+  if (!got_body || !at_end)
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_load: file length does not match its header");
+  if (fnv1a64(body.data(), body.size()) != get_le(head + 32, 8))
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_load: parameter hash does not match");
+  if (!(sc > 0.0) || !std::isfinite(sc)) return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_load: bad scale");
+  *ensemble = ens;
+  *scale = sc;
+  if (!params) return HH_OK;
+  if (capacity < (int64_t)n) return ctx_fail(nullptr, HH_ERR_ARG, "hh_surrogate_load: capacity too small");
+  for (size_t i = 0; i < n; ++i) {
+    const uint32_t u = (uint32_t)get_le(body.data() + 4 * i, 4);
+    std::memcpy(params + i, &u, 4);
+  }
+  return HH_OK;
 }
