@@ -88,3 +88,38 @@ int main(void){
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(B.Options), B.Options.workspace_bytes.offset, B.Options.check_every.offset,
                     ctypes.sizeof(B.Result), B.Result.status.offset]
+
+
+def _declared_arity():
+    """Parameter count of every function declared in include/hh.h."""
+    txt = open(os.path.join(ROOT, "include", "hh.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(hh_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;", txt):
+        params = m.group(2).strip()
+        out[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_header():
+    from paper_2208_02320_gb300 import binding as B
+    ar = _declared_arity()
+    assert set(ar) == set(B._SIGNATURES)
+    for name, (_, args) in B._SIGNATURES.items():
+        assert len(args) == ar[name], name
+
+
+def test_null_arguments_fail_cleanly(lib):
+    """Every entry point answers NULL pointers (a NULL context first) with
+    HH_ERR_ARG and an error text, before any device work."""
+    from paper_2208_02320_gb300 import binding as B
+    skip = {"hh_version", "hh_status_string", "hh_last_error", "hh_cnn_num_params", "hh_destroy"}
+    fill = {ctypes.c_void_p: None, ctypes.c_int: 1, ctypes.c_double: 1.0, ctypes.c_int64: 1,
+            ctypes.c_uint64: 0, ctypes.c_char_p: None}
+    for name, (_, argtypes) in B._SIGNATURES.items():
+        if name in skip:
+            continue
+        args = [fill[t] for t in argtypes]
+        assert getattr(lib, name)(*args) == B.HH_ERR_ARG, name
+        assert lib.hh_last_error(None), name
+    lib.hh_destroy(None)  # a no-op
