@@ -175,14 +175,17 @@ def cpu_baseline(img, ph, boxes, seconds: float):
     t0 = time.perf_counter()
     O.solve_cg(med, O.unit_load(0), fixed_iters=iters)
     dt = time.perf_counter() - t0
+    nproc = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     try:
         from threadpoolctl import threadpool_info
-        cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
+        threads = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
     except Exception:
-        cores = os.cpu_count() or 1
-    return {"value": V * iters / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+        threads = nproc
+    return {"value": V * iters / dt, "unit": UNIT, "cores": int(min(threads, nproc)), "nproc": int(nproc),
+            "kind": "oracle",
             "sample": f"oracle CG, subimage {k} of the partition (Omega_B {tuple(int(v) for v in sub.shape)}, "
-                      f"{V} voxels), load case 11, {iters} iterations in {dt:.1f} s"}
+                      f"{V} voxels), load case 0 (unit E_11), {iters} iterations in {dt:.1f} s; numpy's "
+                      f"BLAS pool of {threads} threads on {nproc} host cores"}
 
 
 def tile_index(i: int, ws: int, rank: int, ntiles: int) -> int:

@@ -146,6 +146,16 @@ hh_status hh_create(hh_ctx **out, int device, void *cuda_stream);
 /* Free everything the context owns. NULL is allowed. */
 void hh_destroy(hh_ctx *ctx);
 
+/* Cap, in bytes, on the device workspace the context's solver calls hold
+ * (fields, spectra, work lists and per-subimage results; the FFT tables and
+ * the surrogate network's buffers are not counted). A call whose workspace
+ * would exceed the cap fails with HH_ERR_OOM before allocating and leaves the
+ * context usable; batched solves size their waves of subimages to 3/4 of the
+ * cap. Setting a cap releases the workspace the context holds (it is
+ * reallocated on demand). 0 (the default) = no cap. Errors: HH_ERR_ARG
+ * (bytes < 0), HH_ERR_CUDA. */
+hh_status hh_set_memory_limit(hh_ctx *ctx, int64_t bytes);
+
 /* Direct (brute-force) homogenization of a whole periodic image: the six load
  * cases of Section 4 on the full grid, averages over the whole grid, C =
  * Sigma Eps^-1 (Section 5: the reference M_N). `out` receives C, K, G. */
@@ -167,7 +177,8 @@ hh_status hh_homogenize_hierarchical(hh_ctx *ctx, const uint8_t *img, int nx, in
 
 /* Two-level scheme on an arbitrary partition. `boxes` holds nbox rows of 7
  * int32 (ox, oy, oz, cnx, cny, cnz, b): core origin, core size, buffer width.
- * Every core edge and origin must be a multiple of `unit`, and the cores must
+ * Every core edge and origin must be a multiple of `unit` (unit <= 0: the
+ * largest unit that divides every core origin and edge), and the cores must
  * tile a box-shaped region of the image (normally the whole image). The
  * coarse image covers that region with unit-size voxels, each subimage
  * filling its block; buffers always wrap periodically in the whole image.
@@ -306,12 +317,13 @@ hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, int e
  * corr[a][l] = (<M M_l> - <M>^2) / (<M^2> - <M>^2) with the pair average over
  * those pairs and <M> = <M^2> over all voxels, and xi[a] the least-squares
  * fit of exp(-l / xi) to corr[a][0..L], L the first l where corr < 0.05. The
- * paper takes subimages of at least 3 xi. Buffers counts[3][lmax+1],
- * corr[3][lmax+1], xi[3] are host memory owned by the caller. Errors:
- * HH_ERR_ARG (lmax outside 1..4096, pore_label outside 0..255, a dimension < 2),
- * HH_ERR_CUDA. */
+ * paper takes subimages of at least 3 xi (Section 2): *n_min (may be NULL)
+ * receives ceil(3 max_a xi[a]), the smallest cubic subimage edge by that
+ * rule. Buffers counts[3][lmax+1], corr[3][lmax+1], xi[3] are host memory
+ * owned by the caller. Errors: HH_ERR_ARG (lmax outside 1..4096, pore_label
+ * outside 0..255, a dimension < 2), HH_ERR_CUDA. */
 hh_status hh_correlation(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz, int img_on_device,
-                         int pore_label, int lmax, int64_t *counts, double *corr, double *xi);
+                         int pore_label, int lmax, int64_t *counts, double *corr, double *xi, int *n_min);
 
 /* Hierarchical homogenization over several levels (Section 3: the coarse
  * image is renormalised again until it is small). Level 1 cuts the image
@@ -368,20 +380,24 @@ hh_status hh_homogenize_partition_surrogate(hh_ctx *ctx, const uint8_t *img, int
  * real-time loops, hosts whose allocator must not be re-entered).
  *
  * q = G * (C : p) as hh_apply_operator computes it, in FP32, on device
- * buffers the caller owns: labels (uint8 [nz][ny][nx]), p and q (float
- * [6][nz][ny][nx], tensor components 11 22 33 23 13 12). `phases` is a host
- * table. Work is enqueued on `cuda_stream` (NULL = legacy default stream)
- * of the current device and the call waits for it before returning.
+ * buffers the caller owns: labels (uint8 [nz][ny][nx], every label < nphase:
+ * checked on the device before the operator runs, HH_ERR_ARG otherwise), p
+ * and q (float [6][nz][ny][nx], tensor components 11 22 33 23 13 12).
+ * `phases` is a host table. Work is enqueued on `cuda_stream` (NULL = legacy
+ * default stream) of the current device; the call synchronizes that stream
+ * twice (after the label check and at the end) before returning.
  *
  * It calls no cudaMalloc, cudaFree or other allocating routine. Its scratch
  * is one fixed device array of HH_NOALLOC_SCRATCH_BYTES inside the library,
  * held by every GPU that loads the library until the process exits; each
  * edge is limited to HH_NOALLOC_MAX_EDGE and the half spectrum must fit the
  * array, else HH_ERR_ARG. The first call on a device looks the array's
- * device address up (cudaGetSymbolAddress) with that device current: make
- * that first call before any stream capture. Every call shares the array
- * (nothing in it needs to start at zero: each call overwrites what it
- * reads), so calls that overlap on the GPU race; serialize them.
+ * device address up (cudaGetSymbolAddress) and raises the kernels'
+ * shared-memory limit, with that device current: make that first call
+ * before any stream capture. Every call shares the array and overwrites
+ * what it reads there (the label check's flag, the one value that must
+ * start at zero, is cleared by each call's copy of its tables), so calls
+ * that overlap on the GPU race; serialize them.
  * Errors: HH_ERR_ARG, HH_ERR_UNSUPPORTED, HH_ERR_CUDA; text via
  * hh_last_error(NULL). */
 #define HH_NOALLOC_SCRATCH_BYTES (16u << 20)

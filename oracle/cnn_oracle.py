@@ -174,6 +174,30 @@ def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
     return theta - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def cosine_step_size(lr, step, total_steps):
+    """Step size of update `step` (counted from 0) of a run of `total_steps`
+    updates: the base rate lr decayed along half a cosine period,
+    lr (1 + cos(pi step / total_steps)) / 2 (lr at the first update, lr / 2
+    half way, approaching 0 at the end)."""
+    return 0.5 * lr * (1.0 + np.cos(np.pi * step / total_steps))
+
+
+def train_full_batch(theta, labels_batch, targets, steps, lr):
+    """`steps` Adam updates, each on the gradient of the whole batch, with the
+    cosine step size: update t (from 0) uses cosine_step_size(lr, t, steps)
+    and Adam's bias correction at t + 1. Returns the final parameters and the
+    batch loss before each update."""
+    theta = np.asarray(theta, dtype=np.float64).copy()
+    m = np.zeros_like(theta)
+    v = np.zeros_like(theta)
+    losses = []
+    for t in range(steps):
+        loss, g, _ = batch_loss_and_grad(theta, labels_batch, targets)
+        losses.append(loss)
+        theta, m, v = adam_step(theta, g, m, v, t + 1, cosine_step_size(lr, t, steps))
+    return theta, np.array(losses)
+
+
 def init_params(uniform01: np.ndarray) -> np.ndarray:
     """He-uniform initial weights from uniform draws in [0, 1) (one per
     parameter, supplied by the caller's seeded generator); biases zero."""

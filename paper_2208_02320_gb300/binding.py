@@ -127,7 +127,8 @@ _SIGNATURES = {
     "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
     "hh_surrogate_save": (_I, [ctypes.c_char_p, _P, _I, _D]),
     "hh_surrogate_load": (_I, [ctypes.c_char_p, _P, ctypes.c_int64, _P, _P]),
-    "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "hh_set_memory_limit": (_I, [_P, ctypes.c_int64]),
     "hh_homogenize_multilevel": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _D,
                                                ctypes.c_uint64, _P, _P, _P, _P, _P]),
@@ -234,6 +235,10 @@ class Context:
         if s != HH_OK:
             raise HHError(s, "hh_create: " + self._lib.hh_last_error(None).decode())
 
+    def set_memory_limit(self, nbytes: int):
+        """Cap the context's device workspace (hh_set_memory_limit; 0 = none)."""
+        self._check(self._lib.hh_set_memory_limit(self._h, int(nbytes)), "hh_set_memory_limit", allow_warn=False)
+
     def close(self):
         if self._h:
             self._lib.hh_destroy(self._h)
@@ -283,7 +288,7 @@ class Context:
         d.update(C_boxes=Cb[:nbox], iters_boxes=It[:nbox])
         return d
 
-    def homogenize_partition(self, img, phases, boxes, unit: int, **opt) -> dict:
+    def homogenize_partition(self, img, phases, boxes, unit: int = 0, **opt) -> dict:
         p, dev, keep = _u8(img)
         nz, ny, nx = img.shape
         ph, nph = _phases(phases)
@@ -454,9 +459,11 @@ class Context:
         counts = np.zeros((3, lmax + 1), dtype=np.int64)
         corr = np.zeros((3, lmax + 1))
         xi = np.zeros(3)
+        n_min = ctypes.c_int()
         self._check(self._lib.hh_correlation(self._h, p, nx, ny, nz, dev, int(pore_label), int(lmax), _ptr(counts),
-                                             _ptr(corr), _ptr(xi)), "hh_correlation", allow_warn=False)
-        return dict(counts=counts, corr=corr, xi=xi, n_min=int(np.ceil(3.0 * xi.max())))
+                                             _ptr(corr), _ptr(xi), ctypes.byref(n_min)), "hh_correlation",
+                    allow_warn=False)
+        return dict(counts=counts, corr=corr, xi=xi, n_min=n_min.value)
 
     def homogenize_multilevel(self, img, phases, levels, **opt) -> dict:
         p, dev, keep = _u8(img)
@@ -484,7 +491,7 @@ class Context:
         th = np.ascontiguousarray(params_ensemble, dtype=np.float32)
         ens = th.shape[0] if th.ndim == 2 else 1
         if unit is None:
-            unit = int(np.gcd.reduce(bx[:, 3:6].ravel()))
+            unit = 0  # the library derives the coarse unit from the partition
         o = options(**opt)
         r = Result()
         nb = len(bx)

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -142,6 +143,7 @@ struct Ctx {
   };
   std::map<std::string, KStat> prof;
   std::map<long long, int> col_tune;  // autotuned column-pass width per (precision, shape)
+  size_t mem_limit = 0;               // cap on the workspace buffers (0: none)
 };
 
 #define HH_CK(call)                                                         \
@@ -157,10 +159,19 @@ struct Ctx {
 static hh_status ensure(Ctx& c, const char* name, size_t bytes, void** out) {
   DevBuf& b = c.bufs[name];
   if (b.n < bytes) {
+    size_t want = std::max<size_t>(bytes, 256);
+    if (c.mem_limit) {
+      size_t held = 0;
+      for (auto& kv : c.bufs) held += kv.second.n;
+      if (held - b.n + want > c.mem_limit) {
+        c.err = std::string("workspace '") + name + "' of " + std::to_string(want) + " bytes would exceed the " +
+                "context's device memory limit of " + std::to_string(c.mem_limit) + " bytes";
+        return HH_ERR_OOM;
+      }
+    }
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.n = 0;
-    size_t want = std::max<size_t>(bytes, 256);
     HH_CK(cudaMalloc(&b.p, want));
     b.n = want;
   }
@@ -407,6 +418,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     for (auto& kv : c.bufs) have += kv.second.n;
     budget = (size_t)((fr + have) * 0.75);
   }
+  if (c.mem_limit) budget = std::min(budget, c.mem_limit / 4 * 3);
 
   // shared memory: a whole plane per plane-pass block when it fits the plane
   // limit, else R rows per block and W kx columns per y-column block (row
@@ -1256,6 +1268,18 @@ extern "C" void hh_destroy(hh_ctx* h) {
   delete h;
 }
 
+extern "C" hh_status hh_set_memory_limit(hh_ctx* h, int64_t bytes) {
+  if (!h || bytes < 0) return fail(h, HH_ERR_ARG, "NULL context or negative limit");
+  Ctx& c = h->c;
+  HH_CK(cudaSetDevice(c.dev));
+  HH_CK(cudaStreamSynchronize(c.st));
+  for (auto& kv : c.bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  c.bufs.clear();
+  c.mem_limit = (size_t)bytes;
+  return HH_OK;
+}
+
 // Order the internal stream after the caller's stream (for device inputs),
 // and start the call's device timer.
 static thread_local long long g_launch0 = 0;
@@ -1539,6 +1563,15 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   return out->status;
 }
 
+// Largest cell edge that divides every core origin and edge (the coarse unit
+// when the caller passes none).
+static int derive_unit(const std::vector<BoxReq>& boxes) {
+  int g = 0;
+  for (const BoxReq& B : boxes)
+    for (int v : {B.ox, B.oy, B.oz, B.cnx, B.cny, B.cnz}) g = std::gcd(g, v);
+  return std::max(g, 1);
+}
+
 // The cores must tile their bounding box (in unit cells); reg receives the
 // box origin and extent in unit cells.
 static hh_status check_tiling(hh_ctx* h, const std::vector<BoxReq>& boxes, int unit, int nx, int ny, int nz, int* reg) {
@@ -1589,6 +1622,7 @@ extern "C" hh_status hh_homogenize_partition(hh_ctx* h, const uint8_t* img, int 
   if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
   std::vector<BoxReq> bx;
   if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
+  if (unit <= 0) unit = derive_unit(bx);
   int reg[6];
   if ((s = check_tiling(h, bx, unit, nx, ny, nz, reg)) != HH_OK) return s;
   if ((s = enter(h)) != HH_OK) return s;
@@ -1636,6 +1670,7 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
   if ((s = check_phases(h, phases, nphase, m)) != HH_OK) return s;
   std::vector<BoxReq> bx;
   if ((s = parse_boxes(h, boxes, nbox, nx, ny, nz, bx)) != HH_OK) return s;
+  if (unit <= 0) unit = derive_unit(bx);
   int reg[6];
   if ((s = check_tiling(h, bx, unit, nx, ny, nz, reg)) != HH_OK) return s;
   // candidates: unbuffered cubic subimages, grouped by edge
@@ -1751,7 +1786,7 @@ static double fit_xi(const double* corr, int n) {
 }
 
 extern "C" hh_status hh_correlation(hh_ctx* h, const uint8_t* img, int nx, int ny, int nz, int on_dev, int pore_label,
-                                    int lmax, int64_t* counts, double* corr, double* xi) {
+                                    int lmax, int64_t* counts, double* corr, double* xi, int* n_min) {
   if (!h || !counts || !corr || !xi || lmax < 1 || lmax > 4096 || pore_label < 0 || pore_label > 255)
     return fail(h, HH_ERR_ARG, "NULL output, lmax outside 1..4096 or pore label outside 0..255");
   if (nx < 2 || ny < 2 || nz < 2) return fail(h, HH_ERR_ARG, "dims must be >= 2");
@@ -1792,6 +1827,8 @@ extern "C" hh_status hh_correlation(hh_ctx* h, const uint8_t* img, int nx, int n
     }
     xi[a] = (m > 0.0 && m < 1.0) ? fit_xi(corr + a * (lmax + 1), nl) : 0.0;
   }
+  // Section 2: subimages of at least three correlation lengths
+  if (n_min) n_min[0] = (int)std::ceil(3.0 * std::max(xi[0], std::max(xi[1], xi[2])));
   return HH_OK;
 }
 
@@ -2161,6 +2198,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 // device current) by the first call made on it.
 constexpr int kNoAllocMaxDevices = 64;
 static void* g_noalloc_addr[kNoAllocMaxDevices];
+static int g_noalloc_optin[kNoAllocMaxDevices];
 static std::mutex g_noalloc_mu;
 
 static size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
@@ -2196,8 +2234,14 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
     set_last_error("hh_apply_operator_noalloc: no usable current device");
     return HH_ERR_CUDA;
   }
+  auto* kf = k_plane_fwd<float, MODE_APPLY>;
+  auto* ki = k_plane_inv<float, MODE_APPLY>;
+  auto* kc = k_column<float, false>;
   void* base = nullptr;
+  int smem_optin = 0;
   {
+    // once per device, with that device current: the scratch array's device
+    // address, and the kernels' shared-memory limit raised to the device's
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
       void* a = nullptr;
@@ -2206,18 +2250,23 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
         set_last_error("hh_apply_operator_noalloc: cudaGetSymbolAddress failed");
         return HH_ERR_CUDA;
       }
+      int optin = 0;
+      if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+          cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess ||
+          cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) != cudaSuccess) {
+        set_last_error("hh_apply_operator_noalloc: device query or kernel attribute failed");
+        return HH_ERR_CUDA;
+      }
+      g_noalloc_optin[dev] = optin;
       g_noalloc_addr[dev] = a;
     }
     base = g_noalloc_addr[dev];
+    smem_optin = g_noalloc_optin[dev];
   }
 
-  // host staging of the small tables, on the stack (no allocation)
+  // host staging of the small tables in static storage (no allocation)
   const int nxh = nx / 2 + 1;
-  int smem_optin = 0;
-  if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
-    set_last_error("hh_apply_operator_noalloc: device query failed");
-    return HH_ERR_CUDA;
-  }
   const int colw = column_width<float>(nz, ny, (size_t)smem_optin);
   const size_t psm = plane_smem_bytes<float>(nx, ny, nphase);
   const size_t csm = column_smem_bytes<float>(colw, nz, ny);
@@ -2227,6 +2276,8 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
   }
   const int ncol = (ny * nxh + colw - 1) / colw;
   struct Staging {
+    int bad_label;  // set on the device by the label check; 0 in every staged copy
+    int pad_[3];
     Prob prob;
     AxisPlan plans[3];
     double tw[2 * 3 * HH_NOALLOC_MAX_EDGE];
@@ -2235,6 +2286,7 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
     int2 items[HH_NOALLOC_MAX_EDGE + HH_NOALLOC_MAX_EDGE * (HH_NOALLOC_MAX_EDGE / 2 + 1)];
   };
   static thread_local Staging h;  // static storage: no heap or stack growth per call
+  h.bad_label = 0;
   std::memset(&h.prob, 0, sizeof(h.prob));
   const int dims[3] = {nx, ny, nz};
   int tw_off = 0, it_off = 0;
@@ -2303,22 +2355,29 @@ extern "C" hh_status hh_apply_operator_noalloc(const uint8_t* labels, const hh_p
   kpp.nitems = nz;
   kpc.items = dst->items + nz;
   kpc.nitems = nc;
-  auto* kf = k_plane_fwd<float, MODE_APPLY>;
-  auto* ki = k_plane_inv<float, MODE_APPLY>;
-  auto* kc = k_column<float, false>;
-  if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
-      cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
-      cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm) != cudaSuccess) {
-    set_last_error("hh_apply_operator_noalloc: kernel attribute failed");
-    return HH_ERR_CUDA;
-  }
   int nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   nsm = std::max(nsm, 1);
+  // every label must index the phase table before the plane pass reads it
+  const long long V = (long long)nx * ny * nz;
+  int bad = 0;
+  k_check_labels<<<(int)std::min<long long>(4LL * nsm, (V + 255) / 256), 256, 0, st>>>(
+      labels, V, nphase, const_cast<int*>(&dst->bad_label));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, &dst->bad_label, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return HH_ERR_CUDA;
+  }
+  if (bad) {
+    set_last_error("hh_apply_operator_noalloc: a label is >= nphase");
+    return HH_ERR_ARG;
+  }
   kf<<<std::min(nz, 4 * nsm), 256, psm, st>>>(kpp);
   kc<<<std::min(nc, 4 * nsm), 256, csm, st>>>(kpc, MODE_APPLY);
   ki<<<std::min(nz, 4 * nsm), 256, psm, st>>>(kpp);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));

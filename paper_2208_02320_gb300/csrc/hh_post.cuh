@@ -54,6 +54,13 @@ __global__ void k_gather(const uint8_t* img, int Nx, int Ny, int Nz, const BoxRe
   }
 }
 
+// Sets *bad when any of the n labels is >= nphase (the phase table of the
+// plane passes has nphase entries).
+__global__ void k_check_labels(const uint8_t* lab, long long n, int nphase, int* bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (lab[i] >= nphase) atomicOr(bad, 1);
+}
+
 // Gauss-Jordan inverse with partial pivoting of a 6x6 row-major matrix.
 __device__ inline bool inv6(const double* A, double* X) {
   double M[6][12];

@@ -89,6 +89,48 @@ def test_adam_first_step_closed_form():
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
 
 
+def test_adam_second_step_written_out():
+    # two steps with gradients g1, g2: m2 = 0.09 g1 + 0.1 g2, v2 = 0.000999 g1^2
+    # + 0.001 g2^2, bias corrections 1 - 0.9^2 = 0.19 and 1 - 0.999^2 = 0.001999
+    theta = RNG.standard_normal(7)
+    g1, g2 = RNG.standard_normal(7), RNG.standard_normal(7)
+    t1, m, v = N.adam_step(theta, g1, np.zeros(7), np.zeros(7), 1, lr=3e-3)
+    t2, m, v = N.adam_step(t1, g2, m, v, 2, lr=2e-3)
+    m2 = 0.09 * g1 + 0.1 * g2
+    v2 = 0.000999 * g1 * g1 + 0.001 * g2 * g2
+    step2 = 2e-3 * (m2 / 0.19) / (np.sqrt(v2 / 0.001999) + 1e-8)
+    assert np.allclose(t2, t1 - step2, rtol=0, atol=1e-15)
+
+
+def test_cosine_step_size_special_values():
+    lr, T = 0.02, 40
+    assert N.cosine_step_size(lr, 0, T) == lr
+    assert abs(N.cosine_step_size(lr, T // 2, T) - lr / 2) < 1e-18
+    assert abs(N.cosine_step_size(lr, T, T)) < 1e-18
+    s = np.array([N.cosine_step_size(lr, t, T) for t in range(T + 1)])
+    # half a cosine period: decreasing, and symmetric about the midpoint
+    assert np.all(np.diff(s) < 0)
+    assert np.allclose(s + s[::-1], lr, rtol=0, atol=1e-17)
+
+
+def test_train_full_batch_first_update_is_the_closed_form_step():
+    theta = init_small()
+    labels = RNG.integers(0, 3, size=(2, 4, 4, 4)).astype(np.uint8)
+    targets = RNG.standard_normal((2, N.NOUT))
+    new, losses = N.train_full_batch(theta, labels, targets, 1, 1e-3)
+    loss, g, _ = N.batch_loss_and_grad(theta, labels, targets)
+    # one update at the full step size: lr g / (|g| + 1e-8) per parameter
+    assert losses[0] == loss
+    assert np.allclose(new, theta - 1e-3 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
+    # and the loss falls over a few updates on a fixed batch
+    _, losses = N.train_full_batch(theta, labels, targets, 6, 1e-2)
+    assert losses[-1] < losses[0]
+
+
+def init_small():
+    return N.init_params(np.random.default_rng(5).random(N.n_params()))
+
+
 def test_init_params_bounds():
     theta = N.init_params(RNG.random(N.n_params()))
     p = N.unflatten(theta)

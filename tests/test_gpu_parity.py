@@ -263,6 +263,45 @@ def test_grf32_fixed_iteration_parity(ctx):
         assert rel(gs["C"][k], r["C"]) < 1e-5
 
 
+@pytest.fixture(scope="module")
+def grf32_oracle():
+    """The oracle's converged two-level run of the 32^3 workload (about 30 s)."""
+    w = synth.workload("grf32")
+    return w, O.homogenize_hierarchical(w["image"], w["phases"], w["boxes"], unit=8, tol=1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_grf32_converged_hierarchical_against_oracle(ctx, grf32_oracle, precision):
+    """The 32^3 two-phase workload (correlation length 4, porosity 0.20,
+    contrast 4.4e5) solved end to end to tol 1e-6: 64 cores of 8^3 without
+    buffer, their C_R, the 4^3 intermediate image and its level-2 solve, the
+    moduli and the arithmetic means, against the oracle's run at the same tol.
+    FP64 takes the oracle's iteration counts and agrees to 1e-9. FP32 cannot
+    reach 1e-6 at this contrast on every load case (the true residual stalls
+    near 1e-5 and the solve ends with the not-converged warning), so its error
+    is reported per result and held to 5e-4 on C (a tenth of the 0.5 %
+    accuracy criterion of the benchmark) and 1e-4 on K, G, K_am, G_am."""
+    w, ref = grf32_oracle
+    got = ctx.homogenize_partition(w["image"], w["phases"], w["boxes"], unit=8, precision=precision, tol=1e-6)
+    ref_boxes = np.array([r["C"] for r in ref["per_box"]])
+    ref_iters = np.array([r["iters"] for r in ref["per_box"]])
+    errs = {"C_boxes": rel(got["C_boxes"], ref_boxes), "C_sym": rel(got["C_sym"], ref["C_sym"])}
+    for k in ("K", "G", "K_am", "G_am"):
+        errs[k] = abs(got[k] - ref[k]) / ref[k]
+    msg = (f"{precision}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()) +
+           f"; status {got['status']}, resid_max {got['resid_max']:.2e}, K {got['K']:.6f} vs {ref['K']:.6f}, "
+           f"G {got['G']:.6f} vs {ref['G']:.6f}")
+    print(msg)
+    if precision == "fp64":
+        assert got["status"] == 0, msg
+        assert np.array_equal(got["iters_boxes"], ref_iters), msg
+        assert max(errs.values()) < 1e-9, msg
+    else:
+        assert got["status"] in (0, 1), msg
+        assert errs["C_boxes"] < 5e-4 and errs["C_sym"] < 5e-4, msg
+        assert max(errs[k] for k in ("K", "G", "K_am", "G_am")) < 1e-4, msg
+
+
 # ---------------------------------------------------------- A11-A12 ---------
 
 def test_fit_inverse_n_parity(ctx, golden_dir):
@@ -315,6 +354,57 @@ def test_error_paths(ctx):
     lab = synth.grf_two_phase(n=8, ell=2.0, seed=2)
     r = ctx.homogenize_direct(lab, synth.PHASES_SOLID_PORE, max_iter=3)
     assert r["status"] == B.HH_WARN_NOT_CONVERGED and r["iters_max"] == 3
+
+
+def test_nonfinite_solver_values_are_reported(ctx):
+    """Moduli that are finite in FP64 but whose stresses overflow FP32 make the
+    FP32 transforms non-finite: the solve reports HH_ERR_NONFINITE. The same
+    image in FP64 solves."""
+    from paper_2208_02320_gb300 import HHError
+    from paper_2208_02320_gb300 import binding as B
+    lab = synth.grf_two_phase(n=8, ell=2.0, seed=2)
+    huge = [[1e38, 1e38], [1e37, 1e37]]
+    with pytest.raises(HHError) as e:
+        ctx.homogenize_direct(lab, huge, precision="fp32")
+    assert e.value.status == B.HH_ERR_NONFINITE
+    r = ctx.homogenize_direct(lab, huge, precision="fp64", tol=1e-8)
+    assert r["status"] == B.HH_OK and np.isfinite(r["K"])
+
+
+def test_memory_limit_gives_out_of_memory(ctx):
+    """A device memory cap below what a call needs fails it with HH_ERR_OOM
+    before any allocation; the context stays usable, a cap that fits lets the
+    call run (in smaller waves of subimages), and removing the cap restores
+    the uncapped result."""
+    from paper_2208_02320_gb300 import HHError
+    from paper_2208_02320_gb300 import binding as B
+    img = synth.grf_two_phase(n=24, ell=3.0, porosity=0.3, seed=31)
+    ph = synth.PHASES_APPENDIX_B
+    ref = ctx.homogenize_hierarchical(img, ph, 6, 1, precision="fp64", tol=1e-10)
+    try:
+        ctx.set_memory_limit(1 << 20)
+        with pytest.raises(HHError) as e:
+            ctx.homogenize_direct(img, ph, precision="fp64")
+        assert e.value.status == B.HH_ERR_OOM
+        assert b"memory limit" in ctx.raw()[0].hh_last_error(ctx.raw()[1])
+        ctx.set_memory_limit(64 << 20)
+        got = ctx.homogenize_hierarchical(img, ph, 6, 1, precision="fp64", tol=1e-10)
+        assert rel(got["C_sym"], ref["C_sym"]) < 1e-12
+    finally:
+        ctx.set_memory_limit(0)
+    got = ctx.homogenize_hierarchical(img, ph, 6, 1, precision="fp64", tol=1e-10)
+    assert rel(got["C_sym"], ref["C_sym"]) < 1e-12
+
+
+def test_partition_derives_its_coarse_unit(ctx):
+    """unit <= 0: the library takes the largest unit dividing every core
+    origin and edge (here 4); the result equals the call with unit 4."""
+    img = synth.grf_two_phase(n=24, ell=3.0, porosity=0.3, seed=13)
+    ph = synth.PHASES_APPENDIX_B
+    boxes = synth.uneven_partition(N=24, counts=((4, 2), (8, 2)), bmax=3, seed=14)
+    a = ctx.homogenize_partition(img, ph, boxes, unit=0, precision="fp64", tol=1e-11)
+    b = ctx.homogenize_partition(img, ph, boxes, unit=4, precision="fp64", tol=1e-11)
+    assert np.array_equal(a["C_sym"], b["C_sym"])
 
 
 # ----------------------------------------------- A5-alt basic scheme -------
@@ -459,6 +549,10 @@ def test_correlation_parity(ctx, shape, lmax):
     assert np.array_equal(got["counts"], ref_counts)  # integer pair counts, bit-exact
     ref_corr = O.correlation_function(img, 2, lmax)
     assert np.abs(got["corr"] - ref_corr).max() < 1e-12
+    xis = []
     for a in range(3):
         xi = O.fit_correlation_length(ref_corr[a, :min(lmax, img.shape[2 - a] - 1) + 1])
         assert abs(got["xi"][a] - xi) <= 1e-6 * xi
+        xis.append(xi)
+    # Section 2: subimages of at least three correlation lengths
+    assert got["n_min"] == int(np.ceil(3.0 * max(xis)))

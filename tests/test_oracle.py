@@ -196,6 +196,87 @@ def test_basic_scheme_reaches_the_cg_solution():
     assert np.abs(xb - xc).max() < 1e-8 * np.abs(xc).max()
 
 
+# ------------------------------------------ Green operator of the basic scheme
+# The basic scheme's Gamma0 is the Green operator of an isotropic reference
+# medium C0 = (lam0, mu0). Per mode with unit wave vector n it is fixed by
+# three facts that do not depend on how it is written out: it inverts C0 on
+# compatible strains (Gamma0 : C0 : sym(a (x) n) = sym(a (x) n)), it vanishes
+# on equilibrated polarizations (tau n = 0), and Gamma0 C0 Gamma0 = Gamma0.
+# The reference medium below has mu0 != 1 and lam0 != mu0, so a dropped or
+# misplaced factor of mu0 or (lam0 + 2 mu0) changes the result.
+
+LAM0, MU0 = 5.3, 3.7
+
+
+def _hooke0(e6, lam0=LAM0, mu0=MU0):
+    """Isotropic Hooke's law of the reference medium on six stored components."""
+    tr = e6[0] + e6[1] + e6[2]
+    s = 2.0 * mu0 * e6
+    s[0:3] = s[0:3] + lam0 * tr
+    return s
+
+
+def _sym_outer(a, n):
+    """Six stored components of sym(a (x) n) per mode (a, n shaped (3, ...))."""
+    return np.stack([0.5 * (a[i] * n[j] + a[j] * n[i]) for (i, j) in O.PAIRS])
+
+
+def _unit(xi):
+    norm = np.sqrt(np.sum(xi * xi, axis=0))
+    return xi / np.where(norm > 0, norm, 1.0)
+
+
+def _rand_c(shape):
+    return RNG.standard_normal(shape) + 1j * RNG.standard_normal(shape)
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 7), (4, 4, 6)])
+def test_gamma0_inverts_the_reference_medium_on_compatible_strains(shape):
+    xi, zero = O.wave_vectors(shape)
+    eps = _sym_outer(_rand_c((3,) + shape), _unit(xi))
+    got = O.gamma0_apply(_hooke0(eps), xi, zero, LAM0, MU0)
+    eps[:, zero] = 0.0
+    assert np.abs(got - eps).max() < 1e-12 * np.abs(eps).max()
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 7), (4, 4, 6)])
+def test_gamma0_vanishes_on_equilibrated_polarizations(shape):
+    xi, zero = O.wave_vectors(shape)
+    n = _unit(xi)
+    # t1, t2: an orthonormal pair perpendicular to n (through the coordinate
+    # axis least aligned with n); tau built from them has tau n = 0
+    e = np.zeros_like(n)
+    ax = np.argmin(np.abs(n), axis=0)
+    for i in range(3):
+        e[i] = (ax == i)
+    t1 = np.cross(n, e, axis=0)
+    t1 = t1 / np.where(np.linalg.norm(t1, axis=0) > 0, np.linalg.norm(t1, axis=0), 1.0)
+    t2 = np.cross(n, t1, axis=0)
+    c = _rand_c((3,) + shape)
+    tau = c[0] * _sym_outer(t1, t1) + c[1] * _sym_outer(t1, t2) + c[2] * _sym_outer(t2, t2)
+    tau[:, zero] = 0.0
+    assert np.abs(np.einsum("ij...,j...->i...", O.to_full(tau), n)).max() < 1e-12 * np.abs(tau).max()
+    got = O.gamma0_apply(tau, xi, zero, LAM0, MU0)
+    assert np.abs(got).max() < 1e-12 * np.abs(tau).max()
+
+
+@pytest.mark.parametrize("rule", ["component", "mode"])
+def test_gamma0_is_a_projection_in_the_reference_metric(rule):
+    shape = (4, 5, 6)
+    xi, zero = O.wave_vectors(shape, rule)
+    tau = _rand_c((6,) + shape)
+    g = O.gamma0_apply(tau, xi, zero, LAM0, MU0)
+    gg = O.gamma0_apply(_hooke0(g), xi, zero, LAM0, MU0)
+    assert np.abs(gg - g).max() < 1e-12 * np.abs(g).max()
+    # symmetric in the Frobenius product, mode by mode
+    sig = _rand_c((6,) + shape)
+    w = O.FROB_W[:, None, None, None]
+    lhs = np.sum(w * sig * g, axis=0)
+    rhs = np.sum(w * O.gamma0_apply(sig, xi, zero, LAM0, MU0) * tau, axis=0)
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(lhs).max()
+    assert np.all(g[:, zero] == 0.0)
+
+
 # --------------------------------------------------------- closed forms ----
 
 def test_homogeneous_isotropic_returns_phase_moduli_exactly():
@@ -546,6 +627,36 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     monkeypatch.setattr(O, "FROB_W", np.array([1.0, 1, 1, 1, 1, 1]))
     with pytest.raises(AssertionError):
         test_homogeneous_isotropic_returns_phase_moduli_exactly()
+    monkeypatch.setattr(O, "FROB_W", np.array([1.0, 1, 1, 2, 2, 2]))
+
+    # 6, 7. Green operator of the basic scheme with a wrong factor: the n n
+    #    coefficient (lam0 + mu0) / (lam0 + 2 mu0) without its 1 / mu0, and
+    #    the symmetric part without its 1 / (2 mu0)
+    good_g0 = O.gamma0_apply
+
+    def g0_with(ca, cb):
+        def g0(tau_hat, xi, zero, lam0, mu0):
+            n = _unit(xi)
+            v = np.einsum("ij...,j...->i...", O.to_full(tau_hat), n)
+            s = np.einsum("i...,i...->...", n, v)
+            out = (ca(lam0, mu0) * (np.einsum("i...,j...->ij...", n, v) + np.einsum("i...,j...->ij...", v, n))
+                   - cb(lam0, mu0) * np.einsum("i...,j...->ij...", n, n) * s)
+            o6 = O.from_full(out)
+            o6[:, zero] = 0.0
+            return o6
+        return g0
+
+    g0_factor = g0_with(lambda l, m: 1.0 / (2.0 * m), lambda l, m: (l + m) / (l + 2.0 * m))
+    g0_half = g0_with(lambda l, m: 1.0, lambda l, m: (l + m) / (m * (l + 2.0 * m)))
+    # the same helper with the right coefficients passes
+    monkeypatch.setattr(O, "gamma0_apply", g0_with(lambda l, m: 1.0 / (2.0 * m),
+                                                   lambda l, m: (l + m) / (m * (l + 2.0 * m))))
+    test_gamma0_inverts_the_reference_medium_on_compatible_strains((5, 6, 7))
+    for bad in (g0_factor, g0_half):
+        monkeypatch.setattr(O, "gamma0_apply", bad)
+        with pytest.raises(AssertionError):
+            test_gamma0_inverts_the_reference_medium_on_compatible_strains((5, 6, 7))
+    monkeypatch.setattr(O, "gamma0_apply", good_g0)
 
 
 # ------------------------------------------------- multi-level renormalisation

@@ -75,3 +75,29 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                       binding.HH_NYQ_ZERO_COMPONENT, None)
     assert s == binding.HH_ERR_ARG
     assert b"HH_NOALLOC_MAX_EDGE" in lib.hh_last_error(None)
+
+
+def test_noalloc_rejects_a_label_outside_the_phase_table():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("a GPU test ran without a CUDA device")
+    from paper_2208_02320_gb300 import binding
+    lib = binding.load()
+    phases, nph = binding._phases(PH)
+    shape = (8, 8, 8)
+    lab = torch.zeros(shape, dtype=torch.uint8, device="cuda")
+    lab[3, 4, 5] = nph  # one past the table
+    p = torch.zeros((6,) + shape, dtype=torch.float32, device="cuda")
+    q = torch.zeros_like(p)
+    stream = torch.cuda.current_stream()
+    s = lib.hh_apply_operator_noalloc(ctypes.c_void_p(lab.data_ptr()), phases, nph, 8, 8, 8,
+                                      ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                      binding.HH_NYQ_ZERO_COMPONENT, ctypes.c_void_p(stream.cuda_stream))
+    assert s == binding.HH_ERR_ARG
+    assert b"label" in lib.hh_last_error(None)
+    # the flag does not stick: a valid call right after succeeds
+    lab[3, 4, 5] = nph - 1
+    s = lib.hh_apply_operator_noalloc(ctypes.c_void_p(lab.data_ptr()), phases, nph, 8, 8, 8,
+                                      ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(q.data_ptr()),
+                                      binding.HH_NYQ_ZERO_COMPONENT, ctypes.c_void_p(stream.cuda_stream))
+    assert s == binding.HH_OK, lib.hh_last_error(None)
