@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--fp64-compare", type=int, default=0,
                     help="also solve the first N rows of the last timed tile in FP64 (plain CG, no residual "
                          "replacement) and report time and K, G differences")
+    ap.add_argument("--headline-rows", type=int, default=6,
+                    help="y-rows of the last timed tile on which the plain FP64 solver (one subimage at a time) "
+                         "and the batched FP32 solver are timed against each other (0: skip)")
     return ap.parse_args()
 
 
@@ -367,7 +370,57 @@ def run_gb300(args):
             "iters_max": [r32["iters_max"], r64["iters_max"]]}
     if args.cost_scaling and ws == 1:
         line["cost_scaling"] = cost_scaling(ctx, img, ph, args.tol)
+    if args.headline_rows > 0 and ws == 1:
+        sl = slabs[tile_index(args.warmup + args.steps - 1, ws, rank, len(slabs))]
+        ys = np.unique(sl[:, 1])[:args.headline_rows]
+        line["headline"] = headline(ctx, dimg, ph, sl[np.isin(sl[:, 1], ys)], args.tol, len(slabs))
     print(json.dumps(line))
+
+
+def headline(ctx, dimg, ph, cores, tol, ntiles):
+    """The same cores homogenized (level 1, assembly, level 2) by the plain
+    FP64 solver -- FP64 fields, one subimage per wave of launches, no
+    surrogate -- and by the batched FP32 solver, with wall times (host clock
+    around each synchronous call) and the FP32 result's error against FP64:
+    relative K and G of the two-level result, and of every subimage's C_R
+    (isotropic Voigt projection of its symmetric part)."""
+    import numpy as np
+    import torch
+
+    def run(**o):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = ctx.homogenize_partition(dimg, ph, cores, unit=8, tol=tol, **o)
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    r64, t64 = run(precision="fp64", wave_boxes=1)
+    r32, t32 = run(precision="fp32")
+
+    def kg(C):
+        S = 0.5 * (C + np.swapaxes(C, -1, -2))
+        d = S[..., 0, 0] + S[..., 1, 1] + S[..., 2, 2]
+        o = S[..., 0, 1] + S[..., 0, 2] + S[..., 1, 2]
+        sh = S[..., 3, 3] + S[..., 4, 4] + S[..., 5, 5]
+        return (d + 2 * o) / 9.0, (d - o + 3 * sh) / 15.0
+
+    K32, G32 = kg(r32["C_boxes"])
+    K64, G64 = kg(r64["C_boxes"])
+    eb = np.maximum(np.abs(K32 - K64) / K64, np.abs(G32 - G64) / G64)
+    return {
+        "cores": int(len(cores)), "tol": tol,
+        "plain_fp64": {"wall_s": t64, "device_ms": r64["device_ms"], "launches": r64["kernel_launches"],
+                       "iters_max": r64["iters_max"], "status": r64["status"], "K": r64["K"], "G": r64["G"]},
+        "fp32_batched": {"wall_s": t32, "device_ms": r32["device_ms"], "launches": r32["kernel_launches"],
+                         "iters_max": r32["iters_max"], "status": r32["status"], "K": r32["K"], "G": r32["G"]},
+        "speedup_vs_plain_fp64": t64 / t32,
+        "K_rel_err": abs(r32["K"] - r64["K"]) / r64["K"], "G_rel_err": abs(r32["G"] - r64["G"]) / r64["G"],
+        "subimage_KG_rel_err": {"max": float(eb.max()), "median": float(np.median(eb)),
+                                "p99": float(np.quantile(eb, 0.99))},
+        "whole_image_estimate_s": {"plain_fp64": t64 * ntiles * 180 / len(cores),
+                                   "fp32_batched": t32 * ntiles * 180 / len(cores),
+                                   "note": "per-tile wall time x tiles in the 512^3 image (one tile measured)"},
+    }
 
 
 def cost_scaling(ctx, img, ph, tol):

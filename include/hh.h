@@ -95,6 +95,10 @@ typedef struct {
                              block) is chosen per subimage shape by timing the
                              candidates once per context; 0: a fixed rule. The width
                              changes no result, only the speed */
+    int wave_boxes;       /* > 0: at most this many subimages are solved together (one
+                             wave of launches); 1 solves the subimages one at a time,
+                             the plain unbatched solver. 0 (default): as many as the
+                             workspace budget allows. Changes no result */
 } hh_options;
 
 typedef struct {

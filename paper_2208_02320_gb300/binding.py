@@ -48,6 +48,7 @@ class Options(ctypes.Structure):
         ("profile", ctypes.c_int),
         ("plane_smem_limit", ctypes.c_int),
         ("autotune", ctypes.c_int),
+        ("wave_boxes", ctypes.c_int),
     ]
 
 

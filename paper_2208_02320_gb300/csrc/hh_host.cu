@@ -515,7 +515,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     // ---- choose the wave [b0, b1)
     int b1 = b0;
     size_t used = 0;
-    while (b1 < nbox && (b1 == b0 || used + box_bytes(b1) <= budget)) used += box_bytes(b1++);
+    while (b1 < nbox && (b1 == b0 || (used + box_bytes(b1) <= budget && (o.wave_boxes <= 0 || b1 - b0 < o.wave_boxes))))
+      used += box_bytes(b1++);
     const int nb = b1 - b0;
     const int np = 6 * nb;
     std::vector<Prob> probs(np);
@@ -1326,8 +1327,8 @@ static hh_status check_opts(hh_ctx* h, const hh_options* o) {
   if (o->max_iter < 1 || o->fixed_iters < 0) return fail(h, HH_ERR_ARG, "bad iteration limits");
   if (o->nyquist != HH_NYQ_ZERO_COMPONENT && o->nyquist != HH_NYQ_ZERO_MODE) return fail(h, HH_ERR_ARG, "bad nyquist");
   if (o->scheme != HH_CG && o->scheme != HH_BASIC) return fail(h, HH_ERR_ARG, "bad scheme");
-  if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1)
-    return fail(h, HH_ERR_ARG, "bad check_every, replace or max_restarts");
+  if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1 || o->wave_boxes < 0)
+    return fail(h, HH_ERR_ARG, "bad check_every, replace, max_restarts or wave_boxes");
   return HH_OK;
 }
 

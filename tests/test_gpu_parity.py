@@ -396,6 +396,19 @@ def test_memory_limit_gives_out_of_memory(ctx):
     assert rel(got["C_sym"], ref["C_sym"]) < 1e-12
 
 
+def test_unbatched_waves_change_no_result(ctx):
+    """wave_boxes = 1 (the plain solver: one subimage per wave of launches)
+    gives the batched solver's result."""
+    img = synth.grf_two_phase(n=24, ell=3.0, porosity=0.3, seed=13)
+    ph = synth.PHASES_APPENDIX_B
+    boxes = synth.uneven_partition(N=24, counts=((4, 2), (8, 2)), bmax=3, seed=14)
+    a = ctx.homogenize_partition(img, ph, boxes, unit=4, precision="fp64", tol=1e-10, wave_boxes=1)
+    b = ctx.homogenize_partition(img, ph, boxes, unit=4, precision="fp64", tol=1e-10)
+    assert np.array_equal(a["iters_boxes"], b["iters_boxes"])
+    assert rel(a["C_boxes"], b["C_boxes"]) < 1e-13 and rel(a["C_sym"], b["C_sym"]) < 1e-13
+    assert a["kernel_launches"] > b["kernel_launches"]
+
+
 def test_partition_derives_its_coarse_unit(ctx):
     """unit <= 0: the library takes the largest unit dividing every core
     origin and edge (here 4); the result equals the call with unit 4."""
