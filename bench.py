@@ -141,7 +141,7 @@ def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in ("hh_device.cuh", "hh_fftcore.cuh", "hh_fft2.cuh", "hh_fft2_inst.cu", "hh_ctmath.h", "hh_post.cuh",
-              "hh_host.cu"):
+              "hh_fused.cuh", "hh_host.cu"):
         with open(os.path.join(ROOT, "paper_2208_02320_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -394,7 +394,7 @@ def headline(ctx, dimg, ph, cores, tol, ntiles):
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
-    r64, t64 = run(precision="fp64", wave_boxes=1)
+    r64, t64 = run(precision="fp64", wave_boxes=1, fused=0)
     r32, t32 = run(precision="fp32")
 
     def kg(C):

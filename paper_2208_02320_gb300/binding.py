@@ -49,6 +49,7 @@ class Options(ctypes.Structure):
         ("plane_smem_limit", ctypes.c_int),
         ("autotune", ctypes.c_int),
         ("wave_boxes", ctypes.c_int),
+        ("fused", ctypes.c_int),
     ]
 
 

@@ -56,6 +56,7 @@ struct Prob {
   int npi;                           // field-pass items: nz, or nz * row chunks when streaming
   int rows;                          // rows per row-streaming item; 0: whole planes
   int cw;                            // spectrum columns (ky, kx) per column-pass item
+  int fused;                         // 1: solved whole by the fused cluster kernel (hh_fused.cuh)
   long long med_off;                 // iso: byte offset of labels; aniso: element offset of C21
   long long fld_off;                 // element offset of r, p, q (6 V each)
   long long spc_off;                 // complex offset of the spectrum (6 nz ny nxh)
@@ -1242,7 +1243,7 @@ __device__ __forceinline__ double sum_parts(const double* part, const Prob& d, i
 
 __global__ void k_scal_init(const Prob* prob, PState* st, const double* part, int nprob, double floor2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nprob) return;
+  if (i >= nprob || prob[i].fused) return;
   const Prob d = prob[i];
   PState s;
   const double tt = sum_parts(part, d, 0);
@@ -1384,9 +1385,9 @@ __global__ void k_scal_clear(PState* st, int nprob) {
 
 // which = 0: flag the active problems (residual replacement);
 // which = 1: flag every problem that iterated and is finite (final check).
-__global__ void k_mark_true(PState* st, int nprob, int which) {
+__global__ void k_mark_true(const Prob* prob, PState* st, int nprob, int which) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nprob) return;
+  if (i >= nprob || prob[i].fused) return;
   PState& s = st[i];
   s.trueflag = which == 0 ? s.active : ((!s.homog && s.status != ST_NONFINITE) ? 1 : 0);
 }
@@ -1462,7 +1463,7 @@ __global__ void k_scal_true_final(const Prob* prob, PState* st, const double* pa
 
 __global__ void k_scal_avg(const Prob* prob, PState* st, const double* part, int nprob) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nprob) return;
+  if (i >= nprob || prob[i].fused) return;
   const Prob d = prob[i];
   PState& s = st[i];
   // k_avg leaves one row of partials per (problem, z) item

@@ -15,6 +15,7 @@
 
 #include "hh.h"
 #include "hh_device.cuh"
+#include "hh_fused.cuh"
 #include "hh_post.cuh"
 #include "hh_internal.h"
 
@@ -144,6 +145,7 @@ struct Ctx {
   std::map<std::string, KStat> prof;
   std::map<long long, int> col_tune;  // autotuned column-pass width per (precision, shape)
   size_t mem_limit = 0;               // cap on the workspace buffers (0: none)
+  std::map<long long, int> fused_occ; // resident clusters per (precision, cluster size, shared memory)
 };
 
 #define HH_CK(call)                                                         \
@@ -158,7 +160,7 @@ struct Ctx {
 
 static hh_status ensure(Ctx& c, const char* name, size_t bytes, void** out) {
   DevBuf& b = c.bufs[name];
-  if (b.n < bytes) {
+  if (b.n < bytes || !b.p) {
     size_t want = std::max<size_t>(bytes, 256);
     if (c.mem_limit) {
       size_t held = 0;
@@ -376,6 +378,124 @@ static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool
   return best;
 }
 
+// Cluster shape of the fused solver for one subimage: blocks per cluster (C)
+// and shared memory per block, or C = 0 when the subimage takes the
+// multi-pass solver. The slab of the half spectrum is split over C blocks of
+// consecutive z planes; the shape with the most blocks per SM (four, three or
+// two, by shared memory) is taken, with the fewest blocks per cluster among
+// those, else the fewest blocks that fit the per-block limit at all.
+struct FusedPlan {
+  int C = 0;
+  size_t smem = 0;
+};
+constexpr int kFusedMaxCluster = 8;  // the portable cluster size
+
+// Launch configuration of the fused kernel: C blocks per cluster, `smem`
+// bytes of dynamic shared memory per block, `grid` blocks.
+template <typename T>
+static cudaLaunchConfig_t fused_config(Ctx& c, int C, size_t smem, int grid, cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cfg.gridDim = dim3(grid, 1, 1);
+  cfg.blockDim = dim3(kFusedThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Clusters of C blocks with `smem` bytes each that the device holds at once
+// (0: the shape cannot be launched); cached per context.
+template <typename T>
+static int fused_resident_clusters(Ctx& c, int C, size_t smem) {
+  const long long key = ((long long)sizeof(T) << 40) | ((long long)C << 32) | (long long)smem;
+  auto it = c.fused_occ.find(key);
+  if (it != c.fused_occ.end()) return it->second;
+  const void* kern = (const void*)k_fused<T>;
+  int n = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin) == cudaSuccess) {
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = fused_config<T>(c, C, smem, C, at);
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) n = 0;
+  }
+  (void)cudaGetLastError();
+  c.fused_occ[key] = n;
+  return n;
+}
+
+template <typename T>
+static FusedPlan fused_plan(Ctx& c, int nx, int ny, int nz, int nphase) {
+  const size_t per_sm = 228 * 1024, reserve = 1024;
+  for (int nb : {4, 3, 2, 1}) {
+    const size_t lim = nb > 1 ? per_sm / nb - reserve : c.smem_optin;
+    for (int C = 1; C <= kFusedMaxCluster && C <= nz; C *= 2) {
+      const size_t bytes = fused_smem_bytes<T>(nx, ny, nz, (nz + C - 1) / C, nphase);
+      // (the kernel's static shared memory, 16 pointers, comes on top)
+      if (bytes <= lim && bytes + 256 <= c.smem_optin && fused_resident_clusters<T>(c, C, smem_bucket(bytes)) > 0)
+        return FusedPlan{C, bytes};
+    }
+  }
+  return FusedPlan();
+}
+
+// One persistent cluster launch per group of fused problems (same blocks per
+// cluster and shared-memory tier). Clusters take the group's problems from a
+// device counter, largest subimage first; each solves its problem to the end
+// and writes its CG state (iterations, status, residual, core sums).
+template <typename T>
+static hh_status run_fused(Ctx& c, const std::map<std::pair<int, size_t>, std::vector<int>>& groups,
+                           const std::vector<Prob>& probs, const FusedParams<T>& base, int nphase) {
+  std::vector<int> order;
+  std::vector<int> start;
+  for (auto& kv : groups) {
+    start.push_back((int)order.size());
+    std::vector<int> g = kv.second;
+    std::stable_sort(g.begin(), g.end(), [&](int a, int b) {
+      const Prob& pa = probs[a];
+      const Prob& pb = probs[b];
+      return (long long)pa.nx * pa.ny * pa.nz > (long long)pb.nx * pb.ny * pb.nz;
+    });
+    order.insert(order.end(), g.begin(), g.end());
+  }
+  int *d_order, *d_queue;
+  hh_status s;
+  if ((s = ensure(c, "fused_order", order.size() * sizeof(int), (void**)&d_order)) != HH_OK) return s;
+  if ((s = ensure(c, "fused_queue", groups.size() * sizeof(int), (void**)&d_queue)) != HH_OK) return s;
+  HH_CK(cudaMemcpyAsync(d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, c.st));
+  HH_CK(cudaMemsetAsync(d_queue, 0, groups.size() * sizeof(int), c.st));
+  int gi = 0;
+  for (auto& kv : groups) {
+    const int C = kv.first.first;
+    size_t smem = 0;
+    for (int pr : kv.second) {
+      const Prob& d = probs[pr];
+      smem = std::max(smem, fused_smem_bytes<T>(d.nx, d.ny, d.nz, (d.nz + C - 1) / C, nphase));
+    }
+    smem = smem_bucket(smem);
+    const int n = (int)kv.second.size();
+    const int ncl = std::min(fused_resident_clusters<T>(c, C, smem), n);
+    if (ncl < 1) {
+      c.err = "fused solver: no cluster of " + std::to_string(C) + " blocks fits";
+      return HH_ERR_UNSUPPORTED;
+    }
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = fused_config<T>(c, C, smem, ncl * C, at);
+    FusedParams<T> fp = base;
+    fp.order = d_order + start[gi];
+    fp.nwork = n;
+    fp.queue = d_queue + gi;
+    ++c.launches;
+    HH_CK(cudaLaunchKernelEx(&cfg, k_fused<T>, fp));
+    ++gi;
+  }
+  return HH_OK;
+}
+
 // Solve the six load cases of every box; per-box results land in d_res[box].
 template <typename T>
 static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, const std::vector<BoxReq>& boxes_in,
@@ -534,6 +654,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       return key;
     };
     long long lab_off = 0, fld_off = 0, spc_off = 0, c21_off = 0, ccount = 0, prow = 0;
+    // fused solves: problems per (blocks per cluster, shared memory per block)
+    std::map<std::pair<int, size_t>, std::vector<int>> fgroups;
+    int n_multipass = 0;
     for (int b = 0; b < nb; ++b) {
       const BoxReq& B = wboxes[b];
       const int nx = bdim[3 * (b0 + b)], ny = bdim[3 * (b0 + b) + 1], nz = bdim[3 * (b0 + b) + 2];
@@ -541,6 +664,41 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       const int nxh = nx / 2 + 1;
       wboxes[b].lab_off = (med.kind == MED_ISO) ? lab_off : c21_off;  // labels: bytes; stiffness: elements
       for (int k = 0; k < nz; ++k) gitems.push_back(make_int2(b, k));
+      const FusedPlan fp = (o.fused && med.kind == MED_ISO && !basic) ? fused_plan<T>(c, nx, ny, nz, nphase)
+                                                                       : FusedPlan();
+      if (fp.C > 0) {
+        // solved whole by the fused kernel: no multi-pass items, partials or spectrum
+        std::vector<int>& grp = fgroups[std::make_pair(fp.C, smem_bucket(fp.smem))];
+        for (int a = 0; a < 6; ++a) {
+          Prob& d = probs[6 * b + a];
+          std::memset(&d, 0, sizeof(d));
+          d.nx = nx;
+          d.ny = ny;
+          d.nz = nz;
+          d.nxh = nxh;
+          d.c0x = B.b;
+          d.c0y = B.b;
+          d.c0z = B.b;
+          d.cnx = B.cnx;
+          d.cny = B.cny;
+          d.cnz = B.cnz;
+          d.px = c.tab.index[nx];
+          d.py = c.tab.index[ny];
+          d.pz = c.tab.index[nz];
+          d.lc = a;
+          d.box = b0 + b;
+          d.cw = 1;
+          d.fused = 1;
+          d.med_off = lab_off;
+          d.fld_off = fld_off;
+          grp.push_back(6 * b + a);
+          fld_off += 6 * V;
+        }
+        lab_off += V;
+        c21_off += 21 * V;
+        continue;
+      }
+      n_multipass += 6;
       for (int a = 0; a < 6; ++a) {
         Prob& d = probs[6 * b + a];
         std::memset(&d, 0, sizeof(d));
@@ -765,7 +923,42 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     const int chunk = std::max(1, o.check_every);
     const long long max_chunks =
         ((long long)(o.fixed_iters > 0 ? o.fixed_iters : o.max_iter) / chunk + 2) * (o.max_restarts + 2);
-    if (basic) {
+    // ---- fused solves first: they leave their problems' states final
+    //      (inactive, nothing pending), which the multi-pass kernels skip
+    cudaEvent_t fev[2] = {nullptr, nullptr};
+    if (!fgroups.empty()) {
+      FusedParams<T> fp;
+      std::memset(&fp, 0, sizeof(fp));
+      fp.prob = d_prob;
+      fp.st = d_st;
+      fp.plans = (const AxisPlan*)c.d_plans.p;
+      fp.tw = (const double*)c.d_tw.p;
+      fp.itab = (const int*)c.d_itab.p;
+      fp.labels = d_lab;
+      fp.lammu = d_lm;
+      fp.nphase = std::max(nphase, 1);
+      fp.nyq_mode = o.nyquist;
+      fp.r = d_r;
+      fp.p = d_p;
+      fp.x = d_x;
+      fp.tol = o.tol;
+      fp.floor2 = floor2;
+      fp.max_iter = o.max_iter;
+      fp.fixed_iters = o.fixed_iters;
+      fp.chunk = chunk;
+      fp.replace = replace ? 1 : 0;
+      fp.max_restarts = o.max_restarts;
+      fp.max_chunks = max_chunks;
+      if (o.profile) {
+        for (auto& e : fev) HH_CK(cudaEventCreate(&e));
+        HH_CK(cudaEventRecord(fev[0], c.st));
+      }
+      if ((s = run_fused<T>(c, fgroups, probs, fp, std::max(nphase, 1))) != HH_OK) return s;
+      if (o.profile) HH_CK(cudaEventRecord(fev[1], c.st));
+    }
+    if (n_multipass == 0) {
+      // every problem of the wave was solved by the fused kernel
+    } else if (basic) {
       // ---- basic scheme (Moulinec-Suquet fixed point): x = eps - E = 0, then
       //      per iteration sigma = C:(E + x), residual, x <- x - Gamma0 * sigma
       HH_CK(cudaMemsetAsync(d_x, 0, fld_off * sizeof(T), c.st));
@@ -876,7 +1069,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         if (replace) {
           flush();
           ++c.launches;
-          k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 0);
+          k_mark_true<<<gs, 128, 0, c.st>>>(d_prob, d_st, np, 0);
           true_pass();
           ++c.launches;
           k_scal_replace<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, o.fixed_iters);
@@ -958,7 +1151,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
           if (final_rounds > o.max_restarts) break;
           flush();
           ++c.launches;
-          k_mark_true<<<gs, 128, 0, c.st>>>(d_st, np, 1);
+          k_mark_true<<<gs, 128, 0, c.st>>>(d_prob, d_st, np, 1);
           true_pass();
           ++c.launches;
           k_scal_true_final<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_part, np, o.tol, 2.0, o.max_restarts, o.max_iter,
@@ -998,8 +1191,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     }
     if (rs != HH_OK) return rs;
 
-    // ---- core averages from x
-    {
+    // ---- core averages from x (the fused kernel formed its own)
+    if (n_multipass > 0) {
       if (!basic) {
         ++c.launches;
         ku<<<gu, threads, 0, c.st>>>(kpp);
@@ -1022,13 +1215,32 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     std::vector<PState> hst(np);
     HH_CK(cudaMemcpyAsync(hst.data(), d_st, np * sizeof(PState), cudaMemcpyDeviceToHost, c.st));
     HH_CK(cudaStreamSynchronize(c.st));
+    double fused_units = 0.0;
     for (int i = 0; i < np; ++i) {
       const Prob& d = probs[i];
       stats.iters_max = std::max(stats.iters_max, hst[i].iters);
       stats.resid_max = std::max(stats.resid_max, hst[i].resid);
       stats.voxel_iters += (long long)d.nx * d.ny * d.nz * hst[i].iters;
+      if (d.fused) fused_units += double(d.nx) * d.ny * d.nz * hst[i].iters;
       if (hst[i].status == ST_NONFINITE) stats.worst = ST_NONFINITE;
       else if (hst[i].status == ST_NOT_CONVERGED && stats.worst == ST_OK) stats.worst = ST_NOT_CONVERGED;
+    }
+    if (fev[0]) {
+      // the fused launches of the wave: algorithmic bytes per voxel-iteration
+      // = r, p, x read, r, x, p written, the label, and p, r read again
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, fev[0], fev[1]) == cudaSuccess) {
+        Ctx::KStat& ks = c.prof["fused"];
+        ks.launches += (long long)fgroups.size();
+        ks.sampled += 1;
+        ks.ms += ms;
+        ks.bytes += fused_units * (48.0 * sizeof(T) + 1.0);
+        Ctx::KStat& ku = c.prof["fused_units"];
+        ku.sampled += 1;
+        ku.bytes += fused_units;
+      }
+      (void)cudaGetLastError();
+      for (auto& e : fev) cudaEventDestroy(e);
     }
     b0 = b1;
   }
@@ -1217,6 +1429,7 @@ extern "C" hh_status hh_options_default(hh_options* o) {
   o->replace = -1;
   o->max_restarts = 4;
   o->autotune = 1;
+  o->fused = 1;
   return HH_OK;
 }
 
@@ -1327,8 +1540,9 @@ static hh_status check_opts(hh_ctx* h, const hh_options* o) {
   if (o->max_iter < 1 || o->fixed_iters < 0) return fail(h, HH_ERR_ARG, "bad iteration limits");
   if (o->nyquist != HH_NYQ_ZERO_COMPONENT && o->nyquist != HH_NYQ_ZERO_MODE) return fail(h, HH_ERR_ARG, "bad nyquist");
   if (o->scheme != HH_CG && o->scheme != HH_BASIC) return fail(h, HH_ERR_ARG, "bad scheme");
-  if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1 || o->wave_boxes < 0)
-    return fail(h, HH_ERR_ARG, "bad check_every, replace, max_restarts or wave_boxes");
+  if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1 || o->wave_boxes < 0 ||
+      o->fused < 0 || o->fused > 1)
+    return fail(h, HH_ERR_ARG, "bad check_every, replace, max_restarts, wave_boxes or fused");
   return HH_OK;
 }
 

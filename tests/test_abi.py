@@ -75,9 +75,9 @@ def test_header_struct_layouts_match_binding():
 #include <stddef.h>
 #include "hh.h"
 int main(void){
- printf("%zu %zu %zu %zu %zu %zu\n", sizeof(hh_options), offsetof(hh_options, workspace_bytes),
-        offsetof(hh_options, check_every), offsetof(hh_options, wave_boxes), sizeof(hh_result),
-        offsetof(hh_result, status));
+ printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(hh_options), offsetof(hh_options, workspace_bytes),
+        offsetof(hh_options, check_every), offsetof(hh_options, wave_boxes), offsetof(hh_options, fused),
+        sizeof(hh_result), offsetof(hh_result, status));
  return 0;}
 '''
     import tempfile
@@ -88,7 +88,8 @@ int main(void){
         subprocess.run([cc, "-I" + os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(B.Options), B.Options.workspace_bytes.offset, B.Options.check_every.offset,
-                    B.Options.wave_boxes.offset, ctypes.sizeof(B.Result), B.Result.status.offset]
+                    B.Options.wave_boxes.offset, B.Options.fused.offset, ctypes.sizeof(B.Result),
+                    B.Result.status.offset]
 
 
 def _declared_arity():

@@ -110,16 +110,42 @@ def _boxes_whole(shape):
     return np.array([[0, 0, 0, nx, ny, nz, 0]], dtype=np.int32)
 
 
-@pytest.mark.parametrize("shape", [(9, 10, 11), (16, 16, 16)])
+# Shapes (z, y, x) chosen so that the fused solver uses clusters of 1, 2, 4 and
+# 8 blocks, with plane counts that leave the last blocks of a cluster with
+# fewer planes or none ((9, 40, 40): 8 blocks of up to 2 planes; (5, 40, 40):
+# 4 blocks of 2, 2, 1, 0 planes); fused = 0 is the multi-pass solver.
+@pytest.mark.parametrize("shape,fused", [((9, 10, 11), 1), ((16, 16, 16), 1), ((6, 6, 6), 1), ((12, 12, 12), 1),
+                                         ((7, 13, 17), 1), ((9, 40, 40), 1), ((5, 40, 40), 1), ((17, 36, 36), 1),
+                                         ((9, 10, 11), 0), ((16, 16, 16), 0), ((9, 40, 40), 0)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
-def test_cg_fixed_iterations_parity(ctx, shape, precision, tol):
+def test_cg_fixed_iterations_parity(ctx, shape, fused, precision, tol):
     lab = RNG.integers(0, 3, size=shape).astype(np.uint8)
     ph = synth.PHASES_SOLID_CLAY_PORE
-    got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=15)
+    got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=15, fused=fused)
     ref = O.homogenize_box(O.IsoMedium.from_labels(lab, ph), (slice(None),) * 3, fixed_iters=15)
     assert np.all(got["iters"] == 15)
     assert rel(got["Sigma"][0], ref["Sigma"]) < tol
     assert rel(got["C"][0], ref["C"]) < tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_and_multipass_solvers_agree(ctx, precision):
+    """Buffered uneven subimages of the sphere pack (contrast 4.4e5) solved to
+    tolerance by the fused cluster kernel and by the multi-pass solver: the
+    same CG arithmetic up to the order of the partial sums. FP64: the same
+    iteration counts and C to 1e-9; FP32 (whose true residual stalls near the
+    tolerance at this contrast) C to 1e-4 of its largest entry."""
+    img = synth.boolean_spheres(n=96, seed=5)
+    boxes = synth.uneven_partition(N=96, counts=((16, 3), (24, 1), (24, 1)), bmax=8, seed=9)[:24]
+    ph = synth.PHASES_SOLID_PORE
+    tol = 1e-8 if precision == "fp64" else 1e-5
+    a = ctx.solve_subimages(img, ph, boxes, precision=precision, tol=tol, fused=1)
+    b = ctx.solve_subimages(img, ph, boxes, precision=precision, tol=tol, fused=0)
+    if precision == "fp64":
+        assert np.array_equal(a["iters"], b["iters"])
+        assert rel(a["C"], b["C"]) < 1e-9
+    else:
+        assert rel(a["C"], b["C"]) < 1e-4
 
 
 @pytest.mark.parametrize("precision,tol,solver_tol", [("fp64", 1e-9, 1e-11), ("fp32", 1e-5, 1e-6)])
@@ -265,37 +291,49 @@ def test_grf32_fixed_iteration_parity(ctx):
 
 @pytest.fixture(scope="module")
 def grf32_oracle():
-    """The oracle's converged two-level run of the 32^3 workload (about 30 s)."""
+    """The oracle's converged two-level runs of the 32^3 workload at the
+    workload's tol 1e-6 and at 1e-11 (about a minute and a half together)."""
     w = synth.workload("grf32")
-    return w, O.homogenize_hierarchical(w["image"], w["phases"], w["boxes"], unit=8, tol=1e-6)
+    return w, {tol: O.homogenize_hierarchical(w["image"], w["phases"], w["boxes"], unit=8, tol=tol)
+               for tol in (1e-6, 1e-11)}
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_grf32_converged_hierarchical_against_oracle(ctx, grf32_oracle, precision):
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("fp64", 1e-11), ("fp32", 1e-6)])
+def test_grf32_converged_hierarchical_against_oracle(ctx, grf32_oracle, precision, tol):
     """The 32^3 two-phase workload (correlation length 4, porosity 0.20,
-    contrast 4.4e5) solved end to end to tol 1e-6: 64 cores of 8^3 without
-    buffer, their C_R, the 4^3 intermediate image and its level-2 solve, the
-    moduli and the arithmetic means, against the oracle's run at the same tol.
-    FP64 takes the oracle's iteration counts and agrees to 1e-9. FP32 cannot
-    reach 1e-6 at this contrast on every load case (the true residual stalls
-    near 1e-5 and the solve ends with the not-converged warning), so its error
-    is reported per result and held to 5e-4 on C (a tenth of the 0.5 %
-    accuracy criterion of the benchmark) and 1e-4 on K, G, K_am, G_am."""
-    w, ref = grf32_oracle
-    got = ctx.homogenize_partition(w["image"], w["phases"], w["boxes"], unit=8, precision=precision, tol=1e-6)
+    contrast 4.4e5) solved end to end: 64 cores of 8^3 without buffer, their
+    C_R, the 4^3 intermediate image and its level-2 solve, the moduli and the
+    arithmetic means, against the oracle's run at the same tol.
+
+    FP64 at tol 1e-11 agrees to 1e-9. At the workload's tol 1e-6 two correct
+    FP64 runs can stop one iteration apart (at this contrast the rounding of
+    the two implementations separates the residual histories by more than the
+    margin by which a residual crosses tol), so a subimage's C_R is held to
+    10 tol and the two-level K, G, K_am, G_am to tol. FP32 cannot reach 1e-6 on
+    every load case at this contrast (its true residual stalls near 1e-5 and
+    the solve ends with the not-converged warning): its error is reported per
+    result and held to 5e-4 on C (a tenth of the benchmark's 0.5 % accuracy
+    criterion) and 1e-4 on K, G, K_am, G_am."""
+    w, refs = grf32_oracle
+    ref = refs[tol]
+    got = ctx.homogenize_partition(w["image"], w["phases"], w["boxes"], unit=8, precision=precision, tol=tol)
     ref_boxes = np.array([r["C"] for r in ref["per_box"]])
     ref_iters = np.array([r["iters"] for r in ref["per_box"]])
     errs = {"C_boxes": rel(got["C_boxes"], ref_boxes), "C_sym": rel(got["C_sym"], ref["C_sym"])}
     for k in ("K", "G", "K_am", "G_am"):
         errs[k] = abs(got[k] - ref[k]) / ref[k]
-    msg = (f"{precision}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()) +
-           f"; status {got['status']}, resid_max {got['resid_max']:.2e}, K {got['K']:.6f} vs {ref['K']:.6f}, "
-           f"G {got['G']:.6f} vs {ref['G']:.6f}")
+    dit = int(np.abs(got["iters_boxes"] - ref_iters).max())
+    msg = (f"{precision} tol {tol}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()) +
+           f"; iteration counts differ by up to {dit}; status {got['status']}, resid_max {got['resid_max']:.2e}, "
+           f"K {got['K']:.6f} vs {ref['K']:.6f}, G {got['G']:.6f} vs {ref['G']:.6f}")
     print(msg)
     if precision == "fp64":
         assert got["status"] == 0, msg
-        assert np.array_equal(got["iters_boxes"], ref_iters), msg
-        assert max(errs.values()) < 1e-9, msg
+        if tol < 1e-9:
+            assert max(errs.values()) < 1e-9, msg
+        else:
+            assert errs["C_boxes"] < 10 * tol and errs["C_sym"] < 10 * tol, msg
+            assert max(errs[k] for k in ("K", "G", "K_am", "G_am")) < tol, msg
     else:
         assert got["status"] in (0, 1), msg
         assert errs["C_boxes"] < 5e-4 and errs["C_sym"] < 5e-4, msg
@@ -478,7 +516,7 @@ def test_streaming_rows_fixed_iterations_parity(ctx, shape, limit, precision, to
     lab = RNG.integers(0, 3, size=shape).astype(np.uint8)
     ph = synth.PHASES_SOLID_CLAY_PORE
     got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=12,
-                              plane_smem_limit=limit)
+                              plane_smem_limit=limit, fused=0)
     ref = O.homogenize_box(O.IsoMedium.from_labels(lab, ph), (slice(None),) * 3, fixed_iters=12)
     assert np.all(got["iters"] == 12)
     assert rel(got["Sigma"][0], ref["Sigma"]) < tol
@@ -489,7 +527,7 @@ def test_streaming_and_whole_plane_agree_converged(ctx):
     img = synth.grf_two_phase(n=24, ell=3.0, porosity=0.3, seed=11)
     ph = synth.PHASES_APPENDIX_B
     a = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-10)
-    b = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-10, plane_smem_limit=8000)
+    b = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-10, plane_smem_limit=8000, fused=0)
     assert rel(b["C"], a["C"]) < 1e-9
     c = ctx.homogenize_direct(img, ph, precision="fp64", tol=1e-9, plane_smem_limit=8000, scheme="basic",
                               max_iter=5000)
@@ -509,23 +547,25 @@ def test_streaming_anisotropic_level2_parity(ctx):
 def test_autotuned_column_width_changes_no_result(ctx):
     img = synth.boolean_spheres(n=96, seed=5)
     boxes = synth.uneven_partition(N=96, counts=((16, 3), (24, 1), (24, 1)), bmax=8, seed=9)[:12]
-    a = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=0)
-    b = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=1)
+    a = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=0, fused=0)
+    b = ctx.solve_subimages(img, synth.PHASES_SOLID_PORE, boxes, precision="fp32", tol=1e-5, autotune=1, fused=0)
     assert np.array_equal(a["C"], b["C"]) and np.array_equal(a["iters"], b["iters"])
 
 
-def test_batched_mixed_x_extents_match_single_solves(ctx):
+@pytest.mark.parametrize("fused", [0, 1])
+def test_batched_mixed_x_extents_match_single_solves(ctx, fused):
     """Subimages that share their y and z extents but differ in x are solved
-    together (one column-pass launch, widths tuned per shape) exactly as when
-    each is solved alone."""
+    together (multi-pass: one column-pass launch, widths tuned per shape;
+    fused: one persistent launch per cluster shape) exactly as when each is
+    solved alone."""
     img = synth.boolean_spheres(n=64, seed=12)
     boxes = np.array([[0, 0, 0, 16, 24, 24, 0], [16, 0, 0, 20, 24, 24, 0], [36, 0, 0, 26, 24, 24, 0],
                       [0, 24, 0, 30, 24, 24, 0], [30, 24, 0, 34, 24, 24, 0]], dtype=np.int32)
     ph = synth.PHASES_SOLID_CLAY_PORE[:2]
     lab = np.minimum(img, 1).astype(np.uint8)
-    together = ctx.solve_subimages(lab, ph, boxes, precision="fp32", fixed_iters=20)
+    together = ctx.solve_subimages(lab, ph, boxes, precision="fp32", fixed_iters=20, fused=fused)
     for i, b in enumerate(boxes):
-        alone = ctx.solve_subimages(lab, ph, b[None], precision="fp32", fixed_iters=20)
+        alone = ctx.solve_subimages(lab, ph, b[None], precision="fp32", fixed_iters=20, fused=fused)
         assert np.array_equal(alone["C"][0], together["C"][i]), i
 
 
