@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--fp64-compare", type=int, default=0,
                     help="also solve the first N rows of the last timed tile in FP64 (plain CG, no residual "
                          "replacement) and report time and K, G differences")
+    ap.add_argument("--cufft", type=int, default=1,
+                    help="1: also time cuFFT (through torch.fft) on the forward and inverse 3D real transforms of "
+                         "the six components of every problem of the last timed tile (a comparator only)")
     ap.add_argument("--headline-rows", type=int, default=6,
                     help="y-rows of the last timed tile on which the plain FP64 solver (one subimage at a time) "
                          "and the batched FP32 solver are timed against each other (0: skip)")
@@ -370,11 +373,55 @@ def run_gb300(args):
             "iters_max": [r32["iters_max"], r64["iters_max"]]}
     if args.cost_scaling and ws == 1:
         line["cost_scaling"] = cost_scaling(ctx, img, ph, args.tol)
+    if args.cufft and ws == 1:
+        sl = slabs[tile_index(args.warmup + args.steps - 1, ws, rank, len(slabs))]
+        line["cufft_comparator"] = cufft_comparator(sl, value)
     if args.headline_rows > 0 and ws == 1:
         sl = slabs[tile_index(args.warmup + args.steps - 1, ws, rank, len(slabs))]
         ys = np.unique(sl[:, 1])[:args.headline_rows]
         line["headline"] = headline(ctx, dimg, ph, sl[np.isin(sl[:, 1], ys)], args.tol, len(slabs))
     print(json.dumps(line))
+
+
+def cufft_comparator(cores, value):
+    """cuFFT (library transforms through torch.fft, timed only; nothing of the
+    product uses it) on the transforms of one operator application for every
+    (subimage, load case) problem of a tile: the six stress components of each
+    problem's buffered box, forward real-to-complex and inverse
+    complex-to-real, batched per box shape. Reported as voxel-iterations per
+    second of these transforms alone, beside the product's whole-iteration
+    rate (constitutive law, transforms, projection, CG update and reductions)."""
+    import numpy as np
+    import torch
+    shapes = {}
+    for b in cores:
+        sh = (int(b[5] + 2 * b[6]), int(b[4] + 2 * b[6]), int(b[3] + 2 * b[6]))
+        shapes[sh] = shapes.get(sh, 0) + 1
+    fields = {sh: torch.randn((6 * n * 6,) + sh, device="cuda", dtype=torch.float32) for sh, n in shapes.items()}
+    units = sum(6 * n * int(np.prod(sh)) for sh, n in shapes.items())
+
+    def sweep():
+        for sh, f in fields.items():
+            spec = torch.fft.rfftn(f, dim=(-3, -2, -1))
+            torch.fft.irfftn(spec, s=sh, dim=(-3, -2, -1))
+
+    for _ in range(3):
+        sweep()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        sweep()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del fields
+    torch.cuda.empty_cache()
+    return {"what": "cuFFT R2C + C2R of 6 components x 6 load cases per subimage of the tile, batched per shape "
+                    f"({len(shapes)} shapes), FP32, torch.fft", "ms_per_operator_application": ms,
+            "transform_voxel_iters_per_s": units / (ms / 1e3), "product_whole_iteration_voxel_iters_per_s": value,
+            "product_over_cufft_transforms_only": value / (units / (ms / 1e3))}
 
 
 def headline(ctx, dimg, ph, cores, tol, ntiles):

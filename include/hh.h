@@ -124,7 +124,7 @@ typedef struct {
     long long kernel_launches; /* libhh kernels launched by this call */
     double device_ms;     /* device time of the call: CUDA events on the library's stream */
     hh_status status;
-    int pad2_;
+    int n_fused;          /* level-1 subimages solved by the fused cluster kernel (options.fused) */
 } hh_result;
 
 /* Per-kernel timing gathered while options.profile = 1. */

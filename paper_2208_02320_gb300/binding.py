@@ -72,7 +72,7 @@ class Result(ctypes.Structure):
         ("kernel_launches", ctypes.c_longlong),
         ("device_ms", ctypes.c_double),
         ("status", ctypes.c_int),
-        ("pad2_", ctypes.c_int),
+        ("n_fused", ctypes.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -82,7 +82,7 @@ class Result(ctypes.Structure):
                     n_subimages=self.n_subimages, n_surrogate_accepted=self.n_surrogate_accepted,
                     n_clipped=self.n_clipped, resid_max=self.resid_max,
                     voxel_iters=self.voxel_iters, kernel_launches=self.kernel_launches,
-                    device_ms=self.device_ms, status=self.status)
+                    device_ms=self.device_ms, status=self.status, n_fused=self.n_fused)
 
 
 class KernelStat(ctypes.Structure):

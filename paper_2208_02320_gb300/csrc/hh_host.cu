@@ -278,6 +278,7 @@ struct Stats {
   double resid_max = 0.0;
   long long voxel_iters = 0;
   int worst = ST_OK;
+  int fused_boxes = 0;  // subimages solved by the fused cluster kernel
 };
 
 template <typename T>
@@ -418,7 +419,11 @@ static int fused_resident_clusters(Ctx& c, int C, size_t smem) {
   if (it != c.fused_occ.end()) return it->second;
   const void* kern = (const void*)k_fused<T>;
   int n = 0;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin) == cudaSuccess) {
+  cudaFuncAttributes fa;
+  // the dynamic limit leaves room for the kernel's static shared memory
+  if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && smem + fa.sharedSizeBytes <= c.smem_optin &&
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(c.smem_optin - fa.sharedSizeBytes)) == cudaSuccess) {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = fused_config<T>(c, C, smem, C, at);
     if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) n = 0;
@@ -1222,6 +1227,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       stats.resid_max = std::max(stats.resid_max, hst[i].resid);
       stats.voxel_iters += (long long)d.nx * d.ny * d.nz * hst[i].iters;
       if (d.fused) fused_units += double(d.nx) * d.ny * d.nz * hst[i].iters;
+      if (d.fused && d.lc == 0) ++stats.fused_boxes;
       if (hst[i].status == ST_NONFINITE) stats.worst = ST_NONFINITE;
       else if (hst[i].status == ST_NOT_CONVERGED && stats.worst == ST_OK) stats.worst = ST_NOT_CONVERGED;
     }
@@ -1587,6 +1593,7 @@ static void fill_result(hh_result* out, const BoxRes& R, const Stats& st) {
   out->iters_max = st.iters_max;
   out->resid_max = st.resid_max;
   out->voxel_iters = st.voxel_iters;
+  out->n_fused = st.fused_boxes;
   out->status = st.worst == ST_NONFINITE ? HH_ERR_NONFINITE : (st.worst == ST_NOT_CONVERGED ? HH_WARN_NOT_CONVERGED : HH_OK);
 }
 
@@ -1764,6 +1771,7 @@ static hh_status hierarchical_core(hh_ctx* h, const hh_options& o, Medium& m, co
   tot.resid_max = std::max(st1.resid_max, st2.resid_max);
   tot.voxel_iters = st1.voxel_iters + st2.voxel_iters;
   tot.worst = std::max(st1.worst, st2.worst);
+  tot.fused_boxes = st1.fused_boxes;
   std::memset(out, 0, sizeof(*out));
   fill_result(out, R, tot);
   out->K_am = am[0];

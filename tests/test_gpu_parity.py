@@ -126,26 +126,40 @@ def test_cg_fixed_iterations_parity(ctx, shape, fused, precision, tol):
     assert np.all(got["iters"] == 15)
     assert rel(got["Sigma"][0], ref["Sigma"]) < tol
     assert rel(got["C"][0], ref["C"]) < tol
+    # the same box through the two-level call reports which solver took it
+    r = ctx.homogenize_partition(lab, ph, _boxes_whole(shape), unit=0, precision=precision, fixed_iters=15,
+                                 fused=fused)
+    assert r["n_fused"] == fused
+    assert rel(r["C_boxes"][0], ref["C"]) < tol
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_fused_and_multipass_solvers_agree(ctx, precision):
-    """Buffered uneven subimages of the sphere pack (contrast 4.4e5) solved to
-    tolerance by the fused cluster kernel and by the multi-pass solver: the
-    same CG arithmetic up to the order of the partial sums. FP64: the same
-    iteration counts and C to 1e-9; FP32 (whose true residual stalls near the
-    tolerance at this contrast) C to 1e-4 of its largest entry."""
+    """The 96^3 sphere pack (contrast 4.4e5) cut into 125 uneven buffered
+    subimages (edges 16..40), homogenized by the fused cluster kernel and by
+    the multi-pass solver: the same CG arithmetic up to the order of the
+    partial sums. FP64 (where the largest subimages do not fit a cluster and
+    take the multi-pass solver in the same call): a different order of the
+    partial sums can move a stop across tol by an iteration or two at this
+    contrast, so iteration counts within 2 and C within 10 tol; FP32 (whose
+    true residual stalls near the tolerance at this contrast): every
+    subimage fused, C_R to 1e-4 of the largest entry."""
     img = synth.boolean_spheres(n=96, seed=5)
-    boxes = synth.uneven_partition(N=96, counts=((16, 3), (24, 1), (24, 1)), bmax=8, seed=9)[:24]
+    boxes = synth.uneven_partition(N=96, counts=((16, 3), (24, 1), (24, 1)), bmax=8, seed=9)
     ph = synth.PHASES_SOLID_PORE
     tol = 1e-8 if precision == "fp64" else 1e-5
-    a = ctx.solve_subimages(img, ph, boxes, precision=precision, tol=tol, fused=1)
-    b = ctx.solve_subimages(img, ph, boxes, precision=precision, tol=tol, fused=0)
+    a = ctx.homogenize_partition(img, ph, boxes, unit=0, precision=precision, tol=tol, fused=1)
+    b = ctx.homogenize_partition(img, ph, boxes, unit=0, precision=precision, tol=tol, fused=0)
+    print(f"{precision}: {a['n_fused']} of {len(boxes)} subimages fused; device ms fused {a['device_ms']:.1f}, "
+          f"multi-pass {b['device_ms']:.1f}; C_R {rel(a['C_boxes'], b['C_boxes']):.2e}")
+    assert b["n_fused"] == 0
     if precision == "fp64":
-        assert np.array_equal(a["iters"], b["iters"])
-        assert rel(a["C"], b["C"]) < 1e-9
+        assert 0 < a["n_fused"] < len(boxes)
+        assert np.abs(a["iters_boxes"] - b["iters_boxes"]).max() <= 2
+        assert rel(a["C_boxes"], b["C_boxes"]) < 10 * tol and rel(a["C_sym"], b["C_sym"]) < 10 * tol
     else:
-        assert rel(a["C"], b["C"]) < 1e-4
+        assert a["n_fused"] == len(boxes)
+        assert rel(a["C_boxes"], b["C_boxes"]) < 1e-4
 
 
 @pytest.mark.parametrize("precision,tol,solver_tol", [("fp64", 1e-9, 1e-11), ("fp32", 1e-5, 1e-6)])
