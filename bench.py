@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--fixed-iters", type=int, default=0,
+                    help="> 0: every load case runs exactly this many iterations (short launches for profiling "
+                         "runs; the default solves to tol)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--tile-rows", type=int, default=6)
@@ -285,6 +288,8 @@ def run_gb300(args):
     dimg = torch.from_numpy(img).to(f"cuda:{local}")
     ctx = Context(local)
     opt = dict(precision=args.precision, tol=args.tol, profile=1)
+    if args.fixed_iters > 0:
+        opt["fixed_iters"] = args.fixed_iters
 
     def step(i, device=True):
         sl = slabs[tile_index(i, ws, rank, len(slabs))]

@@ -139,9 +139,11 @@ def test_fused_and_multipass_solvers_agree(ctx, precision):
     subimages (edges 16..40), homogenized by the fused cluster kernel and by
     the multi-pass solver: the same CG arithmetic up to the order of the
     partial sums. FP64 (where the largest subimages do not fit a cluster and
-    take the multi-pass solver in the same call): a different order of the
-    partial sums can move a stop across tol by an iteration or two at this
-    contrast, so iteration counts within 2 and C within 10 tol; FP32 (whose
+    take the multi-pass solver in the same call): after thousands of
+    iterations at this contrast a different order of the partial sums shifts
+    where the residual crosses tol (measured: up to 104 of about 4800
+    iterations, with C_R still agreeing to 7.7e-9), so iteration counts within
+    5 % and C within 10 tol; FP32 (whose
     true residual stalls near the tolerance at this contrast): every
     subimage fused, C_R to 1e-4 of the largest entry."""
     img = synth.boolean_spheres(n=96, seed=5)
@@ -155,7 +157,7 @@ def test_fused_and_multipass_solvers_agree(ctx, precision):
     assert b["n_fused"] == 0
     if precision == "fp64":
         assert 0 < a["n_fused"] < len(boxes)
-        assert np.abs(a["iters_boxes"] - b["iters_boxes"]).max() <= 2
+        assert (np.abs(a["iters_boxes"] - b["iters_boxes"]) <= 0.05 * b["iters_boxes"] + 2).all()
         assert rel(a["C_boxes"], b["C_boxes"]) < 10 * tol and rel(a["C_sym"], b["C_sym"]) < 10 * tol
     else:
         assert a["n_fused"] == len(boxes)
