@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--fused", type=int, default=-1,
+                    help="1: level-1 solves by the fused cluster kernel, 0: the multi-pass solver, -1: the "
+                         "library's default")
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="> 0: every load case runs exactly this many iterations (short launches for profiling "
                          "runs; the default solves to tol)")
@@ -290,6 +293,8 @@ def run_gb300(args):
     opt = dict(precision=args.precision, tol=args.tol, profile=1)
     if args.fixed_iters > 0:
         opt["fixed_iters"] = args.fixed_iters
+    if args.fused >= 0:
+        opt["fused"] = args.fused
 
     def step(i, device=True):
         sl = slabs[tile_index(i, ws, rank, len(slabs))]
@@ -384,7 +389,7 @@ def run_gb300(args):
     if args.headline_rows > 0 and ws == 1:
         sl = slabs[tile_index(args.warmup + args.steps - 1, ws, rank, len(slabs))]
         ys = np.unique(sl[:, 1])[:args.headline_rows]
-        line["headline"] = headline(ctx, dimg, ph, sl[np.isin(sl[:, 1], ys)], args.tol, len(slabs))
+        line["headline"] = headline(ctx, dimg, ph, sl[np.isin(sl[:, 1], ys)], args.tol, len(slabs), args.fused)
     print(json.dumps(line))
 
 
@@ -429,7 +434,7 @@ def cufft_comparator(cores, value):
             "product_over_cufft_transforms_only": value / (units / (ms / 1e3))}
 
 
-def headline(ctx, dimg, ph, cores, tol, ntiles):
+def headline(ctx, dimg, ph, cores, tol, ntiles, fused=-1):
     """The same cores homogenized (level 1, assembly, level 2) by the plain
     FP64 solver -- FP64 fields, one subimage per wave of launches, no
     surrogate -- and by the batched FP32 solver, with wall times (host clock
@@ -447,7 +452,7 @@ def headline(ctx, dimg, ph, cores, tol, ntiles):
         return r, time.perf_counter() - t0
 
     r64, t64 = run(precision="fp64", wave_boxes=1, fused=0)
-    r32, t32 = run(precision="fp32")
+    r32, t32 = run(precision="fp32", **({"fused": fused} if fused >= 0 else {}))
 
     def kg(C):
         S = 0.5 * (C + np.swapaxes(C, -1, -2))

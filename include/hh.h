@@ -99,13 +99,13 @@ typedef struct {
                              wave of launches); 1 solves the subimages one at a time,
                              the plain unbatched solver. 0 (default): as many as the
                              workspace budget allows. Changes no result */
-    int fused;            /* 1 (default): every level-1 CG solve of isotropic phases whose
-                             half spectrum fits the shared memory of a cluster of up to 8
+    int fused;            /* 1: every level-1 CG solve of isotropic phases whose half
+                             spectrum fits the shared memory of a cluster of up to 8
                              thread blocks runs whole in one cluster (iterations, residual
                              checks and averages on chip; one persistent launch per
-                             cluster shape, fed by a device work counter); 0: the
-                             multi-pass solver for every subimage. Same arithmetic but
-                             for the order of the partial sums */
+                             cluster size, fed by a device work counter); 0 (default):
+                             the multi-pass solver for every subimage. Same arithmetic
+                             but for the order of the partial sums */
 } hh_options;
 
 typedef struct {
