@@ -488,7 +488,6 @@ __device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_
 template <typename T>
 __device__ __forceinline__ void unpack_rows(C2<T>* S, int nrows, int RP, int nx, int nxh, const int* pfx) {
   const int rpr = max(1, (kPackPerThread * (int)blockDim.x) / nxh);
-  const FDiv dn(nxh);
   for (int r0 = 0; r0 < nrows; r0 += rpr) {
     const int tot = min(rpr, nrows - r0) * nxh;
     C2<T> A[kPackPerThread], B[kPackPerThread];
@@ -498,7 +497,7 @@ __device__ __forceinline__ void unpack_rows(C2<T>* S, int nrows, int RP, int nx,
       const int e = threadIdx.x + i * blockDim.x;
       o[i] = -1;
       if (e < tot) {
-        const int rr = dn.div(e);
+        const int rr = e / nxh;
         const int k = e - rr * nxh;
         const C2<T>* R = S + (r0 + rr) * RP;
         const C2<T> a = R[pfx[k]];
@@ -524,7 +523,6 @@ __device__ __forceinline__ void unpack_rows(C2<T>* S, int nrows, int RP, int nx,
 template <typename T>
 __device__ __forceinline__ void pack_rows(C2<T>* S, int nrows, int RP, int nx, int nxh, const int* pfx) {
   const int rpr = max(1, (kPackPerThread * (int)blockDim.x) / nx);
-  const FDiv dn(nx);
   for (int r0 = 0; r0 < nrows; r0 += rpr) {
     const int tot = min(rpr, nrows - r0) * nx;
     C2<T> Z[kPackPerThread];
@@ -534,7 +532,7 @@ __device__ __forceinline__ void pack_rows(C2<T>* S, int nrows, int RP, int nx, i
       const int e = threadIdx.x + i * blockDim.x;
       o[i] = -1;
       if (e < tot) {
-        const int rr = dn.div(e);
+        const int rr = e / nx;
         const int k = e - rr * nx;
         const C2<T>* R = S + (r0 + rr) * RP;
         C2<T> A, B;

@@ -124,8 +124,8 @@ __device__ __forceinline__ void dft_reg(C2<T>* a) {
 }
 
 // Element k of line l: base + off(l) + k * es, off(l) = (l / lpg) gstride + (l % lpg) lstride.
-__device__ __forceinline__ int line_off(const Lines& L, const FDiv& lpg, int l) {
-  const int g = lpg.div(l);
+__device__ __forceinline__ int line_off(const Lines& L, int l) {
+  const int g = l / L.lpg;
   return g * L.gstride + (l - g * L.lpg) * L.lstride;
 }
 
@@ -138,26 +138,22 @@ __device__ __forceinline__ int line_off(const Lines& L, const FDiv& lpg, int l) 
 template <typename T, int N1, int N2, bool INV>
 __device__ __noinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>* tw) {
   const int nthr = blockDim.x;
-  const FDiv lpg(L.lpg);
-  // (pair index idx = t * lpr + l over the lpr lines of a round: the divisor
-  // lpr is the same in every round, the last round's missing lines idle)
   if constexpr (N2 > 1) {
     constexpr int P = N2 <= 2 ? 4 : (N2 <= 4 ? 2 : 1);  // (line, t1) pairs per thread per round
     const int lpr = (P * nthr) / N1;    // whole lines per round
-    const FDiv dl(lpr);
     for (int l0 = 0; l0 < L.n; l0 += lpr) {
       const int nl = min(lpr, L.n - l0);
+      const int tot = nl * N1;
       C2<T> v[P][N2];
       C2<T>* xs[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         const int idx = threadIdx.x + i * nthr;
-        const int t1 = dl.div(idx);
-        const int ll = idx - t1 * lpr;
         xs[i] = nullptr;
-        if (t1 < N1 && ll < nl) {
-          const int line = l0 + ll;
-          C2<T>* x = base + line_off(L, lpg, line) + t1 * L.es;
+        if (idx < tot) {
+          const int t1 = idx / nl;
+          const int line = l0 + (idx - t1 * nl);
+          C2<T>* x = base + line_off(L, line) + t1 * L.es;
           xs[i] = x;
           sfor<0, N2>([&](auto mm) {
             constexpr int m = decltype(mm)::value;
@@ -188,21 +184,20 @@ __device__ __noinline__ void fft2_lines(C2<T>* base, const Lines L, const C2<T>*
   {
     constexpr int P = N1 <= 2 ? 4 : (N1 <= 4 ? 2 : 1);  // (line, k2) pairs per thread per round
     const int lpr = (P * nthr) / N2;
-    const FDiv dl(lpr);
     for (int l0 = 0; l0 < L.n; l0 += lpr) {
       const int nl = min(lpr, L.n - l0);
+      const int tot = nl * N2;
       C2<T> v[P][N1];
       C2<T>* xs[P];
 #pragma unroll
       for (int i = 0; i < P; ++i) {
         const int idx = threadIdx.x + i * nthr;
-        const int k2 = dl.div(idx);
-        const int ll = idx - k2 * lpr;
         xs[i] = nullptr;
-        if (k2 < N2 && ll < nl) {
-          const int line = l0 + ll;
+        if (idx < tot) {
+          const int k2 = idx / nl;
+          const int line = l0 + (idx - k2 * nl);
           const int es = L.es;
-          C2<T>* x = base + line_off(L, lpg, line);
+          C2<T>* x = base + line_off(L, line);
           xs[i] = x + k2 * es;  // output k2 + N2 k1 sits at xs + N2 k1 es
           const C2<T>* y = x + k2 * N1 * es;
           sfor<0, N1>([&](auto tt) {

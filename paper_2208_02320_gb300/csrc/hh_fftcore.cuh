@@ -84,23 +84,6 @@ __device__ __forceinline__ void small_dft(C2<T>* a, const C2<T>* tw, int N) {
   }
 }
 
-// Quotient floor(n / d) for 0 <= n < 2^22 and d >= 1 by a loop-invariant
-// reciprocal: n is exact in FP32 and r = fl(1 / d) has a relative error below
-// 2^-24, so n r differs from n / d by less than 1/2 and its truncation is the
-// quotient or one off; the remainder n - q d corrects it in one step. Used in
-// place of integer division in the index arithmetic of the transforms.
-struct FDiv {
-  int d;
-  float r;
-  __device__ __forceinline__ explicit FDiv(int dv) : d(dv), r(1.0f / float(dv)) {}
-  __device__ __forceinline__ int div(int n) const {
-    int q = int(float(n) * r);
-    const int rem = n - q * d;
-    q += (rem >= d) - (rem < 0);
-    return q;
-  }
-};
-
 // Lines addressed as off(l) = (l / lpg) * gstride + (l % lpg) * lstride, element
 // k of a line at off(l) + k * es.
 struct Lines {

@@ -40,7 +40,7 @@ namespace hh {
 
 namespace cgr = cooperative_groups;
 
-constexpr int kFusedThreads = 1024;  // one block per SM: 32 warps
+constexpr int kFusedThreads = 256;
 constexpr int kFusedRed = 12;  // largest block reduction (the core averages)
 
 template <typename T>
@@ -65,13 +65,8 @@ struct FusedParams {
   long long max_chunks;
 };
 
-// Spectrum columns per z-phase round: about 512 z elements per component and
-// round in FP32 (256 in FP64), between 2 and 32 columns.
-template <typename T>
-__host__ __device__ inline int fused_cols(int nz) {
-  const int w = (512 / nz) / (int)(sizeof(T) / 4);
-  return w < 2 ? 2 : (w > 32 ? 32 : w);
-}
+// Spectrum columns per z-phase round: about 256 z lines of work per round.
+__host__ __device__ inline int fused_cols(int nz) { return nz >= 128 ? 2 : (256 / nz < 2 ? 2 : (256 / nz > 16 ? 16 : 256 / nz)); }
 
 // Shared-memory layout of a block for one problem (the same in every block
 // of the cluster, so that a remote block's slab sits at the same offset).
@@ -90,14 +85,7 @@ struct FusedSmem {
   int* sfy;        // ny
   int* sfz;        // nz
   C2<T>* slab;     // zper * 3 * ny * RP
-  C2<T>* zt;       // W * 6 * nz: [(c * nz + z) * W + jl]
-  int* zo;         // 6 * nz: owner rank (low 4 bits) and slab offset (<< 4) of component c at plane z
-  T* zx;           // nz: wave-vector z component of each z position (component rule applied)
-  int* zn;         // nz: 1 where the z frequency is a Nyquist frequency
-  int* co;         // W: slab offset ky * RP + kx of each column of the round
-  T* cx0;          // W: wave-vector x and y components of each column
-  T* cx1;
-  int* cn;         // W: 1 where the x or y frequency is a Nyquist frequency
+  C2<T>* zt;       // W * 6 * nz
 };
 
 __host__ __device__ inline size_t fused_align(size_t v) { return (v + 15) & ~size_t(15); }
@@ -107,7 +95,7 @@ static_assert(sizeof(PState) <= 256, "the problem state must fit its shared-memo
 template <typename T>
 __host__ __device__ inline size_t fused_smem_bytes(int nx, int ny, int nz, int zper, int nphase) {
   const size_t RP = (size_t)((nx + 2) | 1);
-  const int W = fused_cols<T>(nz);
+  const int W = fused_cols(nz);
   size_t o = kFusedFixed;
   o = fused_align(o + sizeof(T) * 2 * (size_t)nphase);
   o = fused_align(o + sizeof(C2<T>) * (size_t)(nx + ny + nz));
@@ -139,16 +127,6 @@ __device__ __forceinline__ FusedSmem<T> fused_layout(char* base, int nx, int ny,
   s.slab = reinterpret_cast<C2<T>*>(base + o);
   o = fused_align(o + sizeof(C2<T>) * (size_t)zper * 3 * ny * RP);
   s.zt = reinterpret_cast<C2<T>*>(base + o);
-  const int W = fused_cols<T>(nz);
-  o = fused_align(o + sizeof(C2<T>) * (size_t)W * 6 * nz);
-  s.zx = reinterpret_cast<T*>(base + o);
-  s.zo = reinterpret_cast<int*>(s.zx + nz);
-  s.zn = s.zo + 6 * nz;
-  o = fused_align(o + sizeof(int) * (size_t)6 * nz + (sizeof(T) + sizeof(int)) * (size_t)nz);
-  s.cx0 = reinterpret_cast<T*>(base + o);
-  s.cx1 = s.cx0 + W;
-  s.co = reinterpret_cast<int*>(s.cx1 + W);
-  s.cn = s.co + W;
   return s;
 }
 
@@ -311,16 +289,11 @@ __device__ __forceinline__ void fused_cluster_sum(double (&v)[K], double* red, d
 
 // Forward transforms of the block's planes (x real-to-complex with the pair
 // packing, unpack, y), then the z phase over the cluster, with the
-// projection (Appendix A) of every mode, then the inverse y and x transforms.
-// The z phase walks this block's share of the ny * nxh spectrum columns in
-// rounds of W: thread t handles column jl = t % W of the round and rows
-// (component, z) = t / W, t / W + T / W, ... of it, through the offset tables
-// zo (per component and plane) and co (per column), so no element needs an
-// integer division.
+// projection (Appendix A) of every mode.
 template <typename T>
 __device__ __noinline__ void fused_spectral(const FusedParams<T>& P, const FusedGeo& g, const FusedSmem<T>& sm,
-                                            const AxisPlan& ax, const AxisPlan& ay, const AxisPlan& az,
-                                            C2<T>* const* rb, cgr::cluster_group& cl) {
+                               const AxisPlan& ax, const AxisPlan& ay, const AxisPlan& az, C2<T>* const* rb,
+                               cgr::cluster_group& cl) {
   const int ny = g.ny, nz = g.nz, nxh = g.nxh, RP = g.RP;
   if (g.zc > 0) {
     fft_lines<T, false>(sm.slab, Lines{3 * ny * g.zc, 1 << 30, 0, RP, 1, false}, ax, sm.twx);
@@ -328,64 +301,72 @@ __device__ __noinline__ void fused_spectral(const FusedParams<T>& P, const Fused
     fft_lines<T, false>(sm.slab, Lines{6 * nxh * g.zc, 2 * nxh, ny * RP, 1, RP, true}, ay, sm.twy);
   }
   cl.sync();  // every block's planes are transformed in x and y
+  // z phase: this block's share of the ny * nxh spectrum columns
   const int C = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const long long J = (long long)ny * nxh;
   const int jb = (int)(J * rank / C), je = (int)(J * (rank + 1) / C);
-  const int W = fused_cols<T>(nz);
-  const int jl = threadIdx.x % W;
-  const int rs = blockDim.x / W;            // rows per pass
-  const int r0 = threadIdx.x / W;
-  const bool on = r0 < rs;
+  const int zper = g.zper;
+  const int W = fused_cols(nz);
   for (int j0 = jb; j0 < je; j0 += W) {
     const int Wc = min(W, je - j0);
-    if ((int)threadIdx.x < Wc) {
-      const int j = j0 + threadIdx.x;
+    const int tot = 6 * nz * Wc;
+    // gather: zt[(c * nz + z) * Wc + jl] = component c of column j0 + jl at plane z
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int jl = e % Wc;
+      const int cz = e / Wc;
+      const int c = cz / nz;
+      const int z = cz - c * nz;
+      const int j = j0 + jl;
+      const int ky = j / nxh;
+      const int kx = j - ky * nxh;
+      const int ow = z / zper;
+      const int zl = z - ow * zper;
+      sm.zt[e] = rb[ow][((zl * 3 + (c >> 1)) * ny + ky) * RP + (c & 1) * nxh + kx];
+    }
+    __syncthreads();
+    const Lines Lz{6 * Wc, Wc, nz * Wc, 1, Wc, true};
+    fft_lines<T, false>(sm.zt, Lz, az, sm.twz);
+    for (int e = threadIdx.x; e < nz * Wc; e += blockDim.x) {
+      const int jl = e % Wc;
+      const int kzp = e / Wc;
+      const int j = j0 + jl;
       const int kyp = j / nxh;
       const int kx = j - kyp * nxh;
       const int my = sm.sfy[kyp];
+      const int mz = sm.sfz[kzp];
       const bool nyq_x = (g.nx % 2 == 0) && (2 * kx == g.nx);
       const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
-      sm.co[threadIdx.x] = kyp * RP + kx;
-      sm.cx0[threadIdx.x] = nyq_x ? T(0) : T(kx) / T(g.nx);
-      sm.cx1[threadIdx.x] = nyq_y ? T(0) : T(my) / T(ny);
-      sm.cn[threadIdx.x] = (nyq_x || nyq_y) ? 1 : 0;
-    }
-    __syncthreads();
-    // gather: zt[(c * nz + z) * W + jl] = component c of column j0 + jl at plane z
-    if (on && jl < Wc) {
-      const int cof = sm.co[jl];
-      for (int cz = r0; cz < 6 * nz; cz += rs) {
-        const int zo = sm.zo[cz];
-        sm.zt[cz * W + jl] = rb[zo & 15][(zo >> 4) + cof];
+      const bool nyq_z = (nz % 2 == 0) && (2 * mz == nz);
+      T x0 = T(kx) / T(g.nx), x1 = T(my) / T(ny), x2 = T(mz) / T(nz);
+      if (P.nyq_mode == 0) {
+        if (nyq_x) x0 = T(0);
+        if (nyq_y) x1 = T(0);
+        if (nyq_z) x2 = T(0);
+      } else if (nyq_x || nyq_y || nyq_z) {
+        x0 = x1 = x2 = T(0);
       }
-    }
-    __syncthreads();
-    const Lines Lz{6 * Wc, Wc, nz * W, 1, W, true};
-    fft_lines<T, false>(sm.zt, Lz, az, sm.twz);
-    if (on && jl < Wc) {
-      const T c0 = sm.cx0[jl], c1 = sm.cx1[jl];
-      const int cnq = sm.cn[jl];
-      for (int kz = r0; kz < nz; kz += rs) {
-        T x0 = c0, x1 = c1, x2 = sm.zx[kz];
-        if (P.nyq_mode != 0 && (cnq || sm.zn[kz])) x0 = x1 = x2 = T(0);
-        C2<T> t[6];
+      C2<T> t[6];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) t[c] = sm.zt[(c * nz + kz) * W + jl];
-        project_mode<T>(t, x0, x1, x2);
+      for (int c = 0; c < 6; ++c) t[c] = sm.zt[(c * nz + kzp) * Wc + jl];
+      project_mode<T>(t, x0, x1, x2);
 #pragma unroll
-        for (int c = 0; c < 6; ++c) sm.zt[(c * nz + kz) * W + jl] = t[c];
-      }
+      for (int c = 0; c < 6; ++c) sm.zt[(c * nz + kzp) * Wc + jl] = t[c];
     }
     __syncthreads();
     fft_lines<T, true>(sm.zt, Lz, az, sm.twz);
     // scatter back to the owners' slabs
-    if (on && jl < Wc) {
-      const int cof = sm.co[jl];
-      for (int cz = r0; cz < 6 * nz; cz += rs) {
-        const int zo = sm.zo[cz];
-        rb[zo & 15][(zo >> 4) + cof] = sm.zt[cz * W + jl];
-      }
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int jl = e % Wc;
+      const int cz = e / Wc;
+      const int c = cz / nz;
+      const int z = cz - c * nz;
+      const int j = j0 + jl;
+      const int ky = j / nxh;
+      const int kx = j - ky * nxh;
+      const int ow = z / zper;
+      const int zl = z - ow * zper;
+      rb[ow][((zl * 3 + (c >> 1)) * ny + ky) * RP + (c & 1) * nxh + kx] = sm.zt[e];
     }
     __syncthreads();
   }
@@ -397,31 +378,15 @@ __device__ __noinline__ void fused_spectral(const FusedParams<T>& P, const Fused
   }
 }
 
-// Rows of nx voxels of the block's planes: thread t takes voxel x = t % nx of
-// rows t / nx, t / nx + step, ... (step = threads / nx; the last t % nx
-// threads idle), with the (plane, y) of the row kept by increments.
-struct RowWalk {
-  int x, row, zl, y, step;
-};
-
-__device__ __forceinline__ RowWalk row_walk(const FusedGeo& g) {
-  RowWalk w;
-  w.step = blockDim.x / g.nx;
-  w.x = threadIdx.x % g.nx;
-  w.row = threadIdx.x / g.nx;
-  if (w.row >= w.step) w.row = 1 << 30;  // idle thread
-  w.zl = w.row / g.ny;
-  w.y = w.row - w.zl * g.ny;
-  return w;
-}
-
-__device__ __forceinline__ void row_next(RowWalk& w, int ny) {
-  w.row += w.step;
-  w.y += w.step;
-  while (w.y >= ny) {
-    w.y -= ny;
-    ++w.zl;
-  }
+// Voxel v of the block's planes: its offset in Omega_B and the slab position
+// of its first component pair (pairs c2 = 1, 2 follow at c2 * ny * RP).
+__device__ __forceinline__ void fused_voxel_at(const FusedGeo& g, int v, long long& vo, int& so) {
+  const int zl = v / g.pl;
+  const int rem = v - zl * g.pl;
+  const int y = rem / g.nx;
+  const int x = rem - y * g.nx;
+  vo = (long long)(g.z0 + zl) * g.pl + rem;
+  so = (zl * 3 * g.ny + y) * g.RP + x;
 }
 
 // One operator application q = G*(C:e) in mode MODE with the voxel work of
@@ -445,10 +410,11 @@ __device__ __noinline__ void fused_apply(const FusedParams<T>& P, const Prob& d,
   const T alpha = T(sm.ps->alpha), beta = T(sm.ps->beta);
   const bool pend = sm.ps->pending != 0;
   DotAcc<T> a0;
-  const int nrow = g.zc * g.ny;
-  for (RowWalk w = row_walk(g); w.row < nrow; row_next(w, g.ny)) {
-    const long long vo = (long long)(g.z0 + w.zl) * g.pl + w.y * g.nx + w.x;
-    const int so = (w.zl * 3 * g.ny + w.y) * g.RP + w.x;
+  const int nv = g.zc * g.pl;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    long long vo;
+    int so;
+    fused_voxel_at(g, v, vo, so);
     const int lb = lab[vo];
     T e[6];
     if (MODE == MODE_RHS) {
@@ -505,9 +471,10 @@ __device__ __noinline__ void fused_apply(const FusedParams<T>& P, const Prob& d,
   // inverse voxel phase
   DotAcc<T> a1, a2, a3;
   const T invV = T(1) / T(V);
-  for (RowWalk w = row_walk(g); w.row < nrow; row_next(w, g.ny)) {
-    const long long vo = (long long)(g.z0 + w.zl) * g.pl + w.y * g.nx + w.x;
-    const int so = (w.zl * 3 * g.ny + w.y) * g.RP + w.x;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    long long vo;
+    int so;
+    fused_voxel_at(g, v, vo, so);
     T qv[6];
 #pragma unroll
     for (int c2 = 0; c2 < 3; ++c2) {
@@ -566,10 +533,11 @@ __device__ __noinline__ void fused_flush(const FusedParams<T>& P, const Prob& d,
   const T* __restrict__ Pp = P.p + d.fld_off;
   T* __restrict__ X = P.x + d.fld_off;
   const T alpha = T(sm.ps->alpha);
-  const int nrow = g.zc * g.ny;
-  for (RowWalk w = row_walk(g); w.row < nrow; row_next(w, g.ny)) {
-    const long long vo = (long long)(g.z0 + w.zl) * g.pl + w.y * g.nx + w.x;
-    const int so = (w.zl * 3 * g.ny + w.y) * g.RP + w.x;
+  const int nv = g.zc * g.pl;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    long long vo;
+    int so;
+    fused_voxel_at(g, v, vo, so);
 #pragma unroll
     for (int c2 = 0; c2 < 3; ++c2) {
       const C2<T> qq = sm.slab[so + c2 * sstr];
@@ -593,12 +561,16 @@ __device__ __noinline__ void fused_averages(const FusedParams<T>& P, const Prob&
   double acc[kFusedRed];
 #pragma unroll
   for (int k = 0; k < kFusedRed; ++k) acc[k] = 0.0;
-  const int nrow = g.zc * g.ny;
-  for (RowWalk w = row_walk(g); w.row < nrow; row_next(w, g.ny)) {
-    const int z = g.z0 + w.zl, y = w.y, x = w.x;
+  const int nv = g.zc * g.pl;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const int zl = v / g.pl;
+    const int rem = v - zl * g.pl;
+    const int y = rem / g.nx;
+    const int x = rem - y * g.nx;
+    const int z = g.z0 + zl;
     if (z < d.c0z || z >= d.c0z + d.cnz || y < d.c0y || y >= d.c0y + d.cny || x < d.c0x || x >= d.c0x + d.cnx)
       continue;
-    const long long vo = (long long)z * g.pl + y * g.nx + x;
+    const long long vo = (long long)z * g.pl + rem;
     T e[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -621,7 +593,7 @@ __device__ __noinline__ void fused_averages(const FusedParams<T>& P, const Prob&
 // The persistent kernel.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(kFusedThreads, 1) k_fused(FusedParams<T> P) {
+__global__ void __launch_bounds__(kFusedThreads, 4) k_fused(FusedParams<T> P) {
   extern __shared__ __align__(16) char smem[];
   cgr::cluster_group cl = cgr::this_cluster();
   const int C = (int)cl.num_blocks();
@@ -660,22 +632,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_fused(FusedParams<T> P) {
     for (int t = threadIdx.x; t < d.nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
     for (int t = threadIdx.x; t < 2 * P.nphase; t += blockDim.x) sm.lm[t] = P.lammu[t];
     if (threadIdx.x < C) rb[threadIdx.x] = cl.map_shared_rank(sm.slab, (int)threadIdx.x);
-    // z-phase tables: owner and slab offset of component c at plane z, and
-    // the z components of the wave vector (Appendix A; Nyquist rules as in
-    // the multi-pass column pass)
-    for (int t = threadIdx.x; t < 6 * d.nz; t += blockDim.x) {
-      const int c = t / d.nz;
-      const int z = t - c * d.nz;
-      const int ow = z / g.zper;
-      const int zl = z - ow * g.zper;
-      sm.zo[t] = ow | ((((zl * 3 + (c >> 1)) * d.ny) * g.RP + (c & 1) * d.nxh) << 4);
-    }
-    for (int t = threadIdx.x; t < d.nz; t += blockDim.x) {
-      const int mz = P.itab[az.sf_off + t];
-      const bool nyq = (d.nz % 2 == 0) && (2 * mz == d.nz);
-      sm.zx[t] = nyq ? T(0) : T(mz) / T(d.nz);
-      sm.zn[t] = nyq ? 1 : 0;
-    }
     __syncthreads();
 
     double sums[4];

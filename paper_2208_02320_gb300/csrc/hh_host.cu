@@ -382,9 +382,9 @@ static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool
 // Cluster shape of the fused solver for one subimage: blocks per cluster (C)
 // and shared memory per block, or C = 0 when the subimage takes the
 // multi-pass solver. The slab of the half spectrum is split over C blocks of
-// consecutive z planes; a block has 1024 threads, so one block per SM, and the
-// fewest blocks whose slabs fit the per-block shared memory are taken (the
-// least traffic between the blocks of a cluster).
+// consecutive z planes; the shape with the most blocks per SM (four, three or
+// two, by shared memory) is taken, with the fewest blocks per cluster among
+// those, else the fewest blocks that fit the per-block limit at all.
 struct FusedPlan {
   int C = 0;
   size_t smem = 0;
@@ -435,16 +435,21 @@ static int fused_resident_clusters(Ctx& c, int C, size_t smem) {
 
 template <typename T>
 static FusedPlan fused_plan(Ctx& c, int nx, int ny, int nz, int nphase) {
-  for (int C = 1; C <= kFusedMaxCluster && C <= nz; C *= 2) {
-    const size_t bytes = fused_smem_bytes<T>(nx, ny, nz, (nz + C - 1) / C, nphase);
-    // (the kernel's static shared memory, 16 pointers, comes on top)
-    if (bytes + 256 <= c.smem_optin && fused_resident_clusters<T>(c, C, bytes) > 0) return FusedPlan{C, bytes};
+  const size_t per_sm = 228 * 1024, reserve = 1024;
+  for (int nb : {4, 3, 2, 1}) {
+    const size_t lim = nb > 1 ? per_sm / nb - reserve : c.smem_optin;
+    for (int C = 1; C <= kFusedMaxCluster && C <= nz; C *= 2) {
+      const size_t bytes = fused_smem_bytes<T>(nx, ny, nz, (nz + C - 1) / C, nphase);
+      // (the kernel's static shared memory, 16 pointers, comes on top)
+      if (bytes <= lim && bytes + 256 <= c.smem_optin && fused_resident_clusters<T>(c, C, smem_bucket(bytes)) > 0)
+        return FusedPlan{C, bytes};
+    }
   }
   return FusedPlan();
 }
 
 // One persistent cluster launch per group of fused problems (same blocks per
-// cluster; the launch asks for the group's largest shared memory). Clusters take the group's problems from a
+// cluster and shared-memory tier). Clusters take the group's problems from a
 // device counter, largest subimage first; each solves its problem to the end
 // and writes its CG state (iterations, status, residual, core sums).
 template <typename T>
@@ -476,6 +481,7 @@ static hh_status run_fused(Ctx& c, const std::map<std::pair<int, size_t>, std::v
       const Prob& d = probs[pr];
       smem = std::max(smem, fused_smem_bytes<T>(d.nx, d.ny, d.nz, (d.nz + C - 1) / C, nphase));
     }
+    smem = smem_bucket(smem);
     const int n = (int)kv.second.size();
     const int ncl = std::min(fused_resident_clusters<T>(c, C, smem), n);
     if (ncl < 1) {
@@ -667,7 +673,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
                                                                        : FusedPlan();
       if (fp.C > 0) {
         // solved whole by the fused kernel: no multi-pass items, partials or spectrum
-        std::vector<int>& grp = fgroups[std::make_pair(fp.C, size_t(0))];
+        std::vector<int>& grp = fgroups[std::make_pair(fp.C, smem_bucket(fp.smem))];
         for (int a = 0; a < 6; ++a) {
           Prob& d = probs[6 * b + a];
           std::memset(&d, 0, sizeof(d));
