@@ -149,9 +149,10 @@ def measured_peaks():
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("hh_device.cuh", "hh_fftcore.cuh", "hh_fft2.cuh", "hh_fft2_inst.cu", "hh_ctmath.h", "hh_post.cuh",
-              "hh_fused.cuh", "hh_host.cu"):
-        with open(os.path.join(ROOT, "paper_2208_02320_gb300", "csrc", f), "rb") as fh:
+    # the sources of the multi-pass field kernels and the compile flags
+    for f in ("csrc/hh_device.cuh", "csrc/hh_fftcore.cuh", "csrc/hh_fft2.cuh", "csrc/hh_fft2_inst.cu",
+              "csrc/hh_ctmath.h", "_build.py"):
+        with open(os.path.join(ROOT, "paper_2208_02320_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 

@@ -1,15 +1,17 @@
 """FP64 CPU oracle of the subimage surrogate network -- TEST INFRASTRUCTURE ONLY.
 
 The paper has no learned part. The library adds one for the first
-hierarchical level: a small 3D CNN that maps a subimage's phase voxels to the
-21 upper-triangle components of its effective Voigt stiffness, trained on
-subimages that the FFT solver homogenized, and a gate that defers to the FFT
-solver whenever the ensemble's prediction is not trustworthy. This module
-states what that network computes, plainly and in FP64, so that the CUDA
-kernels (BF16 operands, FP32 accumulation) can be checked against it:
+hierarchical level: a small 3D CNN that maps a buffered subimage's phase
+voxels to the 21 upper-triangle components of its core's effective Voigt
+stiffness, trained on subimages that the FFT solver homogenized, and a gate
+that defers to the FFT solver whenever the ensemble's prediction is not
+trustworthy. This module states what that network computes, plainly and in
+FP64, so that the CUDA kernels (BF16 operands, FP32 accumulation) can be
+checked against it:
 
-  input   one-hot of the labels 0, 1, 2 (3 channels, edge D)
-  conv1   3 -> 16, 3x3x3, stride 1, zero padding 1, bias, ReLU
+  input   one-hot of the labels 0, 1, 2 and the core mask (4 channels, box
+          Omega_B of any shape: the core Omega_R is 1, the buffer 0)
+  conv1   4 -> 16, 3x3x3, stride 1, zero padding 1, bias, ReLU
   conv2  16 -> 32, stride 2, ReLU
   conv3  32 -> 64, stride 2, ReLU
   conv4  64 -> 64, stride 1, ReLU
@@ -21,12 +23,15 @@ Flat parameter layout (shared with the CUDA path): for each conv layer the
 weights W[tap][ci][co] with tap = (kz * 3 + ky) * 3 + kx, then the bias[co];
 for each fully connected layer W[in][out], then bias[out]; layers in order.
 
+A core is given as (ox, oy, oz, cnx, cny, cnz): origin and size of Omega_R
+inside the box, x fastest like the boxes of the solver; None is the whole box.
+
 Only tests/, the package's smoke check and bench.py may use this module.
 """
 
 import numpy as np
 
-CONVS = [(3, 16, 1), (16, 32, 2), (32, 64, 2), (64, 64, 1)]  # (ci, co, stride)
+CONVS = [(4, 16, 1), (16, 32, 2), (32, 64, 2), (64, 64, 1)]  # (ci, co, stride)
 FCS = [(64, 128), (128, 21)]
 NCH = 3
 NOUT = 21
@@ -65,6 +70,24 @@ def one_hot(labels: np.ndarray) -> np.ndarray:
     """(D, H, W) uint8 labels -> (3, D, H, W) one-hot (labels >= 3 give a zero vector)."""
     lab = np.asarray(labels)
     return np.stack([(lab == c).astype(np.float64) for c in range(NCH)])
+
+
+def core_mask(shape, core=None) -> np.ndarray:
+    """(D, H, W) mask: 1 on the core Omega_R = (ox, oy, oz, cnx, cny, cnz), 0 on
+    the buffer (all ones when core is None)."""
+    m = np.zeros(shape)
+    if core is None:
+        m[...] = 1.0
+    else:
+        ox, oy, oz, cx, cy, cz = (int(v) for v in core)
+        m[oz:oz + cz, oy:oy + cy, ox:ox + cx] = 1.0
+    return m
+
+
+def net_input(labels, core=None) -> np.ndarray:
+    """(4, D, H, W): the one-hot labels and the core mask."""
+    lab = np.asarray(labels)
+    return np.concatenate([one_hot(lab), core_mask(lab.shape, core)[None]])
 
 
 def out_size(n: int, stride: int) -> int:
@@ -115,10 +138,11 @@ def relu(a):
     return np.maximum(a, 0.0)
 
 
-def forward(theta, labels):
-    """Network output (21,) for one subimage, and the activations for backward."""
+def forward(theta, labels, core=None):
+    """Network output (21,) for one subimage (with its core), and the
+    activations for backward."""
     p = unflatten(theta)
-    acts = [one_hot(labels)]
+    acts = [net_input(labels, core)]
     for i, (_, _, s) in enumerate(CONVS):
         acts.append(relu(conv3d(acts[-1], p["conv%d.w" % (i + 1)], p["conv%d.b" % (i + 1)], s)))
     h0 = acts[-1].mean(axis=(1, 2, 3))
@@ -150,14 +174,14 @@ def backward(theta, cache, dout):
     return flatten(g)
 
 
-def batch_loss_and_grad(theta, labels_batch, targets):
+def batch_loss_and_grad(theta, labels_batch, targets, cores=None):
     """Mean squared error over the batch and the 21 outputs, and its gradient."""
     B = len(labels_batch)
     loss = 0.0
     grad = np.zeros(n_params())
     outs = []
-    for lab, t in zip(labels_batch, targets):
-        out, cache = forward(theta, lab)
+    for i, (lab, t) in enumerate(zip(labels_batch, targets)):
+        out, cache = forward(theta, lab, None if cores is None else cores[i])
         outs.append(out)
         r = out - np.asarray(t, dtype=np.float64)
         loss += float(r @ r)
@@ -182,7 +206,7 @@ def cosine_step_size(lr, step, total_steps):
     return 0.5 * lr * (1.0 + np.cos(np.pi * step / total_steps))
 
 
-def train_full_batch(theta, labels_batch, targets, steps, lr):
+def train_full_batch(theta, labels_batch, targets, steps, lr, cores=None):
     """`steps` Adam updates, each on the gradient of the whole batch, with the
     cosine step size: update t (from 0) uses cosine_step_size(lr, t, steps)
     and Adam's bias correction at t + 1. Returns the final parameters and the
@@ -192,7 +216,7 @@ def train_full_batch(theta, labels_batch, targets, steps, lr):
     v = np.zeros_like(theta)
     losses = []
     for t in range(steps):
-        loss, g, _ = batch_loss_and_grad(theta, labels_batch, targets)
+        loss, g, _ = batch_loss_and_grad(theta, labels_batch, targets, cores)
         losses.append(loss)
         theta, m, v = adam_step(theta, g, m, v, t + 1, cosine_step_size(lr, t, steps))
     return theta, np.array(losses)
@@ -233,23 +257,28 @@ def moduli_voigt(C):
     return K, G
 
 
-def phase_bounds(labels, phases):
+def phase_bounds(labels, phases, core=None):
     """Voigt (arithmetic) and Reuss (harmonic) means of the phase K and G over
-    the subimage: (K_R, K_V, G_R, G_V)."""
-    lab = np.asarray(labels).ravel()
+    the core of the subimage (the whole subimage when core is None):
+    (K_R, K_V, G_R, G_V)."""
+    lab = np.asarray(labels)
+    if core is not None:
+        ox, oy, oz, cx, cy, cz = (int(v) for v in core)
+        lab = lab[oz:oz + cz, oy:oy + cy, ox:ox + cx]
+    lab = lab.ravel()
     ph = np.asarray(phases, dtype=np.float64)
     f = np.bincount(lab, minlength=len(ph)).astype(np.float64) / lab.size
     K, G = ph[:, 0], ph[:, 1]
     return 1.0 / np.sum(f / K), float(np.sum(f * K)), 1.0 / np.sum(f / G), float(np.sum(f * G))
 
 
-def gate(members_c21, labels, phases, spread):
+def gate(members_c21, labels, phases, spread, core=None):
     """Accept (True, mean C21) when every member's Voigt-projected K and G lie in
-    the subimage's own [Reuss, Voigt] bounds, the relative spread
-    (max - min) / mean of the members' K and of their G is <= spread, and the
-    mean stiffness is positive definite; else (False, mean C21)."""
+    the [Reuss, Voigt] bounds of the core's own phase fractions, the relative
+    spread (max - min) / mean of the members' K and of their G is <= spread,
+    and the mean stiffness is positive definite; else (False, mean C21)."""
     mem = np.asarray(members_c21, dtype=np.float64)
-    KR, KV, GR, GV = phase_bounds(labels, phases)
+    KR, KV, GR, GV = phase_bounds(labels, phases, core)
     Ks, Gs = zip(*[moduli_voigt(c21_to_full(c)) for c in mem])
     Ks, Gs = np.array(Ks), np.array(Gs)
     mean = mem.mean(axis=0)

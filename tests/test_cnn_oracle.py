@@ -32,8 +32,22 @@ def test_conv3d_matches_scipy_correlate():
 def test_output_sizes():
     assert [N.out_size(32, s) for s in (1, 2)] == [32, 16]
     assert N.out_size(16, 2) == 8 and N.out_size(7, 2) == 4
-    assert N.n_params() == 27 * 3 * 16 + 16 + 27 * 16 * 32 + 32 + 27 * 32 * 64 + 64 + 27 * 64 * 64 + 64 + \
+    assert N.n_params() == 27 * 4 * 16 + 16 + 27 * 16 * 32 + 32 + 27 * 32 * 64 + 64 + 27 * 64 * 64 + 64 + \
         64 * 128 + 128 + 128 * 21 + 21
+
+
+def test_input_channels_and_core_mask():
+    lab = np.array([[[0, 1, 2, 3]]], dtype=np.uint8)  # (1, 1, 4): one voxel of each label
+    x = N.net_input(lab)
+    assert x.shape == (4, 1, 1, 4)
+    assert np.array_equal(x[:3, 0, 0], [[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 1, 0]])  # label 3: no phase
+    assert np.all(x[3] == 1.0)  # no core given: the whole box is the core
+    m = N.core_mask((5, 6, 7), (1, 2, 3, 4, 3, 2))  # x0 1, y0 2, z0 3; 4 x 3 x 2 voxels
+    assert m.sum() == 4 * 3 * 2 and m[3:5, 2:5, 1:5].all()
+    # a non-cubic box runs through the global pool
+    theta = N.init_params(RNG.random(N.n_params()))
+    out, cache = N.forward(theta, RNG.integers(0, 3, size=(9, 6, 13)).astype(np.uint8), (2, 1, 2, 9, 4, 5))
+    assert out.shape == (21,) and cache["acts"][-1].shape == (64, 3, 2, 4)
 
 
 def _fd(f, a, idx, h=1e-6):
@@ -66,10 +80,11 @@ def test_conv3d_backward_finite_differences(stride):
 def test_network_gradient_finite_differences():
     theta = N.init_params(RNG.random(N.n_params()))
     theta += 0.01 * RNG.standard_normal(theta.size)  # nonzero biases
-    labs = [RNG.integers(0, 3, size=(8, 8, 8)).astype(np.uint8) for _ in range(2)]
+    labs = [RNG.integers(0, 3, size=(8, 8, 8)).astype(np.uint8), RNG.integers(0, 3, size=(6, 9, 7)).astype(np.uint8)]
+    cores = [None, (1, 2, 1, 5, 5, 4)]  # a buffered, non-cubic box with its core
     tg = RNG.standard_normal((2, N.NOUT))
-    loss, grad, _ = N.batch_loss_and_grad(theta, labs, tg)
-    f = lambda: N.batch_loss_and_grad(theta, labs, tg)[0]
+    loss, grad, _ = N.batch_loss_and_grad(theta, labs, tg, cores)
+    f = lambda: N.batch_loss_and_grad(theta, labs, tg, cores)[0]
     # one coordinate in every layer's weights and biases
     o = 0
     for name, shape in N.layer_shapes():

@@ -87,15 +87,17 @@ def test_training_updates_match_oracle_adam_cosine(ctx, steps):
     update on the gradient of the same cubes, against the oracle's full-batch
     Adam with the cosine step size (lr, 0.75 lr, 0.25 lr for three updates).
 
-    Adam's first update is lr times the sign of each gradient entry, so an
-    entry whose gradient lies within the BF16 resolution of zero can take
-    either sign. Those entries (|g| below a fifth of the layer's RMS gradient
-    in the oracle) are left out; the gradients are heavy-tailed, so this
-    keeps 38 % of the parameters on these cubes, and at least a quarter must
-    remain. Every remaining parameter's change must agree
-    with the oracle's to 10 %, element by element (at most one in a thousand
-    may miss: single BF16 products can carry larger errors), and the batch
-    losses before each update to 2e-2."""
+    Adam's update of an entry is its gradient's sign for the first step and
+    m / sqrt(v) of the gradient history after it, so it is well defined only
+    where the entry's gradient stays clear of zero and keeps its sign: entries
+    whose oracle gradient is below a fifth of the layer's RMS at any update,
+    or changes sign between updates, are left out (the gradients are
+    heavy-tailed: 38 % of the parameters remain on these cubes for one update;
+    at least a sixth must remain). Every remaining parameter's change must
+    agree with the oracle's to 10 %, element by element (at most one in a
+    thousand may miss: single BF16 products can carry larger errors), and the
+    batch losses before each update to 2e-3 (they follow the whole
+    trajectory, step sizes included)."""
     theta = _params(13).astype(np.float32).astype(np.float64)
     labs = _cubes(4, 8, seed=9)
     tg = synth.uniform01(14, 0, 4 * N.NOUT).reshape(4, N.NOUT)
@@ -103,23 +105,31 @@ def test_training_updates_match_oracle_adam_cosine(ctx, steps):
     got, hist = ctx.surrogate_train(labs, tg.astype(np.float32), theta.astype(np.float32), epochs=steps, batch=4,
                                     lr=lr, seed=1)
     ref, losses = N.train_full_batch(theta, list(labs), tg, steps, lr)
-    _, g0, _ = N.batch_loss_and_grad(theta, list(labs), tg)
+    # the oracle's gradient at each update, along its own trajectory
+    th, m, v, grads = theta.copy(), np.zeros_like(theta), np.zeros_like(theta), []
+    for t in range(steps):
+        _, g, _ = N.batch_loss_and_grad(th, list(labs), tg)
+        grads.append(g)
+        th, m, v = N.adam_step(th, g, m, v, t + 1, N.cosine_step_size(lr, t, steps))
+    assert np.array_equal(th, ref)
+    keep = np.ones(theta.size, dtype=bool)
+    for g in grads:
+        o = 0
+        for name, shape in N.layer_shapes():
+            n = int(np.prod(shape))
+            gl = g[o:o + n]
+            keep[o:o + n] &= np.abs(gl) >= 0.2 * np.sqrt(np.mean(gl * gl))
+            o += n
+        keep &= np.sign(g) == np.sign(grads[0])
     dg = got.astype(np.float64) - theta
     dr = ref - theta
-    keep = np.zeros(theta.size, dtype=bool)
-    o = 0
-    for name, shape in N.layer_shapes():
-        n = int(np.prod(shape))
-        g = g0[o:o + n]
-        keep[o:o + n] = np.abs(g) >= 0.2 * np.sqrt(np.mean(g * g))
-        o += n
     err = np.abs(dg - dr)
     bad = keep & (err > 0.1 * np.abs(dr) + 1e-9)
     print(f"{steps} updates: {keep.sum()} of {theta.size} parameters compared, {bad.sum()} outside 10 %; "
           f"max |d_gpu - d_oracle| / lr {err[keep].max() / lr:.3f}; losses {hist} vs {losses}")
-    assert keep.mean() > 0.25
+    assert keep.mean() > 1.0 / 6.0
     assert bad.sum() <= max(3, 1e-3 * keep.sum())
-    assert np.allclose(hist, losses, rtol=2e-2, atol=0)
+    assert np.allclose(hist, losses, rtol=2e-3, atol=0)
 
 
 def test_gate_matches_oracle(ctx):
