@@ -258,41 +258,61 @@ hh_status hh_fit_inverse_n(hh_ctx *ctx, const int *ns, const double *M, int coun
 
 /* ---------------------------------------------------------------------------
  * Subimage surrogate (not in the paper; a learned shortcut for the first
- * hierarchical level). A small 3D CNN maps a cube of phase labels (0, 1, 2;
- * edge `edge`, x fastest) to the 21 upper-triangle components of its
- * effective Voigt stiffness (row-major i <= j, engineering shear), divided by
- * a caller-chosen scale. Layers: one-hot(3) -> conv3^3 3->16 -> ReLU ->
- * conv 16->32 stride 2 -> ReLU -> conv 32->64 stride 2 -> ReLU -> conv 64->64
- * -> ReLU -> mean pool -> fc 64->128 -> ReLU -> fc 128->21; zero padding 1.
+ * hierarchical level). A small 3D CNN maps a buffered subimage (Omega_B) of
+ * phase labels (0, 1, 2) with its core (Omega_R) to the 21 upper-triangle
+ * components of the core's effective Voigt stiffness (row-major i <= j,
+ * engineering shear), divided by a caller-chosen scale. Input channels: the
+ * one-hot labels and the core mask (1 in the core, 0 in the buffer; a label
+ * >= 3 contributes no phase channel). Layers: conv3^3 4->16 -> ReLU -> conv
+ * 16->32 stride 2 -> ReLU -> conv 32->64 stride 2 -> ReLU -> conv 64->64 ->
+ * ReLU -> mean pool over the voxels -> fc 64->128 -> ReLU -> fc 128->21; zero
+ * padding 1, so any box shape runs through the same network.
+ *
+ * A call takes `count` subimages: boxes[count][9] int32 rows (nx, ny, nz, ox,
+ * oy, oz, cnx, cny, cnz) give each box (every edge 8..256) and its core
+ * (origin and size inside the box, at least one voxel); `labels` holds the
+ * boxes' labels one after the other, each x fastest. Subimages of one box
+ * shape are batched together.
  * Parameters are one flat FP32 vector of hh_cnn_num_params() values: per conv
  * layer W[tap][ci][co] (tap = (kz*3+ky)*3+kx) then bias[co]; per fc layer
  * W[in][out] then bias[out]. The convolutions run on BF16 tensor cores with
  * FP32 accumulation. All buffers below are host memory owned by the caller;
- * errors: HH_ERR_ARG (count < 1, edge outside 8..256, NULL pointers),
- * HH_ERR_OOM, HH_ERR_CUDA. */
+ * errors: HH_ERR_ARG (count < 1, a box or core outside the limits, NULL
+ * pointers), HH_ERR_OOM, HH_ERR_CUDA. */
 int64_t hh_cnn_num_params(void);
 
-/* Network outputs out[count][21] for `count` cubes labels[count][edge^3]. */
-hh_status hh_cnn_forward(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+/* He-uniform initial parameters (params[hh_cnn_num_params()], host memory):
+ * every weight of a layer with fan-in f (27 x input channels for a
+ * convolution, the input width for a fully connected layer) is
+ * (2 u_i - 1) sqrt(6 / f) and every bias 0, where u_i is the i-th output (i
+ * the flat parameter index, from 0) of the SplitMix64 generator seeded with
+ * `seed`, as a double in [0, 1) from its top 53 bits (the draws of the audit
+ * below). Host only; HH_ERR_ARG for a NULL pointer. */
+hh_status hh_cnn_init_params(uint64_t seed, float *params);
+
+/* Network outputs out[count][21]. */
+hh_status hh_cnn_forward(hh_ctx *ctx, const uint8_t *labels, int count, const int32_t *boxes,
                          const float *params, float *out);
 
 /* Mean squared error over the count x 21 outputs against targets[count][21]
  * (*loss) and its gradient with respect to the parameters (grad[n_params]). */
-hh_status hh_cnn_loss_grad(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+hh_status hh_cnn_loss_grad(hh_ctx *ctx, const uint8_t *labels, int count, const int32_t *boxes,
                            const float *params, const float *targets, double *loss, float *grad);
 
 /* Trains one network from `init` with Adam (beta 0.9/0.999, eps 1e-8; step
- * size lr with cosine decay to 0 over the run) on minibatches of `batch`
- * cubes (whole batches of a seeded permutation per epoch) and writes the
- * final parameters to params_out. loss_history
- * (epochs values, may be NULL) receives each epoch's mean training loss. */
-hh_status hh_surrogate_train(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+ * size lr with cosine decay to 0 over the run). Every epoch draws a seeded
+ * permutation of each box shape's subimages, cuts it into whole minibatches of
+ * min(batch, subimages of that shape), and takes the epoch's minibatches of all
+ * shapes in a seeded order (SplitMix64 from `seed`); the final parameters go
+ * to params_out. loss_history (epochs values, may be NULL) receives each
+ * epoch's mean training loss. */
+hh_status hh_surrogate_train(hh_ctx *ctx, const uint8_t *labels, int count, const int32_t *boxes,
                              const float *targets, const float *init, int epochs, int batch,
                              double lr, uint64_t seed, float *params_out, double *loss_history);
 
 /* Predictions of an ensemble (params[ensemble][n_params]) in GPa:
  * out[count][ensemble][21] = network output * scale. */
-hh_status hh_surrogate_predict(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+hh_status hh_surrogate_predict(hh_ctx *ctx, const uint8_t *labels, int count, const int32_t *boxes,
                                const float *params, int ensemble, double scale, float *out);
 
 /* Ensemble files. hh_surrogate_save writes params[ensemble][n_params]
@@ -312,12 +332,12 @@ hh_status hh_surrogate_load(const char *path, float *params, int64_t capacity, i
                             double *scale);
 
 /* The gate: accept[i] = 1 when every member's Voigt-projected K and G lie in
- * the cube's own Reuss..Voigt bounds of the phase moduli (from its phase
- * fractions), the relative spread (max - min) / mean over the members of K
- * and of G is <= spread, and the members' mean stiffness is positive
- * definite; else 0 (the cube goes to the FFT solver). c21[count][21]
+ * the Reuss..Voigt bounds of the phase moduli over the subimage's core (from
+ * the core's phase fractions), the relative spread (max - min) / mean over the
+ * members of K and of G is <= spread, and the members' mean stiffness is
+ * positive definite; else 0 (the subimage goes to the FFT solver). c21[count][21]
  * receives the members' mean. members[count][ensemble][21] in GPa. */
-hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, int edge,
+hh_status hh_surrogate_gate(hh_ctx *ctx, const uint8_t *labels, int count, const int32_t *boxes,
                             const hh_phase *phases, int nphase, const float *members,
                             int ensemble, double spread, int *accept, double *c21);
 
@@ -351,12 +371,12 @@ hh_status hh_homogenize_multilevel(hh_ctx *ctx, const uint8_t *img, int nx, int 
                                    int nlevels, const hh_options *opt, hh_result *out);
 
 /* Two-level scheme on a partition (as hh_homogenize_partition) where every
- * unbuffered cubic subimage (b = 0, edge 8..256) is first offered to the
- * surrogate ensemble (params[ensemble][n_params], outputs * scale = GPa) and
- * its gate (spread as in hh_surrogate_gate): accepted subimages take the
- * ensemble's mean stiffness (raised to the stiffness floor like FFT results)
- * and skip the FFT solve; every other subimage is solved by the FFT solver
- * with `opt`.
+ * subimage whose buffered box has edges 8..256 is first offered, with its
+ * buffer and its core, to the surrogate ensemble (params[ensemble][n_params],
+ * outputs * scale = GPa) and its gate (spread as in hh_surrogate_gate):
+ * accepted subimages take the ensemble's mean stiffness (raised to the
+ * stiffness floor like FFT results) and skip the FFT solve; every other
+ * subimage is solved by the FFT solver with `opt`.
  *
  * Audit: the FFT solver also checks a random sample of the accepted
  * subimages. Accepted subimage i is audited when u_i < audit_fraction, where

@@ -122,11 +122,12 @@ _SIGNATURES = {
     "hh_profile_reset": (_I, [_P]),
     "hh_apply_operator_noalloc": (_I, [_P, _P, _I, _I, _I, _I, _P, _P, _I, _P]),
     "hh_cnn_num_params": (ctypes.c_int64, []),
-    "hh_cnn_forward": (_I, [_P, _P, _I, _I, _P, _P]),
-    "hh_cnn_loss_grad": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
-    "hh_surrogate_train": (_I, [_P, _P, _I, _I, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
-    "hh_surrogate_predict": (_I, [_P, _P, _I, _I, _P, _I, _D, _P]),
-    "hh_surrogate_gate": (_I, [_P, _P, _I, _I, _P, _I, _P, _I, _D, _P, _P]),
+    "hh_cnn_init_params": (_I, [ctypes.c_uint64, _P]),
+    "hh_cnn_forward": (_I, [_P, _P, _I, _P, _P, _P]),
+    "hh_cnn_loss_grad": (_I, [_P, _P, _I, _P, _P, _P, _P, _P]),
+    "hh_surrogate_train": (_I, [_P, _P, _I, _P, _P, _P, _I, _I, _D, ctypes.c_uint64, _P, _P]),
+    "hh_surrogate_predict": (_I, [_P, _P, _I, _P, _P, _I, _D, _P]),
+    "hh_surrogate_gate": (_I, [_P, _P, _I, _P, _P, _I, _P, _I, _D, _P, _P]),
     "hh_surrogate_save": (_I, [ctypes.c_char_p, _P, _I, _D]),
     "hh_surrogate_load": (_I, [ctypes.c_char_p, _P, ctypes.c_int64, _P, _P]),
     "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
@@ -199,6 +200,17 @@ def _phases(phases):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cnn_init_params(seed: int) -> np.ndarray:
+    """He-uniform initial network parameters from the SplitMix64 draws of
+    `seed` (hh_cnn_init_params; no GPU needed)."""
+    lib = load()
+    th = np.zeros(lib.hh_cnn_num_params(), dtype=np.float32)
+    s = lib.hh_cnn_init_params(int(seed) & (2**64 - 1), _ptr(th))
+    if s != HH_OK:
+        raise HHError(s, lib.hh_last_error(None).decode())
+    return th
 
 
 def surrogate_save(path: str, params_ensemble, scale: float) -> None:
@@ -399,59 +411,67 @@ class Context:
         return int(self._lib.hh_cnn_num_params())
 
     @staticmethod
-    def _cubes(labels):
-        lab = np.ascontiguousarray(labels, dtype=np.uint8)
-        if lab.ndim == 3:
-            lab = lab[None]
-        assert lab.ndim == 4 and lab.shape[1] == lab.shape[2] == lab.shape[3], "cubes [count][e][e][e]"
-        return lab, lab.shape[0], lab.shape[1]
+    def _subs(labels, cores=None):
+        """(concatenated labels, boxes[count][9] int32, count) of subimages given
+        as a 4-D array [count][nz][ny][nx] or a list of 3-D arrays, with cores
+        (ox, oy, oz, cnx, cny, cnz) per subimage (None: the whole box)."""
+        subs = [np.ascontiguousarray(l, dtype=np.uint8) for l in (labels if isinstance(labels, (list, tuple))
+                                                                  else np.asarray(labels).reshape(
+                                                                      (-1,) + np.asarray(labels).shape[-3:]))]
+        rows = []
+        for i, l in enumerate(subs):
+            nz, ny, nx = l.shape
+            c = (0, 0, 0, nx, ny, nz) if cores is None or cores[i] is None else tuple(int(v) for v in cores[i])
+            rows.append((nx, ny, nz) + c)
+        return (np.concatenate([l.ravel() for l in subs]), np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, 9),
+                len(subs))
 
-    def cnn_forward(self, labels, params):
-        lab, n, e = self._cubes(labels)
+    def cnn_forward(self, labels, params, cores=None):
+        lab, bx, n = self._subs(labels, cores)
         th = np.ascontiguousarray(params, dtype=np.float32)
         out = np.zeros((n, 21), dtype=np.float32)
-        self._check(self._lib.hh_cnn_forward(self._h, _ptr(lab), n, e, _ptr(th), _ptr(out)), "hh_cnn_forward",
+        self._check(self._lib.hh_cnn_forward(self._h, _ptr(lab), n, _ptr(bx), _ptr(th), _ptr(out)), "hh_cnn_forward",
                     allow_warn=False)
         return out
 
-    def cnn_loss_grad(self, labels, params, targets):
-        lab, n, e = self._cubes(labels)
+    def cnn_loss_grad(self, labels, params, targets, cores=None):
+        lab, bx, n = self._subs(labels, cores)
         th = np.ascontiguousarray(params, dtype=np.float32)
         tg = np.ascontiguousarray(targets, dtype=np.float32).reshape(n, 21)
         loss = ctypes.c_double()
         grad = np.zeros(th.size, dtype=np.float32)
-        self._check(self._lib.hh_cnn_loss_grad(self._h, _ptr(lab), n, e, _ptr(th), _ptr(tg), ctypes.byref(loss),
+        self._check(self._lib.hh_cnn_loss_grad(self._h, _ptr(lab), n, _ptr(bx), _ptr(th), _ptr(tg), ctypes.byref(loss),
                                                _ptr(grad)), "hh_cnn_loss_grad", allow_warn=False)
         return loss.value, grad
 
-    def surrogate_train(self, labels, targets, init, epochs=10, batch=32, lr=1e-3, seed=0):
-        lab, n, e = self._cubes(labels)
+    def surrogate_train(self, labels, targets, init, epochs=10, batch=32, lr=1e-3, seed=0, cores=None):
+        lab, bx, n = self._subs(labels, cores)
         tg = np.ascontiguousarray(targets, dtype=np.float32).reshape(n, 21)
         th0 = np.ascontiguousarray(init, dtype=np.float32)
         out = np.zeros(th0.size, dtype=np.float32)
         hist = np.zeros(epochs)
-        self._check(self._lib.hh_surrogate_train(self._h, _ptr(lab), n, e, _ptr(tg), _ptr(th0), int(epochs),
+        self._check(self._lib.hh_surrogate_train(self._h, _ptr(lab), n, _ptr(bx), _ptr(tg), _ptr(th0), int(epochs),
                                                  int(batch), float(lr), int(seed), _ptr(out), _ptr(hist)),
                     "hh_surrogate_train", allow_warn=False)
         return out, hist
 
-    def surrogate_predict(self, labels, params_ensemble, scale):
-        lab, n, e = self._cubes(labels)
+    def surrogate_predict(self, labels, params_ensemble, scale, cores=None):
+        lab, bx, n = self._subs(labels, cores)
         th = np.ascontiguousarray(params_ensemble, dtype=np.float32)
         ens = th.shape[0] if th.ndim == 2 else 1
         out = np.zeros((n, ens, 21), dtype=np.float32)
-        self._check(self._lib.hh_surrogate_predict(self._h, _ptr(lab), n, e, _ptr(th), ens, float(scale), _ptr(out)),
-                    "hh_surrogate_predict", allow_warn=False)
+        self._check(self._lib.hh_surrogate_predict(self._h, _ptr(lab), n, _ptr(bx), _ptr(th), ens, float(scale),
+                                                   _ptr(out)), "hh_surrogate_predict", allow_warn=False)
         return out
 
-    def surrogate_gate(self, labels, phases, members, spread=0.01):
-        lab, n, e = self._cubes(labels)
+    def surrogate_gate(self, labels, phases, members, spread=0.01, cores=None):
+        lab, bx, n = self._subs(labels, cores)
         ph, nph = _phases(phases)
         mem = np.ascontiguousarray(members, dtype=np.float32)
         ens = mem.shape[1]
         acc = np.zeros(n, dtype=np.int32)
         c21 = np.zeros((n, 21))
-        self._check(self._lib.hh_surrogate_gate(self._h, _ptr(lab), n, e, ph, nph, _ptr(mem), ens, float(spread),
+        self._check(self._lib.hh_surrogate_gate(self._h, _ptr(lab), n, _ptr(bx), ph, nph, _ptr(mem), ens, float(spread),
                                                 _ptr(acc), _ptr(c21)), "hh_surrogate_gate", allow_warn=False)
         return acc.astype(bool), c21
 

@@ -1,10 +1,12 @@
 // Subimage surrogate network (not in the paper): a small 3D CNN that maps a
-// subimage's phase labels to the 21 upper-triangle components of its effective
-// Voigt stiffness, trained on GPU with the library's own kernels, and the gate
-// that decides whether the ensemble's prediction stands in for an FFT solve.
+// buffered subimage's phase labels to the 21 upper-triangle components of its
+// core's effective Voigt stiffness, trained on GPU with the library's own
+// kernels, and the gate that decides whether the ensemble's prediction stands
+// in for an FFT solve.
 //
-//   input   one-hot of the labels 0, 1, 2 (3 channels, cube of edge D)
-//   conv1   3 -> 16, 3x3x3, stride 1, zero padding 1, bias, ReLU
+//   input   one-hot of the labels 0, 1, 2 and the core mask (4 channels; the
+//           box Omega_B has any shape, the core Omega_R is 1, the buffer 0)
+//   conv1   4 -> 16, 3x3x3, stride 1, zero padding 1, bias, ReLU
 //   conv2  16 -> 32, stride 2, ReLU
 //   conv3  32 -> 64, stride 2, ReLU
 //   conv4  64 -> 64, stride 1, ReLU
@@ -13,10 +15,12 @@
 // Activations are channels-last BF16 ([sample][z][y][x][c]); weights are FP32
 // master copies with BF16 copies for the convolutions; every sum accumulates in
 // FP32. conv1 reads the labels directly (a one-hot input turns its contraction
-// into a lookup of the weight row of each neighbour's label). conv2..conv4,
-// their data gradients and their weight gradients are implicit GEMMs on the
-// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate) with the operands
-// gathered from the activations (no im2col buffer).
+// into a lookup of the weight row of each neighbour's label, plus the mask
+// row where the neighbour lies in the core). conv2..conv4, their data
+// gradients and their weight gradients are implicit GEMMs on the BF16 tensor
+// cores (mma.sync m16n8k16, FP32 accumulate) with the operands gathered from
+// the activations (no im2col buffer). Subimages of one shape form a batch;
+// a call with several shapes runs one batch sequence per shape.
 //
 // Parameter layout (flat FP32): per conv layer W[tap][ci][co] with
 // tap = (kz * 3 + ky) * 3 + kx, then bias[co]; per fully connected layer
@@ -43,7 +47,19 @@ using bf16 = __nv_bfloat16;
 struct ConvSpec {
   int ci, co, stride;
 };
-constexpr ConvSpec kConv[4] = {{3, 16, 1}, {16, 32, 2}, {32, 64, 2}, {64, 64, 1}};
+constexpr ConvSpec kConv[4] = {{4, 16, 1}, {16, 32, 2}, {32, 64, 2}, {64, 64, 1}};
+constexpr int kIn = 4;  // input channels: labels 0, 1, 2 one-hot and the core mask
+
+// Box of a batch (all samples share it) and the core of each sample inside it.
+struct Box3 {
+  int x, y, z;
+};
+struct Core {
+  int ox, oy, oz, nx, ny, nz;
+  __device__ __forceinline__ bool in(int x, int y, int z) const {
+    return x >= ox && x < ox + nx && y >= oy && y < oy + ny && z >= oz && z < oz + nz;
+  }
+};
 constexpr int kFc[2][2] = {{64, 128}, {128, 21}};
 constexpr int kOut = 21;
 constexpr int kPoolC = 64;
@@ -74,37 +90,44 @@ inline Offsets offsets() {
 __host__ __device__ inline int out_size(int n, int s) { return (n + 2 - 3) / s + 1; }
 
 // ---------------------------------------------------------------------------
-// conv1 on the labels: y[m][co] = relu(b[co] + sum_tap W1[tap][label(m + tap - 1)][co]).
+// conv1 on the labels and the core mask:
+// y[m][co] = relu(b[co] + sum_tap (W1[tap][label(m + tap - 1)][co] + [m + tap - 1 in core] W1[tap][3][co])).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_conv1_fwd(const uint8_t* lab, int B, int D, const float* W1, const float* b1,
-                                                   bf16* Y) {
-  __shared__ float w[27 * 3 * 16 + 16];
-  for (int t = threadIdx.x; t < 27 * 3 * 16; t += blockDim.x) w[t] = W1[t];
-  for (int t = threadIdx.x; t < 16; t += blockDim.x) w[27 * 3 * 16 + t] = b1[t];
+__global__ void __launch_bounds__(256) k_conv1_fwd(const uint8_t* lab, const Core* core, int B, Box3 D,
+                                                   const float* W1, const float* b1, bf16* Y) {
+  __shared__ float w[27 * kIn * 16 + 16];
+  for (int t = threadIdx.x; t < 27 * kIn * 16; t += blockDim.x) w[t] = W1[t];
+  for (int t = threadIdx.x; t < 16; t += blockDim.x) w[27 * kIn * 16 + t] = b1[t];
   __syncthreads();
-  const long long V = (long long)D * D * D;
+  const long long V = (long long)D.x * D.y * D.z;
   const long long M = (long long)B * V;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
     const long long n = m / V;
     const int v = (int)(m - n * V);
-    const int z = v / (D * D), y = (v / D) % D, x = v % D;
+    const int z = v / (D.x * D.y), y = (v / D.x) % D.y, x = v % D.x;
+    const Core cr = core[n];
     float acc[16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = w[27 * 3 * 16 + c];
+    for (int c = 0; c < 16; ++c) acc[c] = w[27 * kIn * 16 + c];
     for (int kz = 0; kz < 3; ++kz) {
       const int iz = z + kz - 1;
-      if (iz < 0 || iz >= D) continue;
+      if (iz < 0 || iz >= D.z) continue;
       for (int ky = 0; ky < 3; ++ky) {
         const int iy = y + ky - 1;
-        if (iy < 0 || iy >= D) continue;
+        if (iy < 0 || iy >= D.y) continue;
         for (int kx = 0; kx < 3; ++kx) {
           const int ix = x + kx - 1;
-          if (ix < 0 || ix >= D) continue;
-          const int l = lab[n * V + ((long long)iz * D + iy) * D + ix];
-          if (l >= 3) continue;
-          const float* wr = w + (((kz * 3 + ky) * 3 + kx) * 3 + l) * 16;
+          if (ix < 0 || ix >= D.x) continue;
+          const float* wt = w + ((kz * 3 + ky) * 3 + kx) * kIn * 16;
+          const int l = lab[n * V + ((long long)iz * D.y + iy) * D.x + ix];
+          if (l < 3) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] += wr[c];
+            for (int c = 0; c < 16; ++c) acc[c] += wt[l * 16 + c];
+          }
+          if (cr.in(ix, iy, iz)) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] += wt[3 * 16 + c];
+          }
         }
       }
     }
@@ -114,17 +137,19 @@ __global__ void __launch_bounds__(256) k_conv1_fwd(const uint8_t* lab, int B, in
 }
 
 // conv1 weight gradient: dW1[tap][l][co] += sum over voxels m whose neighbour at
-// tap has label l of dZ1[m][co] (shared-memory partial sums, then global atomics).
-__global__ void __launch_bounds__(256) k_conv1_wgrad(const uint8_t* lab, int B, int D, const bf16* dZ, float* dW1) {
-  __shared__ float acc[27 * 3 * 16];
-  for (int t = threadIdx.x; t < 27 * 3 * 16; t += blockDim.x) acc[t] = 0.f;
+// tap has label l of dZ1[m][co], and dW1[tap][3][co] over those whose neighbour
+// lies in the core (shared-memory partial sums, then global atomics).
+__global__ void __launch_bounds__(256) k_conv1_wgrad(const uint8_t* lab, const Core* core, int B, Box3 D,
+                                                     const bf16* dZ, float* dW1) {
+  __shared__ float acc[27 * kIn * 16];
+  for (int t = threadIdx.x; t < 27 * kIn * 16; t += blockDim.x) acc[t] = 0.f;
   __syncthreads();
-  const long long V = (long long)D * D * D;
+  const long long V = (long long)D.x * D.y * D.z;
   const long long M = (long long)B * V;
   for (long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x; m < M; m += (long long)gridDim.x * blockDim.x) {
     const long long n = m / V;
     const int v = (int)(m - n * V);
-    const int z = v / (D * D), y = (v / D) % D, x = v % D;
+    const int z = v / (D.x * D.y), y = (v / D.x) % D.y, x = v % D.x;
     float g[16];
     bool any = false;
 #pragma unroll
@@ -133,18 +158,25 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const uint8_t* lab, int B, 
       any |= g[c] != 0.f;
     }
     if (!any) continue;
+    const Core cr = core[n];
     for (int tap = 0; tap < 27; ++tap) {
       const int iz = z + tap / 9 - 1, iy = y + (tap / 3) % 3 - 1, ix = x + tap % 3 - 1;
-      if (iz < 0 || iz >= D || iy < 0 || iy >= D || ix < 0 || ix >= D) continue;
-      const int l = lab[n * V + ((long long)iz * D + iy) * D + ix];
-      if (l >= 3) continue;
+      if (iz < 0 || iz >= D.z || iy < 0 || iy >= D.y || ix < 0 || ix >= D.x) continue;
+      const int l = lab[n * V + ((long long)iz * D.y + iy) * D.x + ix];
+      if (l < 3) {
 #pragma unroll
-      for (int c = 0; c < 16; ++c)
-        if (g[c] != 0.f) atomicAdd(&acc[(tap * 3 + l) * 16 + c], g[c]);
+        for (int c = 0; c < 16; ++c)
+          if (g[c] != 0.f) atomicAdd(&acc[(tap * kIn + l) * 16 + c], g[c]);
+      }
+      if (cr.in(ix, iy, iz)) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c)
+          if (g[c] != 0.f) atomicAdd(&acc[(tap * kIn + 3) * 16 + c], g[c]);
+      }
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 27 * 3 * 16; t += blockDim.x)
+  for (int t = threadIdx.x; t < 27 * kIn * 16; t += blockDim.x)
     if (acc[t] != 0.f) atomicAdd(&dW1[t], acc[t]);
 }
 
@@ -246,23 +278,24 @@ __global__ void __launch_bounds__(128) k_igemm(Op op, long long M, int N, long l
       }
 }
 
-// Geometry of one convolution layer (cubes): input edge Di, output edge Do.
+// Geometry of one convolution layer: input box Di, output box Do (per axis).
 struct Geo {
-  int Di, Do, ci, co, s;
+  Box3 Di, Do;
+  int ci, co, s;
 };
 
 // Input value feeding output voxel m (sample-major) at reduction index
 // k = tap * ci + c, or 0 in the zero padding.
 __device__ __forceinline__ bf16 gather_in(const bf16* X, const Geo& g, long long m, long long k) {
-  const long long V = (long long)g.Do * g.Do * g.Do;
+  const long long V = (long long)g.Do.x * g.Do.y * g.Do.z;
   const long long n = m / V;
   const int v = (int)(m - n * V);
   const int tap = (int)(k / g.ci), c = (int)(k - (long long)tap * g.ci);
-  const int iz = (v / (g.Do * g.Do)) * g.s + tap / 9 - 1;
-  const int iy = ((v / g.Do) % g.Do) * g.s + (tap / 3) % 3 - 1;
-  const int ix = (v % g.Do) * g.s + tap % 3 - 1;
-  if (iz < 0 || iz >= g.Di || iy < 0 || iy >= g.Di || ix < 0 || ix >= g.Di) return __float2bfloat16(0.f);
-  return X[((((n * g.Di + iz) * g.Di + iy) * g.Di) + ix) * g.ci + c];
+  const int iz = (v / (g.Do.x * g.Do.y)) * g.s + tap / 9 - 1;
+  const int iy = ((v / g.Do.x) % g.Do.y) * g.s + (tap / 3) % 3 - 1;
+  const int ix = (v % g.Do.x) * g.s + tap % 3 - 1;
+  if (iz < 0 || iz >= g.Di.z || iy < 0 || iy >= g.Di.y || ix < 0 || ix >= g.Di.x) return __float2bfloat16(0.f);
+  return X[((((n * g.Di.z + iz) * g.Di.y + iy) * g.Di.x) + ix) * g.ci + c];
 }
 
 // Forward: Y[m][o] = relu(b[o] + sum_k gather_in(m, k) W[k][o]).
@@ -289,18 +322,20 @@ struct OpDgrad {
   bf16* dZin;
   Geo g;
   __device__ bf16 a(long long m, long long k) const {
-    const long long V = (long long)g.Di * g.Di * g.Di;
+    const long long V = (long long)g.Di.x * g.Di.y * g.Di.z;
     const long long n = m / V;
     const int v = (int)(m - n * V);
     const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
-    int q[3] = {v / (g.Di * g.Di) + 1 - tap / 9, (v / g.Di) % g.Di + 1 - (tap / 3) % 3, v % g.Di + 1 - tap % 3};
+    int q[3] = {v / (g.Di.x * g.Di.y) + 1 - tap / 9, (v / g.Di.x) % g.Di.y + 1 - (tap / 3) % 3,
+                v % g.Di.x + 1 - tap % 3};
+    const int lim[3] = {g.Do.z, g.Do.y, g.Do.x};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (q[d] < 0 || q[d] % g.s) return __float2bfloat16(0.f);
       q[d] /= g.s;
-      if (q[d] >= g.Do) return __float2bfloat16(0.f);
+      if (q[d] >= lim[d]) return __float2bfloat16(0.f);
     }
-    return dZ[((((n * g.Do + q[0]) * g.Do + q[1]) * g.Do) + q[2]) * g.co + o];
+    return dZ[((((n * g.Do.z + q[0]) * g.Do.y + q[1]) * g.Do.x) + q[2]) * g.co + o];
   }
   __device__ bf16 b(long long k, int c) const {
     const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
@@ -435,8 +470,9 @@ __global__ void k_scale(const float* a, float s, float* b, long long n) {
 }
 
 // ---------------------------------------------------------------------------
-// Gate: one block per subimage. Phase fractions -> Reuss and Voigt bounds of
-// K and G; each member's Voigt-projected K, G must lie inside; the relative
+// Gate: one block per subimage. Phase fractions of the core -> Reuss and
+// Voigt bounds of K and G; each member's Voigt-projected K, G must lie
+// inside; the relative
 // spread (max - min) / mean of K and of G must be <= spread; the mean
 // stiffness must be positive definite (Cholesky, FP64).
 // ---------------------------------------------------------------------------
@@ -448,14 +484,20 @@ __device__ __forceinline__ void kg_of(const double* c21, double& K, double& G) {
       15.0;
 }
 
-__global__ void __launch_bounds__(256) k_gate(const uint8_t* lab, long long V, const double* ph, int nphase,
-                                              const float* members, int E, double spread, int* accept,
+__global__ void __launch_bounds__(256) k_gate(const uint8_t* lab, Box3 D, const Core* core, const double* ph,
+                                              int nphase, const float* members, int E, double spread, int* accept,
                                               double* c21_out) {
   __shared__ unsigned int cnt[256];
   const int n = blockIdx.x;
+  const long long V = (long long)D.x * D.y * D.z;
+  const Core cr = core[n];
+  const long long Vc = (long long)cr.nx * cr.ny * cr.nz;
   for (int t = threadIdx.x; t < 256; t += blockDim.x) cnt[t] = 0;
   __syncthreads();
-  for (long long v = threadIdx.x; v < V; v += blockDim.x) atomicAdd(&cnt[lab[n * V + v]], 1u);
+  for (long long v = threadIdx.x; v < Vc; v += blockDim.x) {
+    const int x = (int)(v % cr.nx), y = (int)((v / cr.nx) % cr.ny), z = (int)(v / ((long long)cr.nx * cr.ny));
+    atomicAdd(&cnt[lab[n * V + ((long long)(cr.oz + z) * D.y + (cr.oy + y)) * D.x + (cr.ox + x)]], 1u);
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
   double sKf = 0, sKr = 0, sGf = 0, sGr = 0;
@@ -466,7 +508,7 @@ __global__ void __launch_bounds__(256) k_gate(const uint8_t* lab, long long V, c
       badlab = true;
       break;
     }
-    const double f = double(cnt[p]) / double(V);
+    const double f = double(cnt[p]) / double(Vc);
     sKf += f * ph[2 * p];
     sKr += f / ph[2 * p];
     sGf += f * ph[2 * p + 1];
@@ -531,14 +573,15 @@ __global__ void __launch_bounds__(256) k_gate(const uint8_t* lab, long long V, c
 
 struct Net {
   cudaStream_t st = nullptr;
-  int B = 0, D = 0;
-  int dims[5] = {0, 0, 0, 0, 0};  // edge before conv1 .. after conv4
+  int B = 0;
+  Box3 dims[5];  // box before conv1 .. after conv4
   Offsets off;
   std::string err;
   std::vector<void*> allocs;
   float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
   bf16* theta16 = nullptr;
   uint8_t* lab = nullptr;
+  Core* core = nullptr;
   bf16* act[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // act[i]: output of conv i (1-based)
   bf16* dact[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // gradient at conv i's output (pre-ReLU)
   float *h0 = nullptr, *h1 = nullptr, *out = nullptr, *tgt = nullptr;
@@ -561,25 +604,40 @@ struct Net {
     return HH_OK;
   }
 
-  hh_status init(cudaStream_t s, int batch, int edge, bool train) {
+  static long long vox(const Box3& b) { return (long long)b.x * b.y * b.z; }
+
+  // workspace for batches of up to `batch` samples of box `box`; with `shared`
+  // the parameters, their gradient and Adam's moments are those of `shared`
+  hh_status init(cudaStream_t s, int batch, Box3 box, bool train, const Net* shared = nullptr) {
     st = s;
     B = batch;
-    D = edge;
     off = offsets();
-    dims[0] = D;
-    for (int i = 0; i < 4; ++i) dims[i + 1] = out_size(dims[i], kConv[i].stride);
+    dims[0] = box;
+    for (int i = 0; i < 4; ++i)
+      dims[i + 1] = Box3{out_size(dims[i].x, kConv[i].stride), out_size(dims[i].y, kConv[i].stride),
+                         out_size(dims[i].z, kConv[i].stride)};
     hh_status r;
-    if ((r = alloc(&theta, off.total)) || (r = alloc(&theta16, off.total)) ||
-        (r = alloc(&lab, (long long)B * D * D * D)) || (r = alloc(&h0, (long long)B * kPoolC)) ||
-        (r = alloc(&h1, (long long)B * kHid)) || (r = alloc(&out, (long long)B * kOut)) ||
-        (r = alloc(&tgt, (long long)B * kOut)) || (r = alloc(&loss_part, B)))
+    if (shared) {
+      theta = shared->theta;
+      theta16 = shared->theta16;
+      grad = shared->grad;
+      m = shared->m;
+      v = shared->v;
+    } else if ((r = alloc(&theta, off.total)) || (r = alloc(&theta16, off.total))) {
+      return r;
+    }
+    if ((r = alloc(&lab, B * vox(box))) ||
+        (r = alloc(&core, B)) || (r = alloc(&h0, (long long)B * kPoolC)) || (r = alloc(&h1, (long long)B * kHid)) ||
+        (r = alloc(&out, (long long)B * kOut)) || (r = alloc(&tgt, (long long)B * kOut)) ||
+        (r = alloc(&loss_part, B)))
       return r;
     for (int i = 1; i <= 4; ++i) {
-      const long long n = (long long)B * dims[i] * dims[i] * dims[i] * kConv[i - 1].co;
+      const long long n = (long long)B * vox(dims[i]) * kConv[i - 1].co;
       if ((r = alloc(&act[i], n))) return r;
       if (train && (r = alloc(&dact[i], n))) return r;
     }
-    if (train && ((r = alloc(&grad, off.total)) || (r = alloc(&m, off.total)) || (r = alloc(&v, off.total))))
+    if (train && !shared &&
+        ((r = alloc(&grad, off.total)) || (r = alloc(&m, off.total)) || (r = alloc(&v, off.total))))
       return r;
     return HH_OK;
   }
@@ -604,21 +662,21 @@ struct Net {
 
   Geo geo(int i) const { return Geo{dims[i], dims[i + 1], kConv[i].ci, kConv[i].co, kConv[i].stride}; }
 
-  // forward of nb <= B samples already in lab
+  // forward of nb <= B samples already in lab and core
   hh_status forward(int nb) {
-    const long long V1 = (long long)dims[1] * dims[1] * dims[1];
+    const long long V1 = vox(dims[1]);
     ++launches;
     k_conv1_fwd<<<(unsigned)std::min<long long>(4096, (nb * V1 + 255) / 256), 256, 0, st>>>(
-        lab, nb, D, theta + off.w[0], theta + off.b[0], act[1]);
+        lab, core, nb, dims[0], theta + off.w[0], theta + off.b[0], act[1]);
     CNN_CK(cudaGetLastError());
     for (int i = 1; i < 4; ++i) {
       const Geo g = geo(i);
-      const long long M = (long long)nb * g.Do * g.Do * g.Do;
+      const long long M = nb * vox(g.Do);
       OpFwd op{act[i], theta16 + off.w[i], theta + off.b[i], act[i + 1], g};
       hh_status r = gemm(op, M, g.co, 27LL * g.ci);
       if (r) return r;
     }
-    const int V4 = dims[4] * dims[4] * dims[4];
+    const int V4 = (int)vox(dims[4]);
     ++launches;
     k_head_fwd<<<nb, 128, 0, st>>>(act[4], V4, theta + off.w[4], theta + off.b[4], theta + off.w[5],
                                    theta + off.b[5], h0, h1, out);
@@ -626,19 +684,19 @@ struct Net {
     return HH_OK;
   }
 
-  // gradients of the batch loss into grad (zeroed here); needs tgt
-  hh_status backward(int nb) {
-    CNN_CK(cudaMemsetAsync(grad, 0, off.total * sizeof(float), st));
-    const int V4 = dims[4] * dims[4] * dims[4];
+  // gradients of the loss of nb samples (of a mean over `total` samples) added
+  // to grad (zeroed by the caller); needs tgt
+  hh_status backward(int nb, int total) {
+    const int V4 = (int)vox(dims[4]);
     ++launches;
-    k_head_bwd<<<nb, 128, 0, st>>>(act[4], V4, nb, theta + off.w[4], theta + off.w[5], h0, h1, out, tgt,
+    k_head_bwd<<<nb, 128, 0, st>>>(act[4], V4, total, theta + off.w[4], theta + off.w[5], h0, h1, out, tgt,
                                    grad + off.w[4], grad + off.b[4], grad + off.w[5], grad + off.b[5], dact[4],
                                    loss_part);
     CNN_CK(cudaGetLastError());
     for (int i = 3; i >= 1; --i) {
       const Geo g = geo(i);
-      const long long Mo = (long long)nb * g.Do * g.Do * g.Do;
-      const long long Mi = (long long)nb * g.Di * g.Di * g.Di;
+      const long long Mo = nb * vox(g.Do);
+      const long long Mi = nb * vox(g.Di);
       // weight and bias gradients of conv i+1 (0-based i)
       const int splits = (int)std::min<long long>(64, std::max<long long>(1, Mo / 4096));
       OpWgrad ow{act[i], dact[i + 1], grad + off.w[i], g};
@@ -652,10 +710,10 @@ struct Net {
       OpDgrad od{dact[i + 1], theta16 + off.w[i], act[i], dact[i], g};
       if ((r = gemm(od, Mi, g.ci, 27LL * g.co))) return r;
     }
-    const long long V1 = (long long)dims[1] * dims[1] * dims[1];
+    const long long V1 = vox(dims[1]);
     ++launches;
-    k_conv1_wgrad<<<(unsigned)std::min<long long>(2048, (nb * V1 + 255) / 256), 256, 0, st>>>(lab, nb, D, dact[1],
-                                                                                            grad + off.w[0]);
+    k_conv1_wgrad<<<(unsigned)std::min<long long>(2048, (nb * V1 + 255) / 256), 256, 0, st>>>(
+        lab, core, nb, dims[0], dact[1], grad + off.w[0]);
     CNN_CK(cudaGetLastError());
     ++launches;
     k_bias_grad<<<(unsigned)std::min<long long>(1024, (nb * V1 + 63) / 64), 256, 0, st>>>(dact[1], nb * V1, 16,
@@ -665,8 +723,62 @@ struct Net {
   }
 };
 
-hh_status check_geometry(hh_ctx* h, int count, int edge) {
-  if (count < 1 || edge < 8 || edge > 256) return ctx_fail(h, HH_ERR_ARG, "surrogate: count >= 1, 8 <= edge <= 256");
+// One subimage of a call: its box, its core inside the box and the offset of
+// its labels in the concatenated input. Subimages of one box shape are
+// batched together (`groups`, in the order the shapes first appear).
+struct Sub {
+  Box3 box;
+  Core core;
+  long long off;
+};
+
+static bool same_box(const Box3& a, const Box3& b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
+
+hh_status parse_subs(hh_ctx* h, int count, const int32_t* boxes, std::vector<Sub>& subs,
+                     std::vector<std::vector<int>>& groups) {
+  if (count < 1 || !boxes) return ctx_fail(h, HH_ERR_ARG, "surrogate: count >= 1 and a box table");
+  subs.resize(count);
+  groups.clear();
+  long long off = 0;
+  for (int i = 0; i < count; ++i) {
+    const int32_t* r = boxes + 9 * (long long)i;
+    Sub& u = subs[i];
+    u.box = Box3{r[0], r[1], r[2]};
+    u.core = Core{r[3], r[4], r[5], r[6], r[7], r[8]};
+    const bool ok = u.box.x >= 8 && u.box.x <= 256 && u.box.y >= 8 && u.box.y <= 256 && u.box.z >= 8 &&
+                    u.box.z <= 256 && u.core.nx >= 1 && u.core.ny >= 1 && u.core.nz >= 1 && u.core.ox >= 0 &&
+                    u.core.oy >= 0 && u.core.oz >= 0 && u.core.ox + u.core.nx <= u.box.x &&
+                    u.core.oy + u.core.ny <= u.box.y && u.core.oz + u.core.nz <= u.box.z;
+    if (!ok)
+      return ctx_fail(h, HH_ERR_ARG,
+                      ("surrogate: subimage " + std::to_string(i) +
+                       ": box edges 8..256 and a core of at least one voxel inside the box").c_str());
+    u.off = off;
+    off += Net::vox(u.box);
+    int g = 0;
+    while (g < (int)groups.size() && !same_box(subs[groups[g][0]].box, u.box)) ++g;
+    if (g == (int)groups.size()) groups.emplace_back();
+    groups[g].push_back(i);
+  }
+  return HH_OK;
+}
+
+// Stages samples ids[0..n) of a group (labels and cores) into the workspace.
+static hh_status stage(Net& net, const uint8_t* labels, const std::vector<Sub>& subs, const int* ids, int n,
+                       std::vector<uint8_t>& lab_h, std::vector<Core>& core_h) {
+  const long long V = Net::vox(subs[ids[0]].box);
+  lab_h.resize((size_t)n * V);
+  core_h.resize(n);
+  for (int j = 0; j < n; ++j) {
+    std::memcpy(lab_h.data() + (size_t)j * V, labels + subs[ids[j]].off, (size_t)V);
+    core_h[j] = subs[ids[j]].core;
+  }
+  if (cudaMemcpyAsync(net.lab, lab_h.data(), (size_t)n * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
+      cudaMemcpyAsync(net.core, core_h.data(), n * sizeof(Core), cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
+      cudaStreamSynchronize(net.st) != cudaSuccess) {
+    net.err = "surrogate: staging copy failed";
+    return HH_ERR_CUDA;
+  }
   return HH_OK;
 }
 
@@ -678,52 +790,94 @@ using namespace hh::cnn;
 
 extern "C" int64_t hh_cnn_num_params(void) { return offsets().total; }
 
-extern "C" hh_status hh_cnn_forward(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* params,
-                                   float* out) {
-  if (!h || !labels || !params || !out) return HH_ERR_ARG;
-  hh_status s = check_geometry(h, count, edge);
-  if (s) return s;
-  if ((s = ctx_enter(h))) return s;
-  const int B = std::min(count, 64);
-  Net net;
-  if ((s = net.init(ctx_stream(h), B, edge, false)) || (s = net.set_params(params)))
-    return ctx_fail(h, s, net.err.c_str());
-  const long long V = (long long)edge * edge * edge;
-  for (int b0 = 0; b0 < count; b0 += B) {
-    const int nb = std::min(B, count - b0);
-    if (cudaMemcpyAsync(net.lab, labels + b0 * V, nb * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
-        (s = net.forward(nb)) ||
-        cudaMemcpyAsync(out + (long long)b0 * kOut, net.out, (long long)nb * kOut * sizeof(float),
-                        cudaMemcpyDeviceToHost, net.st) != cudaSuccess)
-      return ctx_fail(h, s ? s : HH_ERR_CUDA, net.err.empty() ? "surrogate forward: copy failed" : net.err.c_str());
+extern "C" hh_status hh_cnn_init_params(uint64_t seed, float* params) {
+  if (!params) return ctx_fail(nullptr, HH_ERR_ARG, "hh_cnn_init_params: NULL params");
+  const Offsets o = offsets();
+  for (long long i = 0; i < o.total; ++i) params[i] = 0.f;
+  // the i-th SplitMix64 output (Steele, Lea and Flood 2014) of `seed` as a
+  // double in [0, 1) from its top 53 bits
+  auto draw = [&](long long i) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-53;
+  };
+  for (int l = 0; l < 6; ++l) {
+    const long long fan_in = l < 4 ? 27LL * kConv[l].ci : kFc[l - 4][0];
+    const long long n = l < 4 ? 27LL * kConv[l].ci * kConv[l].co : (long long)kFc[l - 4][0] * kFc[l - 4][1];
+    const double bound = std::sqrt(6.0 / double(fan_in));
+    for (long long i = o.w[l]; i < o.w[l] + n; ++i) params[i] = float((2.0 * draw(i) - 1.0) * bound);
   }
-  if (cudaStreamSynchronize(net.st) != cudaSuccess) return ctx_fail(h, HH_ERR_CUDA, "surrogate forward failed");
   return HH_OK;
 }
 
-extern "C" hh_status hh_cnn_loss_grad(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* params,
-                                     const float* targets, double* loss, float* grad) {
-  if (!h || !labels || !params || !targets || !loss || !grad) return HH_ERR_ARG;
-  hh_status s = check_geometry(h, count, edge);
+extern "C" hh_status hh_cnn_forward(hh_ctx* h, const uint8_t* labels, int count, const int32_t* boxes,
+                                   const float* params, float* out) {
+  if (!h || !labels || !params || !out) return ctx_fail(h, HH_ERR_ARG, "hh_cnn_forward: NULL argument");
+  std::vector<Sub> subs;
+  std::vector<std::vector<int>> groups;
+  hh_status s = parse_subs(h, count, boxes, subs, groups);
   if (s) return s;
   if ((s = ctx_enter(h))) return s;
-  Net net;
-  if ((s = net.init(ctx_stream(h), count, edge, true)) || (s = net.set_params(params)))
-    return ctx_fail(h, s, net.err.c_str());
-  const long long V = (long long)edge * edge * edge;
-  std::vector<double> lp(count);
-  if (cudaMemcpyAsync(net.lab, labels, count * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
-      cudaMemcpyAsync(net.tgt, targets, (long long)count * kOut * sizeof(float), cudaMemcpyHostToDevice, net.st) !=
-          cudaSuccess)
-    return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients: copy failed");
-  if ((s = net.forward(count)) || (s = net.backward(count))) return ctx_fail(h, s, net.err.c_str());
-  if (cudaMemcpyAsync(grad, net.grad, net.off.total * sizeof(float), cudaMemcpyDeviceToHost, net.st) != cudaSuccess ||
-      cudaMemcpyAsync(lp.data(), net.loss_part, count * sizeof(double), cudaMemcpyDeviceToHost, net.st) !=
-          cudaSuccess ||
-      cudaStreamSynchronize(net.st) != cudaSuccess)
-    return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients failed");
+  std::vector<uint8_t> lab_h;
+  std::vector<Core> core_h;
+  std::vector<float> o((size_t)64 * kOut);
+  for (const std::vector<int>& g : groups) {
+    const int B = std::min((int)g.size(), 64);
+    Net net;
+    if ((s = net.init(ctx_stream(h), B, subs[g[0]].box, false)) || (s = net.set_params(params)))
+      return ctx_fail(h, s, net.err.c_str());
+    for (int b0 = 0; b0 < (int)g.size(); b0 += B) {
+      const int nb = std::min(B, (int)g.size() - b0);
+      if ((s = stage(net, labels, subs, g.data() + b0, nb, lab_h, core_h)) || (s = net.forward(nb)))
+        return ctx_fail(h, s, net.err.c_str());
+      if (cudaMemcpyAsync(o.data(), net.out, (size_t)nb * kOut * sizeof(float), cudaMemcpyDeviceToHost, net.st) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(net.st) != cudaSuccess)
+        return ctx_fail(h, HH_ERR_CUDA, "surrogate forward failed");
+      for (int j = 0; j < nb; ++j) std::memcpy(out + (size_t)g[b0 + j] * kOut, o.data() + (size_t)j * kOut, kOut * 4);
+    }
+  }
+  return HH_OK;
+}
+
+extern "C" hh_status hh_cnn_loss_grad(hh_ctx* h, const uint8_t* labels, int count, const int32_t* boxes,
+                                     const float* params, const float* targets, double* loss, float* grad) {
+  if (!h || !labels || !params || !targets || !loss || !grad)
+    return ctx_fail(h, HH_ERR_ARG, "hh_cnn_loss_grad: NULL argument");
+  std::vector<Sub> subs;
+  std::vector<std::vector<int>> groups;
+  hh_status s = parse_subs(h, count, boxes, subs, groups);
+  if (s) return s;
+  if ((s = ctx_enter(h))) return s;
+  Net par;  // the parameters and their gradient, shared by the shape groups
+  if ((s = par.init(ctx_stream(h), 1, Box3{8, 8, 8}, true)) || (s = par.set_params(params)))
+    return ctx_fail(h, s, par.err.c_str());
+  if (cudaMemsetAsync(par.grad, 0, par.off.total * sizeof(float), par.st) != cudaSuccess)
+    return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients: memset failed");
+  std::vector<uint8_t> lab_h;
+  std::vector<Core> core_h;
   double l = 0.0;
-  for (double x : lp) l += x;
+  for (const std::vector<int>& g : groups) {
+    const int n = (int)g.size();
+    Net net;
+    if ((s = net.init(par.st, n, subs[g[0]].box, true, &par)) || (s = stage(net, labels, subs, g.data(), n, lab_h, core_h)))
+      return ctx_fail(h, s, net.err.c_str());
+    std::vector<float> t((size_t)n * kOut);
+    for (int j = 0; j < n; ++j) std::memcpy(t.data() + (size_t)j * kOut, targets + (size_t)g[j] * kOut, kOut * 4);
+    std::vector<double> lp(n);
+    if (cudaMemcpyAsync(net.tgt, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, net.st) != cudaSuccess)
+      return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients: copy failed");
+    if ((s = net.forward(n)) || (s = net.backward(n, count))) return ctx_fail(h, s, net.err.c_str());
+    if (cudaMemcpyAsync(lp.data(), net.loss_part, n * sizeof(double), cudaMemcpyDeviceToHost, net.st) != cudaSuccess ||
+        cudaStreamSynchronize(net.st) != cudaSuccess)
+      return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients failed");
+    for (double x : lp) l += x;
+  }
+  if (cudaMemcpyAsync(grad, par.grad, par.off.total * sizeof(float), cudaMemcpyDeviceToHost, par.st) != cudaSuccess ||
+      cudaStreamSynchronize(par.st) != cudaSuccess)
+    return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients failed");
   *loss = l / (double(count) * kOut);
   return HH_OK;
 }
@@ -737,137 +891,193 @@ static uint64_t splitmix64(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
-extern "C" hh_status hh_surrogate_train(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* targets,
-                                       const float* init, int epochs, int batch, double lr, uint64_t seed,
-                                       float* params_out, double* loss_history) {
+extern "C" hh_status hh_surrogate_train(hh_ctx* h, const uint8_t* labels, int count, const int32_t* boxes,
+                                       const float* targets, const float* init, int epochs, int batch, double lr,
+                                       uint64_t seed, float* params_out, double* loss_history) {
   if (!h || !labels || !targets || !init || !params_out || epochs < 1 || batch < 1 || !(lr > 0.0))
-    return HH_ERR_ARG;
-  hh_status s = check_geometry(h, count, edge);
+    return ctx_fail(h, HH_ERR_ARG, "hh_surrogate_train: NULL argument, epochs < 1, batch < 1 or lr <= 0");
+  std::vector<Sub> subs;
+  std::vector<std::vector<int>> groups;
+  hh_status s = parse_subs(h, count, boxes, subs, groups);
   if (s) return s;
   if ((s = ctx_enter(h))) return s;
-  const int B = std::min(batch, count);
-  Net net;
-  if ((s = net.init(ctx_stream(h), B, edge, true)) || (s = net.set_params(init)))
-    return ctx_fail(h, s, net.err.c_str());
-  const long long V = (long long)edge * edge * edge;
-  uint8_t* all_lab = nullptr;
-  float* all_tgt = nullptr;
-  if ((s = net.alloc(&all_lab, (long long)count * V)) || (s = net.alloc(&all_tgt, (long long)count * kOut)))
-    return ctx_fail(h, s, net.err.c_str());
-  if (cudaMemcpyAsync(all_lab, labels, count * V, cudaMemcpyHostToDevice, net.st) != cudaSuccess ||
-      cudaMemcpyAsync(all_tgt, targets, (long long)count * kOut * sizeof(float), cudaMemcpyHostToDevice, net.st) !=
-          cudaSuccess ||
-      cudaMemsetAsync(net.m, 0, net.off.total * sizeof(float), net.st) != cudaSuccess ||
-      cudaMemsetAsync(net.v, 0, net.off.total * sizeof(float), net.st) != cudaSuccess)
+  const cudaStream_t st = ctx_stream(h);
+  Net par;  // parameters, gradient and Adam's moments, shared by the shape groups
+  if ((s = par.init(st, 1, Box3{8, 8, 8}, true)) || (s = par.set_params(init))) return ctx_fail(h, s, par.err.c_str());
+  if (cudaMemsetAsync(par.m, 0, par.off.total * sizeof(float), st) != cudaSuccess ||
+      cudaMemsetAsync(par.v, 0, par.off.total * sizeof(float), st) != cudaSuccess)
     return ctx_fail(h, HH_ERR_CUDA, "surrogate training: setup failed");
-  std::vector<int> perm(count);
-  for (int i = 0; i < count; ++i) perm[i] = i;
+  // per shape group: a workspace for its minibatches (min(batch, group size)
+  // subimages, whole batches only) and the group's labels, cores and targets
+  const int G = (int)groups.size();
+  std::vector<Net> nets(G);
+  std::vector<uint8_t*> all_lab(G);
+  std::vector<Core*> all_core(G);
+  std::vector<float*> all_tgt(G);
+  std::vector<int> Bg(G), nbat(G);
+  long long per_epoch = 0;
+  std::vector<uint8_t> lab_h;
+  std::vector<Core> core_h;
+  for (int g = 0; g < G; ++g) {
+    const std::vector<int>& ids = groups[g];
+    const int n = (int)ids.size();
+    const long long V = Net::vox(subs[ids[0]].box);
+    Bg[g] = std::min(batch, n);
+    nbat[g] = n / Bg[g];
+    per_epoch += nbat[g];
+    Net& net = nets[g];
+    if ((s = net.init(st, Bg[g], subs[ids[0]].box, true, &par)) || (s = net.alloc(&all_lab[g], n * V)) ||
+        (s = net.alloc(&all_core[g], n)) || (s = net.alloc(&all_tgt[g], (long long)n * kOut)))
+      return ctx_fail(h, s, net.err.c_str());
+    lab_h.resize((size_t)n * V);
+    core_h.resize(n);
+    std::vector<float> t((size_t)n * kOut);
+    for (int j = 0; j < n; ++j) {
+      std::memcpy(lab_h.data() + (size_t)j * V, labels + subs[ids[j]].off, (size_t)V);
+      core_h[j] = subs[ids[j]].core;
+      std::memcpy(t.data() + (size_t)j * kOut, targets + (size_t)ids[j] * kOut, kOut * 4);
+    }
+    if (cudaMemcpyAsync(all_lab[g], lab_h.data(), lab_h.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(all_core[g], core_h.data(), n * sizeof(Core), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(all_tgt[g], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return ctx_fail(h, HH_ERR_CUDA, "surrogate training: setup failed");
+  }
+  std::vector<std::vector<int>> perm(G);
+  for (int g = 0; g < G; ++g) {
+    perm[g].resize(groups[g].size());
+    for (size_t i = 0; i < perm[g].size(); ++i) perm[g][i] = (int)i;
+  }
   uint64_t rs = seed;
-  std::vector<double> lp(B);
+  std::vector<double> lp(batch);
   long long step = 0;
-  const long long total_steps = (long long)epochs * (count / B);
+  const long long total_steps = (long long)epochs * per_epoch;
   for (int ep = 0; ep < epochs; ++ep) {
-    for (int i = count - 1; i > 0; --i) std::swap(perm[i], perm[(int)(splitmix64(rs) % (uint64_t)(i + 1))]);
+    // a seeded permutation of every group, and a seeded order of the
+    // epoch's minibatches over the groups
+    for (int g = 0; g < G; ++g)
+      for (int i = (int)perm[g].size() - 1; i > 0; --i)
+        std::swap(perm[g][i], perm[g][(int)(splitmix64(rs) % (uint64_t)(i + 1))]);
+    std::vector<std::pair<int, int>> order;
+    for (int g = 0; g < G; ++g)
+      for (int b = 0; b < nbat[g]; ++b) order.emplace_back(g, b);
+    for (int i = (int)order.size() - 1; i > 0; --i)
+      std::swap(order[i], order[(int)(splitmix64(rs) % (uint64_t)(i + 1))]);
     double ep_loss = 0.0;
     long long ep_n = 0;
-    for (int b0 = 0; b0 + B <= count; b0 += B) {  // whole batches only
+    for (const std::pair<int, int>& gb : order) {
+      const int g = gb.first, B = Bg[g];
+      Net& net = nets[g];
+      const long long V = Net::vox(net.dims[0]);
       for (int j = 0; j < B; ++j) {
-        const int k = perm[b0 + j];
-        if (cudaMemcpyAsync(net.lab + j * V, all_lab + k * V, V, cudaMemcpyDeviceToDevice, net.st) != cudaSuccess ||
-            cudaMemcpyAsync(net.tgt + j * kOut, all_tgt + (long long)k * kOut, kOut * sizeof(float),
-                            cudaMemcpyDeviceToDevice, net.st) != cudaSuccess)
+        const int k = perm[g][gb.second * B + j];
+        if (cudaMemcpyAsync(net.lab + j * V, all_lab[g] + k * V, V, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(net.core + j, all_core[g] + k, sizeof(Core), cudaMemcpyDeviceToDevice, st) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(net.tgt + j * kOut, all_tgt[g] + (long long)k * kOut, kOut * sizeof(float),
+                            cudaMemcpyDeviceToDevice, st) != cudaSuccess)
           return ctx_fail(h, HH_ERR_CUDA, "surrogate training: batch copy failed");
       }
-      if ((s = net.forward(B)) || (s = net.backward(B))) return ctx_fail(h, s, net.err.c_str());
+      if (cudaMemsetAsync(par.grad, 0, par.off.total * sizeof(float), st) != cudaSuccess)
+        return ctx_fail(h, HH_ERR_CUDA, "surrogate training: memset failed");
+      if ((s = net.forward(B)) || (s = net.backward(B, B))) return ctx_fail(h, s, net.err.c_str());
       // cosine decay of the step size over the whole run
       const double lr_t = 0.5 * lr * (1.0 + cos(3.14159265358979323846 * double(step) / double(total_steps)));
       ++step;
       const float c1 = 1.f - powf(0.9f, (float)step), c2 = 1.f - powf(0.999f, (float)step);
-      k_adam<<<256, 256, 0, net.st>>>(net.theta, net.grad, net.m, net.v, net.off.total, (float)lr_t, c1, c2,
-                                      net.theta16);
+      k_adam<<<256, 256, 0, st>>>(par.theta, par.grad, par.m, par.v, par.off.total, (float)lr_t, c1, c2,
+                                  par.theta16);
       ++net.launches;
       if (cudaGetLastError() != cudaSuccess) return ctx_fail(h, HH_ERR_CUDA, "surrogate training: adam failed");
       if (loss_history) {
-        if (cudaMemcpyAsync(lp.data(), net.loss_part, B * sizeof(double), cudaMemcpyDeviceToHost, net.st) !=
+        if (cudaMemcpyAsync(lp.data(), net.loss_part, B * sizeof(double), cudaMemcpyDeviceToHost, st) !=
                 cudaSuccess ||
-            cudaStreamSynchronize(net.st) != cudaSuccess)
+            cudaStreamSynchronize(st) != cudaSuccess)
           return ctx_fail(h, HH_ERR_CUDA, "surrogate training failed");
-        for (double x : lp) ep_loss += x;
+        for (int j = 0; j < B; ++j) ep_loss += lp[j];
         ep_n += B;
       }
     }
     if (loss_history) loss_history[ep] = ep_n ? ep_loss / (double(ep_n) * kOut) : 0.0;
   }
-  if (cudaMemcpyAsync(params_out, net.theta, net.off.total * sizeof(float), cudaMemcpyDeviceToHost, net.st) !=
+  if (cudaMemcpyAsync(params_out, par.theta, par.off.total * sizeof(float), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
-      cudaStreamSynchronize(net.st) != cudaSuccess)
+      cudaStreamSynchronize(st) != cudaSuccess)
     return ctx_fail(h, HH_ERR_CUDA, "surrogate training failed");
   return HH_OK;
 }
 
-extern "C" hh_status hh_surrogate_predict(hh_ctx* h, const uint8_t* labels, int count, int edge, const float* params,
-                                         int ensemble, double scale, float* out) {
-  if (!h || !labels || !params || !out || ensemble < 1 || !(scale > 0.0)) return HH_ERR_ARG;
-  hh_status s = check_geometry(h, count, edge);
-  if (s) return s;
+extern "C" hh_status hh_surrogate_predict(hh_ctx* h, const uint8_t* labels, int count, const int32_t* boxes,
+                                         const float* params, int ensemble, double scale, float* out) {
+  if (!h || !labels || !params || !out || ensemble < 1 || !(scale > 0.0))
+    return ctx_fail(h, HH_ERR_ARG, "hh_surrogate_predict: NULL argument, ensemble < 1 or scale <= 0");
+  if (count < 1) return ctx_fail(h, HH_ERR_ARG, "hh_surrogate_predict: count >= 1");
   const long long np = offsets().total;
   std::vector<float> tmp((size_t)count * kOut);
   for (int e = 0; e < ensemble; ++e) {
-    if ((s = hh_cnn_forward(h, labels, count, edge, params + e * np, tmp.data()))) return s;
+    hh_status s = hh_cnn_forward(h, labels, count, boxes, params + e * np, tmp.data());
+    if (s) return s;
     for (int i = 0; i < count; ++i)
       for (int j = 0; j < kOut; ++j) out[((long long)i * ensemble + e) * kOut + j] = float(tmp[(size_t)i * kOut + j] * scale);
   }
   return HH_OK;
 }
 
-extern "C" hh_status hh_surrogate_gate(hh_ctx* h, const uint8_t* labels, int count, int edge, const hh_phase* phases,
-                                      int nphase, const float* members, int ensemble, double spread, int* accept,
-                                      double* c21) {
+extern "C" hh_status hh_surrogate_gate(hh_ctx* h, const uint8_t* labels, int count, const int32_t* boxes,
+                                      const hh_phase* phases, int nphase, const float* members, int ensemble,
+                                      double spread, int* accept, double* c21) {
   if (!h || !labels || !phases || nphase < 1 || nphase > 256 || !members || ensemble < 1 || !accept || !c21 ||
       !(spread >= 0.0))
-    return HH_ERR_ARG;
-  hh_status s = check_geometry(h, count, edge);
+    return ctx_fail(h, HH_ERR_ARG, "hh_surrogate_gate: NULL argument or bad phase count, ensemble or spread");
+  std::vector<Sub> subs;
+  std::vector<std::vector<int>> groups;
+  hh_status s = parse_subs(h, count, boxes, subs, groups);
   if (s) return s;
   for (int i = 0; i < nphase; ++i)
     if (!(phases[i].K > 0.0) || !(phases[i].G > 0.0)) return ctx_fail(h, HH_ERR_ARG, "surrogate gate: phase moduli");
   if ((s = ctx_enter(h))) return s;
   const cudaStream_t st = ctx_stream(h);
-  const long long V = (long long)edge * edge * edge;
-  uint8_t* d_lab = nullptr;
-  double *d_ph = nullptr, *d_c = nullptr;
-  float* d_mem = nullptr;
-  int* d_acc = nullptr;
   std::vector<double> ph(2 * nphase);
   for (int i = 0; i < nphase; ++i) {
     ph[2 * i] = phases[i].K;
     ph[2 * i + 1] = phases[i].G;
   }
-  hh_status r = HH_OK;
-  if (cudaMalloc(&d_lab, count * V) != cudaSuccess || cudaMalloc(&d_ph, ph.size() * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&d_mem, (size_t)count * ensemble * kOut * sizeof(float)) != cudaSuccess ||
-      cudaMalloc(&d_acc, count * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&d_c, (size_t)count * kOut * sizeof(double)) != cudaSuccess) {
-    (void)cudaGetLastError();
-    r = ctx_fail(h, HH_ERR_OOM, "surrogate gate: device allocation failed");
-  } else if (cudaMemcpyAsync(d_lab, labels, count * V, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-             cudaMemcpyAsync(d_ph, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-             cudaMemcpyAsync(d_mem, members, (size_t)count * ensemble * kOut * sizeof(float), cudaMemcpyHostToDevice,
-                             st) != cudaSuccess) {
-    r = ctx_fail(h, HH_ERR_CUDA, "surrogate gate: copy failed");
-  } else {
-    k_gate<<<count, 256, 0, st>>>(d_lab, V, d_ph, nphase, d_mem, ensemble, spread, d_acc, d_c);
+  for (const std::vector<int>& g : groups) {
+    const int n = (int)g.size();
+    Net net;  // only its label and core buffers (and the allocation list) are used
+    net.st = st;
+    double *d_ph = nullptr, *d_c = nullptr;
+    float* d_mem = nullptr;
+    int* d_acc = nullptr;
+    const Box3 box = subs[g[0]].box;
+    if ((s = net.alloc(&net.lab, n * Net::vox(box))) || (s = net.alloc(&net.core, n)) ||
+        (s = net.alloc(&d_ph, 2 * nphase)) || (s = net.alloc(&d_mem, (long long)n * ensemble * kOut)) ||
+        (s = net.alloc(&d_acc, n)) || (s = net.alloc(&d_c, (long long)n * kOut)))
+      return ctx_fail(h, s, "surrogate gate: device allocation failed");
+    std::vector<uint8_t> lab_h;
+    std::vector<Core> core_h;
+    if ((s = stage(net, labels, subs, g.data(), n, lab_h, core_h))) return ctx_fail(h, s, net.err.c_str());
+    std::vector<float> mem((size_t)n * ensemble * kOut);
+    for (int j = 0; j < n; ++j)
+      std::memcpy(mem.data() + (size_t)j * ensemble * kOut, members + (size_t)g[j] * ensemble * kOut,
+                  (size_t)ensemble * kOut * sizeof(float));
+    std::vector<int> acc(n);
+    std::vector<double> c(n * (size_t)kOut);
+    if (cudaMemcpyAsync(d_ph, ph.data(), ph.size() * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_mem, mem.data(), mem.size() * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return ctx_fail(h, HH_ERR_CUDA, "surrogate gate: copy failed");
+    k_gate<<<n, 256, 0, st>>>(net.lab, box, net.core, d_ph, nphase, d_mem, ensemble, spread, d_acc, d_c);
     if (cudaGetLastError() != cudaSuccess ||
-        cudaMemcpyAsync(accept, d_acc, count * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(c21, d_c, (size_t)count * kOut * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(acc.data(), d_acc, n * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(c.data(), d_c, c.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
-      r = ctx_fail(h, HH_ERR_CUDA, "surrogate gate failed");
+      return ctx_fail(h, HH_ERR_CUDA, "surrogate gate failed");
+    for (int j = 0; j < n; ++j) {
+      accept[g[j]] = acc[j];
+      std::memcpy(c21 + (size_t)g[j] * kOut, c.data() + (size_t)j * kOut, kOut * sizeof(double));
+    }
   }
-  cudaFree(d_lab);
-  cudaFree(d_ph);
-  cudaFree(d_mem);
-  cudaFree(d_acc);
-  cudaFree(d_c);
-  return r;
+  return HH_OK;
 }
 
 // ---------------------------------------------------------------------------

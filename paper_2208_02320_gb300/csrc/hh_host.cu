@@ -1896,36 +1896,40 @@ extern "C" hh_status hh_homogenize_partition_surrogate(hh_ctx* h, const uint8_t*
   if (unit <= 0) unit = derive_unit(bx);
   int reg[6];
   if ((s = check_tiling(h, bx, unit, nx, ny, nz, reg)) != HH_OK) return s;
-  // candidates: unbuffered cubic subimages, grouped by edge
-  std::map<int, std::vector<int>> groups;
-  for (int i = 0; i < nbox; ++i)
-    if (bx[i].b == 0 && bx[i].cnx == bx[i].cny && bx[i].cnx == bx[i].cnz && bx[i].cnx >= 8 && bx[i].cnx <= 256)
-      groups[bx[i].cnx].push_back(i);
+  // candidates: every subimage whose buffered box has edges 8..256, offered
+  // to the network with its buffer and its core
+  std::vector<int> cand;
+  std::vector<int32_t> rows, sboxes;
+  long long lab_len = 0;
+  for (int i = 0; i < nbox; ++i) {
+    const int ex = bx[i].cnx + 2 * bx[i].b, ey = bx[i].cny + 2 * bx[i].b, ez = bx[i].cnz + 2 * bx[i].b;
+    if (ex < 8 || ey < 8 || ez < 8 || ex > 256 || ey > 256 || ez > 256) continue;
+    cand.push_back(i);
+    rows.insert(rows.end(), boxes + 7 * i, boxes + 7 * i + 7);
+    const int32_t r[9] = {ex, ey, ez, bx[i].b, bx[i].b, bx[i].b, bx[i].cnx, bx[i].cny, bx[i].cnz};
+    sboxes.insert(sboxes.end(), r, r + 9);
+    lab_len += (long long)ex * ey * ez;
+  }
   std::vector<int> acc_idx, aud_idx;  // accepted: ensemble stiffness used; audited: FFT solve
   std::vector<double> acc_c21, aud_c21;
-  for (auto& kv : groups) {
-    const int e = kv.first;
-    const std::vector<int>& ids = kv.second;
-    const long long V = (long long)e * e * e;
-    std::vector<int32_t> rows;
-    for (int i : ids) rows.insert(rows.end(), boxes + 7 * i, boxes + 7 * i + 7);
-    std::vector<uint8_t> lab(ids.size() * V);
-    std::vector<float> pred(ids.size() * (size_t)ensemble * 21);
-    std::vector<int> ok(ids.size());
-    std::vector<double> c21(ids.size() * 21);
-    if ((s = hh_extract_subimages(h, img, nx, ny, nz, on_dev, rows.data(), (int)ids.size(), lab.data(),
-                                  (int64_t)lab.size())) != HH_OK ||
-        (s = hh_surrogate_predict(h, lab.data(), (int)ids.size(), e, params, ensemble, scale, pred.data())) !=
+  if (!cand.empty()) {
+    const int nc = (int)cand.size();
+    std::vector<uint8_t> lab(lab_len);
+    std::vector<float> pred((size_t)nc * ensemble * 21);
+    std::vector<int> ok(nc);
+    std::vector<double> c21((size_t)nc * 21);
+    if ((s = hh_extract_subimages(h, img, nx, ny, nz, on_dev, rows.data(), nc, lab.data(), (int64_t)lab.size())) !=
             HH_OK ||
-        (s = hh_surrogate_gate(h, lab.data(), (int)ids.size(), e, phases, nphase, pred.data(), ensemble, spread,
+        (s = hh_surrogate_predict(h, lab.data(), nc, sboxes.data(), params, ensemble, scale, pred.data())) != HH_OK ||
+        (s = hh_surrogate_gate(h, lab.data(), nc, sboxes.data(), phases, nphase, pred.data(), ensemble, spread,
                                ok.data(), c21.data())) != HH_OK)
       return s;
-    for (size_t j = 0; j < ids.size(); ++j)
+    for (int j = 0; j < nc; ++j)
       if (ok[j]) {
-        const int i = ids[j];
-        std::vector<int>& to = audit_draw(audit_seed, i) < audit_fraction ? aud_idx : acc_idx;
-        std::vector<double>& c_to = &to == &aud_idx ? aud_c21 : acc_c21;
-        to.push_back(i);
+        const int i = cand[j];
+        const bool audit = audit_draw(audit_seed, i) < audit_fraction;
+        (audit ? aud_idx : acc_idx).push_back(i);
+        std::vector<double>& c_to = audit ? aud_c21 : acc_c21;
         c_to.insert(c_to.end(), c21.begin() + 21 * j, c21.begin() + 21 * j + 21);
       }
   }

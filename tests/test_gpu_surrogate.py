@@ -58,6 +58,15 @@ def test_num_params(ctx):
     assert ctx.cnn_num_params() == N.n_params()
 
 
+def _boxes(shapes, seed):
+    """Three-phase label boxes of the given (nz, ny, nx) shapes."""
+    out = []
+    for i, sh in enumerate(shapes):
+        f = synth.gaussian_random_field(sh, 2.0, seed, stream=i)
+        out.append(np.digitize(f, np.quantile(f, [0.2, 0.35])).astype(np.uint8))
+    return out
+
+
 @pytest.mark.parametrize("edge", [8, 16, 20])
 def test_forward_parity_with_oracle(ctx, edge):
     theta = _params(11)
@@ -67,12 +76,29 @@ def test_forward_parity_with_oracle(ctx, edge):
     assert _rel(got, ref) < 2e-2
 
 
+def test_forward_parity_buffered_boxes_of_mixed_shapes(ctx):
+    """Subimages with a buffer (the core mask channel) and boxes of different,
+    non-cubic shapes in one call (one batch per shape)."""
+    theta = _params(15)
+    shapes = [(10, 14, 9), (18, 12, 16), (10, 14, 9), (8, 8, 8)]
+    cores = [(2, 3, 1, 5, 8, 7), (4, 2, 4, 8, 8, 10), None, (1, 1, 1, 6, 6, 6)]  # (ox, oy, oz, cnx, cny, cnz)
+    labs = _boxes(shapes, seed=16)
+    got = ctx.cnn_forward(labs, theta.astype(np.float32), cores=cores)
+    ref = np.stack([N.forward(theta, l, c)[0] for l, c in zip(labs, cores)])
+    assert _rel(got, ref) < 2e-2
+    for i in range(len(labs)):
+        assert _rel(got[i], ref[i]) < 3e-2, i
+
+
 def test_gradient_parity_with_oracle(ctx):
+    """Two cubes and a buffered non-cubic box: the loss is the mean over all
+    three and the gradient sums the two shape groups' contributions."""
     theta = _params(12)
-    labs = _cubes(2, 16, seed=6)
-    tg = synth.uniform01(7, 0, 2 * N.NOUT).reshape(2, N.NOUT)
-    loss, grad = ctx.cnn_loss_grad(labs, theta.astype(np.float32), tg.astype(np.float32))
-    rloss, rgrad, _ = N.batch_loss_and_grad(theta, list(labs), tg)
+    labs = list(_cubes(2, 16, seed=6)) + _boxes([(12, 10, 14)], seed=17)
+    cores = [None, None, (2, 1, 3, 10, 8, 6)]
+    tg = synth.uniform01(7, 0, 3 * N.NOUT).reshape(3, N.NOUT)
+    loss, grad = ctx.cnn_loss_grad(labs, theta.astype(np.float32), tg.astype(np.float32), cores=cores)
+    rloss, rgrad, _ = N.batch_loss_and_grad(theta, labs, tg, cores)
     assert abs(loss - rloss) <= 2e-2 * rloss
     o = 0
     for name, shape in N.layer_shapes():
@@ -156,6 +182,36 @@ def test_gate_matches_oracle(ctx):
         assert bool(acc[i]) == ok, i
         assert np.allclose(mean[i], m, rtol=1e-6)
     assert acc.sum() >= 3 and not acc[1] and not acc[4]
+
+
+def test_gate_bounds_come_from_the_core(ctx):
+    """Buffered boxes whose core is solid but for one soft voxel and whose
+    buffer is soft: a prediction half way between the core's Reuss and Voigt
+    bounds is accepted, one at the whole box's Voigt average (far below the
+    core's Reuss bound) is not; the decisions equal the oracle's gate with
+    the core."""
+    ph = synth.PHASES_APPENDIX_B
+    labs, cores, members = [], [], []
+    for i, (sh, core) in enumerate([((12, 12, 12), (3, 3, 3, 6, 6, 6)), ((10, 14, 16), (4, 2, 3, 8, 10, 4))]):
+        lab = np.ones(sh, dtype=np.uint8)
+        ox, oy, oz, cx, cy, cz = core
+        lab[oz:oz + cz, oy:oy + cy, ox:ox + cx] = 0
+        lab[oz + 1, oy + 1, ox + 1] = 1
+        KR, KV, GR, GV = N.phase_bounds(lab, ph, core)
+        KVb, GVb = N.phase_bounds(lab, ph)[1], N.phase_bounds(lab, ph)[3]
+        for K, G in [(0.5 * (KR + KV), 0.5 * (GR + GV)), (KVb, GVb)]:
+            lam = K - 2 * G / 3
+            C = np.zeros((6, 6))
+            C[:3, :3] = lam
+            C[np.arange(3), np.arange(3)] += 2 * G
+            C[np.arange(3, 6), np.arange(3, 6)] = G
+            labs.append(lab)
+            cores.append(core)
+            members.append([C[np.triu_indices(6)]] * 4)
+    members = np.array(members, dtype=np.float32)
+    acc, _ = ctx.surrogate_gate(labs, ph, members, spread=0.01, cores=cores)
+    ref = [N.gate(m.astype(np.float64), l, ph, 0.01, c)[0] for m, l, c in zip(members, labs, cores)]
+    assert list(acc) == ref == [True, False, True, False]
 
 
 def _fft_labels(ctx, labs, ph):

@@ -103,3 +103,17 @@ def test_argument_checks(B, tmp_path):
     assert lib.hh_surrogate_load(p, out.ctypes.data_as(ctypes.c_void_p), th.size - 1, ctypes.byref(ens),
                                  ctypes.byref(sc)) == B.HH_ERR_ARG
     assert b"capacity" in lib.hh_last_error(None)
+
+
+def test_initial_parameters_match_the_oracle_initializer(B):
+    """hh_cnn_init_params: He-uniform weights from the i-th SplitMix64 output of
+    the seed (top 53 bits), biases zero, equal to the oracle's initializer fed
+    with the same draws (up to FP32 rounding)."""
+    from oracle import cnn_oracle as N
+    for seed in (0, 2208, 2**64 - 3):
+        got = B.cnn_init_params(seed)
+        n = N.n_params()
+        u = (synth.splitmix64(seed, np.arange(n, dtype=np.uint64)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        ref = N.init_params(u)
+        assert got.shape == (n,) and got.dtype == np.float32
+        assert np.array_equal(got, ref.astype(np.float32))
