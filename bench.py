@@ -65,6 +65,13 @@ def parse():
     ap.add_argument("--headline-rows", type=int, default=6,
                     help="y-rows of the last timed tile on which the plain FP64 solver (one subimage at a time) "
                          "and the batched FP32 solver are timed against each other (0: skip)")
+    ap.add_argument("--surrogate", type=int, default=1,
+                    help="1: train a 4-member CNN ensemble on the subimages of the warm-up tiles, labelled by the "
+                         "FFT solver's C_R from those warm-up steps, and time the two-level homogenization of the "
+                         "headline cores with the surrogate standing in for the subimages its gate accepts "
+                         "(needs --headline-rows > 0)")
+    ap.add_argument("--surrogate-epochs", type=int, default=60)
+    ap.add_argument("--surrogate-spread", type=float, default=0.02)
     return ap.parse_args()
 
 
@@ -302,8 +309,10 @@ def run_gb300(args):
         src = dimg if device else img
         return ctx.homogenize_partition(src, ph, sl, unit=8, **opt)
 
+    warm = []  # (cores, FFT C_R) of the warm-up steps: the surrogate's training set
     for i in range(args.warmup):
-        step(i)
+        r = step(i)
+        warm.append((slabs[tile_index(i, ws, rank, len(slabs))], r["C_boxes"]))
     ctx.profile_reset()
     barrier(ws)
     torch.cuda.synchronize()
@@ -390,7 +399,10 @@ def run_gb300(args):
     if args.headline_rows > 0 and ws == 1:
         sl = slabs[tile_index(args.warmup + args.steps - 1, ws, rank, len(slabs))]
         ys = np.unique(sl[:, 1])[:args.headline_rows]
-        line["headline"] = headline(ctx, dimg, ph, sl[np.isin(sl[:, 1], ys)], args.tol, len(slabs), args.fused)
+        hl, runs = headline(ctx, dimg, ph, sl[np.isin(sl[:, 1], ys)], args.tol, len(slabs), args.fused)
+        line["headline"] = hl
+        if args.surrogate:
+            line["surrogate"] = surrogate_arm(ctx, dimg, ph, warm, sl[np.isin(sl[:, 1], ys)], args, runs, len(slabs))
     print(json.dumps(line))
 
 
@@ -435,6 +447,16 @@ def cufft_comparator(cores, value):
             "product_over_cufft_transforms_only": value / (units / (ms / 1e3))}
 
 
+def voigt_kg(C):
+    """Voigt-average K and G of the symmetric part of 6x6 stiffnesses in Voigt notation."""
+    import numpy as np
+    S = 0.5 * (C + np.swapaxes(C, -1, -2))
+    d = S[..., 0, 0] + S[..., 1, 1] + S[..., 2, 2]
+    o = S[..., 0, 1] + S[..., 0, 2] + S[..., 1, 2]
+    sh = S[..., 3, 3] + S[..., 4, 4] + S[..., 5, 5]
+    return (d + 2 * o) / 9.0, (d - o + 3 * sh) / 15.0
+
+
 def headline(ctx, dimg, ph, cores, tol, ntiles, fused=-1):
     """The same cores homogenized (level 1, assembly, level 2) by the plain
     FP64 solver -- FP64 fields, one subimage per wave of launches, no
@@ -455,17 +477,10 @@ def headline(ctx, dimg, ph, cores, tol, ntiles, fused=-1):
     r64, t64 = run(precision="fp64", wave_boxes=1, fused=0)
     r32, t32 = run(precision="fp32", **({"fused": fused} if fused >= 0 else {}))
 
-    def kg(C):
-        S = 0.5 * (C + np.swapaxes(C, -1, -2))
-        d = S[..., 0, 0] + S[..., 1, 1] + S[..., 2, 2]
-        o = S[..., 0, 1] + S[..., 0, 2] + S[..., 1, 2]
-        sh = S[..., 3, 3] + S[..., 4, 4] + S[..., 5, 5]
-        return (d + 2 * o) / 9.0, (d - o + 3 * sh) / 15.0
-
-    K32, G32 = kg(r32["C_boxes"])
-    K64, G64 = kg(r64["C_boxes"])
+    K32, G32 = voigt_kg(r32["C_boxes"])
+    K64, G64 = voigt_kg(r64["C_boxes"])
     eb = np.maximum(np.abs(K32 - K64) / K64, np.abs(G32 - G64) / G64)
-    return {
+    return ({
         "cores": int(len(cores)), "tol": tol,
         "plain_fp64": {"wall_s": t64, "device_ms": r64["device_ms"], "launches": r64["kernel_launches"],
                        "iters_max": r64["iters_max"], "status": r64["status"], "K": r64["K"], "G": r64["G"]},
@@ -478,6 +493,70 @@ def headline(ctx, dimg, ph, cores, tol, ntiles, fused=-1):
         "whole_image_estimate_s": {"plain_fp64": t64 * ntiles * 180 / len(cores),
                                    "fp32_batched": t32 * ntiles * 180 / len(cores),
                                    "note": "per-tile wall time x tiles in the 512^3 image (one tile measured)"},
+    }, {"r64": r64, "t64": t64, "r32": r32, "t32": t32})
+
+
+def surrogate_arm(ctx, dimg, ph, warm, cores, args, runs, ntiles):
+    """The surrogate standing in for subimage solves on the headline cores.
+
+    Training set: every buffered subimage of the warm-up tiles, labelled by
+    the upper triangle of the symmetric part of its C_R from the FFT solver
+    in those warm-up steps (no oracle, no extra solves). Four members from
+    the library's He-uniform initializer, Adam with the cosine step size.
+    Then the headline cores are homogenized with the surrogate (the gate's
+    accepted subimages take the ensemble mean, the rest the FFT solver) and
+    compared with the plain FP64 and the batched FP32 runs of the same
+    cores: wall time, the two-level K and G, and every accepted subimage's
+    K/G error against the FFT solver's C_R."""
+    import numpy as np
+    import torch
+    from paper_2208_02320_gb300 import binding
+    scale = 100.0
+    iu = np.triu_indices(6)
+    boxes = np.concatenate([w[0] for w in warm])
+    C = np.concatenate([w[1] for w in warm])
+    labs = ctx.extract_subimages(dimg, boxes)
+    tcores = [(int(b[6]), int(b[6]), int(b[6]), int(b[3]), int(b[4]), int(b[5])) for b in boxes]
+    y = np.stack([(0.5 * (c + c.T))[iu] for c in C]) / scale
+    members, hist = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for m in range(4):
+        th, h = ctx.surrogate_train(labs, y.astype(np.float32), binding.cnn_init_params(4100 + m),
+                                    epochs=args.surrogate_epochs, batch=8, lr=2e-3, seed=m, cores=tcores)
+        members.append(th)
+        hist.append([float(h[0]), float(h[-1])])
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    members = np.stack(members)
+    opt = dict(precision="fp32", tol=args.tol, **({"fused": args.fused} if args.fused >= 0 else {}))
+    ctx.homogenize_partition_surrogate(dimg, ph, cores, members, unit=8, scale=scale, spread=args.surrogate_spread,
+                                       **opt)  # warm
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rs = ctx.homogenize_partition_surrogate(dimg, ph, cores, members, unit=8, scale=scale,
+                                            spread=args.surrogate_spread, **opt)
+    torch.cuda.synchronize()
+    t_sur = time.perf_counter() - t0
+    r64, t64, r32, t32 = runs["r64"], runs["t64"], runs["r32"], runs["t32"]
+    acc = rs["accepted"]
+    Ks, Gs = voigt_kg(rs["C_boxes"])
+    Kf, Gf = voigt_kg(r32["C_boxes"])
+    eb = np.maximum(np.abs(Ks - Kf) / Kf, np.abs(Gs - Gf) / Gf)[acc]
+    return {
+        "training": {"subimages": int(len(boxes)), "shapes": int(len({l.shape for l in labs})), "members": 4,
+                     "epochs": args.surrogate_epochs, "batch": 8, "wall_s": t_train,
+                     "loss_first_last": hist,
+                     "note": "subimages of the warm-up tiles, labelled by their FFT C_R from the warm-up steps"},
+        "cores": int(len(cores)), "accepted": int(acc.sum()), "spread": args.surrogate_spread,
+        "wall_s": t_sur, "speedup_vs_plain_fp64": t64 / t_sur, "speedup_vs_fp32_batched": t32 / t_sur,
+        "K": rs["K"], "G": rs["G"],
+        "K_rel_err_vs_plain_fp64": abs(rs["K"] - r64["K"]) / r64["K"],
+        "G_rel_err_vs_plain_fp64": abs(rs["G"] - r64["G"]) / r64["G"],
+        "accepted_subimage_KG_rel_err_vs_fft": ({"max": float(eb.max()), "median": float(np.median(eb))}
+                                                if eb.size else None),
+        "whole_image_estimate_s": {"surrogate": t_sur * ntiles * 180 / len(cores) + t_train,
+                                   "note": "per-tile wall time x tiles, plus the training once"},
     }
 
 
