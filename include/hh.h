@@ -39,6 +39,8 @@ typedef int hh_status;
                                      max_iter reached, or its restarts spent or no longer
                                      reducing the residual (the FP32 floor at high phase
                                      contrast); results filled, resid_max reported */
+#define HH_WARN_TARGET_UNMET 2    /* hh_plan_partition: no candidate meets the error target;
+                                     the candidate with the least predicted error is returned */
 #define HH_ERR_ARG (-1)           /* invalid argument (dims, labels, moduli, partition, options) */
 #define HH_ERR_OOM (-2)           /* device or pinned allocation failed */
 #define HH_ERR_CUDA (-3)          /* a CUDA runtime call failed */
@@ -369,6 +371,30 @@ hh_status hh_correlation(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz
 hh_status hh_homogenize_multilevel(hh_ctx *ctx, const uint8_t *img, int nx, int ny, int nz, int img_on_device,
                                    const hh_phase *phases, int nphase, const int *ns, const int *bs,
                                    int nlevels, const hh_options *opt, hh_result *out);
+
+/* Choice of the subimage edge n and buffer width b (Section 2: n at least
+ * 3 xi, see hh_correlation; Section 3, Eq. 2: the cost of the level-1
+ * solves; Section 5: the HH error falls as C_b / n, with a constant C_b for
+ * each buffer width, Table fit_pad). No GPU and no context needed.
+ *
+ * Candidates: every n with max(n_min, 1) <= n <= min(nx, ny, nz) that
+ * divides nx, ny and nz, combined with every bs[i] (i < nb) such that the
+ * buffered box edge n + 2 bs[i] has no prime factor above 31 (the FFT lengths
+ * the solver takes). For each: predicted relative error c_rel[i] / n, where
+ * c_rel[i] = |C_b| / M_inf is the fitted constant of buffer bs[i] (for
+ * example from hh_extrapolate at that buffer), and predicted cost
+ * (nx ny nz / n^3) (n + 2 bs[i])^a, in units of one solve of a 1-voxel box,
+ * with a the exponent of the single-solve time against the edge (the paper
+ * measured 3.66). The cheapest candidate whose error is <= eps is returned;
+ * equal costs go to the smaller error, then the larger n, then the smaller
+ * b. If no candidate meets eps, the one with the least error (then the
+ * least cost) is returned with HH_WARN_TARGET_UNMET.
+ * Outputs (host): *n_out, *b_out, *err_out and *cost_out (the last two may
+ * be NULL). Errors: HH_ERR_ARG (a dimension < 1, NULL bs, c_rel, n_out or
+ * b_out, nb < 1, a buffer < 0, a constant negative or not finite, a <= 0,
+ * eps <= 0, or no candidate at all). */
+hh_status hh_plan_partition(int nx, int ny, int nz, int n_min, const int *bs, const double *c_rel, int nb,
+                            double a, double eps, int *n_out, int *b_out, double *err_out, double *cost_out);
 
 /* Two-level scheme on a partition (as hh_homogenize_partition) where every
  * subimage whose buffered box has edges 8..256 is first offered, with its

@@ -687,3 +687,52 @@ def fit_inverse_n(ns, M):
     A = np.stack([np.ones_like(ns), 1.0 / ns], axis=1)
     sol, *_ = np.linalg.lstsq(A, M, rcond=None)
     return float(sol[0]), float(sol[1])
+
+
+# --------------------------------------------------------------------------
+# Choice of subimage edge and buffer (Section 2, Section 3 Eq. 2, Section 5).
+# --------------------------------------------------------------------------
+
+def largest_prime_factor(m: int) -> int:
+    """Trial division (m >= 1; 1 for m = 1)."""
+    p, big = 2, 1
+    while p * p <= m:
+        while m % p == 0:
+            big, m = p, m // p
+        p += 1
+    return max(big, m) if m > 1 else big
+
+
+def plan_partition(shape, n_min: int, bs, c_rel, a: float, eps: float):
+    """Every candidate (n, b) written out and the best one picked.
+
+    n runs over the common divisors of the image edges with n >= n_min
+    (Section 2: subimages of at least 3 xi), b over the buffers whose fitted
+    constant is known, skipping buffered edges n + 2b with a prime factor
+    above 31 (FFT lengths the solver does not take). Predicted relative
+    error: c_rel / n (Section 5, the C / n term of Eq. fit_power_law, one
+    constant per buffer width as in Table fit_pad). Predicted cost: the
+    number of subimages (N/n)^3 times the single-solve time of a box of edge
+    n + 2b, taken as (n + 2b)^a (Section 3, Eq. 2 with the buffered box).
+    Rule: cheapest among those meeting eps (ties: smaller error, larger n,
+    smaller b); if none meets eps, least error (ties: cheaper).
+    Returns (n, b, err, cost, met, table) with table the list of all
+    candidates as (n, b, err, cost)."""
+    nz, ny, nx = shape
+    V = float(nx) * float(ny) * float(nz)
+    table = []
+    for n in range(max(n_min, 1), min(nx, ny, nz) + 1):
+        if nx % n or ny % n or nz % n:
+            continue
+        for b, c in zip(bs, c_rel):
+            if largest_prime_factor(n + 2 * b) > 31:
+                continue
+            table.append((n, int(b), c / n, V / float(n) ** 3 * float(n + 2 * b) ** a))
+    if not table:
+        raise ValueError("no candidate: no edge n >= n_min divides the image with a supported box")
+    met = [t for t in table if t[2] <= eps]
+    if met:
+        best = min(met, key=lambda t: (t[3], t[2], -t[0], t[1]))
+    else:
+        best = min(table, key=lambda t: (t[2], t[3], -t[0], t[1]))
+    return best[0], best[1], best[2], best[3], bool(met), table

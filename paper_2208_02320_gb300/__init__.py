@@ -5,4 +5,5 @@ this package only builds it and marshals arguments through ctypes
 (`binding`). Nothing here computes on the CPU.
 """
 
-from .binding import Context, HHError, load, options, surrogate_load, surrogate_save  # noqa: F401
+from .binding import (Context, HHError, cnn_init_params, load, options, plan_partition,  # noqa: F401
+                      surrogate_load, surrogate_save)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libhh.so")
 
 HH_OK = 0
 HH_WARN_NOT_CONVERGED = 1
+HH_WARN_TARGET_UNMET = 2
 HH_ERR_ARG = -1
 HH_ERR_OOM = -2
 HH_ERR_CUDA = -3
@@ -131,6 +132,7 @@ _SIGNATURES = {
     "hh_surrogate_save": (_I, [ctypes.c_char_p, _P, _I, _D]),
     "hh_surrogate_load": (_I, [ctypes.c_char_p, _P, ctypes.c_int64, _P, _P]),
     "hh_correlation": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "hh_plan_partition": (_I, [_I, _I, _I, _I, _P, _P, _I, _D, _D, _P, _P, _P, _P]),
     "hh_set_memory_limit": (_I, [_P, ctypes.c_int64]),
     "hh_homogenize_multilevel": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _P, _I, _P, _P]),
     "hh_homogenize_partition_surrogate": (_I, [_P, _P, _I, _I, _I, _I, _P, _I, _P, _I, _I, _P, _I, _D, _D, _D,
@@ -211,6 +213,26 @@ def cnn_init_params(seed: int) -> np.ndarray:
     if s != HH_OK:
         raise HHError(s, lib.hh_last_error(None).decode())
     return th
+
+
+def plan_partition(shape, n_min: int, bs, c_rel, a: float = 3.66, eps: float = 0.01) -> dict:
+    """Subimage edge n and buffer b of least predicted cost whose predicted
+    relative error c_rel[i] / n is at most eps (hh_plan_partition; no GPU
+    needed). shape = (nz, ny, nx) of the image; c_rel[i] = |C_b| / M_inf
+    fitted at buffer bs[i]. `met` is False when no candidate meets eps (the
+    least-error candidate is returned)."""
+    lib = load()
+    nz, ny, nx = (int(v) for v in shape)
+    b_arr = np.ascontiguousarray(bs, dtype=np.int32)
+    c_arr = np.ascontiguousarray(c_rel, dtype=np.float64)
+    if b_arr.size != c_arr.size:
+        raise ValueError("bs and c_rel must have the same length")
+    n, b, err, cost = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    s = lib.hh_plan_partition(nx, ny, nz, int(n_min), _ptr(b_arr), _ptr(c_arr), int(b_arr.size), float(a),
+                              float(eps), ctypes.byref(n), ctypes.byref(b), ctypes.byref(err), ctypes.byref(cost))
+    if s < 0:
+        raise HHError(s, lib.hh_last_error(None).decode())
+    return dict(n=n.value, b=b.value, err=err.value, cost=cost.value, met=s == HH_OK)
 
 
 def surrogate_save(path: str, params_ensemble, scale: float) -> None:

@@ -1406,6 +1406,7 @@ extern "C" const char* hh_status_string(hh_status s) {
   switch (s) {
     case HH_OK: return "ok";
     case HH_WARN_NOT_CONVERGED: return "warning: not converged within max_iter";
+    case HH_WARN_TARGET_UNMET: return "warning: no candidate meets the error target";
     case HH_ERR_ARG: return "error: invalid argument";
     case HH_ERR_OOM: return "error: out of memory";
     case HH_ERR_CUDA: return "error: CUDA runtime failure";
@@ -2057,6 +2058,65 @@ extern "C" hh_status hh_correlation(hh_ctx* h, const uint8_t* img, int nx, int n
   // Section 2: subimages of at least three correlation lengths
   if (n_min) n_min[0] = (int)std::ceil(3.0 * std::max(xi[0], std::max(xi[1], xi[2])));
   return HH_OK;
+}
+
+// Choice of the subimage edge n and buffer b from the error model of
+// Section 5 (HH error ~ C_b / n for each buffer width, Eq. fit_power_law with
+// the constants fitted per buffer as in Table fit_pad) and the cost model of
+// Section 3 (Eq. 2: (N/n)^3 subimage solves, each costing (n + 2b)^a, the
+// solved box being the buffered one), subject to n >= n_min (Section 2).
+extern "C" hh_status hh_plan_partition(int nx, int ny, int nz, int n_min, const int* bs, const double* c_rel, int nb,
+                                       double a, double eps, int* n_out, int* b_out, double* err_out,
+                                       double* cost_out) {
+  if (nx < 1 || ny < 1 || nz < 1 || !bs || !c_rel || nb < 1 || !(a > 0.0) || !(eps > 0.0) || !n_out || !b_out)
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_plan_partition: bad dimensions, NULL array, nb < 1, a <= 0 or eps <= 0");
+  for (int i = 0; i < nb; ++i)
+    if (bs[i] < 0 || !(c_rel[i] >= 0.0) || !std::isfinite(c_rel[i]))
+      return ctx_fail(nullptr, HH_ERR_ARG, "hh_plan_partition: a buffer < 0 or a constant that is negative or not finite");
+  const int lo = std::max(n_min, 1), hi = std::min(nx, std::min(ny, nz));
+  const double V = (double)nx * (double)ny * (double)nz;
+  int bn = 0, bb = 0;
+  double be = 0.0, bc = 0.0;
+  bool bmet = false;
+  for (int n = lo; n <= hi; ++n) {
+    if (nx % n || ny % n || nz % n) continue;
+    for (int i = 0; i < nb; ++i) {
+      const int edge = n + 2 * bs[i];
+      int rad[kMaxStages], nst = 0;
+      if (!factorize(edge, rad, &nst)) continue;  // an FFT length the solver does not take
+      const double err = c_rel[i] / n;
+      const double cost = V / ((double)n * n * n) * std::pow((double)edge, a);
+      const bool met = err <= eps;
+      // order: candidates meeting eps first; among them (cost, error), else
+      // (error, cost); then the larger n, then the smaller b
+      bool better;
+      if (bn == 0) {
+        better = true;
+      } else if (met != bmet) {
+        better = met;
+      } else {
+        const double k1 = met ? cost : err, k1b = met ? bc : be;
+        const double k2 = met ? err : cost, k2b = met ? be : bc;
+        if (k1 != k1b) better = k1 < k1b;
+        else if (k2 != k2b) better = k2 < k2b;
+        else better = n > bn || (n == bn && bs[i] < bb);
+      }
+      if (better) {
+        bn = n;
+        bb = bs[i];
+        be = err;
+        bc = cost;
+        bmet = met;
+      }
+    }
+  }
+  if (bn == 0)
+    return ctx_fail(nullptr, HH_ERR_ARG, "hh_plan_partition: no edge n >= n_min divides the image with a supported box");
+  *n_out = bn;
+  *b_out = bb;
+  if (err_out) *err_out = be;
+  if (cost_out) *cost_out = bc;
+  return bmet ? HH_OK : HH_WARN_TARGET_UNMET;
 }
 
 // Cubic cores of edge n tiling an nx x ny x nz grid (x fastest), buffer b.
