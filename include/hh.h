@@ -56,6 +56,12 @@ typedef int hh_status;
 #define HH_BASIC 1                /* basic fixed point with an isotropic reference medium
                                      (Moulinec-Suquet, cited in Appendix A) for the subimage
                                      and direct solves; the level-2 solve always uses CG */
+#define HH_EYRE_MILTON 2          /* accelerated fixed point (Eyre-Milton) with an isotropic
+                                     reference medium C0: tau = (C - C0) : eps,
+                                     B = E - eps - Gamma0 * tau,
+                                     eps <- eps + 2 (C + C0)^-1 C0 : B; stops after the
+                                     iteration whose ||B|| / ||E|| <= tol (Frobenius norms);
+                                     isotropic phases only; level 2 uses CG */
 #define HH_NYQ_ZERO_COMPONENT 0   /* even N: Nyquist wave-vector component set to 0 */
 #define HH_NYQ_ZERO_MODE 1        /* even N: projection zero on every Nyquist mode */
 
@@ -72,13 +78,15 @@ typedef struct {
                              HH_BASIC: stop when the equilibrium residual
                              ||G*sigma|| / ||<sigma>|| <= tol; default 1e-6 */
     int max_iter;         /* per load case, default 20000 */
-    int scheme;           /* HH_CG (default) or HH_BASIC */
+    int scheme;           /* HH_CG (default), HH_BASIC or HH_EYRE_MILTON */
     int nyquist;          /* HH_NYQ_ZERO_COMPONENT (default) or HH_NYQ_ZERO_MODE */
     int fixed_iters;      /* > 0: run exactly this many iterations, ignore tol (parity runs) */
-    double ref_lambda;    /* HH_BASIC reference medium (Lame lambda, mu, GPa). When ref_mu <= 0
-                             or lambda + 2 mu / 3 <= 0: the means of the smallest and largest
-                             phase lambda and mu (isotropic phases only; an anisotropic
-                             medium with no valid reference returns HH_ERR_UNSUPPORTED) */
+    double ref_lambda;    /* HH_BASIC / HH_EYRE_MILTON reference medium (Lame lambda, mu, GPa).
+                             When ref_mu <= 0 or lambda + 2 mu / 3 <= 0: for HH_BASIC the means
+                             of the smallest and largest phase lambda and mu, for
+                             HH_EYRE_MILTON K0 = sqrt(K_min K_max), mu0 = sqrt(mu_min mu_max)
+                             over the phases (isotropic phases only; an anisotropic medium
+                             with no valid reference returns HH_ERR_UNSUPPORTED) */
     double ref_mu;
     int64_t workspace_bytes; /* device workspace budget for batched solves; 0 = 3/4 of free memory */
     int use_graphs;       /* 1 (default): capture the iteration loop in CUDA graphs */

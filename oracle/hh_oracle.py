@@ -384,6 +384,59 @@ def solve_basic(medium, E: np.ndarray, lam0: float, mu0: float, tol: float = 1e-
     return eps - E[:, None, None, None], it, float(res)
 
 
+def solve_eyre_milton(medium, E: np.ndarray, lam0: float, mu0: float, tol: float = 1e-6,
+                      max_iter: int = 100000, nyquist: str = "component", fixed_iters: int | None = None):
+    """Accelerated fixed point of Eyre and Milton (from the FFT-scheme
+    literature cited in Appendix A), in strain form with an isotropic
+    reference medium C0 (lam0, mu0). With the polarization
+    tau^k = (C - C0) : eps^k and the Lippmann-Schwinger residual
+
+        B^k = E - eps^k - Gamma0 * tau^k          (Gamma0 vanishes at xi = 0),
+
+    each iteration sets eps^{k+1} = eps^k + 2 (C + C0)^-1 C0 : B^k. The
+    iterates need not be compatible; a fixed point (B = 0) is the solution
+    eps = E - Gamma0 * (C - C0) eps of the basic scheme. For isotropic C (K,
+    mu) and C0 (K0 = lam0 + 2 mu0 / 3, mu0) the local factor scales the
+    spherical part of B by 2 K0 / (K + K0) and the deviatoric part by
+    2 mu0 / (mu + mu0). The iteration that computes a residual
+    ||B^k|| / ||E|| <= tol (Frobenius norms over the box) still applies its
+    update and is the last. Returns (eps - E, iterations, residual)."""
+    shape = medium.shape
+    xi, zero = wave_vectors(shape, nyquist)
+    V = float(np.prod(shape))
+    K0 = lam0 + 2.0 * mu0 / 3.0
+    pol = IsoMedium(medium.K - K0, medium.mu - mu0)  # tau = (C - C0) : eps
+    fs = 2.0 * K0 / (medium.K + K0)
+    fd = 2.0 * mu0 / (medium.mu + mu0)
+    normE = np.sqrt(np.sum(FROB_W * E * E) * V)
+    eps = np.broadcast_to(E[:, None, None, None], (6,) + tuple(shape)).copy()
+    it = 0
+    limit = fixed_iters if fixed_iters is not None else max_iter
+    while True:
+        q = np.real(ifft3(gamma0_apply(fft3(pol.stress(eps)), xi, zero, lam0, mu0)))
+        B = E[:, None, None, None] - eps - q
+        res = np.sqrt(inner(B, B)) / normE
+        sph = (B[0] + B[1] + B[2]) / 3.0
+        upd = fd * B
+        upd[0:3] += (fs - fd) * sph
+        eps = eps + upd
+        it += 1
+        if it >= limit or (fixed_iters is None and res <= tol):
+            break
+    return eps - E[:, None, None, None], it, float(res)
+
+
+def eyre_milton_reference(phases):
+    """Default reference medium of the accelerated scheme: the geometric means
+    K0 = sqrt(K_min K_max), mu0 = sqrt(mu_min mu_max) of the phase moduli
+    (the choice that gives the contraction factor (sqrt(k) - 1) / (sqrt(k) + 1)
+    for a contrast k). Returns (lam0, mu0)."""
+    ph = np.asarray(phases, dtype=np.float64)
+    K0 = np.sqrt(ph[:, 0].min() * ph[:, 0].max())
+    mu0 = np.sqrt(ph[:, 1].min() * ph[:, 1].max())
+    return K0 - 2.0 * mu0 / 3.0, mu0
+
+
 # --------------------------------------------------------------------------
 # Averages and effective stiffness (Section 4).
 # --------------------------------------------------------------------------
@@ -409,6 +462,9 @@ def homogenize_box(medium, core, tol: float = 1e-6, max_iter: int = 20000,
         E = unit_load(a)
         if scheme == "cg":
             x, it, rr = solve_cg(medium, E, tol, max_iter, nyquist, fixed_iters)
+        elif scheme == "em":
+            lam0, mu0 = ref
+            x, it, rr = solve_eyre_milton(medium, E, lam0, mu0, tol, max_iter, nyquist, fixed_iters)
         else:
             lam0, mu0 = ref
             x, it, rr = solve_basic(medium, E, lam0, mu0, tol, max_iter, nyquist, fixed_iters)

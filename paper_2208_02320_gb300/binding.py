@@ -27,7 +27,7 @@ HH_ERR_DEVICE_TIMEOUT = -5
 HH_ERR_BAD_STIFFNESS = -6
 HH_ERR_UNSUPPORTED = -7
 HH_FP32, HH_FP64 = 0, 1
-HH_CG, HH_BASIC = 0, 1
+HH_CG, HH_BASIC, HH_EYRE_MILTON = 0, 1, 2
 HH_NYQ_ZERO_COMPONENT, HH_NYQ_ZERO_MODE = 0, 1
 
 
@@ -171,7 +171,7 @@ def options(**kw) -> Options:
         if k == "precision" and isinstance(v, str):
             v = {"fp32": HH_FP32, "fp64": HH_FP64}[v]
         if k == "scheme" and isinstance(v, str):
-            v = {"cg": HH_CG, "basic": HH_BASIC}[v]
+            v = {"cg": HH_CG, "basic": HH_BASIC, "em": HH_EYRE_MILTON}[v]
         if k == "nyquist" and isinstance(v, str):
             v = {"component": HH_NYQ_ZERO_COMPONENT, "mode": HH_NYQ_ZERO_MODE}[v]
         setattr(o, k, v)

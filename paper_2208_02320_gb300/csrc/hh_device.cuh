@@ -93,7 +93,7 @@ struct KParams {
   int nitems;
   int medium;         // MED_ISO / MED_ANISO
   int nyq_mode;       // 0 component rule, 1 mode rule
-  int pad0;
+  int em;             // MODE_BASIC runs the accelerated (Eyre-Milton) scheme
   int nphase;
   const AxisPlan* plans;
   const double* tw;   // interleaved (re, im) twiddles
@@ -981,7 +981,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
 // stores and partial sums (acc: MODE_ITER <p,q>, <r,q>, <q,q>; RHS/TRUE <r,r>).
 template <typename T, int MODE>
 __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, long long V, long long vo,
-                                          const T (&qv)[6], DotAcc<T> (&acc)[3]) {
+                                          const T (&qv)[6], const T* lm, DotAcc<T> (&acc)[3]) {
   T* __restrict__ rr = P.r + d.fld_off + vo;
   T* __restrict__ pp = P.p + d.fld_off + vo;
   T* __restrict__ qq = P.q + d.fld_off + vo;
@@ -1012,6 +1012,25 @@ __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, lo
       acc[1].add(rv[c], wq);
       acc[2].add(qv[c], wq);
     }
+  } else if (MODE == MODE_BASIC && P.em) {
+    // accelerated scheme: the Lippmann-Schwinger residual B = E - eps -
+    // Gamma0 * tau = -(x + q) (x holds eps - E, q = Gamma0 * tau) and the
+    // update x <- x + 2 (C + C0)^-1 C0 : B, whose spherical and deviatoric
+    // factors per phase the launch passes in lm; partial ||B||^2_F
+    const int lab = P.labels[d.med_off + vo];
+    T xv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) xv[c] = xx[c * V];
+    const T fs = lm[2 * lab], fd = lm[2 * lab + 1];
+    T bv[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) bv[c] = -(xv[c] + qv[c]);
+    const T sph = (bv[0] + bv[1] + bv[2]) * T(1.0 / 3.0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      xx[c * V] = xv[c] + fd * bv[c] + (c < 3 ? (fs - fd) * sph : T(0));
+      acc[0].add(bv[c], frob_t(c, bv[c]));
+    }
   } else {
 #pragma unroll
     for (int c = 0; c < 6; ++c) qq[c * V] = qv[c];
@@ -1031,7 +1050,7 @@ __device__ __forceinline__ void inv_partials(const KParams<T>& P, long long row,
       pt[14] = acc[1];
       pt[15] = acc[2];
     }
-  } else if (MODE != MODE_APPLY && MODE != MODE_BASIC) {
+  } else if ((MODE != MODE_APPLY && MODE != MODE_BASIC) || (MODE == MODE_BASIC && P.em)) {
     double a1[1] = {acc[0]};
     block_reduce<1>(a1, red);
     if (threadIdx.x == 0) P.part[row * 16 + 12] = a1[0];
@@ -1092,7 +1111,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
         qv[2 * c2] = zz.x * invV;
         qv[2 * c2 + 1] = zz.y * invV;
       }
-      inv_voxel<T, MODE>(P, d, V, zoff + v, qv, acc);
+      inv_voxel<T, MODE>(P, d, V, zoff + v, qv, sm.lm, acc);
     }
     inv_partials<T, MODE>(P, d.part0 + z, acc, sm.red);
     __syncthreads();
@@ -1143,7 +1162,7 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_rows_inv(KParams<T> 
         qv[2 * c2] = zz.x * invV;
         qv[2 * c2 + 1] = zz.y * invV;
       }
-      inv_voxel<T, MODE>(P, d, V, off0 + v, qv, acc);
+      inv_voxel<T, MODE>(P, d, V, off0 + v, qv, sm.lm, acc);
     }
     const int nch = (ny + R - 1) / R;
     inv_partials<T, MODE>(P, d.part0 + z * nch + y0 / R, acc, sm.red);
@@ -1342,13 +1361,36 @@ __global__ void k_scal_basic_init(PState* st, int nprob) {
 // Parseval sum h |P sigma^|^2 / sum_c w_c (Re sigma^_c(0))^2) of the current
 // strain decides; otherwise the update x <- x - Gamma0 * sigma that the
 // inverse pass stored in q is applied by the next forward pass.
-__global__ void k_scal_basic(const Prob* prob, PState* st, const double* cpart, int nprob, double tol,
-                             int max_iter, int fixed_iters) {
+//
+// Accelerated scheme (em = 1): the inverse pass of iteration k has applied
+// its update and left the partials of ||B^k||^2_F (slot 12); the residual
+// ||B^k|| / ||E|| (||E||^2 = V w_lc E_lc^2 for the unit load) decides
+// whether that iteration was the last. Nothing is left pending.
+__global__ void k_scal_basic(const Prob* prob, PState* st, const double* cpart, const double* part, int nprob,
+                             double tol, int max_iter, int fixed_iters, int em) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nprob || !st[i].active) return;
   const Prob d = prob[i];
   PState& s = st[i];
   s.pending = 0;
+  if (em) {
+    const double Ed = d.lc < 3 ? 1.0 : 0.5;
+    const double nE2 = (double)d.nx * d.ny * d.nz * frob_w(d.lc) * Ed * Ed;
+    const double res = sqrt(sum_parts(part, d, 12) / nE2);
+    if (!isfinite(res)) {
+      s.active = 0;
+      s.status = ST_NONFINITE;
+      return;
+    }
+    s.resid = res;
+    s.iters += 1;
+    const bool stop = fixed_iters > 0 ? (s.iters >= fixed_iters) : (res <= tol);
+    if (stop || s.iters >= max_iter) {
+      s.active = 0;
+      if (!stop) s.status = ST_NOT_CONVERGED;
+    }
+    return;
+  }
   const int n = (d.ny * d.nxh + d.cw - 1) / d.cw;
   double eq = 0.0, m[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
   for (int j = 0; j < n; ++j) {

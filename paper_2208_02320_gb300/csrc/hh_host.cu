@@ -622,17 +622,59 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   if ((s = ensure(c, "lammu", lm.size() * sizeof(T), (void**)&d_lm)) != HH_OK) return s;
   HH_CK(cudaMemcpyAsync(d_lm, lm.data(), lm.size() * sizeof(T), cudaMemcpyHostToDevice, c.st));
 
-  // basic scheme: isotropic reference medium, given or the means of the
-  // extreme phase values of lambda and mu
-  const bool basic = o.scheme == HH_BASIC;
+  // basic and accelerated schemes: isotropic reference medium, given, or
+  // for the basic scheme the means of the extreme phase values of lambda and
+  // mu, for the accelerated scheme the geometric means of the extreme phase
+  // values of K and mu
+  const bool em = o.scheme == HH_EYRE_MILTON;
+  const bool basic = o.scheme == HH_BASIC || em;
+  if (em && med.kind != MED_ISO) {
+    c.err = "the accelerated scheme takes isotropic phases only";
+    return HH_ERR_UNSUPPORTED;
+  }
   double lam0 = o.ref_lambda, mu0 = o.ref_mu;
   if (basic && !(mu0 > 0.0 && lam0 + 2.0 * mu0 / 3.0 > 0.0)) {
     if (med.kind != MED_ISO || nphase < 1) {
       c.err = "the basic scheme on an anisotropic medium needs ref_lambda and ref_mu";
       return HH_ERR_UNSUPPORTED;
     }
-    lam0 = 0.5 * (*std::min_element(med.lam.begin(), med.lam.end()) + *std::max_element(med.lam.begin(), med.lam.end()));
-    mu0 = 0.5 * (*std::min_element(med.mu.begin(), med.mu.end()) + *std::max_element(med.mu.begin(), med.mu.end()));
+    if (em) {
+      double kmin = 1e300, kmax = 0.0, mmin = 1e300, mmax = 0.0;
+      for (int i = 0; i < nphase; ++i) {
+        const double K = med.lam[i] + 2.0 * med.mu[i] / 3.0;
+        kmin = std::min(kmin, K);
+        kmax = std::max(kmax, K);
+        mmin = std::min(mmin, med.mu[i]);
+        mmax = std::max(mmax, med.mu[i]);
+      }
+      mu0 = std::sqrt(mmin * mmax);
+      lam0 = std::sqrt(kmin * kmax) - 2.0 * mu0 / 3.0;
+    } else {
+      lam0 = 0.5 * (*std::min_element(med.lam.begin(), med.lam.end()) +
+                    *std::max_element(med.lam.begin(), med.lam.end()));
+      mu0 = 0.5 * (*std::min_element(med.mu.begin(), med.mu.end()) + *std::max_element(med.mu.begin(), med.mu.end()));
+    }
+  }
+  // accelerated scheme: per phase the polarization moduli (lambda - lam0,
+  // mu - mu0) for the forward pass and the factors of 2 (C + C0)^-1 C0
+  // (spherical 2 K0 / (K + K0), deviatoric 2 mu0 / (mu + mu0)) for the
+  // inverse pass
+  T* d_lm_tau = nullptr;
+  T* d_lm_em = nullptr;
+  if (em) {
+    const double K0 = lam0 + 2.0 * mu0 / 3.0;
+    std::vector<T> lt(2 * std::max(nphase, 1)), le(2 * std::max(nphase, 1));
+    for (int i = 0; i < nphase; ++i) {
+      const double K = med.lam[i] + 2.0 * med.mu[i] / 3.0;
+      lt[2 * i] = T(med.lam[i] - lam0);
+      lt[2 * i + 1] = T(med.mu[i] - mu0);
+      le[2 * i] = T(2.0 * K0 / (K + K0));
+      le[2 * i + 1] = T(2.0 * mu0 / (med.mu[i] + mu0));
+    }
+    if ((s = ensure(c, "lm_tau", lt.size() * sizeof(T), (void**)&d_lm_tau)) != HH_OK) return s;
+    if ((s = ensure(c, "lm_em", le.size() * sizeof(T), (void**)&d_lm_em)) != HH_OK) return s;
+    HH_CK(cudaMemcpyAsync(d_lm_tau, lt.data(), lt.size() * sizeof(T), cudaMemcpyHostToDevice, c.st));
+    HH_CK(cudaMemcpyAsync(d_lm_em, le.data(), le.size() * sizeof(T), cudaMemcpyHostToDevice, c.st));
   }
   const double floor2 = (sizeof(T) == 4) ? 1e-12 : 1e-28;
   int b0 = 0;
@@ -965,18 +1007,25 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       // every problem of the wave was solved by the fused kernel
     } else if (basic) {
       // ---- basic scheme (Moulinec-Suquet fixed point): x = eps - E = 0, then
-      //      per iteration sigma = C:(E + x), residual, x <- x - Gamma0 * sigma
+      //      per iteration sigma = C:(E + x), residual, x <- x - Gamma0 * sigma.
+      //      Accelerated scheme: tau = (C - C0):(E + x) forward, the inverse
+      //      pass applies x <- x + 2 (C + C0)^-1 C0 : B with B = -(x + Gamma0 * tau)
       HH_CK(cudaMemsetAsync(d_x, 0, fld_off * sizeof(T), c.st));
       ++c.launches;
       k_scal_basic_init<<<gs, 128, 0, c.st>>>(d_st, np);
       HH_CK(cudaGetLastError());
+      kp.em = em ? 1 : 0;
       auto basic_chunk = [&]() {
         for (int m = 0; m < chunk; ++m) {
+          if (em) kp.lammu = d_lm_tau;
           fwd_pass(MODE_BASIC);
           column_pass(MODE_BASIC);
+          if (em) kp.lammu = d_lm_em;
           inv_pass(MODE_BASIC);
+          kp.lammu = d_lm;
           ++c.launches;
-          k_scal_basic<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_cpart, np, o.tol, o.max_iter, o.fixed_iters);
+          k_scal_basic<<<gs, 128, 0, c.st>>>(d_prob, d_st, d_cpart, d_part, np, o.tol, o.max_iter, o.fixed_iters,
+                                             em ? 1 : 0);
         }
       };
       cudaGraphExec_t bexec = nullptr;
@@ -1546,7 +1595,7 @@ static hh_status check_opts(hh_ctx* h, const hh_options* o) {
   if (!(o->tol > 0.0) && o->fixed_iters <= 0) return fail(h, HH_ERR_ARG, "tol must be > 0");
   if (o->max_iter < 1 || o->fixed_iters < 0) return fail(h, HH_ERR_ARG, "bad iteration limits");
   if (o->nyquist != HH_NYQ_ZERO_COMPONENT && o->nyquist != HH_NYQ_ZERO_MODE) return fail(h, HH_ERR_ARG, "bad nyquist");
-  if (o->scheme != HH_CG && o->scheme != HH_BASIC) return fail(h, HH_ERR_ARG, "bad scheme");
+  if (o->scheme != HH_CG && o->scheme != HH_BASIC && o->scheme != HH_EYRE_MILTON) return fail(h, HH_ERR_ARG, "bad scheme");
   if (o->check_every < 0 || o->max_restarts < 0 || o->replace < -1 || o->replace > 1 || o->wave_boxes < 0 ||
       o->fused < 0 || o->fused > 1)
     return fail(h, HH_ERR_ARG, "bad check_every, replace, max_restarts, wave_boxes or fused");

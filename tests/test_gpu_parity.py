@@ -522,6 +522,47 @@ def test_basic_explicit_reference_and_anisotropic_medium(ctx):
     assert rel(got["C"], cg["C"]) < 1e-7
 
 
+# ------------------------------- (f4) accelerated scheme (Eyre and Milton) --
+
+@pytest.mark.parametrize("shape,limit", [((9, 10, 11), 0), ((16, 18, 12), 0), ((7, 33, 20), 3000)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
+def test_eyre_milton_fixed_iterations_parity(ctx, shape, limit, precision, tol):
+    """Twelve iterations of the accelerated scheme on a three-phase box
+    (whole-plane passes, and the row-streaming passes with a ragged chunk)
+    against the oracle: stresses, C and the last residual ||B|| / ||E||."""
+    lab = RNG.integers(0, 3, size=shape).astype(np.uint8)
+    ph = np.array([[37.0, 44.0], [21.0, 7.0], [2.5, 1.5]])  # contrast ~30
+    extra = dict(plane_smem_limit=limit) if limit else {}
+    got = ctx.solve_subimages(lab, ph, _boxes_whole(shape), precision=precision, fixed_iters=12, scheme="em",
+                              **extra)
+    ref = O.homogenize_box(O.IsoMedium.from_labels(lab, ph), (slice(None),) * 3, fixed_iters=12, scheme="em",
+                           ref=O.eyre_milton_reference(ph))
+    assert np.all(got["iters"] == 12)
+    assert rel(got["Sigma"][0], ref["Sigma"]) < tol
+    assert rel(got["C"][0], ref["C"]) < tol
+    assert rel(got["resid"][0], ref["resid"]) < (1e-8 if precision == "fp64" else 1e-3)
+
+
+@pytest.mark.parametrize("precision,solver_tol,tol", [("fp64", 1e-10, 1e-7), ("fp32", 2e-6, 5e-5)])
+def test_eyre_milton_converges_to_the_cg_solution_in_fewer_iterations(ctx, precision, solver_tol, tol):
+    img = synth.grf_two_phase(n=14, ell=2.0, porosity=0.35, seed=3)
+    ph = np.array([[37.0, 44.0], [0.37, 0.44]])  # contrast 100
+    ref = O.homogenize_direct(img, ph, tol=1e-12)
+    em = ctx.homogenize_direct(img, ph, precision=precision, tol=solver_tol, scheme="em", max_iter=5000)
+    assert em["status"] == 0 and em["resid_max"] <= solver_tol
+    assert rel(em["C"], ref["C"]) < tol
+    basic = ctx.homogenize_direct(img, ph, precision=precision, tol=solver_tol, scheme="basic", max_iter=20000)
+    assert 3 * em["iters_max"] < basic["iters_max"]
+
+
+def test_eyre_milton_rejects_an_anisotropic_medium(ctx):
+    from paper_2208_02320_gb300 import HHError
+    from paper_2208_02320_gb300 import binding as B
+    with pytest.raises(HHError) as e:
+        ctx.homogenize_aniso(c21_of(rand_spd_field((4, 5, 6), RNG)), scheme="em")
+    assert e.value.status == B.HH_ERR_UNSUPPORTED
+
+
 # ------------------------------------------- A10 row-streaming passes ------
 
 @pytest.mark.parametrize("shape,limit", [((10, 26, 28), 6000), ((7, 33, 20), 3000), ((9, 12, 45), 9000)])

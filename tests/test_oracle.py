@@ -196,6 +196,82 @@ def test_basic_scheme_reaches_the_cg_solution():
     assert np.abs(xb - xc).max() < 1e-8 * np.abs(xc).max()
 
 
+# ------------------------------------- accelerated scheme (Eyre and Milton)
+
+def _layer_recurrence(labels, ph, E, lam0, mu0, steps):
+    """The accelerated scheme on a laminate along z, written out per layer by
+    hand: every field depends on z only and is constant in each phase's
+    layers, so each layer keeps one strain (6 tensor components). For such
+    fields Gamma0 with n = e_z keeps only the 33, 23 and 13 components of the
+    polarization and maps them to (tau_33 - <tau_33>) / (lam0 + 2 mu0) and
+    (tau_i3 - <tau_i3>) / (2 mu0) (the in-plane components vanish since
+    n_i = 0 for i = 1, 2). B = E - eps - Gamma0 tau; the local factor
+    2 (C + C0)^-1 C0 scales the spherical part of B by 2 K0 / (K + K0) and
+    the deviatoric part by 2 mu0 / (mu + mu0)."""
+    nz = len(labels)
+    K = ph[labels, 0]
+    mu = ph[labels, 1]
+    lam = K - 2 * mu / 3
+    K0 = lam0 + 2 * mu0 / 3
+    eps = np.tile(E, (nz, 1))
+    for _ in range(steps):
+        tr = eps[:, 0] + eps[:, 1] + eps[:, 2]
+        tau = 2 * (mu - mu0)[:, None] * eps
+        tau[:, :3] += ((lam - lam0) * tr)[:, None]
+        g = np.zeros_like(eps)
+        g[:, 2] = (tau[:, 2] - tau[:, 2].mean()) / (lam0 + 2 * mu0)
+        g[:, 3] = (tau[:, 3] - tau[:, 3].mean()) / (2 * mu0)
+        g[:, 4] = (tau[:, 4] - tau[:, 4].mean()) / (2 * mu0)
+        B = E - eps - g
+        sph = (B[:, 0] + B[:, 1] + B[:, 2]) / 3
+        fs = 2 * K0 / (K + K0)
+        fd = 2 * mu0 / (mu + mu0)
+        upd = fd[:, None] * B
+        upd[:, :3] += ((fs - fd) * sph)[:, None]
+        eps = eps + upd
+    return eps
+
+
+@pytest.mark.parametrize("load", [2, 4])
+def test_eyre_milton_on_a_laminate_matches_the_layer_recurrence(load):
+    labels = np.array([0, 0, 1, 2, 1, 1, 0])  # odd nz: no Nyquist plane
+    ph = np.array([[37.0, 44.0], [2.5, 1.5], [21.0, 7.0]])
+    img = synth.laminate((7, 2, 3), labels)
+    med = O.IsoMedium.from_labels(img, ph)
+    lam0, mu0 = O.eyre_milton_reference(ph)
+    E = O.unit_load(load)
+    for steps in (1, 2, 3):
+        x, it, _ = O.solve_eyre_milton(med, E, lam0, mu0, fixed_iters=steps)
+        assert it == steps
+        want = _layer_recurrence(labels, ph, E, lam0, mu0, steps)
+        got = (x + E[:, None, None, None])[:, :, 0, 0].T  # (nz, 6)
+        assert np.abs(got - want).max() < 1e-12
+        assert np.ptp(x, axis=(2, 3)).max() < 1e-12  # constant in x and y
+
+
+def test_eyre_milton_reaches_the_cg_solution_faster_than_the_basic_scheme():
+    img = (RNG.random((7, 7, 7)) < 0.5).astype(np.uint8)
+    ph = np.array([[37.0, 44.0], [0.37, 0.44]])  # contrast 100
+    med = O.IsoMedium.from_labels(img, ph)
+    E = O.unit_load(3)
+    lam0, mu0 = O.eyre_milton_reference(ph)
+    xe, ite, res = O.solve_eyre_milton(med, E, lam0, mu0, tol=1e-10)
+    xc, _, _ = O.solve_cg(med, E, tol=1e-12)
+    assert res <= 1e-10
+    assert np.abs(xe - xc).max() < 1e-7 * np.abs(xc).max()
+    lam = ph[:, 0] - 2 * ph[:, 1] / 3
+    _, itb, _ = O.solve_basic(med, E, 0.5 * (lam.min() + lam.max()), 0.5 * (ph[:, 1].min() + ph[:, 1].max()),
+                              tol=1e-6, max_iter=5000)
+    _, ite6, _ = O.solve_eyre_milton(med, E, lam0, mu0, tol=1e-6)
+    assert 3 * ite6 < itb
+
+
+def test_eyre_milton_reference_is_the_geometric_mean():
+    ph = np.array([[37.0, 44.0], [1e-4, 1e-4], [21.0, 7.0]])
+    lam0, mu0 = O.eyre_milton_reference(ph)
+    assert np.isclose(mu0, np.sqrt(1e-4 * 44.0)) and np.isclose(lam0 + 2 * mu0 / 3, np.sqrt(1e-4 * 37.0))
+
+
 # ------------------------------------------ Green operator of the basic scheme
 # The basic scheme's Gamma0 is the Green operator of an isotropic reference
 # medium C0 = (lam0, mu0). Per mode with unit wave vector n it is fixed by
@@ -657,6 +733,39 @@ def test_pins_catch_planted_mistakes(monkeypatch):
         with pytest.raises(AssertionError):
             test_gamma0_inverts_the_reference_medium_on_compatible_strains((5, 6, 7))
     monkeypatch.setattr(O, "gamma0_apply", good_g0)
+
+    # 8, 9. accelerated scheme with the relaxation factor 1 instead of 2, or
+    #    with the basic scheme's increment E - <eps> - Gamma0 * (C : eps) in
+    #    place of the Lippmann-Schwinger residual (equal only on compatible
+    #    iterates): the laminate recurrence catches both
+    good_em = O.solve_eyre_milton
+
+    def em_with(relax, lippmann_schwinger):
+        def em(medium, E, lam0, mu0, tol=1e-6, max_iter=100000, nyquist="component", fixed_iters=None):
+            xi, zero = O.wave_vectors(medium.shape, nyquist)
+            K0 = lam0 + 2.0 * mu0 / 3.0
+            fs, fd = relax * K0 / (medium.K + K0), relax * mu0 / (medium.mu + mu0)
+            eps = np.broadcast_to(E[:, None, None, None], (6,) + tuple(medium.shape)).copy()
+            for _ in range(fixed_iters):
+                if lippmann_schwinger:
+                    tau = O.IsoMedium(medium.K - K0, medium.mu - mu0).stress(eps)
+                    B = E[:, None, None, None] - eps - np.real(O.ifft3(O.gamma0_apply(O.fft3(tau), xi, zero, lam0, mu0)))
+                else:
+                    B = (E - eps.mean(axis=(1, 2, 3)))[:, None, None, None] - np.real(
+                        O.ifft3(O.gamma0_apply(O.fft3(medium.stress(eps)), xi, zero, lam0, mu0)))
+                upd = fd * B
+                upd[0:3] += (fs - fd) * (B[0] + B[1] + B[2]) / 3.0
+                eps = eps + upd
+            return eps - E[:, None, None, None], fixed_iters, 0.0
+        return em
+
+    monkeypatch.setattr(O, "solve_eyre_milton", em_with(2.0, True))
+    test_eyre_milton_on_a_laminate_matches_the_layer_recurrence(2)
+    for bad in (em_with(1.0, True), em_with(2.0, False)):
+        monkeypatch.setattr(O, "solve_eyre_milton", bad)
+        with pytest.raises(AssertionError):
+            test_eyre_milton_on_a_laminate_matches_the_layer_recurrence(2)
+    monkeypatch.setattr(O, "solve_eyre_milton", good_em)
 
 
 # ------------------------------------------------- multi-level renormalisation
