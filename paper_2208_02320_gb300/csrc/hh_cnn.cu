@@ -17,10 +17,12 @@
 // FP32. conv1 reads the labels directly (a one-hot input turns its contraction
 // into a lookup of the weight row of each neighbour's label, plus the mask
 // row where the neighbour lies in the core). conv2..conv4, their data
-// gradients and their weight gradients are implicit GEMMs on the BF16 tensor
-// cores (mma.sync m16n8k16, FP32 accumulate) with the operands gathered from
-// the activations (no im2col buffer). Subimages of one shape form a batch;
-// a call with several shapes runs one batch sequence per shape.
+// gradients and their weight gradients are implicit GEMMs on the fifth-
+// generation tensor cores (tcgen05.mma kind::f16, BF16 operands staged in
+// shared memory, FP32 accumulator in tensor memory) with the operands
+// gathered from the channels-last activations in 16-byte runs of channels
+// (no im2col buffer). Subimages of one shape form a batch; a call with
+// several shapes runs one batch sequence per shape.
 //
 // Parameter layout (flat FP32): per conv layer W[tap][ci][co] with
 // tap = (kz * 3 + ky) * 3 + kx, then bias[co]; per fully connected layer
@@ -196,167 +198,347 @@ __global__ void __launch_bounds__(256) k_bias_grad(const bf16* dZ, long long M, 
   for (int t = threadIdx.x; t < C; t += blockDim.x) atomicAdd(&db[t], acc[t]);
 }
 
-// ---------------------------------------------------------------------------
-// Implicit GEMM C[M][N] = sum_k A(m, k) B(k, n) on the BF16 tensor cores.
-// Block tile 64 x 64, k step 32, 4 warps of 32 x 32 (2 x 4 mma tiles of
-// 16 x 8). The operands are gathered through Op::a / Op::b into shared memory;
-// Op::store receives each FP32 result. blockIdx.z splits K (Op::store then
-// accumulates with atomics).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-      "{%0, %1, %2, %3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-template <class Op>
-__global__ void __launch_bounds__(128) k_igemm(Op op, long long M, int N, long long K, long long kper) {
-  __shared__ bf16 As[64][40];
-  __shared__ bf16 Bs[32][72];
-  const long long m0 = (long long)blockIdx.x * 64;
-  const int n0 = blockIdx.y * 64;
-  const long long kb = (long long)blockIdx.z * kper;
-  const long long ke = min(K, kb + kper);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  const bf16 zero = __float2bfloat16(0.f);
-  for (long long k0 = kb; k0 < ke; k0 += 32) {
-    for (int e = threadIdx.x; e < 64 * 32; e += 128) {
-      const int r = e >> 5, c = e & 31;
-      As[r][c] = (m0 + r < M && k0 + c < ke) ? op.a(m0 + r, k0 + c) : zero;
-      const int kr = e >> 6, nc = e & 63;
-      Bs[kr][nc] = (k0 + kr < ke && n0 + nc < N) ? op.b(k0 + kr, n0 + nc) : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 32; kk += 16) {
-      uint32_t a[2][4], b[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + 16 * i + g, c = kk + 2 * t;
-        a[i][0] = pack2(As[r][c], As[r][c + 1]);
-        a[i][1] = pack2(As[r + 8][c], As[r + 8][c + 1]);
-        a[i][2] = pack2(As[r][c + 8], As[r][c + 9]);
-        a[i][3] = pack2(As[r + 8][c + 8], As[r + 8][c + 9]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = wn + 8 * j + g, k = kk + 2 * t;
-        b[j][0] = pack2(Bs[k][n], Bs[k + 1][n]);
-        b[j][1] = pack2(Bs[k + 8][n], Bs[k + 9][n]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long long m = m0 + wm + 16 * i + g + (q >= 2 ? 8 : 0);
-        const int n = n0 + wn + 8 * j + 2 * t + (q & 1);
-        if (m < M && n < N) op.store(m, n, acc[i][j][q]);
-      }
-}
-
 // Geometry of one convolution layer: input box Di, output box Do (per axis).
 struct Geo {
   Box3 Di, Do;
   int ci, co, s;
 };
 
-// Input value feeding output voxel m (sample-major) at reduction index
-// k = tap * ci + c, or 0 in the zero padding.
-__device__ __forceinline__ bf16 gather_in(const bf16* X, const Geo& g, long long m, long long k) {
+// ---------------------------------------------------------------------------
+// Implicit GEMM on the fifth-generation tensor cores (tcgen05, sm_100 family):
+// D[M][N] = sum_k A(m, k) B(n, k), M tile 128, N <= 64 (a multiple of 16),
+// K in chunks of 64. Four warps stage each chunk's A (128 x 64) and B (N x 64)
+// BF16 tiles into shared memory in the no-swizzle K-major layout of the
+// matrix descriptors (8-row x 16-byte core matrices; core (i, j) of rows
+// 8i..8i+7 and K elements 8j..8j+7 at byte ((8 i) + j) * 128, so the K step
+// between core matrices is 128 bytes and the row-group step 1024 bytes); one
+// thread issues the chunk's four 128 x N x 16 MMAs with the FP32 accumulator
+// in tensor memory and commits them to the chunk buffer's mbarrier. Two
+// chunk buffers: the staging of chunk i + 1 overlaps the MMAs of chunk i.
+// The epilogue reads the accumulator back (tcgen05.ld, one row per thread)
+// and hands each row to Op::store_row. Every mbarrier wait is bounded (about
+// a second of the global timer); a wait that runs out sets *err, and the
+// kernel still waits (bounded) for its MMAs before freeing tensor memory.
+// blockIdx.y splits K (Op::store_row then accumulates with atomics).
+// ---------------------------------------------------------------------------
+namespace tc {
+
+constexpr int kChunkK = 64;
+constexpr int kABytes = 128 * kChunkK * 2;  // 16 KB
+constexpr int kBBytes = 64 * kChunkK * 2;   // 8 KB (N <= 64)
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kSmemBytes = 2 * kStageBytes + 1024;  // two stages, 1 KB alignment slack
+constexpr int kTmemCols = 64;
+
+// Byte offset of the 16-byte segment (row r, K elements 8 k8 .. 8 k8 + 7).
+__device__ __forceinline__ uint32_t kmaj(int r, int k8) {
+  return (uint32_t)(((((r >> 3) << 3) + k8) << 7) + ((r & 7) << 4));
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address / 16
+  d |= (uint64_t)(128 >> 4) << 16;                  // leading (K) byte offset / 16
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride (row-group) byte offset / 16
+  d |= (uint64_t)1 << 46;                           // descriptor version 1; no swizzle, base offset 0
+  return d;
+}
+
+// kind::f16 instruction descriptor: BF16 A and B, FP32 D, both K-major.
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void st_u16(uint32_t addr, unsigned short v) {
+  asm volatile("st.shared.u16 [%0], %1;\n" ::"r"(addr), "h"(v) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (gtimer() - t0 > 1000000000ull) return false;
+  }
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <class Op>
+__global__ void __launch_bounds__(128) k_gemm(Op op, long long M, int N, long long K, long long kper, int* err) {
+  extern __shared__ __align__(1024) uint8_t dsm[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  const uint32_t base = ((uint32_t)__cvta_generic_to_shared(dsm) + 1023u) & ~1023u;
+  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
+  const uint32_t bar1 = (uint32_t)__cvta_generic_to_shared(&bars[1]);
+  const int warp = threadIdx.x >> 5;
+  const long long m0 = (long long)blockIdx.x * 128;
+  const long long kb = (long long)blockIdx.y * kper;
+  const long long ke = min(K, kb + kper);
+  const int nch = ke > kb ? (int)((ke - kb + kChunkK - 1) / kChunkK) : 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(&tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t id = idesc_bf16(128, N);
+  bool ok = true;
+  for (int i = 0; i < nch; ++i) {
+    const int b = i & 1;
+    const uint32_t bar = b ? bar1 : bar0;
+    if (i >= 2 && ok) ok = mbar_wait(bar, (uint32_t)((i - 2) >> 1) & 1u);  // this buffer's MMAs are done
+    const uint32_t sA = base + (uint32_t)b * kStageBytes, sB = sA + kABytes;
+    op.stage(m0, kb + (long long)i * kChunkK, ke, M, N, sA, sB);
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+      for (int s = 0; s < kChunkK / 16; ++s)
+        mma(tmem, sdesc(sA + 256u * s), sdesc(sB + 256u * s), id, (i > 0 || s > 0) ? 1u : 0u);
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                   : "memory");
+    }
+  }
+  if (nch > 0 && ok) ok = mbar_wait((nch - 1) & 1 ? bar1 : bar0, (uint32_t)((nch - 1) >> 1) & 1u);
+  ok = __syncthreads_and(ok) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (ok && nch > 0) {
+    const long long m = m0 + threadIdx.x;
+    float v[64];
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int j = 0; j < N; j += 16) ld16(lane_addr + (uint32_t)j, v + j);
+    if (m < M) op.store_row(m, v, N);
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    // bounded wait for the MMAs this block issued before tensor memory is freed
+    if (nch > 0) (void)mbar_wait((nch - 1) & 1 ? bar1 : bar0, (uint32_t)((nch - 1) >> 1) & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+// Output voxel m's input voxel at tap (or -1 in the zero padding).
+__device__ __forceinline__ long long in_voxel(const Geo& g, long long m, int tap) {
   const long long V = (long long)g.Do.x * g.Do.y * g.Do.z;
   const long long n = m / V;
   const int v = (int)(m - n * V);
-  const int tap = (int)(k / g.ci), c = (int)(k - (long long)tap * g.ci);
   const int iz = (v / (g.Do.x * g.Do.y)) * g.s + tap / 9 - 1;
   const int iy = ((v / g.Do.x) % g.Do.y) * g.s + (tap / 3) % 3 - 1;
   const int ix = (v % g.Do.x) * g.s + tap % 3 - 1;
-  if (iz < 0 || iz >= g.Di.z || iy < 0 || iy >= g.Di.y || ix < 0 || ix >= g.Di.x) return __float2bfloat16(0.f);
-  return X[((((n * g.Di.z + iz) * g.Di.y + iy) * g.Di.x) + ix) * g.ci + c];
+  if (iz < 0 || iz >= g.Di.z || iy < 0 || iy >= g.Di.y || ix < 0 || ix >= g.Di.x) return -1;
+  return ((n * g.Di.z + iz) * g.Di.y + iy) * g.Di.x + ix;
 }
 
-// Forward: Y[m][o] = relu(b[o] + sum_k gather_in(m, k) W[k][o]).
-struct OpFwd {
+// Input voxel m's output voxel reached through tap (or -1): the output
+// voxel o with o * s + tap offset - 1 = in(m) on every axis.
+__device__ __forceinline__ long long out_voxel(const Geo& g, long long m, int tap) {
+  const long long V = (long long)g.Di.x * g.Di.y * g.Di.z;
+  const long long n = m / V;
+  const int v = (int)(m - n * V);
+  int q[3] = {v / (g.Di.x * g.Di.y) + 1 - tap / 9, (v / g.Di.x) % g.Di.y + 1 - (tap / 3) % 3, v % g.Di.x + 1 - tap % 3};
+  const int lim[3] = {g.Do.z, g.Do.y, g.Do.x};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (q[d] < 0 || q[d] % g.s) return -1;
+    q[d] /= g.s;
+    if (q[d] >= lim[d]) return -1;
+  }
+  return ((n * g.Do.z + q[0]) * g.Do.y + q[1]) * g.Do.x + q[2];
+}
+
+// Forward: Y[m][o] = relu(b[o] + sum_{tap, c} X[in(m, tap)][c] W[tap][c][o]);
+// A rows = output voxels (16-byte runs of 8 input channels), B rows = o from
+// Wt[tap][o][c] (the weights transposed so that c is contiguous).
+struct Fwd {
   const bf16* X;
-  const bf16* W;
+  const bf16* Wt;
   const float* bias;
   bf16* Y;
   Geo g;
-  __device__ bf16 a(long long m, long long k) const { return gather_in(X, g, m, k); }
-  __device__ bf16 b(long long k, int n) const { return W[k * g.co + n]; }
-  __device__ void store(long long m, int n, float v) const {
-    Y[m * g.co + n] = __float2bfloat16(fmaxf(v + bias[n], 0.f));
+  __device__ __forceinline__ void stage(long long m0, long long k0, long long ke, long long M, int N, uint32_t sA,
+                                        uint32_t sB) const {
+    for (int e = threadIdx.x; e < 128 * 8; e += 128) {
+      const int r = e >> 3, k8 = e & 7;
+      const long long m = m0 + r, k = k0 + 8 * k8;
+      const bf16* src = X;
+      int bytes = 0;
+      if (m < M && k < ke) {
+        const int tap = (int)(k / g.ci), c = (int)(k - (long long)tap * g.ci);
+        const long long iv = in_voxel(g, m, tap);
+        if (iv >= 0) {
+          src = X + iv * g.ci + c;
+          bytes = 16;
+        }
+      }
+      cp16(sA + kmaj(r, k8), src, bytes);
+    }
+    for (int e = threadIdx.x; e < N * 8; e += 128) {
+      const int n = e >> 3, k8 = e & 7;
+      const long long k = k0 + 8 * k8;
+      const bf16* src = Wt;
+      int bytes = 0;
+      if (k < ke) {
+        const int tap = (int)(k / g.ci), c = (int)(k - (long long)tap * g.ci);
+        src = Wt + ((long long)tap * g.co + n) * g.ci + c;
+        bytes = 16;
+      }
+      cp16(sB + kmaj(n, k8), src, bytes);
+    }
+  }
+  __device__ __forceinline__ void store_row(long long m, const float* v, int N) const {
+    bf16* y = Y + m * g.co;
+    for (int n = 0; n < N; n += 2)
+      *reinterpret_cast<__nv_bfloat162*>(y + n) =
+          __floats2bfloat162_rn(fmaxf(v[n] + bias[n], 0.f), fmaxf(v[n + 1] + bias[n + 1], 0.f));
   }
 };
 
 // Data gradient masked by the ReLU of the layer's input:
-// dZin[m][c] = [X[m][c] > 0] sum_{tap, o} dZ[out(m, tap)][o] W[tap][c][o],
-// out(m, tap) = (in(m) + 1 - k) / s where that divides exactly and lands inside.
-struct OpDgrad {
+// dZin[m][c] = [X[m][c] > 0] sum_{tap, o} dZ[out(m, tap)][o] W[tap][c][o];
+// A rows = input voxels (runs of 8 output channels of dZ), B rows = c
+// (runs of 8 o of W[tap][c][.], contiguous in the parameter layout).
+struct Dgrad {
   const bf16* dZ;
   const bf16* W;
   const bf16* X;
   bf16* dZin;
   Geo g;
-  __device__ bf16 a(long long m, long long k) const {
-    const long long V = (long long)g.Di.x * g.Di.y * g.Di.z;
-    const long long n = m / V;
-    const int v = (int)(m - n * V);
-    const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
-    int q[3] = {v / (g.Di.x * g.Di.y) + 1 - tap / 9, (v / g.Di.x) % g.Di.y + 1 - (tap / 3) % 3,
-                v % g.Di.x + 1 - tap % 3};
-    const int lim[3] = {g.Do.z, g.Do.y, g.Do.x};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (q[d] < 0 || q[d] % g.s) return __float2bfloat16(0.f);
-      q[d] /= g.s;
-      if (q[d] >= lim[d]) return __float2bfloat16(0.f);
+  __device__ __forceinline__ void stage(long long m0, long long k0, long long ke, long long M, int N, uint32_t sA,
+                                        uint32_t sB) const {
+    for (int e = threadIdx.x; e < 128 * 8; e += 128) {
+      const int r = e >> 3, k8 = e & 7;
+      const long long m = m0 + r, k = k0 + 8 * k8;
+      const bf16* src = dZ;
+      int bytes = 0;
+      if (m < M && k < ke) {
+        const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
+        const long long ov = out_voxel(g, m, tap);
+        if (ov >= 0) {
+          src = dZ + ov * g.co + o;
+          bytes = 16;
+        }
+      }
+      cp16(sA + kmaj(r, k8), src, bytes);
     }
-    return dZ[((((n * g.Do.z + q[0]) * g.Do.y + q[1]) * g.Do.x) + q[2]) * g.co + o];
+    for (int e = threadIdx.x; e < N * 8; e += 128) {
+      const int n = e >> 3, k8 = e & 7;
+      const long long k = k0 + 8 * k8;
+      const bf16* src = W;
+      int bytes = 0;
+      if (k < ke) {
+        const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
+        src = W + ((long long)tap * g.ci + n) * g.co + o;
+        bytes = 16;
+      }
+      cp16(sB + kmaj(n, k8), src, bytes);
+    }
   }
-  __device__ bf16 b(long long k, int c) const {
-    const int tap = (int)(k / g.co), o = (int)(k - (long long)tap * g.co);
-    return W[((long long)tap * g.ci + c) * g.co + o];
-  }
-  __device__ void store(long long m, int c, float v) const {
-    const long long i = m * g.ci + c;
-    dZin[i] = __float2bfloat16(__bfloat162float(X[i]) > 0.f ? v : 0.f);
+  __device__ __forceinline__ void store_row(long long m, const float* v, int N) const {
+    const bf16* x = X + m * g.ci;
+    bf16* d = dZin + m * g.ci;
+    for (int n = 0; n < N; ++n) d[n] = __float2bfloat16(__bfloat162float(x[n]) > 0.f ? v[n] : 0.f);
   }
 };
 
-// Weight gradient: dW[k][o] += sum_m gather_in(m, k) dZ[m][o] (rows = k).
-struct OpWgrad {
+// Weight gradient: dW[tap][c][o] += sum_m X[in(m, tap)][c] dZ[m][o]; rows
+// r = tap * ci + c, K = output voxels m. Both operands run along the
+// channels in memory, so each 16-byte load (8 channels of one voxel) is
+// written to shared memory transposed, one BF16 element per K position.
+struct Wgrad {
   const bf16* X;
   const bf16* dZ;
   float* dW;
   Geo g;
-  __device__ bf16 a(long long k, long long m) const { return gather_in(X, g, m, k); }
-  __device__ bf16 b(long long m, int o) const { return dZ[m * g.co + o]; }
-  __device__ void store(long long k, int o, float v) const { atomicAdd(&dW[k * g.co + o], v); }
+  __device__ __forceinline__ void stage(long long r0, long long k0, long long ke, long long M, int N, uint32_t sA,
+                                        uint32_t sB) const {
+    for (int e = threadIdx.x; e < 16 * kChunkK; e += 128) {
+      const int r8 = e / kChunkK, kl = e - r8 * kChunkK;  // rows 8 r8 .. 8 r8 + 7 at K position kl
+      const long long r = r0 + 8 * r8, m = k0 + kl;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (r < M && m < ke) {
+        const int tap = (int)(r / g.ci), c = (int)(r - (long long)tap * g.ci);
+        const long long iv = in_voxel(g, m, tap);
+        if (iv >= 0) val = *reinterpret_cast<const uint4*>(X + iv * g.ci + c);
+      }
+      const unsigned short* h = reinterpret_cast<const unsigned short*>(&val);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) st_u16(sA + kmaj(8 * r8 + j, kl >> 3) + ((kl & 7) << 1), h[j]);
+    }
+    for (int e = threadIdx.x; e < (N / 8) * kChunkK; e += 128) {
+      const int n8 = e / kChunkK, kl = e - n8 * kChunkK;
+      const long long m = k0 + kl;
+      uint4 val = make_uint4(0u, 0u, 0u, 0u);
+      if (m < ke) val = *reinterpret_cast<const uint4*>(dZ + m * g.co + 8 * n8);
+      const unsigned short* h = reinterpret_cast<const unsigned short*>(&val);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) st_u16(sB + kmaj(8 * n8 + j, kl >> 3) + ((kl & 7) << 1), h[j]);
+    }
+  }
+  __device__ __forceinline__ void store_row(long long r, const float* v, int N) const {
+    float* d = dW + r * g.co;
+    for (int n = 0; n < N; ++n)
+      if (v[n] != 0.f) atomicAdd(d + n, v[n]);
+  }
 };
+
+}  // namespace tc
+
+// Wt[tap][o][c] = W[tap][c][o] (BF16), the forward pass's B operand layout.
+__global__ void k_transpose_w(const bf16* W, bf16* Wt, int ci, int co) {
+  const int n = 27 * ci * co;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int tap = i / (ci * co), rem = i - tap * ci * co, c = rem / co, o = rem - c * co;
+    Wt[((long long)tap * co + o) * ci + c] = W[i];
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Head: mean pool, fc1 + ReLU, fc2 (one block per sample, FP32).
@@ -580,6 +762,8 @@ struct Net {
   std::vector<void*> allocs;
   float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
   bf16* theta16 = nullptr;
+  bf16* theta16t = nullptr;  // conv weights as Wt[tap][co][ci] (the forward pass's B operand)
+  int* terr = nullptr;       // set by a tensor-core GEMM whose bounded wait ran out
   uint8_t* lab = nullptr;
   Core* core = nullptr;
   bf16* act[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // act[i]: output of conv i (1-based)
@@ -620,11 +804,17 @@ struct Net {
     if (shared) {
       theta = shared->theta;
       theta16 = shared->theta16;
+      theta16t = shared->theta16t;
+      terr = shared->terr;
       grad = shared->grad;
       m = shared->m;
       v = shared->v;
-    } else if ((r = alloc(&theta, off.total)) || (r = alloc(&theta16, off.total))) {
+    } else if ((r = alloc(&theta, off.total)) || (r = alloc(&theta16, off.total)) ||
+               (r = alloc(&theta16t, off.total)) || (r = alloc(&terr, 1))) {
       return r;
+    } else if (cudaMemsetAsync(terr, 0, sizeof(int), st) != cudaSuccess) {
+      err = "device memset failed";
+      return HH_ERR_CUDA;
     }
     if ((r = alloc(&lab, B * vox(box))) ||
         (r = alloc(&core, B)) || (r = alloc(&h0, (long long)B * kPoolC)) || (r = alloc(&h1, (long long)B * kHid)) ||
@@ -650,13 +840,33 @@ struct Net {
     return HH_OK;
   }
 
+  // tensor-core implicit GEMM: M rows in tiles of 128, N (16, 32 or 64)
+  // columns, K split over `splits` blocks in whole chunks of 64
   template <class Op>
   hh_status gemm(const Op& op, long long M, int N, long long K, int splits = 1) {
-    const long long kper = ((K + splits - 1) / splits + 31) / 32 * 32;
-    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)splits);
+    if (N < 16 || N > 64 || N % 16) {
+      err = "surrogate: GEMM width outside 16..64";
+      return HH_ERR_UNSUPPORTED;
+    }
+    const long long kper = ((K + splits - 1) / splits + tc::kChunkK - 1) / tc::kChunkK * tc::kChunkK;
+    const int sp = (int)((K + kper - 1) / kper);
+    CNN_CK(cudaFuncSetAttribute(tc::k_gemm<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    dim3 grid((unsigned)((M + 127) / 128), (unsigned)sp);
     ++launches;
-    k_igemm<Op><<<grid, 128, 0, st>>>(op, M, N, K, kper);
+    tc::k_gemm<Op><<<grid, 128, tc::kSmemBytes, st>>>(op, M, N, K, kper, terr);
     CNN_CK(cudaGetLastError());
+    return HH_OK;
+  }
+
+  // after a synchronization: HH_ERR_DEVICE_TIMEOUT if a GEMM's wait ran out
+  hh_status timeout_check() {
+    int e = 0;
+    CNN_CK(cudaMemcpyAsync(&e, terr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CNN_CK(cudaStreamSynchronize(st));
+    if (e) {
+      err = "surrogate: a tensor-core GEMM's mbarrier wait ran out";
+      return HH_ERR_DEVICE_TIMEOUT;
+    }
     return HH_OK;
   }
 
@@ -670,9 +880,14 @@ struct Net {
         lab, core, nb, dims[0], theta + off.w[0], theta + off.b[0], act[1]);
     CNN_CK(cudaGetLastError());
     for (int i = 1; i < 4; ++i) {
+      ++launches;
+      k_transpose_w<<<64, 256, 0, st>>>(theta16 + off.w[i], theta16t + off.w[i], kConv[i].ci, kConv[i].co);
+      CNN_CK(cudaGetLastError());
+    }
+    for (int i = 1; i < 4; ++i) {
       const Geo g = geo(i);
       const long long M = nb * vox(g.Do);
-      OpFwd op{act[i], theta16 + off.w[i], theta + off.b[i], act[i + 1], g};
+      tc::Fwd op{act[i], theta16t + off.w[i], theta + off.b[i], act[i + 1], g};
       hh_status r = gemm(op, M, g.co, 27LL * g.ci);
       if (r) return r;
     }
@@ -699,7 +914,7 @@ struct Net {
       const long long Mi = nb * vox(g.Di);
       // weight and bias gradients of conv i+1 (0-based i)
       const int splits = (int)std::min<long long>(64, std::max<long long>(1, Mo / 4096));
-      OpWgrad ow{act[i], dact[i + 1], grad + off.w[i], g};
+      tc::Wgrad ow{act[i], dact[i + 1], grad + off.w[i], g};
       hh_status r = gemm(ow, 27LL * g.ci, g.co, Mo, splits);
       if (r) return r;
       ++launches;
@@ -707,7 +922,7 @@ struct Net {
                                                                                       grad + off.b[i]);
       CNN_CK(cudaGetLastError());
       // gradient at the layer's input, masked by the previous ReLU
-      OpDgrad od{dact[i + 1], theta16 + off.w[i], act[i], dact[i], g};
+      tc::Dgrad od{dact[i + 1], theta16 + off.w[i], act[i], dact[i], g};
       if ((r = gemm(od, Mi, g.ci, 27LL * g.co))) return r;
     }
     const long long V1 = vox(dims[1]);
@@ -836,6 +1051,7 @@ extern "C" hh_status hh_cnn_forward(hh_ctx* h, const uint8_t* labels, int count,
               cudaSuccess ||
           cudaStreamSynchronize(net.st) != cudaSuccess)
         return ctx_fail(h, HH_ERR_CUDA, "surrogate forward failed");
+      if ((s = net.timeout_check())) return ctx_fail(h, s, net.err.c_str());
       for (int j = 0; j < nb; ++j) std::memcpy(out + (size_t)g[b0 + j] * kOut, o.data() + (size_t)j * kOut, kOut * 4);
     }
   }
@@ -878,6 +1094,7 @@ extern "C" hh_status hh_cnn_loss_grad(hh_ctx* h, const uint8_t* labels, int coun
   if (cudaMemcpyAsync(grad, par.grad, par.off.total * sizeof(float), cudaMemcpyDeviceToHost, par.st) != cudaSuccess ||
       cudaStreamSynchronize(par.st) != cudaSuccess)
     return ctx_fail(h, HH_ERR_CUDA, "surrogate gradients failed");
+  if ((s = par.timeout_check())) return ctx_fail(h, s, par.err.c_str());
   *loss = l / (double(count) * kOut);
   return HH_OK;
 }
@@ -1004,6 +1221,7 @@ extern "C" hh_status hh_surrogate_train(hh_ctx* h, const uint8_t* labels, int co
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return ctx_fail(h, HH_ERR_CUDA, "surrogate training failed");
+  if ((s = par.timeout_check())) return ctx_fail(h, s, par.err.c_str());
   return HH_OK;
 }
 
