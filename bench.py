@@ -71,6 +71,10 @@ def parse():
                          "headline cores with the surrogate standing in for the subimages its gate accepts "
                          "(needs --headline-rows > 0)")
     ap.add_argument("--surrogate-epochs", type=int, default=60)
+    ap.add_argument("--study", default="", choices=["", "richardson"],
+                    help="richardson: instead of the benchmark, the subimage-size study on the 256^3 three-phase "
+                         "image (direct solve, hierarchical at n = 16..128 and buffers 0, 4, 8, fits in 1/n, "
+                         "the planner's choice); one JSON line")
     ap.add_argument("--surrogate-spread", type=float, default=0.02)
     return ap.parse_args()
 
@@ -584,8 +588,59 @@ def cost_scaling(ctx, img, ph, tol):
             "iters_single": it1, "t_hierarchical_ms": tH, "exponent_single": a, "exponent_hierarchical": b}
 
 
+def richardson_study(args):
+    """The paper's Section 5 study on a synthetic stand-in: the 256^3
+    three-phase Gaussian-random-field image (pore 18 %, clay 12 %, solid;
+    correlation length 6), its direct FP32 solve, the two-level scheme at
+    n = 16, 32, 64, 128 with buffers 0, 4 and 8, the least-squares fits
+    M(n) = M_inf + C / n per buffer, the arithmetic means (AM), a free
+    power-law exponent of the HH error, and the planner's choice of (n, b)
+    for a 0.5 % target from the fitted constants."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_2208_02320_gb300 import Context, _build, plan_partition
+    _build.build()
+    img = synth.grf_three_phase(n=256, ell=6.0, seed=2208023202)
+    ph = synth.PHASES_SOLID_CLAY_PORE
+    dimg = torch.from_numpy(img).cuda()
+    ctx = Context(0)
+    opt = dict(precision=args.precision, tol=args.tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d = ctx.homogenize_direct(dimg, ph, **opt)
+    t_direct = time.perf_counter() - t0
+    ns = [16, 32, 64, 128]
+    rows, fits, crel = [], {}, []
+    for b in (0, 4, 8):
+        t0 = time.perf_counter()
+        e = ctx.extrapolate(dimg, ph, ns, b=b, **opt)
+        t = time.perf_counter() - t0
+        for n, r in zip(ns, e["per_n"]):
+            rows.append(dict(n=n, b=b, K=r["K"], G=r["G"], K_am=r["K_am"], G_am=r["G_am"],
+                             K_err=(r["K"] - d["K"]) / d["K"], G_err=(r["G"] - d["G"]) / d["G"],
+                             K_am_err=(r["K_am"] - d["K"]) / d["K"], G_am_err=(r["G_am"] - d["G"]) / d["G"],
+                             status=r["status"], iters_max=r["iters_max"]))
+        errs = np.array([[abs(x["K_err"]), abs(x["G_err"])] for x in rows if x["b"] == b])
+        slope = [float(np.polyfit(np.log(ns), np.log(np.maximum(errs[:, j], 1e-12)), 1)[0]) for j in range(2)]
+        fits[b] = dict(K_inf=e["K_inf"], C_K=e["C_K"], G_inf=e["G_inf"], C_G=e["C_G"],
+                       K_inf_vs_direct=(e["K_inf"] - d["K"]) / d["K"], G_inf_vs_direct=(e["G_inf"] - d["G"]) / d["G"],
+                       free_exponent_K=slope[0], free_exponent_G=slope[1], wall_s=t)
+        crel.append(max(abs(e["C_K"]) / e["K_inf"], abs(e["C_G"]) / e["G_inf"]))
+    plan = plan_partition(img.shape, 1, [0, 4, 8], crel, a=3.66, eps=0.005)
+    print(json.dumps({"study": "richardson", "image": "grf_three_phase 256^3 (ell 6, pore 18 %, clay 12 %)",
+                      "precision": args.precision, "tol": args.tol,
+                      "direct": dict(K=d["K"], G=d["G"], iters_max=d["iters_max"], status=d["status"],
+                                     wall_s=t_direct),
+                      "rows": rows, "fits": {str(k): v for k, v in fits.items()},
+                      "plan_0.5pct": plan}))
+
+
 def main():
     args = parse()
+    if args.study == "richardson":
+        richardson_study(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
