@@ -451,6 +451,64 @@ __device__ __forceinline__ PlaneSmem<T> plane_layout(char* base, int nx, int ny,
   return s;
 }
 
+// Row-major walk e = hi * W + lo (0 <= lo < W) of one thread's indices
+// e0, e0 + S, e0 + 2 S, ...: after the first position, each step adds the
+// quotient and remainder of S / W with one carry, no division.
+struct Walk2 {
+  int hi, lo;
+  int dhi, dlo, W;
+  __device__ __forceinline__ Walk2(int e0, int S, int W_) : W(W_) {
+    hi = e0 / W_;
+    lo = e0 - hi * W_;
+    dhi = S / W_;
+    dlo = S - dhi * W_;
+  }
+  __device__ __forceinline__ void next() {
+    lo += dlo;
+    hi += dhi;
+    if (lo >= W) {
+      lo -= W;
+      ++hi;
+    }
+  }
+};
+
+// Row-major walk e = (a * B + b) * W + lo (0 <= b < B, 0 <= lo < W) with a
+// fixed stride S, without division after the first position: the row
+// a * B + b advances by S / W or S / W + 1 (when lo carries), and each of the
+// two increments is split into its quotient and remainder by B once.
+struct Walk3 {
+  int a, b, lo;
+  int W, B, dlo, da0, db0, da1, db1;
+  __device__ __forceinline__ Walk3(int e0, int S, int W_, int B_) : W(W_), B(B_) {
+    const int row = e0 / W_;
+    lo = e0 - row * W_;
+    a = row / B_;
+    b = row - a * B_;
+    const int dhi = S / W_;
+    dlo = S - dhi * W_;
+    da0 = dhi / B_;
+    db0 = dhi - da0 * B_;
+    da1 = (dhi + 1) / B_;
+    db1 = (dhi + 1) - da1 * B_;
+  }
+  __device__ __forceinline__ void next() {
+    lo += dlo;
+    int da = da0, db = db0;
+    if (lo >= W) {
+      lo -= W;
+      da = da1;
+      db = db1;
+    }
+    b += db;
+    a += da;
+    if (b >= B) {
+      b -= B;
+      ++a;
+    }
+  }
+};
+
 // x-line and y-line views of the pair-row plane.
 __device__ __forceinline__ Lines plane_rows(int ny, int RP) { return Lines{3 * ny, 1 << 30, 0, RP, 1, false}; }
 __device__ __forceinline__ Lines plane_cols(int ny, int nxh, int RP) {
@@ -463,24 +521,9 @@ __device__ __forceinline__ int plane_spec_at(int c, int ky, int kx, int ny, int 
 
 constexpr int kPackPerThread = 4;
 
-// Global-to-shared copy of n elements, dst[sidx(e)] = src[gidx(e)], by
-// asynchronous element copies (cp.async, sm_80 and later): every copy of a
-// thread is in flight at once and none is staged through registers. The
-// caller waits with copy_async_wait() before its barrier. Elements are 8 or
-// 16 bytes, aligned to their size at both ends.
-template <typename V, typename GI, typename SI>
-__device__ __forceinline__ void copy_async(V* dst, const V* src, int n, GI gidx, SI sidx) {
-  static_assert(sizeof(V) == 8 || sizeof(V) == 16, "8- or 16-byte elements");
-  for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst + sidx(e));
-    const V* g = src + gidx(e);
-    if constexpr (sizeof(V) == 8)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(g) : "memory");
-    else
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
-  }
-}
-
+// Global-to-shared element copies are issued as cp.async (sm_80 and later):
+// every copy of a thread is in flight at once and none is staged through
+// registers; the caller waits with copy_async_wait() before its barrier.
 __device__ __forceinline__ void copy_async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Split every transformed packed row Z = A + iB (A, B spectra of real rows)
@@ -710,9 +753,10 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     DotAcc<T> dot;
     const long long zoff = (long long)z * ny * nx;
     // voxel phase: stress of the whole plane into the pair rows
-    for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
-      const int y = v / nx;
-      const int x = v - y * nx;
+    Walk2 wv(threadIdx.x, blockDim.x, nx);
+    for (int v = threadIdx.x; v < ny * nx; v += blockDim.x, wv.next()) {
+      const int y = wv.hi;
+      const int x = wv.lo;
       T s[6];
       fwd_voxel<T, MODE>(P, d, V, zoff + v, k, sm.lm, s, dot);
 #pragma unroll
@@ -725,11 +769,12 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     // store the plane of the spectrum: spec[c][z][kyp][kx]
     C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
-    for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x) {
-      const int c = e / pl;
-      const int rem = e - c * pl;
-      const int ky = rem / nxh;
-      sp[((long long)c * d.nz + z) * pl + rem] = sm.S[plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP)];
+    {
+      // e = (c * ny + ky) * nxh + kx
+      Walk3 wk(threadIdx.x, blockDim.x, nxh, ny);
+      for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x, wk.next())
+        sp[((long long)wk.a * d.nz + z) * pl + wk.b * nxh + wk.lo] =
+            sm.S[plane_spec_at(wk.a, wk.b, wk.lo, ny, nxh, RP)];
     }
     if (fwd_slot<MODE>() >= 0) {
       double acc[1] = {dot.value()};
@@ -840,6 +885,7 @@ template <typename T>
 struct ColumnSmem {
   C2<T>* tile;  // 6 * nz * cw
   C2<T>* twz;   // nz
+  T* fz;        // nz: wave-vector component m_z / nz of each storage position
   int* sfz;     // nz
   int* sfy;     // ny
   double* red;  // 32 * 7
@@ -853,6 +899,8 @@ __device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int n
   o += sizeof(C2<T>) * 6 * (size_t)nz * cw;
   s.twz = reinterpret_cast<C2<T>*>(base + o);
   o += sizeof(C2<T>) * nz;
+  s.fz = reinterpret_cast<T*>(base + o);
+  o += sizeof(T) * nz;
   s.sfz = reinterpret_cast<int*>(base + o);
   o += sizeof(int) * nz;
   s.sfy = reinterpret_cast<int*>(base + o);
@@ -888,38 +936,57 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     const AxisPlan& ay = P.plans[d.py];  // by reference: no per-thread copy
     if (d.pz != tab_pz || d.py != tab_py || d.cw != tab_cw) {  // same plans and width: same layout
       load_tw<T>(sm.twz, P.tw, az);
-      for (int t = threadIdx.x; t < nz; t += blockDim.x) sm.sfz[t] = P.itab[az.sf_off + t];
+      for (int t = threadIdx.x; t < nz; t += blockDim.x) {
+        const int mz = P.itab[az.sf_off + t];
+        sm.sfz[t] = mz;
+        sm.fz[t] = T(mz) / T(nz);
+      }
       for (int t = threadIdx.x; t < ny; t += blockDim.x) sm.sfy[t] = P.itab[ay.sf_off + t];
       tab_pz = d.pz;
       tab_py = d.py;
       tab_cw = d.cw;
     }
     C2<T>* sp = P.spec + d.spc_off + j0;
-    copy_async(
-        sm.tile, sp, 6 * nz * W,
-        [=](int e) {
-          const int cz = e / W;  // c * nz + z
-          return (long long)cz * pl + (e - cz * W);
-        },
-        [](int e) { return e; });
+    {
+      // tile[e] = sp[cz * pl + jl], e = cz * W + jl (cz = c * nz + z)
+      Walk2 wk(threadIdx.x, blockDim.x, W);
+      for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x, wk.next()) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sm.tile + e);
+        const C2<T>* g = sp + (long long)wk.hi * pl + wk.lo;
+        if constexpr (sizeof(C2<T>) == 8)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(g) : "memory");
+        else
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(g) : "memory");
+      }
+    }
     copy_async_wait();
     __syncthreads();
     const Lines Lz{6 * W, W, nz * W, 1, W, true};
     fft_lines<T, false>(sm.tile, Lz, az, sm.twz);
     // projection (or the basic scheme's Green operator) of every mode
     double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int e = threadIdx.x; e < nz * W; e += blockDim.x) {
-      const int jl = e % W;
-      const int kzp = e / W;
-      const int j = j0 + jl;
-      const int kyp = j / nxh;
-      const int kx = j - kyp * nxh;
-      const int my = sm.sfy[kyp];
+    // (kzp, jl) of mode e = kzp * W + jl by a division-free walk; the column's
+    // (ky, kx) wave-vector components change only with jl
+    Walk2 wm(threadIdx.x, blockDim.x, W);
+    int jl_c = -1, kx = 0, my = 0;
+    T x0c = T(0), x1c = T(0);
+    for (int e = threadIdx.x; e < nz * W; e += blockDim.x, wm.next()) {
+      const int jl = wm.lo;
+      const int kzp = wm.hi;
+      if (jl != jl_c) {
+        jl_c = jl;
+        const int j = j0 + jl;
+        const int kyp = j / nxh;
+        kx = j - kyp * nxh;
+        my = sm.sfy[kyp];
+        x0c = T(kx) / T(nx);
+        x1c = T(my) / T(ny);
+      }
       const int mz = sm.sfz[kzp];
       const bool nyq_x = (nx % 2 == 0) && (2 * kx == nx);
       const bool nyq_y = (ny % 2 == 0) && (2 * my == ny);
       const bool nyq_z = (nz % 2 == 0) && (2 * mz == nz);
-      T x0 = T(kx) / T(nx), x1 = T(my) / T(ny), x2 = T(mz) / T(nz);
+      T x0 = x0c, x1 = x1c, x2 = sm.fz[kzp];
       if (P.nyq_mode == 0) {
         if (nyq_x) x0 = T(0);
         if (nyq_y) x1 = T(0);
@@ -960,10 +1027,10 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
     }
     __syncthreads();
     fft_lines<T, true>(sm.tile, Lz, az, sm.twz);
-    for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x) {
-      const int jl = e % W;
-      const int cz = e / W;
-      sp[(long long)cz * pl + jl] = sm.tile[e];
+    {
+      Walk2 wk(threadIdx.x, blockDim.x, W);
+      for (int e = threadIdx.x; e < 6 * nz * W; e += blockDim.x, wk.next())
+        sp[(long long)wk.hi * pl + wk.lo] = sm.tile[e];
     }
     __syncthreads();
   }
@@ -1080,18 +1147,18 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
     const long long zpl = (long long)z * pl, cpl = (long long)d.nz * pl;
-    copy_async(
-        sm.S, sp, 6 * pl,
-        [=](int e) {
-          const int c = e / pl;
-          return c * cpl + zpl + (e - c * pl);
-        },
-        [=](int e) {
-          const int c = e / pl;
-          const int rem = e - c * pl;
-          const int ky = rem / nxh;
-          return plane_spec_at(c, ky, rem - ky * nxh, ny, nxh, RP);
-        });
+    {
+      // e = (c * ny + ky) * nxh + kx
+      Walk3 wk(threadIdx.x, blockDim.x, nxh, ny);
+      for (int e = threadIdx.x; e < 6 * pl; e += blockDim.x, wk.next()) {
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(sm.S + plane_spec_at(wk.a, wk.b, wk.lo, ny, nxh, RP));
+        const C2<T>* g = sp + wk.a * cpl + zpl + wk.b * nxh + wk.lo;
+        if constexpr (sizeof(C2<T>) == 8)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(g) : "memory");
+        else
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(g) : "memory");
+      }
+    }
     copy_async_wait();
     __syncthreads();
     fft_lines<T, true>(sm.S, plane_cols(ny, nxh, RP), ay, sm.twy);
@@ -1101,9 +1168,10 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
     DotAcc<T> acc[3];
     const T invV = T(1) / T(V);
     const long long zoff = (long long)z * ny * nx;
-    for (int v = threadIdx.x; v < ny * nx; v += blockDim.x) {
-      const int y = v / nx;
-      const int x = v - y * nx;
+    Walk2 wv(threadIdx.x, blockDim.x, nx);
+    for (int v = threadIdx.x; v < ny * nx; v += blockDim.x, wv.next()) {
+      const int y = wv.hi;
+      const int x = wv.lo;
       T qv[6];
 #pragma unroll
       for (int c2 = 0; c2 < 3; ++c2) {

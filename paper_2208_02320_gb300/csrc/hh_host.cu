@@ -216,7 +216,7 @@ static size_t plane_smem_bytes(int nx, int ny, int nphase) {
 
 template <typename T>
 static size_t column_smem_bytes(int cw, int nz, int ny) {
-  size_t o = sizeof(C2<T>) * (6 * (size_t)nz * cw + nz) + sizeof(int) * ((size_t)nz + ny);
+  size_t o = sizeof(C2<T>) * (6 * (size_t)nz * cw + nz) + sizeof(T) * (size_t)nz + sizeof(int) * ((size_t)nz + ny);
   o = (o + 7) & ~size_t(7);
   o += 32 * 7 * sizeof(double);  // block reduction of the basic scheme's residual partials
   return (o + 15) & ~size_t(15);

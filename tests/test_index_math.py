@@ -61,3 +61,64 @@ def test_fused_cluster_index_maps(shape, C):
     if C > nz:
         pytest.skip("a cluster never has more blocks than planes")
     _check_cluster(nx, ny, nz, C)
+
+
+# ------------------------------------------------ division-free index walks
+# The plane and column passes walk e = tid, tid + S, ... (S = 256 threads)
+# through row-major index spaces without dividing after the first position
+# (Walk2: e = hi * W + lo; Walk3: e = (a * B + b) * W + lo). These mirror the
+# device structs step for step and check them against divmod over every
+# extent the passes use.
+
+def _walk2(e0, S, W):
+    hi, lo = divmod(e0, W)
+    dhi, dlo = divmod(S, W)
+    while True:
+        yield hi, lo
+        lo += dlo
+        hi += dhi
+        if lo >= W:
+            lo -= W
+            hi += 1
+
+
+def _walk3(e0, S, W, B):
+    row, lo = divmod(e0, W)
+    a, b = divmod(row, B)
+    dhi, dlo = divmod(S, W)
+    da0, db0 = divmod(dhi, B)
+    da1, db1 = divmod(dhi + 1, B)
+    while True:
+        yield a, b, lo
+        lo += dlo
+        da, db = da0, db0
+        if lo >= W:
+            lo -= W
+            da, db = da1, db1
+        b += db
+        a += da
+        if b >= B:
+            b -= B
+            a += 1
+
+
+def test_walk2_matches_divmod():
+    S = 256
+    for W in list(range(1, 50)) + [64, 96, 128, 255, 256, 257, 300]:
+        n = 6 * 48 * W
+        for tid in range(0, S, 7):
+            g = _walk2(tid, S, W)
+            for e in range(tid, n, S):
+                assert next(g) == divmod(e, W), (W, tid, e)
+
+
+def test_walk3_matches_divmod():
+    S = 256
+    for W in range(1, 26):          # nxh of edges 1..48
+        for B in range(1, 50):      # ny
+            n = 6 * B * W
+            for tid in (0, 1, 37, 128, 255):
+                g = _walk3(tid, S, W, B)
+                for e in range(tid, n, S):
+                    row, lo = divmod(e, W)
+                    assert next(g) == (*divmod(row, B), lo), (W, B, tid, e)
