@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--fused", type=int, default=-1,
                     help="1: level-1 solves by the fused cluster kernel, 0: the multi-pass solver, -1: the "
                          "library's default")
+    ap.add_argument("--shape-kernels", type=int, default=1,
+                    help="1: plane and column passes compiled for the workload's common shapes (the library "
+                         "default), 0: the generic passes for every shape")
     ap.add_argument("--fixed-iters", type=int, default=0,
                     help="> 0: every load case runs exactly this many iterations (short launches for profiling "
                          "runs; the default solves to tol)")
@@ -161,8 +164,8 @@ def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     # the sources of the multi-pass field kernels and the compile flags
-    for f in ("csrc/hh_device.cuh", "csrc/hh_fftcore.cuh", "csrc/hh_fft2.cuh", "csrc/hh_fft2_inst.cu",
-              "csrc/hh_ctmath.h", "_build.py"):
+    for f in ("csrc/hh_device.cuh", "csrc/hh_plane_ct.cuh", "csrc/hh_fftcore.cuh", "csrc/hh_fft2.cuh",
+              "csrc/hh_fft2_inst.cu", "csrc/hh_ctmath.h", "_build.py"):
         with open(os.path.join(ROOT, "paper_2208_02320_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -302,7 +305,7 @@ def run_gb300(args):
     img, ph, boxes, slabs = workload(args.tile_rows)
     dimg = torch.from_numpy(img).to(f"cuda:{local}")
     ctx = Context(local)
-    opt = dict(precision=args.precision, tol=args.tol, profile=1)
+    opt = dict(precision=args.precision, tol=args.tol, profile=1, shape_kernels=args.shape_kernels)
     if args.fixed_iters > 0:
         opt["fixed_iters"] = args.fixed_iters
     if args.fused >= 0:

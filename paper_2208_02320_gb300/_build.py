@@ -24,7 +24,7 @@ UNITS = [("hh_host.cu", "hh_host.o", []), ("hh_cnn.cu", "hh_cnn.o", [])] + [
     for name, t, inv in (("f32_fwd", "float", 0), ("f32_inv", "float", 1), ("f64_fwd", "double", 0),
                          ("f64_inv", "double", 1))]
 DEPS = [os.path.join(CSRC, f) for f in ("hh_host.cu", "hh_cnn.cu", "hh_fft2_inst.cu", "hh_device.cuh", "hh_post.cuh",
-                                        "hh_fused.cuh",
+                                        "hh_fused.cuh", "hh_plane_ct.cuh",
                                         "hh_fftcore.cuh", "hh_fft2.cuh", "hh_ctmath.h", "hh_internal.h")] + [
     os.path.join(ROOT, "include", "hh.h"), os.path.abspath(__file__)]
 

@@ -51,6 +51,7 @@ class Options(ctypes.Structure):
         ("autotune", ctypes.c_int),
         ("wave_boxes", ctypes.c_int),
         ("fused", ctypes.c_int),
+        ("shape_kernels", ctypes.c_int),
     ]
 
 

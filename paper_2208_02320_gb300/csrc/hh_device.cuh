@@ -57,6 +57,8 @@ struct Prob {
   int rows;                          // rows per row-streaming item; 0: whole planes
   int cw;                            // spectrum columns (ky, kx) per column-pass item
   int fused;                         // 1: solved whole by the fused cluster kernel (hh_fused.cuh)
+  int ct_plane;                      // plane passes: edge of the square plane's compiled body, 0: generic
+  int ct_col;                        // column pass: nz * 64 + cw of the compiled body, 0: generic
   long long med_off;                 // iso: byte offset of labels; aniso: element offset of C21
   long long fld_off;                 // element offset of r, p, q (6 V each)
   long long spc_off;                 // complex offset of the spectrum (6 nz ny nxh)
@@ -287,11 +289,16 @@ __device__ __forceinline__ double frob_w(int c) { return c < 3 ? 1.0 : 2.0; }
 // to lo. The FP64 pipe of this GPU runs at a small fraction of the FP32 rate,
 // so per-element FP64 arithmetic is avoided; the thread's total is converted
 // to FP64 once, for the block reduction. The _rn intrinsics keep the compiler
-// from contracting the two-sum into fused multiply-adds.
+// from contracting the two-sum into fused multiply-adds. The CG passes in
+// FP32 add one value per voxel and product (add_sum): the sum over the six
+// stored components of the weighted products, formed with fused
+// multiply-adds (its rounding, relative 1e-7 of the voxel's terms, is that of
+// the FP32 fields themselves), so only the sum over voxels is compensated.
 template <typename T>
 struct DotAcc {
   double v = 0.0;
   __device__ __forceinline__ void add(T a, T b) { v = fma(double(a), double(b), v); }
+  __device__ __forceinline__ void add_sum(T p) { v += double(p); }
   __device__ __forceinline__ double value() const { return v; }
 };
 template <>
@@ -305,6 +312,14 @@ struct DotAcc<float> {
     const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(t, e));
+  }
+  // adds a value (no product to split): two-sum of hi + p, error to lo
+  __device__ __forceinline__ void add_sum(float p) {
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    hi = s;
+    lo = __fadd_rn(lo, t);
   }
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
@@ -681,13 +696,18 @@ __device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, lo
         xx[c * V] = xv[c] + k.alpha * pv[c];
       }
     }
+    T rr2 = T(0);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const T pn = rv[c] + k.beta * pv[c];
       pp[c * V] = pn;
       e[c] = pn;
-      acc.add(rv[c], frob_t(c, rv[c]));
+      if constexpr (sizeof(T) == 4)
+        rr2 = fmaf(rv[c], frob_t(c, rv[c]), rr2);
+      else
+        acc.add(rv[c], frob_t(c, rv[c]));
     }
+    if constexpr (sizeof(T) == 4) acc.add_sum(rr2);
   } else if (MODE == MODE_TRUE) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) e[c] = xx[c * V];
@@ -727,6 +747,14 @@ __device__ __forceinline__ int fwd_slot() {
   return MODE == MODE_RHS ? 0 : (MODE == MODE_ITER ? 13 : -1);
 }
 
+// Bodies compiled for one plane shape or z length (hh_plane_ct.cuh): true
+// when the problem's shape code names one and it ran.
+template <typename T, int MODE>
+__device__ __forceinline__ bool plane_fwd_ct(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm,
+                                             const FwdScal<T, MODE>& k);
+template <typename T, int MODE>
+__device__ __forceinline__ bool plane_inv_ct(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm);
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
@@ -749,6 +777,9 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     }
     const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
+    if constexpr (sizeof(T) == 4 && MODE == MODE_ITER) {
+      if (d.ct_plane && plane_fwd_ct<T, MODE>(P, d, z, sm, k)) continue;
+    }
 
     DotAcc<T> dot;
     const long long zoff = (long long)z * ny * nx;
@@ -919,6 +950,9 @@ __device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int n
 //   projection: the mode becomes Gamma0 tau, and the item leaves the partial
 //   sum of h |P tau|^2_F (h = 2 for the kx that stand for a conjugate pair)
 //   and, from the zero mode, Re tau^(0) for the equilibrium residual.
+template <typename T>
+__device__ __forceinline__ bool column_ct(const KParams<T>& P, const Prob& d, int j0, const ColumnSmem<T>& sm);
+
 template <typename T, bool BASIC>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
@@ -945,6 +979,9 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       tab_pz = d.pz;
       tab_py = d.py;
       tab_cw = d.cw;
+    }
+    if constexpr (sizeof(T) == 4 && !BASIC) {
+      if (d.ct_col && column_ct<T>(P, d, j0, sm)) continue;
     }
     C2<T>* sp = P.spec + d.spc_off + j0;
     {
@@ -1071,13 +1108,25 @@ __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, lo
       pv[c] = pp[c * V];
       rv[c] = rr[c * V];
     }
+    T spq = T(0), srq = T(0), sqq = T(0);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       qq[c * V] = qv[c];
       const T wq = frob_t(c, qv[c]);
-      acc[0].add(pv[c], wq);
-      acc[1].add(rv[c], wq);
-      acc[2].add(qv[c], wq);
+      if constexpr (sizeof(T) == 4) {
+        spq = fmaf(pv[c], wq, spq);
+        srq = fmaf(rv[c], wq, srq);
+        sqq = fmaf(qv[c], wq, sqq);
+      } else {
+        acc[0].add(pv[c], wq);
+        acc[1].add(rv[c], wq);
+        acc[2].add(qv[c], wq);
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      acc[0].add_sum(spq);
+      acc[1].add_sum(srq);
+      acc[2].add_sum(sqq);
     }
   } else if (MODE == MODE_BASIC && P.em) {
     // accelerated scheme: the Lippmann-Schwinger residual B = E - eps -
@@ -1143,6 +1192,9 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
       plane_tables<T>(P, sm, ax, ay, nx);
       tab_px = d.px;
       tab_py = d.py;
+    }
+    if constexpr (sizeof(T) == 4 && MODE == MODE_ITER) {
+      if (d.ct_plane && plane_inv_ct<T, MODE>(P, d, z, sm)) continue;
     }
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;
@@ -1621,3 +1673,5 @@ __global__ void k_count_active(const PState* st, const Prob* prob, int nprob, in
 }
 
 }  // namespace hh
+
+#include "hh_plane_ct.cuh"

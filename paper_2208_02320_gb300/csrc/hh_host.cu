@@ -295,11 +295,15 @@ static int grid_for(Ctx& c, const void* kern, int threads, size_t smem, int nite
 // (8 problems, zero spectrum) for the widths that fit, once per context. The
 // width changes no arithmetic (every z line is transformed and projected the
 // same way), only the speed.
+// With `ct` (a z length that has compiled column bodies) the candidates are
+// the compiled widths, timed through those bodies.
 template <typename T>
-static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool enabled) {
-  const int rule = column_width<T>(nz, ny, c.smem_optin);
+static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool enabled, bool ct = false) {
+  int rule = column_width<T>(nz, ny, c.smem_optin);
+  if (ct) rule = rule >= 32 ? 32 : 16;
   if (!enabled) return rule;
-  const long long key = ((long long)sizeof(T) << 48) | ((long long)nz << 32) | ((long long)ny << 16) | nx;
+  const long long key = ((long long)ct << 56) | ((long long)sizeof(T) << 48) | ((long long)nz << 32) |
+                        ((long long)ny << 16) | nx;
   auto it = c.col_tune.find(key);
   if (it != c.col_tune.end()) return it->second;
   const int nxh = nx / 2 + 1, np = 8;
@@ -318,7 +322,8 @@ static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool
   auto* kc = k_column<T, false>;
   ok = ok && cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c.smem_optin) == cudaSuccess;
-  for (int cw : {rule / 2, rule, rule * 2}) {
+  const std::vector<int> cands = ct ? std::vector<int>{16, 32} : std::vector<int>{rule / 2, rule, rule * 2};
+  for (int cw : cands) {
     if (!ok || cw < 1 || column_smem_bytes<T>(cw, nz, ny) > c.smem_optin) continue;
     std::vector<Prob> probs(np);
     std::vector<int2> items;
@@ -333,6 +338,7 @@ static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool
       d.py = c.tab.index[ny];
       d.pz = c.tab.index[nz];
       d.cw = cw;
+      d.ct_col = ct ? nz * 64 + cw : 0;
       d.spc_off = (long long)i * 6 * nz * pl;
       for (int j0 = 0; j0 < pl; j0 += cw) items.push_back(make_int2(i, j0));
     }
@@ -765,7 +771,9 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.lc = a;
         d.box = b0 + b;
         d.plane0 = (int)pitems.size();
-        d.cw = tuned_column_width<T>(c, nx, ny, nz, o.nyquist, o.autotune != 0);
+        const bool ct_on = o.shape_kernels != 0 && sizeof(T) == 4;
+        d.cw = tuned_column_width<T>(c, nx, ny, nz, o.nyquist, o.autotune != 0, ct_on && ct_length(nz));
+        d.ct_col = (ct_on && ct_length(nz) && ct_width(d.cw)) ? nz * 64 + d.cw : 0;
         d.col0 = (int)ccount;
         ccount += ((long long)ny * nxh + d.cw - 1) / d.cw;
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;
@@ -777,6 +785,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         if (plane_smem_bytes<T>(nx, ny, nphase) <= plane_lim) {
           d.rows = 0;
           d.npi = nz;
+          d.ct_plane = (ct_on && nx == ny && ct_length(nx)) ? nx : 0;
           const size_t pb = plane_smem_bytes<T>(nx, ny, nphase);
           std::vector<int2>& pc = pclass[need(pneed, smem_bucket(pb), pb)];
           for (int k = 0; k < nz; ++k) pc.push_back(make_int2(pr, k));
@@ -1486,6 +1495,7 @@ extern "C" hh_status hh_options_default(hh_options* o) {
   o->max_restarts = 4;
   o->autotune = 1;
   o->fused = 0;
+  o->shape_kernels = 1;
   return HH_OK;
 }
 
