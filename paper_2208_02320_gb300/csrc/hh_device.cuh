@@ -747,14 +747,6 @@ __device__ __forceinline__ int fwd_slot() {
   return MODE == MODE_RHS ? 0 : (MODE == MODE_ITER ? 13 : -1);
 }
 
-// Bodies compiled for one plane shape or z length (hh_plane_ct.cuh): true
-// when the problem's shape code names one and it ran.
-template <typename T, int MODE>
-__device__ __forceinline__ bool plane_fwd_ct(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm,
-                                             const FwdScal<T, MODE>& k);
-template <typename T, int MODE>
-__device__ __forceinline__ bool plane_inv_ct(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm);
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T> P) {
   extern __shared__ __align__(16) char smem[];
@@ -777,9 +769,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_fwd(KParams<T>
     }
     const FwdScal<T, MODE> k(P.st[w.x]);
     __syncthreads();
-    if constexpr (sizeof(T) == 4 && MODE == MODE_ITER) {
-      if (d.ct_plane && plane_fwd_ct<T, MODE>(P, d, z, sm, k)) continue;
-    }
 
     DotAcc<T> dot;
     const long long zoff = (long long)z * ny * nx;
@@ -950,9 +939,6 @@ __device__ __forceinline__ ColumnSmem<T> column_layout(char* base, int cw, int n
 //   projection: the mode becomes Gamma0 tau, and the item leaves the partial
 //   sum of h |P tau|^2_F (h = 2 for the kx that stand for a conjugate pair)
 //   and, from the zero mode, Re tau^(0) for the equilibrium residual.
-template <typename T>
-__device__ __forceinline__ bool column_ct(const KParams<T>& P, const Prob& d, int j0, const ColumnSmem<T>& sm);
-
 template <typename T, bool BASIC>
 __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P, int skip_mode) {
   extern __shared__ __align__(16) char smem[];
@@ -979,9 +965,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_column(KParams<T> P,
       tab_pz = d.pz;
       tab_py = d.py;
       tab_cw = d.cw;
-    }
-    if constexpr (sizeof(T) == 4 && !BASIC) {
-      if (d.ct_col && column_ct<T>(P, d, j0, sm)) continue;
     }
     C2<T>* sp = P.spec + d.spc_off + j0;
     {
@@ -1192,9 +1175,6 @@ __global__ void __launch_bounds__(256, kFieldBlocksPerSM) k_plane_inv(KParams<T>
       plane_tables<T>(P, sm, ax, ay, nx);
       tab_px = d.px;
       tab_py = d.py;
-    }
-    if constexpr (sizeof(T) == 4 && MODE == MODE_ITER) {
-      if (d.ct_plane && plane_inv_ct<T, MODE>(P, d, z, sm)) continue;
     }
     const C2<T>* sp = P.spec + d.spc_off;
     const int pl = ny * nxh;

@@ -319,7 +319,7 @@ static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool
             ensure(c, "tune_items", np * pl * sizeof(int2), (void**)&d_items) == HH_OK &&
             cudaMemsetAsync(d_spec, 0, np * 6 * nz * pl * sizeof(C2<T>), c.st) == cudaSuccess &&
             cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
-  auto* kc = k_column<T, false>;
+  auto* kc = ct ? k_column_ct<T> : k_column<T, false>;
   ok = ok && cudaFuncSetAttribute((const void*)kc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)c.smem_optin) == cudaSuccess;
   const std::vector<int> cands = ct ? std::vector<int>{16, 32} : std::vector<int>{rule / 2, rule, rule * 2};
@@ -359,7 +359,8 @@ static int tuned_column_width(Ctx& c, int nx, int ny, int nz, int nyq_mode, bool
     kp.itab = (const int*)c.d_itab.p;
     kp.spec = d_spec;
     const size_t smem = column_smem_bytes<T>(cw, nz, ny);
-    const int grid = grid_for<T>(c, (const void*)kc, 256, smem, kp.nitems);
+    // (the compiled-shape kernel takes one block per item)
+    const int grid = ct ? kp.nitems : grid_for<T>(c, (const void*)kc, 256, smem, kp.nitems);
     kc<<<grid, 256, smem, c.st>>>(kp, MODE_APPLY);
     cudaEventRecord(e0, c.st);
     for (int r = 0; r < 3; ++r) kc<<<grid, 256, smem, c.st>>>(kp, MODE_APPLY);
@@ -610,11 +611,15 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   };
   auto* kyf = k_ycols<T, false>;
   auto* kyi = k_ycols<T, true>;
+  auto* kfct = k_plane_fwd_ct<T>;
+  auto* kict = k_plane_inv_ct<T>;
+  auto* kcct = k_column_ct<T>;
   for (int m : {MODE_RHS, MODE_ITER, MODE_TRUE, MODE_BASIC})
     for (bool rows : {false, true})
       for (KFn f : {kfwd(m, rows), kinv(m, rows)})
         HH_CK(cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
-  for (const void* f : {(const void*)kc, (const void*)kcb, (const void*)kyf, (const void*)kyi})
+  for (const void* f : {(const void*)kc, (const void*)kcb, (const void*)kyf, (const void*)kyi, (const void*)kfct,
+                        (const void*)kict, (const void*)kcct})
     HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
   const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
 
@@ -787,7 +792,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
           d.npi = nz;
           d.ct_plane = (ct_on && nx == ny && ct_length(nx)) ? nx : 0;
           const size_t pb = plane_smem_bytes<T>(nx, ny, nphase);
-          std::vector<int2>& pc = pclass[need(pneed, smem_bucket(pb), pb)];
+          // compiled-shape problems get launch classes of their own
+          std::vector<int2>& pc = pclass[need(pneed, (smem_bucket(pb) << 1) | (d.ct_plane ? 1 : 0), pb)];
           for (int k = 0; k < nz; ++k) pc.push_back(make_int2(pr, k));
         } else {
           const int R = stream_rows(nx, ny);
@@ -795,8 +801,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
           d.rows = R;
           d.npi = nz * nch;
           const size_t rb = rows_smem_bytes<T>(nx, R, nphase), yb = ycol_smem_bytes<T>(ny, ycw);
-          std::vector<int2>& rc = rclass[need(rneed, smem_bucket(rb), rb)];
-          std::vector<int2>& yc = yclass[need(yneed, smem_bucket(yb), yb)];
+          std::vector<int2>& rc = rclass[need(rneed, smem_bucket(rb) << 1, rb)];
+          std::vector<int2>& yc = yclass[need(yneed, smem_bucket(yb) << 1, yb)];
           for (int k = 0; k < nz; ++k) {
             for (int j = 0; j < nch; ++j) rc.push_back(make_int2(pr, k | ((j * R) << 16)));
             for (int x0 = 0; x0 < nxh; x0 += ycw) yc.push_back(make_int2(pr, k | (x0 << 16)));
@@ -804,7 +810,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         }
         prow += d.npi;
         const size_t cb = column_smem_bytes<T>(d.cw, nz, ny);
-        const size_t ckey = need(cneed, smem_bucket(cb), cb);
+        const size_t ckey = need(cneed, (smem_bucket(cb) << 1) | (d.ct_col ? 1 : 0), cb);
         std::vector<int2>& cc = cclass[ckey];
         for (int j0 = 0; j0 < ny * nxh; j0 += d.cw) cc.push_back(make_int2(6 * b + a, j0));
         fld_off += 6 * V;
@@ -820,6 +826,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       int n;
       int grid_f, grid_i;
       bool rows;
+      bool ct;  // every problem has a compiled shape (k_plane_*_ct, k_column_ct)
+      int grid_fc, grid_ic;
     };
     std::vector<Cls> pcl, ycl, ccl;
     citems.clear();
@@ -834,7 +842,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
                            bool rows) {
       for (auto& kv : m) {
         std::stable_sort(kv.second.begin(), kv.second.end(), by_size);
-        out.push_back({nd[kv.first], (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows});
+        out.push_back({nd[kv.first], (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows,
+                       (kv.first & 1) != 0, 0, 0});
         clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
       }
     };
@@ -934,9 +943,13 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     for (Cls& k : pcl) {
       k.grid_f = grid_for<T>(c, (const void*)kfwd(MODE_ITER, k.rows), threads, k.smem, k.n);
       k.grid_i = grid_for<T>(c, (const void*)kinv(MODE_ITER, k.rows), threads, k.smem, k.n);
+      if (k.ct) k.grid_fc = k.grid_ic = k.n;  // one block per item
     }
     for (Cls& k : ycl) k.grid_f = k.grid_i = grid_for<T>(c, (const void*)kyf, threads, k.smem, k.n);
-    for (Cls& k : ccl) k.grid_f = grid_for<T>(c, (const void*)kc, threads, k.smem, k.n);
+    for (Cls& k : ccl) {
+      k.grid_f = grid_for<T>(c, (const void*)kc, threads, k.smem, k.n);
+      if (k.ct) k.grid_fc = k.n;
+    }
     auto cls_params = [&](const Cls& k) {
       KParams<T> q = kp;
       q.items = d_cit + k.off;
@@ -949,7 +962,10 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
     auto fwd_pass = [&](int mode) {
       for (const Cls& k : pcl) {
         ++c.launches;
-        kfwd(mode, k.rows)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k));
+        if (k.ct && mode == MODE_ITER)
+          kfct<<<k.grid_fc, threads, k.smem, c.st>>>(cls_params(k));
+        else
+          kfwd(mode, k.rows)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k));
       }
       for (const Cls& k : ycl) {
         ++c.launches;
@@ -963,13 +979,19 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       }
       for (const Cls& k : pcl) {
         ++c.launches;
-        kinv(mode, k.rows)<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
+        if (k.ct && mode == MODE_ITER)
+          kict<<<k.grid_ic, threads, k.smem, c.st>>>(cls_params(k));
+        else
+          kinv(mode, k.rows)<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
       }
     };
     auto column_pass = [&](int mode) {
       for (const Cls& k : ccl) {
         ++c.launches;
-        (mode == MODE_BASIC ? kcb : kc)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
+        if (k.ct && mode != MODE_BASIC)
+          kcct<<<k.grid_fc, threads, k.smem, c.st>>>(cls_params(k), mode);
+        else
+          (mode == MODE_BASIC ? kcb : kc)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
       }
     };
     const int gu = grid_for<T>(c, (const void*)ku, threads, 0, kpp.nitems);

@@ -16,7 +16,11 @@
 //     barrier and writes them after it;
 //   * the inverse x transform reads the packed row Z = A + iB straight from
 //     the two half spectra [A | B] (Hermitian extension), without a separate
-//     packing step.
+//     packing step;
+//   * they run as kernels of their own (k_plane_fwd_ct, k_plane_inv_ct,
+//     k_column_ct) with one block per item, on launch classes that hold only
+//     problems with a compiled shape (the CG iterations in FP32; the other
+//     modes take the generic kernels on the same items).
 // Blocks have kNT = 256 threads (the launch shape of the field kernels).
 #pragma once
 
@@ -38,11 +42,32 @@ __host__ __device__ constexpr int split_of(int n) {
   return 0;
 }
 
-// Complex values a thread stages at once in one pass (registers).
+// Complex values a thread stages at once in one pass (registers), and the
+// voxels of a thread whose global loads are issued together in the voxel
+// phases.
 #ifndef HH_CT_STAGE
-#define HH_CT_STAGE 8
+#define HH_CT_STAGE 4
+#endif
+#ifndef HH_CT_VOXELS
+#define HH_CT_VOXELS 1
 #endif
 constexpr int kStage = HH_CT_STAGE;
+constexpr int kVoxels = HH_CT_VOXELS;
+
+}  // namespace ct
+
+// Resident 256-thread blocks per SM the compiled-shape kernels are built for
+// (4: 64 registers per thread, as the generic field kernels; 3: 80).
+#ifndef HH_CT_BLOCKS_PER_SM
+#define HH_CT_BLOCKS_PER_SM 4
+#endif
+#ifndef HH_CT_FWD_BLOCKS_PER_SM
+#define HH_CT_FWD_BLOCKS_PER_SM HH_CT_BLOCKS_PER_SM
+#endif
+constexpr int kCtBlocksPerSM = HH_CT_BLOCKS_PER_SM;
+constexpr int kCtFwdBlocksPerSM = HH_CT_FWD_BLOCKS_PER_SM;
+
+namespace ct {
 
 // NL lines; line l starts at (l / LPG) GS + (l % LPG) LS, element k of it
 // sits ES further on per k.
@@ -56,6 +81,16 @@ struct Geo {
       return (int)((l / LPG) * GS + (l % LPG) * LS);
   }
 };
+
+// The thread index, read so that the compiler cannot treat it as invariant
+// across the persistent item loop: every index a body derives from it is
+// recomputed per item instead of being hoisted out of the loop and held in
+// registers (or spilled) for the whole kernel.
+__device__ __forceinline__ unsigned tid_item() {
+  unsigned t;
+  asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
+  return t;
+}
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(C2<T>* dst_smem, const C2<T>* src) {
@@ -76,7 +111,7 @@ __device__ __forceinline__ void pass1_local(C2<T>* S, const C2<T>* tw) {
   constexpr int TOT = G::NL * N1;
   constexpr int IT = cdiv(TOT, kNT);
   constexpr int B = cmax(1, kStage / N2);
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = tid_item();
 #pragma unroll
   for (int i0 = 0; i0 < IT; i0 += B) {
     C2<T> v[B][N2];
@@ -136,7 +171,7 @@ __device__ __forceinline__ void pass_rounds(C2<T>* S, const C2<T>* tw) {
   constexpr int LPR = cdiv(G::NL, NR);
   constexpr int IT = cdiv(LPR * J, kNT);
   static_assert(KIND == KIND_P2 || G::ES == 1, "packed rows are contiguous");
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = tid_item();
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int L0 = r * LPR;
@@ -223,7 +258,7 @@ __device__ __forceinline__ void unpack_ct(C2<T>* S) {
   constexpr int NR = cdiv(NROWS, RPR0);
   constexpr int RPR = cdiv(NROWS, NR);
   constexpr int IT = cdiv(RPR * NXH, kNT);
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = tid_item();
 #pragma unroll
   for (int r = 0; r < NR; ++r) {
     const int R0 = r * RPR;
@@ -261,15 +296,17 @@ template <typename T, int MODE, int NX, int NY>
 __device__ __forceinline__ void plane_fwd(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm,
                                           const FwdScal<T, MODE>& k) {
   constexpr int NXH = NX / 2 + 1, RP = (NX + 2) | 1, PL = NY * NXH, NV = NX * NY;
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = tid_item();
   const long long V = (long long)NV * d.nz;
   const long long zoff = (long long)z * NV;
   DotAcc<T> dot;
   constexpr int ITV = cdiv(NV, kNT);
 #pragma unroll 1
-  for (int i = 0; i < ITV; ++i) {
+  for (int i0 = 0; i0 < ITV; i0 += kVoxels)
+#pragma unroll
+  for (int i = i0; i < i0 + kVoxels; ++i) {
     const unsigned v = tid + i * kNT;
-    if ((i + 1) * kNT <= NV || v < NV) {
+    if (i < ITV && ((i + 1) * kNT <= NV || v < NV)) {
       const int y = (int)(v / NX), x = (int)(v % NX);
       T s[6];
       fwd_voxel<T, MODE>(P, d, V, zoff + v, k, sm.lm, s, dot);
@@ -306,7 +343,7 @@ __device__ __forceinline__ void plane_fwd(const KParams<T>& P, const Prob& d, in
 template <typename T, int MODE, int NX, int NY>
 __device__ __forceinline__ void plane_inv(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm) {
   constexpr int NXH = NX / 2 + 1, RP = (NX + 2) | 1, PL = NY * NXH, NV = NX * NY;
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = tid_item();
   const long long cpl = (long long)d.nz * PL;
   {
     const C2<T>* sp = P.spec + d.spc_off + (long long)z * PL;
@@ -332,9 +369,11 @@ __device__ __forceinline__ void plane_inv(const KParams<T>& P, const Prob& d, in
   const long long zoff = (long long)z * NV;
   constexpr int ITV = cdiv(NV, kNT);
 #pragma unroll 1
-  for (int i = 0; i < ITV; ++i) {
+  for (int i0 = 0; i0 < ITV; i0 += kVoxels)
+#pragma unroll
+  for (int i = i0; i < i0 + kVoxels; ++i) {
     const unsigned v = tid + i * kNT;
-    if ((i + 1) * kNT <= NV || v < NV) {
+    if (i < ITV && ((i + 1) * kNT <= NV || v < NV)) {
       const int y = (int)(v / NX), x = (int)(v % NX);
       T qv[6];
 #pragma unroll
@@ -359,7 +398,7 @@ __device__ __forceinline__ void column(const KParams<T>& P, const Prob& d, int j
   const int nx = d.nx, ny = d.ny, nxh = d.nxh;
   const int pl = ny * nxh;
   const int W = min(CW, pl - j0);
-  const unsigned tid = threadIdx.x;
+  const unsigned tid = tid_item();
   C2<T>* sp = P.spec + d.spc_off + j0;
   constexpr int TOT = 6 * NZ * CW;
   constexpr int ITL = cdiv(TOT, kNT);
@@ -430,53 +469,115 @@ __host__ __device__ constexpr bool ct_length(int n) { return n >= 16 && n <= 32 
 
 #define HH_CT_LENGTHS(X) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
 
-template <typename T, int MODE>
-__device__ __forceinline__ bool plane_fwd_ct(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm,
-                                             const FwdScal<T, MODE>& k) {
-  switch (d.ct_plane) {
-#define HH_CT_FWD(N)                                \
-  case N:                                           \
-    ct::plane_fwd<T, MODE, N, N>(P, d, z, sm, k);   \
-    return true;
-    HH_CT_LENGTHS(HH_CT_FWD)
-#undef HH_CT_FWD
-    default:
-      return false;
-  }
+// Kernels of the compiled bodies: one block per item of a launch class whose
+// problems all carry a shape code (the host keeps them apart from the generic
+// passes' classes). No persistent loop: inside one, the compiler keeps the
+// bodies' thread-dependent indices live across items, which costs more in
+// registers and spills than reloading the few tables per block saves. The
+// shared-memory layout is taken per shape, so its offsets are constants too.
+namespace ct {
+template <typename T, int N>
+__device__ __forceinline__ void fwd_item(const KParams<T>& P, int2 w, char* smem) {
+  const Prob& d = P.prob[w.x];
+  PlaneSmem<T> sm = plane_layout<T>(smem, N, N, P.nphase);
+  plane_tables<T>(P, sm, P.plans[d.px], P.plans[d.py], N);
+  const FwdScal<T, MODE_ITER> k(P.st[w.x]);
+  __syncthreads();
+  plane_fwd<T, MODE_ITER, N, N>(P, d, w.y, sm, k);
 }
-
-template <typename T, int MODE>
-__device__ __forceinline__ bool plane_inv_ct(const KParams<T>& P, const Prob& d, int z, const PlaneSmem<T>& sm) {
-  switch (d.ct_plane) {
-#define HH_CT_INV(N)                             \
-  case N:                                        \
-    ct::plane_inv<T, MODE, N, N>(P, d, z, sm);   \
-    return true;
-    HH_CT_LENGTHS(HH_CT_INV)
-#undef HH_CT_INV
-    default:
-      return false;
-  }
+template <typename T, int N>
+__device__ __forceinline__ void inv_item(const KParams<T>& P, int2 w, char* smem) {
+  const Prob& d = P.prob[w.x];
+  PlaneSmem<T> sm = plane_layout<T>(smem, N, N, P.nphase);
+  plane_tables<T>(P, sm, P.plans[d.px], P.plans[d.py], N);
+  plane_inv<T, MODE_ITER, N, N>(P, d, w.y, sm);
 }
-
-// Column widths of the specialised column pass.
-__host__ __device__ constexpr bool ct_width(int cw) { return cw == 16 || cw == 32; }
+}  // namespace ct
 
 template <typename T>
-__device__ __forceinline__ bool column_ct(const KParams<T>& P, const Prob& d, int j0, const ColumnSmem<T>& sm) {
-  const int code = d.ct_col;  // nz * 64 + cw
-  switch (code) {
+__global__ void __launch_bounds__(256, kCtFwdBlocksPerSM) k_plane_fwd_ct(KParams<T> P) {
+  if constexpr (sizeof(T) == 4) {
+    extern __shared__ __align__(16) char smem[];
+    if ((int)blockIdx.x >= P.nitems) return;
+    const int2 w = P.items[blockIdx.x];
+    if (skip_problem<T>(P.st, w.x, MODE_ITER)) return;
+    switch (P.prob[w.x].ct_plane) {
+#define HH_CT_FWD(N)                   \
+  case N:                              \
+    ct::fwd_item<T, N>(P, w, smem);    \
+    break;
+      HH_CT_LENGTHS(HH_CT_FWD)
+#undef HH_CT_FWD
+      default:
+        break;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, kCtBlocksPerSM) k_plane_inv_ct(KParams<T> P) {
+  if constexpr (sizeof(T) == 4) {
+    extern __shared__ __align__(16) char smem[];
+    if ((int)blockIdx.x >= P.nitems) return;
+    const int2 w = P.items[blockIdx.x];
+    if (skip_problem<T>(P.st, w.x, MODE_ITER)) return;
+    switch (P.prob[w.x].ct_plane) {
+#define HH_CT_INV(N)                   \
+  case N:                              \
+    ct::inv_item<T, N>(P, w, smem);    \
+    break;
+      HH_CT_LENGTHS(HH_CT_INV)
+#undef HH_CT_INV
+      default:
+        break;
+    }
+  }
+}
+
+// Column widths of the compiled column pass.
+__host__ __device__ constexpr bool ct_width(int cw) { return cw == 16 || cw == 32; }
+
+// Column pass (projection) of the problems with a compiled z length; every
+// mode but the basic scheme's (`skip_mode` as in k_column). One block per item.
+namespace ct {
+template <typename T, int NZ, int CW>
+__device__ __forceinline__ void column_item(const KParams<T>& P, int2 w, char* smem) {
+  const Prob& d = P.prob[w.x];
+  const int ny = d.ny;
+  ColumnSmem<T> sm = column_layout<T>(smem, CW, NZ, ny);
+  const AxisPlan& az = P.plans[d.pz];
+  const AxisPlan& ay = P.plans[d.py];
+  load_tw<T>(sm.twz, P.tw, az);
+  for (int t = threadIdx.x; t < NZ; t += kNT) {
+    const int mz = P.itab[az.sf_off + t];
+    sm.sfz[t] = mz;
+    sm.fz[t] = T(mz) / T(NZ);
+  }
+  for (int t = threadIdx.x; t < ny; t += kNT) sm.sfy[t] = P.itab[ay.sf_off + t];
+  column<T, NZ, CW>(P, d, w.y, sm);
+}
+}  // namespace ct
+
+template <typename T>
+__global__ void __launch_bounds__(256, kCtBlocksPerSM) k_column_ct(KParams<T> P, int skip_mode) {
+  if constexpr (sizeof(T) == 4) {
+    extern __shared__ __align__(16) char smem[];
+    if ((int)blockIdx.x >= P.nitems) return;
+    const int2 w = P.items[blockIdx.x];
+    if (skip_problem<T>(P.st, w.x, skip_mode)) return;
+    switch (P.prob[w.x].ct_col) {
 #define HH_CT_COL(N)                          \
   case N * 64 + 16:                           \
-    ct::column<T, N, 16>(P, d, j0, sm);       \
-    return true;                              \
+    ct::column_item<T, N, 16>(P, w, smem);    \
+    break;                                    \
   case N * 64 + 32:                           \
-    ct::column<T, N, 32>(P, d, j0, sm);       \
-    return true;
-    HH_CT_LENGTHS(HH_CT_COL)
+    ct::column_item<T, N, 32>(P, w, smem);    \
+    break;
+      HH_CT_LENGTHS(HH_CT_COL)
 #undef HH_CT_COL
-    default:
-      return false;
+      default:
+        break;
+    }
   }
 }
 
