@@ -289,16 +289,14 @@ __device__ __forceinline__ double frob_w(int c) { return c < 3 ? 1.0 : 2.0; }
 // to lo. The FP64 pipe of this GPU runs at a small fraction of the FP32 rate,
 // so per-element FP64 arithmetic is avoided; the thread's total is converted
 // to FP64 once, for the block reduction. The _rn intrinsics keep the compiler
-// from contracting the two-sum into fused multiply-adds. The CG passes in
-// FP32 add one value per voxel and product (add_sum): the sum over the six
-// stored components of the weighted products, formed with fused
-// multiply-adds (its rounding, relative 1e-7 of the voxel's terms, is that of
-// the FP32 fields themselves), so only the sum over voxels is compensated.
+// from contracting the two-sum into fused multiply-adds. (Summing a voxel's
+// six weighted products in plain FP32 before the compensated add was tried:
+// at contrast 4.4e5 it moved where FP32 solves stall at their precision floor
+// by up to 1 % of the stiffness, so every product is added exactly.)
 template <typename T>
 struct DotAcc {
   double v = 0.0;
   __device__ __forceinline__ void add(T a, T b) { v = fma(double(a), double(b), v); }
-  __device__ __forceinline__ void add_sum(T p) { v += double(p); }
   __device__ __forceinline__ double value() const { return v; }
 };
 template <>
@@ -312,14 +310,6 @@ struct DotAcc<float> {
     const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(t, e));
-  }
-  // adds a value (no product to split): two-sum of hi + p, error to lo
-  __device__ __forceinline__ void add_sum(float p) {
-    const float s = __fadd_rn(hi, p);
-    const float bb = __fsub_rn(s, hi);
-    const float t = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    hi = s;
-    lo = __fadd_rn(lo, t);
   }
   __device__ __forceinline__ double value() const { return double(hi) + double(lo); }
 };
@@ -696,18 +686,13 @@ __device__ __forceinline__ void fwd_voxel(const KParams<T>& P, const Prob& d, lo
         xx[c * V] = xv[c] + k.alpha * pv[c];
       }
     }
-    T rr2 = T(0);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       const T pn = rv[c] + k.beta * pv[c];
       pp[c * V] = pn;
       e[c] = pn;
-      if constexpr (sizeof(T) == 4)
-        rr2 = fmaf(rv[c], frob_t(c, rv[c]), rr2);
-      else
-        acc.add(rv[c], frob_t(c, rv[c]));
+      acc.add(rv[c], frob_t(c, rv[c]));
     }
-    if constexpr (sizeof(T) == 4) acc.add_sum(rr2);
   } else if (MODE == MODE_TRUE) {
 #pragma unroll
     for (int c = 0; c < 6; ++c) e[c] = xx[c * V];
@@ -1091,25 +1076,13 @@ __device__ __forceinline__ void inv_voxel(const KParams<T>& P, const Prob& d, lo
       pv[c] = pp[c * V];
       rv[c] = rr[c * V];
     }
-    T spq = T(0), srq = T(0), sqq = T(0);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
       qq[c * V] = qv[c];
       const T wq = frob_t(c, qv[c]);
-      if constexpr (sizeof(T) == 4) {
-        spq = fmaf(pv[c], wq, spq);
-        srq = fmaf(rv[c], wq, srq);
-        sqq = fmaf(qv[c], wq, sqq);
-      } else {
-        acc[0].add(pv[c], wq);
-        acc[1].add(rv[c], wq);
-        acc[2].add(qv[c], wq);
-      }
-    }
-    if constexpr (sizeof(T) == 4) {
-      acc[0].add_sum(spq);
-      acc[1].add_sum(srq);
-      acc[2].add_sum(sqq);
+      acc[0].add(pv[c], wq);
+      acc[1].add(rv[c], wq);
+      acc[2].add(qv[c], wq);
     }
   } else if (MODE == MODE_BASIC && P.em) {
     // accelerated scheme: the Lippmann-Schwinger residual B = E - eps -
@@ -1350,6 +1323,10 @@ __global__ void __launch_bounds__(256) k_avg(KParams<T> P) {
   }
 }
 
+// The scalar kernels below are plain (non-template) kernels: defined only in
+// the unit that launches them (units that include this header for the
+// compiled-shape kernels alone define HH_FIELD_TEMPLATES_ONLY).
+#ifndef HH_FIELD_TEMPLATES_ONLY
 // ---------------------------------------------------------------------------
 // FP64 scalar steps of conjugate gradients, one thread per problem. Partials
 // of a problem's plane items are summed in item order (deterministic).
@@ -1651,6 +1628,8 @@ __global__ void k_count_active(const PState* st, const Prob* prob, int nprob, in
     out_vs[1] = ss;
   }
 }
+
+#endif  // HH_FIELD_TEMPLATES_ONLY
 
 }  // namespace hh
 

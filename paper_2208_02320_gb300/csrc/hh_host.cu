@@ -21,6 +21,14 @@
 
 namespace hh {
 
+// The compiled-shape kernels are instantiated in hh_ct_inst.cu.
+extern template __global__ void k_plane_fwd_ct<float>(KParams<float>);
+extern template __global__ void k_plane_fwd_ct<double>(KParams<double>);
+extern template __global__ void k_plane_inv_ct<float>(KParams<float>);
+extern template __global__ void k_plane_inv_ct<double>(KParams<double>);
+extern template __global__ void k_column_ct<float>(KParams<float>, int);
+extern template __global__ void k_column_ct<double>(KParams<double>, int);
+
 // ---------------------------------------------------------------------------
 // FFT planning: radices, twiddles, digit-reversal tables.
 // ---------------------------------------------------------------------------
@@ -777,8 +785,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         d.box = b0 + b;
         d.plane0 = (int)pitems.size();
         const bool ct_on = o.shape_kernels != 0 && sizeof(T) == 4;
-        d.cw = tuned_column_width<T>(c, nx, ny, nz, o.nyquist, o.autotune != 0, ct_on && ct_length(nz));
-        d.ct_col = (ct_on && ct_length(nz) && ct_width(d.cw)) ? nz * 64 + d.cw : 0;
+        d.cw = tuned_column_width<T>(c, nx, ny, nz, o.nyquist, o.autotune != 0, ct_on && ct_col_length(nz));
+        d.ct_col = (ct_on && ct_col_length(nz) && ct_width(d.cw)) ? nz * 64 + d.cw : 0;
         d.col0 = (int)ccount;
         ccount += ((long long)ny * nxh + d.cw - 1) / d.cw;
         d.med_off = (med.kind == MED_ISO) ? lab_off : c21_off;

@@ -112,7 +112,8 @@ __device__ __forceinline__ void pass1_local(C2<T>* S, const C2<T>* tw) {
   constexpr int IT = cdiv(TOT, kNT);
   constexpr int B = cmax(1, kStage / N2);
   const unsigned tid = tid_item();
-#pragma unroll
+  // one chunk of B pairs per trip (the code of one chunk, not of all)
+#pragma unroll 1
   for (int i0 = 0; i0 < IT; i0 += B) {
     C2<T> v[B][N2];
     int o[B], t1s[B];
@@ -170,21 +171,22 @@ __device__ __forceinline__ void pass_rounds(C2<T>* S, const C2<T>* tw) {
   constexpr int NR = cdiv(G::NL, LPR0);
   constexpr int LPR = cdiv(G::NL, NR);
   constexpr int IT = cdiv(LPR * J, kNT);
+  constexpr int TOT = LPR * J;  // pairs of a round (the last may have fewer lines)
   static_assert(KIND == KIND_P2 || G::ES == 1, "packed rows are contiguous");
   const unsigned tid = tid_item();
-#pragma unroll
+  // every round runs the same code (LPR lines, the last round's missing lines
+  // skipped), so the loop is not unrolled and its constants stay constants
+#pragma unroll 1
   for (int r = 0; r < NR; ++r) {
-    const int L0 = r * LPR;
-    const int NLR = cmin(LPR, G::NL - L0);
-    const int TOT = NLR * J;
+    const unsigned L0 = r * LPR;
     C2<T> v[IT][R];
     int o[IT];
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
       const unsigned p = tid + i * kNT;
+      const unsigned line = L0 + p % LPR, jj = p / LPR;
       o[i] = -1;
-      if ((i + 1) * kNT <= TOT || p < (unsigned)TOT) {
-        const unsigned line = L0 + p % (unsigned)NLR, jj = p / (unsigned)NLR;
+      if (((i + 1) * kNT <= TOT || p < (unsigned)TOT) && (NR * LPR == G::NL || line < (unsigned)G::NL)) {
         const int lo = G::off(line);
         if constexpr (KIND == KIND_P2) {
 #pragma unroll
@@ -258,19 +260,19 @@ __device__ __forceinline__ void unpack_ct(C2<T>* S) {
   constexpr int NR = cdiv(NROWS, RPR0);
   constexpr int RPR = cdiv(NROWS, NR);
   constexpr int IT = cdiv(RPR * NXH, kNT);
+  constexpr int TOT = RPR * NXH;
   const unsigned tid = tid_item();
-#pragma unroll
+#pragma unroll 1
   for (int r = 0; r < NR; ++r) {
-    const int R0 = r * RPR;
-    const int TOT = cmin(RPR, NROWS - R0) * NXH;
+    const unsigned R0 = r * RPR;
     C2<T> A[IT], B[IT];
     int o[IT];
 #pragma unroll
     for (int i = 0; i < IT; ++i) {
       const unsigned e = tid + i * kNT;
+      const unsigned row = R0 + e / NXH, k = e % NXH;
       o[i] = -1;
-      if ((i + 1) * kNT <= TOT || e < (unsigned)TOT) {
-        const unsigned row = R0 + e / NXH, k = e % NXH;
+      if (((i + 1) * kNT <= TOT || e < (unsigned)TOT) && (NR * RPR == NROWS || row < (unsigned)NROWS)) {
         const int base = (int)row * RP;
         const C2<T> a = S[base + (int)k];
         const C2<T> b = S[base + (k == 0 ? 0 : NX - (int)k)];
@@ -463,11 +465,14 @@ __device__ __forceinline__ void column(const KParams<T>& P, const Prob& d, int j
 
 }  // namespace ct
 
-// Shape codes of the specialised bodies: the edge (16..32, even) of a square
-// xy plane for the plane passes, the z length for the column pass; 0 = none.
+// Shape codes of the compiled bodies: the edge (16..32, even) of a square xy
+// plane for the plane passes, the z length (16..48, even) for the column
+// pass; 0 = none.
 __host__ __device__ constexpr bool ct_length(int n) { return n >= 16 && n <= 32 && n % 2 == 0; }
+__host__ __device__ constexpr bool ct_col_length(int n) { return n >= 16 && n <= 48 && n % 2 == 0; }
 
 #define HH_CT_LENGTHS(X) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
+#define HH_CT_COL_LENGTHS(X) HH_CT_LENGTHS(X) X(34) X(36) X(38) X(40) X(42) X(44) X(46) X(48)
 
 // Kernels of the compiled bodies: one block per item of a launch class whose
 // problems all carry a shape code (the host keeps them apart from the generic
@@ -573,7 +578,7 @@ __global__ void __launch_bounds__(256, kCtBlocksPerSM) k_column_ct(KParams<T> P,
   case N * 64 + 32:                           \
     ct::column_item<T, N, 32>(P, w, smem);    \
     break;
-      HH_CT_LENGTHS(HH_CT_COL)
+      HH_CT_COL_LENGTHS(HH_CT_COL)
 #undef HH_CT_COL
       default:
         break;

@@ -148,13 +148,18 @@ def test_fused_and_multipass_solvers_agree(ctx, precision):
     iterations, with C_R still agreeing to 7.7e-9), so iteration counts within
     5 % and C within 10 tol; FP32 (whose
     true residual stalls near the tolerance at this contrast): every
-    subimage fused, C_R to 1e-4 of the largest entry."""
+    subimage fused, C_R to 1e-4 of the largest entry against the generic
+    multi-pass kernels (shape_kernels = 0), whose operation order the fused
+    kernel follows (the compiled-shape passes round differently in places, by
+    2e-7 after 20 iterations, which at the FP32 precision floor of this
+    contrast moves where a stalled solve stops: they are held to the generic
+    passes in test_shape_kernels_agree_with_generic_passes)."""
     img = synth.boolean_spheres(n=96, seed=5)
     boxes = synth.uneven_partition(N=96, counts=((16, 3), (24, 1), (24, 1)), bmax=8, seed=9)
     ph = synth.PHASES_SOLID_PORE
     tol = 1e-8 if precision == "fp64" else 1e-5
     a = ctx.homogenize_partition(img, ph, boxes, unit=0, precision=precision, tol=tol, fused=1)
-    b = ctx.homogenize_partition(img, ph, boxes, unit=0, precision=precision, tol=tol, fused=0)
+    b = ctx.homogenize_partition(img, ph, boxes, unit=0, precision=precision, tol=tol, fused=0, shape_kernels=0)
     print(f"{precision}: {a['n_fused']} of {len(boxes)} subimages fused; device ms fused {a['device_ms']:.1f}, "
           f"multi-pass {b['device_ms']:.1f}; C_R {rel(a['C_boxes'], b['C_boxes']):.2e}")
     assert b["n_fused"] == 0
