@@ -116,12 +116,13 @@ typedef struct {
                              cluster size, fed by a device work counter); 0 (default):
                              the multi-pass solver for every subimage. Same arithmetic
                              but for the order of the partial sums */
-    int shape_kernels;    /* 1 (default): FP32 CG iterations of subimages with a square xy
-                             plane of even edge 16..32 take plane passes compiled for that
-                             edge, and z lengths 16..32 (even) a column pass compiled for
-                             that length (column widths 16 or 32); 0: the generic passes
-                             for every shape. Same transforms, voxel arithmetic and
-                             operation order: results agree to FP32 rounding */
+    int shape_kernels;    /* 1 (default): FP32 CG iterations of subimages whose xy plane
+                             has even edges in 16..48 differing by 0, 8 or 16 take plane
+                             passes compiled for that shape, and z lengths 16..48 (even)
+                             a column pass compiled for that length (column widths 16 or
+                             32); 0: the generic passes for every shape. Same transforms,
+                             voxel arithmetic and operation order: results agree to FP32
+                             rounding */
 } hh_options;
 
 typedef struct {

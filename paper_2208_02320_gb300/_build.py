@@ -3,8 +3,9 @@
 The translation units are compiled in parallel as relocatable device code and
 linked into one shared library: the host/kernel unit hh_host.cu, the
 surrogate network hh_cnn.cu, the compiled-shape field kernels hh_ct_inst.cu
-once per kernel, and the two-pass transform table hh_fft2_inst.cu once per
-(precision, direction).
+once per kernel (plane passes in four shape groups, and the column pass),
+and the two-pass transform table hh_fft2_inst.cu once per (precision,
+direction).
 """
 
 import concurrent.futures
@@ -20,7 +21,7 @@ BUILD_DIR = os.path.join(HERE, "_build")
 
 # (source, object name, extra flags)
 UNITS = [("hh_host.cu", "hh_host.o", []), ("hh_cnn.cu", "hh_cnn.o", [])] + [
-    ("hh_ct_inst.cu", "hh_ct_%d.o" % part, ["-DHH_CT_PART=%d" % part]) for part in range(3)] + [
+    ("hh_ct_inst.cu", "hh_ct_%d.o" % part, ["-DHH_CT_PART=%d" % part]) for part in range(9)] + [
     ("hh_fft2_inst.cu", "hh_fft2_%s.o" % name, ["-DHH_FFT2_T=%s" % t, "-DHH_FFT2_INV=%d" % inv,
                                                   "-DHH_FFT2_NAME=fft2_%s" % name])
     for name, t, inv in (("f32_fwd", "float", 0), ("f32_inv", "float", 1), ("f64_fwd", "double", 0),

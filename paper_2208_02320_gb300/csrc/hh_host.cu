@@ -22,10 +22,16 @@
 namespace hh {
 
 // The compiled-shape kernels are instantiated in hh_ct_inst.cu.
-extern template __global__ void k_plane_fwd_ct<float>(KParams<float>);
-extern template __global__ void k_plane_fwd_ct<double>(KParams<double>);
-extern template __global__ void k_plane_inv_ct<float>(KParams<float>);
-extern template __global__ void k_plane_inv_ct<double>(KParams<double>);
+#define HH_CT_EXTERN(G)                                                       \
+  extern template __global__ void k_plane_fwd_ct<float, G>(KParams<float>);   \
+  extern template __global__ void k_plane_fwd_ct<double, G>(KParams<double>); \
+  extern template __global__ void k_plane_inv_ct<float, G>(KParams<float>);   \
+  extern template __global__ void k_plane_inv_ct<double, G>(KParams<double>);
+HH_CT_EXTERN(0)
+HH_CT_EXTERN(1)
+HH_CT_EXTERN(2)
+HH_CT_EXTERN(3)
+#undef HH_CT_EXTERN
 extern template __global__ void k_column_ct<float>(KParams<float>, int);
 extern template __global__ void k_column_ct<double>(KParams<double>, int);
 
@@ -131,6 +137,14 @@ struct DevBuf {
   size_t n = 0;
 };
 
+// Streams a pass's launch classes are spread over: the classes of one pass
+// touch disjoint problems, so they run side by side (branches of the chunk's
+// graph when it is captured) and fill one another's tails. 1: one stream.
+#ifndef HH_PASS_STREAMS
+#define HH_PASS_STREAMS 4
+#endif
+constexpr int kPassStreams = HH_PASS_STREAMS;
+
 struct Ctx {
   int dev = 0;
   int nsm = 0;
@@ -146,6 +160,8 @@ struct Ctx {
   std::string err;
   long long launches = 0;      // kernels launched on this context
   cudaEvent_t ev_call0 = nullptr, ev_call1 = nullptr;
+  cudaStream_t side[kPassStreams] = {};           // the pass streams (fork from st, join back)
+  cudaEvent_t ev_fork = nullptr, ev_join[kPassStreams] = {};
   struct KStat {
     long long launches = 0, sampled = 0;
     double ms = 0.0, bytes = 0.0;
@@ -619,16 +635,18 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
   };
   auto* kyf = k_ycols<T, false>;
   auto* kyi = k_ycols<T, true>;
-  auto* kfct = k_plane_fwd_ct<T>;
-  auto* kict = k_plane_inv_ct<T>;
+  KFn kfct[kCtPlaneGroups] = {k_plane_fwd_ct<T, 0>, k_plane_fwd_ct<T, 1>, k_plane_fwd_ct<T, 2>, k_plane_fwd_ct<T, 3>};
+  KFn kict[kCtPlaneGroups] = {k_plane_inv_ct<T, 0>, k_plane_inv_ct<T, 1>, k_plane_inv_ct<T, 2>, k_plane_inv_ct<T, 3>};
   auto* kcct = k_column_ct<T>;
   for (int m : {MODE_RHS, MODE_ITER, MODE_TRUE, MODE_BASIC})
     for (bool rows : {false, true})
       for (KFn f : {kfwd(m, rows), kinv(m, rows)})
         HH_CK(cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
-  for (const void* f : {(const void*)kc, (const void*)kcb, (const void*)kyf, (const void*)kyi, (const void*)kfct,
-                        (const void*)kict, (const void*)kcct})
+  for (const void* f : {(const void*)kc, (const void*)kcb, (const void*)kyf, (const void*)kyi, (const void*)kcct})
     HH_CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
+  for (int g = 0; g < kCtPlaneGroups; ++g)
+    for (KFn f : {kfct[g], kict[g]})
+      HH_CK(cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem_optin));
   const bool replace = o.replace == 1 || (o.replace == -1 && sizeof(T) == 4);
 
   // lambda/mu table
@@ -798,10 +816,11 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         if (plane_smem_bytes<T>(nx, ny, nphase) <= plane_lim) {
           d.rows = 0;
           d.npi = nz;
-          d.ct_plane = (ct_on && nx == ny && ct_length(nx)) ? nx : 0;
+          const int g = ct_on ? ct_plane_group(nx, ny) : -1;
+          d.ct_plane = g >= 0 ? nx * 64 + ny : 0;
           const size_t pb = plane_smem_bytes<T>(nx, ny, nphase);
-          // compiled-shape problems get launch classes of their own
-          std::vector<int2>& pc = pclass[need(pneed, (smem_bucket(pb) << 1) | (d.ct_plane ? 1 : 0), pb)];
+          // compiled-shape problems get launch classes of their own, one per group
+          std::vector<int2>& pc = pclass[need(pneed, (smem_bucket(pb) << 3) | (g >= 0 ? 1 + g : 0), pb)];
           for (int k = 0; k < nz; ++k) pc.push_back(make_int2(pr, k));
         } else {
           const int R = stream_rows(nx, ny);
@@ -809,8 +828,8 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
           d.rows = R;
           d.npi = nz * nch;
           const size_t rb = rows_smem_bytes<T>(nx, R, nphase), yb = ycol_smem_bytes<T>(ny, ycw);
-          std::vector<int2>& rc = rclass[need(rneed, smem_bucket(rb) << 1, rb)];
-          std::vector<int2>& yc = yclass[need(yneed, smem_bucket(yb) << 1, yb)];
+          std::vector<int2>& rc = rclass[need(rneed, smem_bucket(rb) << 3, rb)];
+          std::vector<int2>& yc = yclass[need(yneed, smem_bucket(yb) << 3, yb)];
           for (int k = 0; k < nz; ++k) {
             for (int j = 0; j < nch; ++j) rc.push_back(make_int2(pr, k | ((j * R) << 16)));
             for (int x0 = 0; x0 < nxh; x0 += ycw) yc.push_back(make_int2(pr, k | (x0 << 16)));
@@ -818,7 +837,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
         }
         prow += d.npi;
         const size_t cb = column_smem_bytes<T>(d.cw, nz, ny);
-        const size_t ckey = need(cneed, (smem_bucket(cb) << 1) | (d.ct_col ? 1 : 0), cb);
+        const size_t ckey = need(cneed, (smem_bucket(cb) << 3) | (d.ct_col ? 1 : 0), cb);
         std::vector<int2>& cc = cclass[ckey];
         for (int j0 = 0; j0 < ny * nxh; j0 += d.cw) cc.push_back(make_int2(6 * b + a, j0));
         fld_off += 6 * V;
@@ -834,7 +853,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       int n;
       int grid_f, grid_i;
       bool rows;
-      bool ct;  // every problem has a compiled shape (k_plane_*_ct, k_column_ct)
+      int ct;   // 1 + group when every problem has a compiled shape (k_plane_*_ct, k_column_ct), else 0
       int grid_fc, grid_ic;
     };
     std::vector<Cls> pcl, ycl, ccl;
@@ -851,7 +870,7 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       for (auto& kv : m) {
         std::stable_sort(kv.second.begin(), kv.second.end(), by_size);
         out.push_back({nd[kv.first], (long long)clsitems.size(), (int)kv.second.size(), 0, 0, rows,
-                       (kv.first & 1) != 0, 0, 0});
+                       (int)(kv.first & 7), 0, 0});
         clsitems.insert(clsitems.end(), kv.second.begin(), kv.second.end());
       }
     };
@@ -964,43 +983,78 @@ static hh_status solve_boxes(Ctx& c, const hh_options& o, const Medium& med, con
       q.nitems = k.n;
       return q;
     };
-    // one launch per class for the plane and column passes
+    // one launch per class for the plane and column passes, the classes of
+    // one group spread over the pass streams (fork from c.st, join back)
+    int nfork = 0;  // pass streams forked in the current group
+    auto gstream = [&](int i, int n) -> cudaStream_t {
+      if (kPassStreams <= 1 || n <= 1) return c.st;
+      const int j = i % kPassStreams;
+      if (j >= nfork) {
+        if (nfork == 0) (void)cudaEventRecord(c.ev_fork, c.st);
+        (void)cudaStreamWaitEvent(c.side[j], c.ev_fork, 0);
+        nfork = j + 1;
+      }
+      return c.side[j];
+    };
+    auto gjoin = [&]() {
+      for (int j = 0; j < nfork; ++j) {
+        (void)cudaEventRecord(c.ev_join[j], c.side[j]);
+        (void)cudaStreamWaitEvent(c.st, c.ev_join[j], 0);
+      }
+      nfork = 0;
+    };
     // forward pass of a mode: whole planes and streaming rows, then the
     // streaming problems' y transforms; the inverse pass in reverse order
     auto fwd_pass = [&](int mode) {
-      for (const Cls& k : pcl) {
+      const int n = (int)pcl.size();
+      for (int i = 0; i < n; ++i) {
+        const Cls& k = pcl[i];
         ++c.launches;
+        cudaStream_t s = gstream(i, n);
         if (k.ct && mode == MODE_ITER)
-          kfct<<<k.grid_fc, threads, k.smem, c.st>>>(cls_params(k));
+          kfct[k.ct - 1]<<<k.grid_fc, threads, k.smem, s>>>(cls_params(k));
         else
-          kfwd(mode, k.rows)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k));
+          kfwd(mode, k.rows)<<<k.grid_f, threads, k.smem, s>>>(cls_params(k));
       }
-      for (const Cls& k : ycl) {
+      gjoin();
+      const int ny_ = (int)ycl.size();
+      for (int i = 0; i < ny_; ++i) {
         ++c.launches;
-        kyf<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
+        kyf<<<ycl[i].grid_f, threads, ycl[i].smem, gstream(i, ny_)>>>(cls_params(ycl[i]), mode);
       }
+      gjoin();
     };
     auto inv_pass = [&](int mode) {
-      for (const Cls& k : ycl) {
+      const int ny_ = (int)ycl.size();
+      for (int i = 0; i < ny_; ++i) {
         ++c.launches;
-        kyi<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k), mode);
+        kyi<<<ycl[i].grid_i, threads, ycl[i].smem, gstream(i, ny_)>>>(cls_params(ycl[i]), mode);
       }
-      for (const Cls& k : pcl) {
+      gjoin();
+      const int n = (int)pcl.size();
+      for (int i = 0; i < n; ++i) {
+        const Cls& k = pcl[i];
         ++c.launches;
+        cudaStream_t s = gstream(i, n);
         if (k.ct && mode == MODE_ITER)
-          kict<<<k.grid_ic, threads, k.smem, c.st>>>(cls_params(k));
+          kict[k.ct - 1]<<<k.grid_ic, threads, k.smem, s>>>(cls_params(k));
         else
-          kinv(mode, k.rows)<<<k.grid_i, threads, k.smem, c.st>>>(cls_params(k));
+          kinv(mode, k.rows)<<<k.grid_i, threads, k.smem, s>>>(cls_params(k));
       }
+      gjoin();
     };
     auto column_pass = [&](int mode) {
-      for (const Cls& k : ccl) {
+      const int n = (int)ccl.size();
+      for (int i = 0; i < n; ++i) {
+        const Cls& k = ccl[i];
         ++c.launches;
+        cudaStream_t s = gstream(i, n);
         if (k.ct && mode != MODE_BASIC)
-          kcct<<<k.grid_fc, threads, k.smem, c.st>>>(cls_params(k), mode);
+          kcct<<<k.grid_fc, threads, k.smem, s>>>(cls_params(k), mode);
         else
-          (mode == MODE_BASIC ? kcb : kc)<<<k.grid_f, threads, k.smem, c.st>>>(cls_params(k), mode);
+          (mode == MODE_BASIC ? kcb : kc)<<<k.grid_f, threads, k.smem, s>>>(cls_params(k), mode);
       }
+      gjoin();
     };
     const int gu = grid_for<T>(c, (const void*)ku, threads, 0, kpp.nitems);
     const int gs = (np + 127) / 128;
@@ -1556,6 +1610,13 @@ extern "C" hh_status hh_create(hh_ctx** out, int device, void* cuda_stream) {
   if ((e = cudaMallocHost((void**)&c.h_dbl, 64 * sizeof(double))) != cudaSuccess) return bad(e);
   if ((e = cudaEventCreate(&c.ev_call0)) != cudaSuccess) return bad(e);
   if ((e = cudaEventCreate(&c.ev_call1)) != cudaSuccess) return bad(e);
+  if (kPassStreams > 1) {
+    if ((e = cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+    for (int j = 0; j < kPassStreams; ++j) {
+      if ((e = cudaStreamCreateWithFlags(&c.side[j], cudaStreamNonBlocking)) != cudaSuccess) return bad(e);
+      if ((e = cudaEventCreateWithFlags(&c.ev_join[j], cudaEventDisableTiming)) != cudaSuccess) return bad(e);
+    }
+  }
   *out = h;
   return HH_OK;
 }
@@ -1574,6 +1635,11 @@ extern "C" void hh_destroy(hh_ctx* h) {
   if (c.h_dbl) cudaFreeHost(c.h_dbl);
   if (c.ev_call0) cudaEventDestroy(c.ev_call0);
   if (c.ev_call1) cudaEventDestroy(c.ev_call1);
+  if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+  for (int j = 0; j < kPassStreams; ++j) {
+    if (c.ev_join[j]) cudaEventDestroy(c.ev_join[j]);
+    if (c.side[j]) cudaStreamDestroy(c.side[j]);
+  }
   if (c.st) cudaStreamDestroy(c.st);
   delete h;
 }

@@ -465,77 +465,112 @@ __device__ __forceinline__ void column(const KParams<T>& P, const Prob& d, int j
 
 }  // namespace ct
 
-// Shape codes of the compiled bodies: the edge (16..32, even) of a square xy
-// plane for the plane passes, the z length (16..48, even) for the column
-// pass; 0 = none.
-__host__ __device__ constexpr bool ct_length(int n) { return n >= 16 && n <= 32 && n % 2 == 0; }
+// Shape codes of the compiled bodies: nx * 64 + ny of the xy plane for the
+// plane passes, nz * 64 + cw (z length and column width) for the column pass;
+// 0 = none. The plane shapes are the buffered boxes of cores whose edges
+// are 16, 24 or 32 (multiples of the coarse unit 8) with one buffer width:
+// both edges even in 16..48, differing by 0, 8 or 16. They are compiled in
+// four groups by nx, one kernel per group and pass, each built on its own.
+__host__ __device__ constexpr int ct_plane_group(int nx, int ny) {
+  const int d = nx > ny ? nx - ny : ny - nx;
+  if (nx % 2 || ny % 2 || nx < 16 || ny < 16 || nx > 48 || ny > 48 || (d != 0 && d != 8 && d != 16)) return -1;
+  return nx <= 22 ? 0 : (nx <= 30 ? 1 : (nx <= 38 ? 2 : 3));
+}
+constexpr int kCtPlaneGroups = 4;
 __host__ __device__ constexpr bool ct_col_length(int n) { return n >= 16 && n <= 48 && n % 2 == 0; }
 
-#define HH_CT_LENGTHS(X) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32)
-#define HH_CT_COL_LENGTHS(X) HH_CT_LENGTHS(X) X(34) X(36) X(38) X(40) X(42) X(44) X(46) X(48)
+#define HH_CT_PLANES_0(X) X(16, 16) X(16, 24) X(16, 32) X(18, 18) X(18, 26) X(18, 34) X(20, 20) X(20, 28) \
+  X(20, 36) X(22, 22) X(22, 30) X(22, 38)
+#define HH_CT_PLANES_1(X) X(24, 16) X(24, 24) X(24, 32) X(24, 40) X(26, 18) X(26, 26) X(26, 34) X(26, 42) \
+  X(28, 20) X(28, 28) X(28, 36) X(28, 44) X(30, 22) X(30, 30) X(30, 38) X(30, 46)
+#define HH_CT_PLANES_2(X) X(32, 16) X(32, 24) X(32, 32) X(32, 40) X(32, 48) X(34, 18) X(34, 26) X(34, 34) \
+  X(34, 42) X(36, 20) X(36, 28) X(36, 36) X(36, 44) X(38, 22) X(38, 30) X(38, 38) X(38, 46)
+#define HH_CT_PLANES_3(X) X(40, 24) X(40, 32) X(40, 40) X(40, 48) X(42, 26) X(42, 34) X(42, 42) X(44, 28) \
+  X(44, 36) X(44, 44) X(46, 30) X(46, 38) X(46, 46) X(48, 32) X(48, 40) X(48, 48)
+#define HH_CT_COL_LENGTHS(X) X(16) X(18) X(20) X(22) X(24) X(26) X(28) X(30) X(32) X(34) X(36) X(38) X(40) \
+  X(42) X(44) X(46) X(48)
 
 // Kernels of the compiled bodies: one block per item of a launch class whose
-// problems all carry a shape code (the host keeps them apart from the generic
-// passes' classes). No persistent loop: inside one, the compiler keeps the
-// bodies' thread-dependent indices live across items, which costs more in
-// registers and spills than reloading the few tables per block saves. The
-// shared-memory layout is taken per shape, so its offsets are constants too.
+// problems all carry a shape code of one group (the host keeps them apart
+// from the generic passes' classes). No persistent loop: inside one, the
+// compiler keeps the bodies' thread-dependent indices live across items,
+// which costs more in registers and spills than reloading the few tables per
+// block saves. The shared-memory layout is taken per shape, so its offsets
+// are constants too.
 namespace ct {
-template <typename T, int N>
+template <typename T, int NX, int NY>
 __device__ __forceinline__ void fwd_item(const KParams<T>& P, int2 w, char* smem) {
   const Prob& d = P.prob[w.x];
-  PlaneSmem<T> sm = plane_layout<T>(smem, N, N, P.nphase);
-  plane_tables<T>(P, sm, P.plans[d.px], P.plans[d.py], N);
+  PlaneSmem<T> sm = plane_layout<T>(smem, NX, NY, P.nphase);
+  plane_tables<T>(P, sm, P.plans[d.px], P.plans[d.py], NX);
   const FwdScal<T, MODE_ITER> k(P.st[w.x]);
   __syncthreads();
-  plane_fwd<T, MODE_ITER, N, N>(P, d, w.y, sm, k);
+  plane_fwd<T, MODE_ITER, NX, NY>(P, d, w.y, sm, k);
 }
-template <typename T, int N>
+template <typename T, int NX, int NY>
 __device__ __forceinline__ void inv_item(const KParams<T>& P, int2 w, char* smem) {
   const Prob& d = P.prob[w.x];
-  PlaneSmem<T> sm = plane_layout<T>(smem, N, N, P.nphase);
-  plane_tables<T>(P, sm, P.plans[d.px], P.plans[d.py], N);
-  plane_inv<T, MODE_ITER, N, N>(P, d, w.y, sm);
+  PlaneSmem<T> sm = plane_layout<T>(smem, NX, NY, P.nphase);
+  plane_tables<T>(P, sm, P.plans[d.px], P.plans[d.py], NX);
+  plane_inv<T, MODE_ITER, NX, NY>(P, d, w.y, sm);
 }
+
+#define HH_CT_FWD_CASE(NX, NY)                  \
+  case NX * 64 + NY:                            \
+    fwd_item<T, NX, NY>(P, w, smem);            \
+    break;
+#define HH_CT_INV_CASE(NX, NY)                  \
+  case NX * 64 + NY:                            \
+    inv_item<T, NX, NY>(P, w, smem);            \
+    break;
+template <typename T, int G, bool FWD>
+__device__ __forceinline__ void plane_item(const KParams<T>& P, int2 w, char* smem) {
+  const int code = P.prob[w.x].ct_plane;
+  if constexpr (FWD) {
+    if constexpr (G == 0) {
+      switch (code) { HH_CT_PLANES_0(HH_CT_FWD_CASE) default: break; }
+    } else if constexpr (G == 1) {
+      switch (code) { HH_CT_PLANES_1(HH_CT_FWD_CASE) default: break; }
+    } else if constexpr (G == 2) {
+      switch (code) { HH_CT_PLANES_2(HH_CT_FWD_CASE) default: break; }
+    } else {
+      switch (code) { HH_CT_PLANES_3(HH_CT_FWD_CASE) default: break; }
+    }
+  } else {
+    if constexpr (G == 0) {
+      switch (code) { HH_CT_PLANES_0(HH_CT_INV_CASE) default: break; }
+    } else if constexpr (G == 1) {
+      switch (code) { HH_CT_PLANES_1(HH_CT_INV_CASE) default: break; }
+    } else if constexpr (G == 2) {
+      switch (code) { HH_CT_PLANES_2(HH_CT_INV_CASE) default: break; }
+    } else {
+      switch (code) { HH_CT_PLANES_3(HH_CT_INV_CASE) default: break; }
+    }
+  }
+}
+#undef HH_CT_FWD_CASE
+#undef HH_CT_INV_CASE
 }  // namespace ct
 
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(256, kCtFwdBlocksPerSM) k_plane_fwd_ct(KParams<T> P) {
   if constexpr (sizeof(T) == 4) {
     extern __shared__ __align__(16) char smem[];
     if ((int)blockIdx.x >= P.nitems) return;
     const int2 w = P.items[blockIdx.x];
     if (skip_problem<T>(P.st, w.x, MODE_ITER)) return;
-    switch (P.prob[w.x].ct_plane) {
-#define HH_CT_FWD(N)                   \
-  case N:                              \
-    ct::fwd_item<T, N>(P, w, smem);    \
-    break;
-      HH_CT_LENGTHS(HH_CT_FWD)
-#undef HH_CT_FWD
-      default:
-        break;
-    }
+    ct::plane_item<T, G, true>(P, w, smem);
   }
 }
 
-template <typename T>
+template <typename T, int G>
 __global__ void __launch_bounds__(256, kCtBlocksPerSM) k_plane_inv_ct(KParams<T> P) {
   if constexpr (sizeof(T) == 4) {
     extern __shared__ __align__(16) char smem[];
     if ((int)blockIdx.x >= P.nitems) return;
     const int2 w = P.items[blockIdx.x];
     if (skip_problem<T>(P.st, w.x, MODE_ITER)) return;
-    switch (P.prob[w.x].ct_plane) {
-#define HH_CT_INV(N)                   \
-  case N:                              \
-    ct::inv_item<T, N>(P, w, smem);    \
-    break;
-      HH_CT_LENGTHS(HH_CT_INV)
-#undef HH_CT_INV
-      default:
-        break;
-    }
+    ct::plane_item<T, G, false>(P, w, smem);
   }
 }
 
