@@ -164,25 +164,26 @@ def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     # the sources of the multi-pass field kernels and the compile flags
-    for f in ("csrc/hh_device.cuh", "csrc/hh_plane_ct.cuh", "csrc/hh_fftcore.cuh", "csrc/hh_fft2.cuh",
-              "csrc/hh_fft2_inst.cu", "csrc/hh_ctmath.h", "_build.py"):
+    for f in ("csrc/hh_device.cuh", "csrc/hh_plane_ct.cuh", "csrc/hh_ct_inst.cu", "csrc/hh_fftcore.cuh",
+              "csrc/hh_fft2.cuh", "csrc/hh_fft2_inst.cu", "csrc/hh_ctmath.h", "_build.py"):
         with open(os.path.join(ROOT, "paper_2208_02320_gb300", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic():
-    """DRAM bytes per algorithmic byte of the dominant kernel from the committed
-    ncu summary (profiles/roofline_traffic.txt); (None, None) if absent or if
-    the kernel sources have changed since the capture."""
+    """DRAM bytes per algorithmic byte of each field pass (plane_fwd,
+    plane_inv, column) from the committed ncu summary
+    (profiles/roofline_traffic.txt); {} if absent or if the kernel sources
+    have changed since the capture."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     try:
         kv = dict(l.strip().split("=", 1) for l in open(p) if "=" in l and not l.startswith("#"))
         if kv.get("kernel_source_sha256_16") != kernel_source_hash():
-            return None, None
-        return kv["kernel"], float(kv["dram_bytes_per_algorithmic_byte"])
-    except (OSError, KeyError, ValueError):
-        return None, None
+            return {}
+        return {k[len("ratio."):]: float(v) for k, v in kv.items() if k.startswith("ratio.")}
+    except (OSError, ValueError):
+        return {}
 
 
 def cpu_baseline(img, ph, boxes, seconds: float):
@@ -357,10 +358,10 @@ def run_gb300(args):
     if dom:
         name, st = dom
         achieved = st["sampled_bytes"] / (st["sampled_ms"] / 1e3) / 1e9
-        tk, ratio = ncu_traffic()
+        ratio = ncu_traffic().get(name)
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"],
-                "traffic": (ratio * st["sampled_bytes"] / st["sampled"]) if (tk == name and ratio) else None,
+                "traffic": (ratio * st["sampled_bytes"] / st["sampled"]) if ratio else None,
                 "algorithmic_bytes_per_launch": st["sampled_bytes"] / max(st["sampled"], 1),
                 "avg_launch_ms": st["sampled_ms"] / max(st["sampled"], 1), "peak_source": peak_src,
                 "kernels": {k: {"sampled": v["sampled"], "avg_ms": v["sampled_ms"] / max(v["sampled"], 1),
