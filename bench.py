@@ -79,6 +79,10 @@ def parse():
                          "image (direct solve, hierarchical at n = 16..128 and buffers 0, 4, 8, fits in 1/n, "
                          "the planner's choice); one JSON line")
     ap.add_argument("--surrogate-spread", type=float, default=0.02)
+    ap.add_argument("--study-buffers", default="0,4,8",
+                    help="richardson study: buffer widths b (comma-separated)")
+    ap.add_argument("--study-ns", default="16,32,64,128",
+                    help="richardson study: core edges n (comma-separated)")
     return ap.parse_args()
 
 
@@ -614,9 +618,12 @@ def richardson_study(args):
     t0 = time.perf_counter()
     d = ctx.homogenize_direct(dimg, ph, **opt)
     t_direct = time.perf_counter() - t0
-    ns = [16, 32, 64, 128]
+    print(json.dumps({"direct": dict(K=d["K"], G=d["G"], iters_max=d["iters_max"], status=d["status"],
+                                     wall_s=t_direct)}), flush=True)
+    ns = [int(v) for v in args.study_ns.split(",")]
+    bs = [int(v) for v in args.study_buffers.split(",")]
     rows, fits, crel = [], {}, []
-    for b in (0, 4, 8):
+    for b in bs:
         t0 = time.perf_counter()
         e = ctx.extrapolate(dimg, ph, ns, b=b, **opt)
         t = time.perf_counter() - t0
@@ -625,13 +632,15 @@ def richardson_study(args):
                              K_err=(r["K"] - d["K"]) / d["K"], G_err=(r["G"] - d["G"]) / d["G"],
                              K_am_err=(r["K_am"] - d["K"]) / d["K"], G_am_err=(r["G_am"] - d["G"]) / d["G"],
                              status=r["status"], iters_max=r["iters_max"]))
+            print(json.dumps({"row": rows[-1]}), flush=True)
         errs = np.array([[abs(x["K_err"]), abs(x["G_err"])] for x in rows if x["b"] == b])
         slope = [float(np.polyfit(np.log(ns), np.log(np.maximum(errs[:, j], 1e-12)), 1)[0]) for j in range(2)]
         fits[b] = dict(K_inf=e["K_inf"], C_K=e["C_K"], G_inf=e["G_inf"], C_G=e["C_G"],
                        K_inf_vs_direct=(e["K_inf"] - d["K"]) / d["K"], G_inf_vs_direct=(e["G_inf"] - d["G"]) / d["G"],
                        free_exponent_K=slope[0], free_exponent_G=slope[1], wall_s=t)
+        print(json.dumps({"fit": {"b": b, **fits[b]}}), flush=True)
         crel.append(max(abs(e["C_K"]) / e["K_inf"], abs(e["C_G"]) / e["G_inf"]))
-    plan = plan_partition(img.shape, 1, [0, 4, 8], crel, a=3.66, eps=0.005)
+    plan = plan_partition(img.shape, 1, bs, crel, a=3.66, eps=0.005)
     print(json.dumps({"study": "richardson", "image": "grf_three_phase 256^3 (ell 6, pore 18 %, clay 12 %)",
                       "precision": args.precision, "tol": args.tol,
                       "direct": dict(K=d["K"], G=d["G"], iters_max=d["iters_max"], status=d["status"],
