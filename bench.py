@@ -165,13 +165,21 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
+    """SHA-256 (16 hex digits) of the field kernels' sources and compile
+    flags, comments and layout removed (a comment edit changes no kernel)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     # the sources of the multi-pass field kernels and the compile flags
     for f in ("csrc/hh_device.cuh", "csrc/hh_plane_ct.cuh", "csrc/hh_ct_inst.cu", "csrc/hh_fftcore.cuh",
               "csrc/hh_fft2.cuh", "csrc/hh_fft2_inst.cu", "csrc/hh_ctmath.h", "_build.py"):
-        with open(os.path.join(ROOT, "paper_2208_02320_gb300", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2208_02320_gb300", f)) as fh:
+            text = fh.read()
+        if f.endswith(".py"):
+            text = re.sub(r"#[^\n]*", "", text)
+        else:
+            text = re.sub(r"/\*.*?\*/", "", re.sub(r"//[^\n]*", "", text), flags=re.S)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -85,10 +85,11 @@ struct Geo {
   }
 };
 
-// The thread index, read so that the compiler cannot treat it as invariant
-// across the persistent item loop: every index a body derives from it is
-// recomputed per item instead of being hoisted out of the loop and held in
-// registers (or spilled) for the whole kernel.
+// The thread index, read so that the compiler cannot treat it as invariant:
+// the indices a body derives from it are recomputed where they are used
+// instead of being hoisted out of the round and chunk loops and held in
+// registers (or spilled) for the whole body. (With a persistent item loop
+// around the bodies such hoisting cost 2-4 KB of spill code per kernel.)
 __device__ __forceinline__ unsigned tid_item() {
   unsigned t;
   asm volatile("mov.u32 %0, %%tid.x;" : "=r"(t));
