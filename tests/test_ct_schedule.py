@@ -261,3 +261,46 @@ def test_column_pass_schedule(NZ, CW):
     assert np.abs(S - ref).max() < 1e-9 * np.abs(ref).max()
     fft_ct(S, NZ, True, g, size)
     assert np.abs(S - NZ * tile).max() < 1e-9 * NZ
+
+
+PROG = r"""
+#include "hh_device.cuh"
+#include <cstdio>
+int main() {
+  for (int nx = 1; nx <= 64; ++nx)
+    for (int ny = 1; ny <= 64; ++ny) {
+      const int g = hh::ct_plane_group(nx, ny);
+      if (g >= 0) std::printf("P %d %d %d\n", nx, ny, g);
+    }
+  for (int n = 1; n <= 64; ++n)
+    if (hh::ct_col_length(n)) std::printf("Z %d\n", n);
+  for (int cw = 1; cw <= 64; ++cw)
+    if (hh::ct_width(cw)) std::printf("W %d\n", cw);
+  return 0;
+}
+"""
+
+
+def test_host_shape_codes_match_the_compiled_bodies(tmp_path):
+    """The host's choice of compiled shapes (ct_plane_group, ct_col_length,
+    ct_width, compiled as host code) names exactly the bodies the kernels'
+    switches contain: a shape the host marks but no kernel compiles would be
+    skipped by the kernel."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("no nvcc")
+    src = tmp_path / "codes.cu"
+    src.write_text(PROG)
+    exe = tmp_path / "codes"
+    inc = os.path.join(os.path.dirname(CSRC), "..", "include")
+    subprocess.run([nvcc, "-std=c++17", "-I", CSRC, "-I", inc, "-o", str(exe), str(src)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    planes = {(int(a), int(b)): int(g) for t, a, b, g in (l.split() for l in out if l.startswith("P"))}
+    assert planes == {p: g for g in range(4) for p in PLANES[g]}
+    assert [int(l.split()[1]) for l in out if l.startswith("Z")] == _col_lengths()
+    assert [int(l.split()[1]) for l in out if l.startswith("W")] == [16, 32]
+    body = CT[CT.index("k_column_ct(KParams<T> P, int skip_mode)"):]
+    assert re.findall(r"case N \* 64 \+ (\d+):", body) == ["16", "32"]
