@@ -1,6 +1,8 @@
-// Field-pass bodies compiled for one shape each: the plane passes of square
-// xy planes and the column pass of z lines, for the even lengths 16..32 that
-// carry most of the work of buffered 16^3 cores (core + 2 b, b = 0..8).
+// Field-pass bodies compiled for one shape each: the plane passes of xy
+// planes whose edges are even in 16..48 and differ by 0, 8 or 16, and the
+// column pass of z lines of even length 16..48 - the buffered boxes of cores
+// with edges 16, 24 or 32 and one buffer width b = 0..8 (edge = core + 2 b),
+// which carry the work of uneven partitions on an 8-voxel coarse unit.
 //
 // The arithmetic is the generic passes' (the same two-pass transforms of
 // hh_fft2.cuh with the same splits, twiddles and operation order, the same
